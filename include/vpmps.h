@@ -1,0 +1,213 @@
+/*
+ * vpmps.h -- C ABI of the GB300 matrix-product-state Vlasov-Poisson library.
+ *
+ * Method: Ye & Loureiro, "A quantum-inspired method for solving the
+ * Vlasov-Poisson equations" (arXiv:2205.11990).  A 1D1V distribution f(x,v)
+ * on a 2^nx x 2^nv grid is stored as a quantized tensor train (MPS, one bit
+ * per site, Sec. "MPS Representation of Classical Data"); one time step
+ * applies the finite-difference MPOs (SI "Derivatives", "Upwind time
+ * evolution"), adds MPS (SI "Addition"), integrates over v (SI
+ * "Integration"), solves Poisson for E (Eq. 2-3 of "Problem Statement") and
+ * recompresses with a QR canonicalisation sweep followed by a truncated SVD
+ * sweep (SI "Canonicalization and Compression"), inside RK4 with compression
+ * level C1 (SI "Compressed time evolution algorithm").
+ *
+ * Conventions
+ *  - Every function returns an int status (VP_OK = 0); vp_last_error() gives
+ *    a one-line description of the last failure on a context.
+ *  - All arithmetic is IEEE FP64 on the GPU.  No function falls back to the
+ *    CPU: without a usable CUDA device vp_ctx_create fails with VP_ECUDA.
+ *  - Handles (vp_ctx, mps_t, mpo_t, vp_sim) are opaque and owned by the
+ *    caller: each *_create has a matching *_destroy.  MPS/MPO/sim objects
+ *    must be destroyed before their context.
+ *  - Device memory is the library's, obtained through the allocator passed to
+ *    vp_ctx_create (or cudaMallocAsync on the context's stream when NULL).
+ *    Pointers documented as "host" are caller-owned host buffers; "device"
+ *    pointers are caller-owned device buffers on the context's device.
+ *  - Work is enqueued on the context's CUDA stream.  Functions that return
+ *    host data synchronise that stream before returning.  A context is not
+ *    re-entrant: use one context per host thread / stream.
+ *  - Site ordering: site 0 is the most significant (coarsest) bit.  With
+ *    VP_SEQ the sites are x_0..x_{nx-1}, v_0..v_{nv-1} (ordering S1); with
+ *    VP_INTERLEAVED they are x_0, v_0, x_1, v_1, ... (ordering IF), leftover
+ *    bits of the longer dimension last.
+ *  - Grid: x_i = xmin + i dx, dx = (xmax - xmin)/2^nx (periodic, right end
+ *    excluded); v_j = vmin + j dv, dv = (vmax - vmin)/(2^nv - 1) (both ends
+ *    included, zero-gradient boundaries).  The v domain must be symmetric
+ *    (vmin = -vmax) so that v > 0 exactly on the upper half of the v grid.
+ *  - Dense arrays f are row-major f[ix * 2^nv + iv] (double).
+ */
+#ifndef VPMPS_H
+#define VPMPS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  VP_OK = 0,
+  VP_EINVAL = 1,     /* bad argument (sizes, NULL, unsupported layout) */
+  VP_ENOMEM = 2,     /* allocator returned NULL */
+  VP_ECAPACITY = 3,  /* a bond or workspace exceeds a documented limit */
+  VP_ECUDA = 4,      /* CUDA runtime error (message in vp_last_error) */
+  VP_ETIMEOUT = 5,   /* a device-side wait gave up after its iteration limit */
+  VP_ENUMERIC = 6,   /* NaN/Inf in singular values or the field */
+  VP_ECFL = 7,       /* time step above the RK4 stability limit */
+  VP_EBUSY = 8       /* object in use by another operation */
+};
+
+enum { VP_SEQ = 0, VP_INTERLEAVED = 1 };
+
+/* Opaque handles. */
+typedef struct vp_ctx vp_ctx;
+typedef struct mps_t mps_t;
+typedef struct mpo_t mpo_t;
+typedef struct vp_sim vp_sim;
+
+/* Device allocator hooks: alloc returns device memory of at least `bytes`
+ * bytes usable on the context's stream (NULL on failure); free releases it. */
+typedef void* (*vp_alloc_fn)(size_t bytes, void* user);
+typedef void (*vp_free_fn)(void* ptr, size_t bytes, void* user);
+
+typedef struct {
+  int nx, nv;      /* bits per dimension, each in [2, 14] */
+  int mapping;     /* VP_SEQ or VP_INTERLEAVED */
+  double xmin, xmax, vmin, vmax;
+} vp_layout;
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context on the current CUDA device.  `cuda_stream` is a
+ * cudaStream_t (NULL = legacy default stream).  alloc/free may both be NULL
+ * (stream-ordered cudaMallocAsync/cudaFreeAsync).  Errors: VP_EINVAL,
+ * VP_ECUDA (no device). */
+int vp_ctx_create(void* cuda_stream, vp_alloc_fn alloc, vp_free_fn free_fn, void* user,
+                  vp_ctx** out);
+int vp_ctx_destroy(vp_ctx* ctx);
+const char* vp_last_error(const vp_ctx* ctx);
+/* Number of kernels this context has launched so far (diagnostics). */
+int64_t vp_kernel_launches(const vp_ctx* ctx);
+
+/* -------------------------------------------------------------------- MPS */
+
+/* a1: f (2^(nx+nv) doubles, row-major f[ix][iv]; host if f_on_device == 0,
+ * else device) -> MPS.  Exact left-canonical decomposition by a chain of
+ * Householder QR factorisations (iterated decomposition of reshapes, Sec.
+ * "MPS Representation", Fig. 1a), then the truncated-SVD sweep with bond cap
+ * chi and tolerance tol (truncation-error equation, Sec. "MPS
+ * Representation").  Errors: VP_EINVAL (layout), VP_ENOMEM. */
+int mps_create(vp_ctx* ctx, const vp_layout* layout, const double* f, int f_on_device, int chi,
+               double tol, mps_t** out);
+
+/* MPS from raw cores (host).  ranks[0..n] with ranks[0] = ranks[n] = 1; the
+ * cores are packed site after site, core k row-major (ranks[k], 2,
+ * ranks[k+1]).  No truncation. */
+int mps_create_cores(vp_ctx* ctx, int n, const int* ranks, const double* cores_host, mps_t** out);
+int mps_destroy(mps_t* mps);
+int mps_num_sites(const mps_t* mps);
+/* ranks_out: n+1 ints (host). */
+int mps_bonds(const mps_t* mps, int* ranks_out);
+/* Packed cores to host (layout as mps_create_cores); `capacity` doubles. */
+int mps_get_cores(vp_ctx* ctx, const mps_t* mps, double* host_out, size_t capacity);
+/* Contract to the dense 2^n vector indexed by site bits (site 0 = MSB), host
+ * output.  n <= 24. */
+int mps_to_dense(vp_ctx* ctx, const mps_t* mps, double* host_out);
+/* Same as a dense f[ix][iv] array for the given layout (undoes the site
+ * permutation of VP_INTERLEAVED). */
+int mps_to_grid(vp_ctx* ctx, const mps_t* mps, const vp_layout* layout, double* host_out);
+
+/* -------------------------------------------------------------------- MPO */
+
+enum {
+  VP_MPO_DX_CENTERED = 0,   /* SI "First Derivative, Centered, Periodic" on the x bits */
+  VP_MPO_DX_FORWARD = 1,    /* SI "First Derivative, Forward, Periodic" */
+  VP_MPO_DX_BACKWARD = 2,   /* SI "First Derivative, Backward, Periodic" */
+  VP_MPO_DV_ZERO_GRAD = 3,  /* SI "First Derivative, Centered, Zero Gradient" on the v bits */
+  VP_MPO_DXX = 4,           /* SI "Second Derivative, Centered, Periodic" on the x bits */
+  VP_MPO_ADVECTION = 5      /* -v+ D_b^x - v- D_f^x (SI "Upwind time evolution") */
+};
+
+/* Build one of the operators above on the full site chain of `layout`
+ * (identity on the other dimension).  Errors: VP_EINVAL. */
+int mpo_create_vp(vp_ctx* ctx, const vp_layout* layout, int kind, mpo_t** out);
+/* L(E) = -v+ D_b^x - v- D_f^x + diag(E) D_c^v with E (2^nx doubles, host) as
+ * an MPS truncated at e_tol (no bond cap). */
+int mpo_create_vlasov(vp_ctx* ctx, const vp_layout* layout, const double* E_host, double e_tol,
+                      mpo_t** out);
+/* MPO from raw cores (host): bonds[0..n], core k row-major (bonds[k], 2_out,
+ * 2_in, bonds[k+1]). */
+int mpo_create_cores(vp_ctx* ctx, int n, const int* bonds, const double* cores_host, mpo_t** out);
+int mpo_destroy(mpo_t* mpo);
+int mpo_bonds(const mpo_t* mpo, int* bonds_out);
+/* Dense 2^n x 2^n operator [out][in] (site-bit indices), host; n <= 12. */
+int mpo_to_dense(vp_ctx* ctx, const mpo_t* mpo, double* host_out);
+
+/* ------------------------------------------------------------ operations */
+
+/* a6: out = mpo * in, per-site contraction C(o) = sum_i B(o,i) A(i), bond
+ * gamma = (alpha, beta) (SI "Matrix-vector multiplication").  No
+ * truncation; out bonds = in bonds * mpo bonds.  `out` is overwritten. */
+int mps_apply_mpo(vp_ctx* ctx, const mpo_t* mpo, const mps_t* in, mps_t* out);
+
+/* a7: out = a*x + b*y with block-diagonal cores (SI "Addition"). */
+int mps_axpby(vp_ctx* ctx, double a, const mps_t* x, double b, const mps_t* y, mps_t* out);
+
+/* a8+a9: QR sweep left to right (R into the next core), then truncated-SVD
+ * sweep right to left keeping r = min(chi, r_tol) singular values per bond,
+ * r_tol the smallest r whose normalised tail sqrt(sum_{i>r} s_i^2)/||s|| is
+ * <= tol (tol = 0: no tolerance cut); a cut that would split a cluster of
+ * values within a relative 1e-5 of each other moves to the cluster start.
+ * trunc_err_out: n-1 doubles (host) or NULL.  Errors: VP_ETIMEOUT,
+ * VP_ENUMERIC. */
+int mps_compress(vp_ctx* ctx, mps_t* inout, int chi, double tol, double* trunc_err_out);
+
+/* a3: rho[ix] = sum_iv f(x_ix, v_iv) dv (SI "Integration", rectangle rule);
+ * rho_dev: 2^nx doubles (device). */
+int vp_density(vp_ctx* ctx, const vp_layout* layout, const mps_t* f, double* rho_dev);
+
+/* a4: periodic second-order Poisson d2phi/dx2 = rho - mean(rho) (zero-mean
+ * phi), E = -(phi_{i+1} - phi_{i-1})/(2 dx).  rho_dev, E_dev: 2^nx doubles
+ * (device); field_energy_host: 1/2 sum E^2 dx (host) or NULL. */
+int vp_poisson(vp_ctx* ctx, const double* rho_dev, int nx, double dx, double* E_dev,
+               double* field_energy_host);
+
+/* --------------------------------------------------------------- stepping */
+
+typedef struct {
+  double dt;        /* fixed step; must satisfy vmax*dt/dx <= 0.6963 (else VP_ECFL) */
+  int chi;          /* bond cap of f_{n+1} */
+  double tol;       /* truncation tolerance of every compression (1e-10) */
+  double e_tol;     /* tolerance of the E-field MPS (1e-10) */
+} vp_config;
+
+typedef struct {
+  double t;             /* time at the start of the step */
+  double field_energy;  /* W_E = 1/2 sum E^2 dx of f_n */
+  double mass;          /* sum f dx dv of f_n */
+  int max_bond;         /* max bond of f_{n+1} */
+  double trunc_err;     /* max per-bond truncation error of the final compression */
+} vp_record;
+
+/* a10: RK4 stepper with compression level C1.  The sim copies f0. */
+int vp_sim_create(vp_ctx* ctx, const vp_layout* layout, const vp_config* cfg, const mps_t* f0,
+                  vp_sim** out);
+int vp_sim_destroy(vp_sim* sim);
+/* Advance nsteps; records[nsteps] (host) receives a11 diagnostics or NULL. */
+int vp_step(vp_sim* sim, int nsteps, vp_record* records);
+/* The current state (owned by the sim; valid until the next vp_step). */
+const mps_t* vp_sim_state(const vp_sim* sim);
+/* Algorithmic FP64 flop count of the factorisations since creation. */
+double vp_sim_flops(const vp_sim* sim);
+
+/* f0 (host dense) -> nsteps of RK4-C1 -> f(T) dense (host, may be NULL) and
+ * records[nsteps] (host, may be NULL). */
+int vp_run(vp_ctx* ctx, const vp_layout* layout, const vp_config* cfg, const double* f0_host,
+           int nsteps, double* fT_host, vp_record* records);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VPMPS_H */

@@ -1,0 +1,206 @@
+"""MPS algebra, TT-SVD and compression (oracle; test infrastructure only).
+
+An MPS is a list of cores ``A[k]`` of shape ``(r_{k-1}, 2, r_k)`` with
+``r_{-1} = r_{n-1} = 1``; site 0 is the most significant bit.  Every function
+follows the paper's own definitions:
+
+* TT-SVD: iterated SVDs of reshapes (main text, "MPS Representation of
+  Classical Data", MPS decomposition equation, Fig. 1a).
+* MPO x MPS: ``C(o) = sum_i B(o,i) A(i)`` with gamma = (alpha, beta)
+  (SI "Matrix-vector multiplication").
+* MPS + MPS: block-diagonal cores, row/column concatenation at the ends
+  (SI "Addition").
+* QR canonicalisation left to right, R absorbed into the next core (SI
+  "Canonicalization and Compression").
+* Truncated-SVD sweep keeping the D largest singular values, with the
+  truncation error of the epsilon_j equation (main text) as tolerance.
+
+LAPACK does the factorisations (``scipy.linalg.qr`` Householder,
+``scipy.linalg.svd`` with ``gesvd``).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import scipy.linalg as sla
+
+# Two singular values closer than this fraction of the smaller kept one are
+# treated as one degenerate cluster that is kept or dropped as a whole, so the
+# kept subspace (and hence f) is unique up to rounding.
+TIE_REL = 1e-5
+
+
+def to_dense(cores):
+    """Contract the MPS into the 2^n vector (index bits: site 0 = MSB)."""
+    t = cores[0].reshape(2, -1)
+    for c in cores[1:]:
+        t = (t @ c.reshape(c.shape[0], -1)).reshape(-1, c.shape[2])
+    return t.reshape(-1)
+
+
+def bonds(cores):
+    return [1] + [c.shape[2] for c in cores]
+
+
+def choose_rank(s, chi, tol):
+    """Number of singular values kept at one bond.
+
+    ``s`` sorted descending.  The normalised values s/||s|| give the
+    truncation error sqrt(sum_{i>=r} s_i^2)/||s|| of the epsilon_j equation
+    when the first r are kept.  Keep r = min(chi, r_tol), where r_tol is the
+    smallest r >= 1 with that error <= tol (tol = 0 keeps every value).  Tail
+    sums run smallest-first.  A cut that would split a cluster of nearly equal
+    values (relative gap <= TIE_REL) moves down to the cluster start.  Returns
+    (r, truncation error).
+    """
+    s = np.asarray(s, dtype=np.float64)
+    m = len(s)
+    nrm2 = float(np.sum(s[::-1] ** 2))
+    if nrm2 == 0.0:
+        return 1, 0.0
+    tail2 = np.zeros(m + 1)
+    acc = 0.0
+    for i in range(m - 1, -1, -1):  # tail2[r] = sum_{i>=r} s_i^2, smallest first
+        acc += s[i] * s[i]
+        tail2[i] = acc
+    if tol > 0.0:
+        thr2 = tol * tol * nrm2
+        r_tol = m
+        for r in range(1, m + 1):
+            if tail2[r] <= thr2:
+                r_tol = r
+                break
+    else:
+        r_tol = m
+    r = min(chi, r_tol, m)
+    while 1 < r < m and (s[r - 1] - s[r]) <= TIE_REL * s[r - 1]:
+        r -= 1
+    r = max(r, 1)
+    return r, math.sqrt(tail2[r] / nrm2)
+
+
+def tt_svd(vec, n, chi=None, tol=0.0):
+    """TT-SVD by iterated SVDs of reshapes, left to right (A1).
+
+    With tol = 0 and chi = None nothing is truncated (exact decomposition).
+    """
+    chi = chi if chi is not None else 1 << n
+    cores = []
+    r = 1
+    rest = np.asarray(vec, dtype=np.float64).reshape(1, -1)
+    for k in range(n - 1):
+        mat = rest.reshape(r * 2, -1)
+        u, s, vt = sla.svd(mat, full_matrices=False, lapack_driver="gesvd")
+        rk, _ = choose_rank(s, chi, tol)
+        cores.append(u[:, :rk].reshape(r, 2, rk))
+        rest = s[:rk, None] * vt[:rk]
+        r = rk
+    cores.append(rest.reshape(r, 2, 1))
+    return cores
+
+
+def apply_mpo(mpo, mps):
+    """C^{(n)}_{(a,b),(a',b')}(o) = sum_i B_{b,b'}(o,i) A_{a,a'}(i); bonds multiply."""
+    out = []
+    for B, A in zip(mpo, mps):
+        C = np.einsum("boic,aid->abodc", B, A)  # bond index = (alpha, beta)
+        s = C.shape
+        out.append(C.reshape(s[0] * s[1], 2, s[3] * s[4]))
+    return out
+
+
+def add(a, b, alpha=1.0, beta=1.0):
+    """alpha*a + beta*b with block-diagonal cores; bonds add (SI "Addition")."""
+    n = len(a)
+    out = []
+    for k in range(n):
+        A, B = a[k], b[k]
+        if k == 0:
+            A, B = alpha * A, beta * B
+        if n == 1:
+            out.append(A + B)
+        elif k == 0:
+            out.append(np.concatenate([A, B], axis=2))
+        elif k == n - 1:
+            out.append(np.concatenate([A, B], axis=0))
+        else:
+            c = np.zeros((A.shape[0] + B.shape[0], 2, A.shape[2] + B.shape[2]))
+            c[:A.shape[0], :, :A.shape[2]] = A
+            c[A.shape[0]:, :, A.shape[2]:] = B
+            out.append(c)
+    return out
+
+
+def qr_sweep(cores):
+    """Left-canonicalise: QR of each (2 r_{k-1} x r_k) reshape, R into core k+1."""
+    out = [c.copy() for c in cores]
+    n = len(out)
+    for k in range(n - 1):
+        c = out[k]
+        rl, _, rr = c.shape
+        q, r = sla.qr(c.reshape(rl * 2, rr), mode="economic")
+        p = q.shape[1]
+        out[k] = q.reshape(rl, 2, p)
+        nxt = out[k + 1]
+        out[k + 1] = (r @ nxt.reshape(rr, -1)).reshape(p, 2, nxt.shape[2])
+    return out
+
+
+def svd_sweep(cores, chi, tol):
+    """Right-to-left truncated SVD sweep on a left-canonical MPS.
+
+    At site k: SVD of the (r_{k-1} x 2 r_k) reshape, keep r per
+    :func:`choose_rank`, core k <- V^T (right-canonical), core k-1 <- core
+    k-1 * U S.  Returns (cores, truncation error per bond, singular values
+    per bond).
+    """
+    out = [c.copy() for c in cores]
+    n = len(out)
+    errs = [0.0] * (n - 1)
+    svals = [None] * (n - 1)
+    for k in range(n - 1, 0, -1):
+        c = out[k]
+        rl, _, rr = c.shape
+        u, s, vt = sla.svd(c.reshape(rl, 2 * rr), full_matrices=False, lapack_driver="gesvd")
+        r, e = choose_rank(s, chi, tol)
+        errs[k - 1] = e
+        svals[k - 1] = s
+        out[k] = vt[:r].reshape(r, 2, rr)
+        prev = out[k - 1]
+        out[k - 1] = (prev.reshape(-1, rl) @ (u[:, :r] * s[:r])).reshape(prev.shape[0], 2, r)
+    return out, errs, svals
+
+
+def compress(cores, chi, tol):
+    """QR sweep left to right, then truncated-SVD sweep right to left."""
+    out, errs, _ = svd_sweep(qr_sweep(cores), chi, tol)
+    return out, errs
+
+
+def from_dense(vec, n, chi, tol):
+    """Exact TT-SVD followed by :func:`compress` (used for f0 and for E)."""
+    return compress(tt_svd(vec, n), chi, tol)[0]
+
+
+def contract_sites(cores, sites, vectors):
+    """Contract the physical leg of ``sites`` with ``vectors[k]`` (length 2).
+
+    Returns the MPS on the remaining sites; the contracted sites' matrices are
+    absorbed into the next remaining site on the right (or the left neighbour
+    at the end).  Used for integration (SI "Integration").
+    """
+    keep = []
+    pending = None
+    for k, c in enumerate(cores):
+        if k in sites:
+            m = np.einsum("aib,i->ab", c, vectors[k])
+            pending = m if pending is None else pending @ m
+        else:
+            if pending is not None:
+                c = np.einsum("ab,bic->aic", pending, c)
+                pending = None
+            keep.append(c)
+    if pending is not None:
+        keep[-1] = np.einsum("aib,bc->aic", keep[-1], pending)
+    return keep

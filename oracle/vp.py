@@ -1,0 +1,228 @@
+"""One-species Vlasov-Poisson in MPS form, RK4 with compression level C1 (oracle).
+
+Test infrastructure only.  Model (main text, "Problem Statement"; Methods,
+normalised units with q_e/m_e = -1 and a uniform neutralising background):
+
+    df/dt = -v df/dx + E df/dv,
+    d2phi/dx2 = n_e - mean(n_e),   E = -dphi/dx,   n_e = int f dv.
+
+Discretisation (Methods, "Time Evolution Procedure"; SI "Upwind time
+evolution"): x advection upwind with the second-order one-sided stencils
+(v > 0 backward, v < 0 forward, as the SI text states), the v derivative
+centred with zero-gradient boundaries, E from the centred periodic first
+derivative of phi, phi from the periodic second-order Laplacian (zero-mean
+pseudo-inverse, SI "Inverse Laplacian"), n_e by the rectangle rule (SI
+"Integration").
+
+Time step (SI "Compressed time evolution algorithm", level C1): per RK4 stage
+i the field E_i comes from f_i, k_i = L(E_i) f_i is never compressed, the
+intermediate states f_{i+1} = f_n + a_i dt k_i (a = 1/2, 1/2, 1) and the
+running sum acc_i = acc_{i-1} + b_i dt k_i (acc_0 = f_n, b = 1/6, 1/3, 1/3)
+are compressed to the tolerance only, and f_{n+1} = acc_3 + dt/6 k_4 is
+compressed to chi and the tolerance.
+"""
+from __future__ import annotations
+
+import functools
+import math
+
+import numpy as np
+
+from . import mpo as M
+from . import mps as S
+
+TOL = 1e-10  # "no compression" threshold for every bond (main text, "State Compressibility")
+
+
+def grid_steps(layout):
+    dx = (layout.xmax - layout.xmin) / layout.Nx
+    dv = (layout.vmax - layout.vmin) / (layout.Nv - 1)
+    return dx, dv
+
+
+def sitemap(layout):
+    """Site -> (dimension, bit).  0 = x, 1 = v; bits most significant first.
+
+    SEQ (S1): all x bits then all v bits.  INTERLEAVED (IF): x_0, v_0, x_1,
+    v_1, ...; when nx != nv the leftover bits of the longer dimension follow
+    in their own order.
+    """
+    nx, nv = layout.nx, layout.nv
+    if layout.mapping == 0:
+        return [(0, b) for b in range(nx)] + [(1, b) for b in range(nv)]
+    out = []
+    for b in range(max(nx, nv)):
+        if b < nx:
+            out.append((0, b))
+        if b < nv:
+            out.append((1, b))
+    return out
+
+
+def dense_to_sites(f, layout):
+    """f[ix, iv] -> vector indexed by the site bits (site 0 most significant)."""
+    nx, nv = layout.nx, layout.nv
+    axes = [b if d == 0 else nx + b for (d, b) in sitemap(layout)]
+    return np.asarray(f, dtype=np.float64).reshape([2] * (nx + nv)).transpose(axes).reshape(-1)
+
+
+def sites_to_dense(vec, layout):
+    nx, nv = layout.nx, layout.nv
+    axes = [b if d == 0 else nx + b for (d, b) in sitemap(layout)]
+    inv = np.argsort(axes)
+    return vec.reshape([2] * (nx + nv)).transpose(inv).reshape(layout.Nx, layout.Nv)
+
+
+def mps_from_f(f, layout, chi, tol=TOL):
+    return S.from_dense(dense_to_sites(f, layout), layout.n, chi, tol)
+
+
+def mps_to_f(cores, layout):
+    return sites_to_dense(S.to_dense(cores), layout)
+
+
+# ---------------------------------------------------------------- density (a3)
+def density(cores, layout):
+    """n_e(x_i) = sum_j f(x_i, v_j) dv: contract every v site with dv*[1,1]
+    (SI "Integration"), then expand the remaining x MPS to the dense vector."""
+    _, dv = grid_steps(layout)
+    sm = sitemap(layout)
+    vsites = {k for k, (d, _) in enumerate(sm) if d == 1}
+    vecs = {k: np.ones(2) for k in vsites}
+    xm = S.contract_sites(cores, vsites, vecs)
+    return S.to_dense(xm) * dv
+
+
+# ---------------------------------------------------------------- Poisson (a4)
+@functools.lru_cache(maxsize=8)
+def _laplacian_pinv(Nx, dx):
+    D2 = M.to_dense(M.second_periodic(int(round(math.log2(Nx))), dx))
+    # the smallest nonzero eigenvalue is 4 sin^2(pi/N)/dx^2, i.e. >= 1e-8 of the
+    # largest for N <= 2^14: a relative cut of 1e-9 drops only the null space
+    return np.linalg.pinv(D2, rtol=1e-9, hermitian=True)
+
+
+def poisson_pinv(rho, dx):
+    """phi = pinv(D2) (rho - mean rho): the zero-mean solution of the periodic
+    second-order Poisson problem (SI "Inverse Laplacian" inverts the dense
+    Laplacian)."""
+    rho = np.asarray(rho, dtype=np.float64)
+    return _laplacian_pinv(len(rho), dx) @ (rho - rho.mean())
+
+
+def poisson_dft(rho, dx):
+    """Same solution through the DFT, which diagonalises the circulant
+    Laplacian: eigenvalue -4 sin^2(pi m / N) / dx^2, mode 0 set to zero."""
+    rho = np.asarray(rho, dtype=np.float64)
+    N = len(rho)
+    s = np.fft.fft(rho - rho.mean())
+    m = np.arange(N)
+    lam = -4.0 * np.sin(np.pi * m / N) ** 2 / (dx * dx)
+    lam[0] = 1.0
+    phi_hat = s / lam
+    phi_hat[0] = 0.0
+    return np.real(np.fft.ifft(phi_hat))
+
+
+def field(rho, dx):
+    """E = -D_c phi (centred periodic), field energy W_E = 1/2 sum E^2 dx."""
+    phi = poisson_pinv(rho, dx) if len(rho) <= 2048 else poisson_dft(rho, dx)
+    E = -(np.roll(phi, -1) - np.roll(phi, 1)) / (2.0 * dx)
+    return E, 0.5 * float(np.sum(E * E)) * dx
+
+
+# ------------------------------------------------------------- operators (a2)
+def _vh_mps(layout, positive):
+    """MPS of v*H(v) (or v*(1-H(v))) on the v bits, found numerically by TT-SVD
+    (SI "Upwind time evolution")."""
+    v = layout.v()
+    h = (v > 0).astype(np.float64) if positive else (v <= 0).astype(np.float64)
+    return S.from_dense(v * h, layout.nv, 1 << layout.nv, 1e-14)
+
+
+@functools.lru_cache(maxsize=16)
+def _static_parts(layout):
+    dx, dv = grid_steps(layout)
+    sm = sitemap(layout)
+    vp = M.diag_from_mps(_vh_mps(layout, True))
+    vm = M.diag_from_mps(_vh_mps(layout, False))
+    # -v+ D_b  -v- D_f  (v > 0 takes the backward stencil, v < 0 the forward one)
+    up = M.mpo_sum(M.place([M.mpo_scale(M.backward_periodic(layout.nx, dx), -1.0), vp], sm),
+                   M.place([M.mpo_scale(M.forward_periodic(layout.nx, dx), -1.0), vm], sm))
+    dvz = M.centered_zero_gradient(layout.nv, dv)
+    return up, dvz
+
+
+def operator(E_cores, layout):
+    """L(E) = -v+ D_b^x - v- D_f^x + diag(E) D_c^v (zero-gradient v)."""
+    up, dvz = _static_parts(layout)
+    et = M.place([M.diag_from_mps(E_cores), dvz], sitemap(layout))
+    return M.mpo_sum(up, et)
+
+
+def field_mps(E, layout, tol=TOL):
+    """E(x) as an MPS on the x bits, tolerance-truncated (no D_F cap)."""
+    return S.from_dense(E, layout.nx, 1 << layout.nx, tol)
+
+
+# ------------------------------------------------------------------ step (a10)
+A_RK = (0.5, 0.5, 1.0)
+B_RK = (1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0)
+
+
+def stage_field(cores, layout, e_tol=TOL):
+    dx, _ = grid_steps(layout)
+    rho = density(cores, layout)
+    E, we = field(rho, dx)
+    return E, we, rho
+
+
+def rhs(cores, layout, e_tol=TOL):
+    E, we, rho = stage_field(cores, layout, e_tol)
+    L = operator(field_mps(E, layout, e_tol), layout)
+    return S.apply_mpo(L, cores), we, rho
+
+
+def rk4_step(f, layout, dt, chi, tol=TOL, e_tol=TOL):
+    """One RK4 step with compression level C1; returns (f_{n+1}, diagnostics)."""
+    acc = f
+    fi = f
+    diag = {}
+    errs = None
+    for i in range(4):
+        k, we, rho = rhs(fi, layout, e_tol)
+        if i == 0:
+            dx, dv = grid_steps(layout)
+            diag["field_energy"] = we
+            diag["mass"] = float(np.sum(rho)) * dx
+        if i < 3:
+            fi, _ = S.compress(S.add(f, k, 1.0, A_RK[i] * dt), 1 << 30, tol)
+            acc, _ = S.compress(S.add(acc, k, 1.0, B_RK[i] * dt), 1 << 30, tol)
+        else:
+            acc, errs = S.compress(S.add(acc, k, 1.0, B_RK[3] * dt), chi, tol)
+    diag["trunc_err"] = errs
+    diag["bonds"] = S.bonds(acc)
+    return acc, diag
+
+
+def stable_dt(layout, dt_cfg=None, cfl=0.6):
+    """Fixed step: dt_cfg divided by the smallest integer s with
+    vmax*dt/dx <= cfl; without dt_cfg, dt = cfl*dx/vmax.  RK4 with the
+    second-order upwind stencil is stable for vmax*dt/dx <= 0.696 (the
+    adaptive 0.9*CFL rule of the Methods section exceeds that)."""
+    dx, _ = grid_steps(layout)
+    vmax = max(abs(layout.vmin), abs(layout.vmax))
+    if dt_cfg is None:
+        return cfl * dx / vmax
+    s = max(1, math.ceil(vmax * dt_cfg / dx / cfl - 1e-12))
+    return dt_cfg / s
+
+
+def run(f0, layout, dt, nsteps, chi, tol=TOL, e_tol=TOL, every=1):
+    cores = mps_from_f(f0, layout, chi, tol)
+    hist = []
+    for step in range(nsteps):
+        cores, d = rk4_step(cores, layout, dt, chi, tol, e_tol)
+        if step % every == 0:
+            hist.append((step * dt, d["field_energy"], d["mass"], max(d["bonds"])))
+    return cores, hist

@@ -1,0 +1,136 @@
+"""Seeded synthetic inputs shared by the CUDA path's tests/bench and the CPU oracle.
+
+This module holds no arithmetic of the MPS method itself: it only samples the
+initial distribution functions of the test problems on the phase-space grid and
+draws seeded random numbers.  Both sides read the same grid convention:
+
+* x is periodic with the right end excluded: ``x_i = xmin + i*dx``,
+  ``dx = (xmax - xmin) / Nx``.
+* v is vertex-centred and includes both ends: ``v_j = vmin + j*dv``,
+  ``dv = (vmax - vmin) / (Nv - 1)`` (zero-gradient boundaries act on the end
+  nodes, Methods: "Time Evolution Procedure").
+
+Arrays are row-major ``f[ix, iv]`` with ``Nx = 2**nx`` rows and ``Nv = 2**nv``
+columns.  The initial conditions follow the Methods section (Landau damping)
+and the standard two-stream and bump-on-tail set-ups with one electron species
+against a fixed neutralising background.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+SEQ = 0          # S1: x bits coarse->fine, then v bits coarse->fine
+INTERLEAVED = 1  # IF: x_1, v_1, x_2, v_2, ... (coarse first)
+
+
+@dataclasses.dataclass(frozen=True)
+class Layout:
+    nx: int
+    nv: int
+    xmin: float
+    xmax: float
+    vmin: float
+    vmax: float
+    mapping: int = SEQ
+
+    @property
+    def Nx(self) -> int:
+        return 1 << self.nx
+
+    @property
+    def Nv(self) -> int:
+        return 1 << self.nv
+
+    @property
+    def n(self) -> int:
+        return self.nx + self.nv
+
+    def x(self) -> np.ndarray:
+        return self.xmin + np.arange(self.Nx) * ((self.xmax - self.xmin) / self.Nx)
+
+    def v(self) -> np.ndarray:
+        return self.vmin + np.arange(self.Nv) * ((self.vmax - self.vmin) / (self.Nv - 1))
+
+
+def maxwellian(v, vth=1.0, u=0.0):
+    return np.exp(-((v - u) ** 2) / (2 * vth * vth)) / math.sqrt(2 * math.pi * vth * vth)
+
+
+def landau(layout: Layout, amp=0.01, k=0.5):
+    """f0 = (1 + A cos kx) exp(-v^2/2)/sqrt(2 pi)."""
+    x, v = layout.x(), layout.v()
+    return np.outer(1.0 + amp * np.cos(k * x), maxwellian(v))
+
+
+def two_stream(layout: Layout, amp=1e-3, k=0.2, v0=3.0):
+    """f0 = (1 + A cos kx) [e^{-(v-v0)^2/2} + e^{-(v+v0)^2/2}] / (2 sqrt(2 pi))."""
+    x, v = layout.x(), layout.v()
+    h = 0.5 * (maxwellian(v, 1.0, v0) + maxwellian(v, 1.0, -v0))
+    return np.outer(1.0 + amp * np.cos(k * x), h)
+
+
+def bump_on_tail(layout: Layout, amp=1e-3, k=0.3, nb=0.1, vb=4.5, sb=0.5):
+    x, v = layout.x(), layout.v()
+    h = (1 - nb) * maxwellian(v) + nb * maxwellian(v, sb, vb)
+    return np.outer(1.0 + amp * np.cos(k * x), h)
+
+
+def saturated_two_stream(layout: Layout, modes=32, eps=0.05, k=0.2, v0=3.0, seed=0):
+    """Two-stream background plus a seeded broadband perturbation.
+
+    f0 = h(v) [1 + eps * sum_m a_m cos(m k x + phi_m) psi_m(v)], with psi_m a
+    Hermite-Gauss shape centred on one of the beams.  With 32 modes the bond
+    at the x/v cut needs 65 singular values and the interior bonds are dense,
+    so a compression to chi <= 64 keeps every middle bond at the cap: the
+    workload of the nonlinear (saturated) phase of the instability.
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    x, v = layout.x(), layout.v()
+    h = 0.5 * (maxwellian(v, 1.0, v0) + maxwellian(v, 1.0, -v0))
+    a = rng.uniform(0.3, 1.0, size=modes) / np.arange(1, modes + 1) ** 0.5
+    phi = rng.uniform(0, 2 * math.pi, size=modes)
+    centre = rng.choice([-v0, v0], size=modes)
+    order = rng.integers(0, 4, size=modes)
+    width = rng.uniform(0.6, 1.4, size=modes)
+    pert = np.zeros((layout.Nx, layout.Nv))
+    for m in range(modes):
+        s = (v - centre[m]) / width[m]
+        psi = np.polynomial.hermite.hermval(s, [0] * order[m] + [1]) * np.exp(-s * s / 2)
+        psi = psi / np.max(np.abs(psi))
+        pert += a[m] * np.outer(np.cos((m + 1) * k * x + phi[m]), psi)
+    return h[None, :] * (1.0 + eps * pert)
+
+
+def random_cores(ranks, seed=0, d=2):
+    """Random MPS cores with the given bond list ``ranks`` (length n+1, ends 1)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return [rng.standard_normal((ranks[k], d, ranks[k + 1])) / math.sqrt(ranks[k] * d)
+            for k in range(len(ranks) - 1)]
+
+
+def random_vector(n, seed=0):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return rng.standard_normal(1 << n)
+
+
+# Named workloads (grid, initial condition, chi, dt).  dt follows the fixed
+# stability rule: CFL_x = vmax*dt/dx <= 0.6 (RK4 with the second-order upwind
+# stencil is stable up to 0.696).
+WORKLOADS = {
+    "landau_64x64": dict(layout=Layout(6, 6, 0.0, 4 * math.pi, -6.0, 6.0, SEQ),
+                         ic="landau", chi=64, dt=0.02),
+    "two_stream_1024x1024_seq": dict(layout=Layout(10, 10, 0.0, 10 * math.pi, -8.0, 8.0, SEQ),
+                                     ic="two_stream", chi=64, dt=0.002),
+    "two_stream_1024x1024_int": dict(layout=Layout(10, 10, 0.0, 10 * math.pi, -8.0, 8.0, INTERLEAVED),
+                                     ic="two_stream", chi=64, dt=0.002),
+    "saturated_two_stream_1024x1024_seq": dict(layout=Layout(10, 10, 0.0, 10 * math.pi, -8.0, 8.0, SEQ),
+                                               ic="saturated_two_stream", chi=64, dt=0.002),
+}
+
+
+def initial_condition(name: str, layout: Layout) -> np.ndarray:
+    return {"landau": landau, "two_stream": two_stream, "bump_on_tail": bump_on_tail,
+            "saturated_two_stream": saturated_two_stream}[name](layout)

@@ -1,0 +1,92 @@
+"""Pins of the oracle's MPS algebra and compression (CPU)."""
+import numpy as np
+import pytest
+
+from oracle import mpo as M
+from oracle import mps as S
+from paper_2205_11990_gb300 import inputs as I
+
+
+@pytest.mark.parametrize("n", [1, 2, 5, 8])
+def test_tt_svd_exact_and_full_rank_profile(n):
+    x = I.random_vector(n, seed=n)
+    cores = S.tt_svd(x, n)
+    np.testing.assert_allclose(S.to_dense(cores), x, atol=1e-12)
+    # main text: exact full-rank bonds r_j = d^min(j, KL-j)
+    assert S.bonds(cores) == [2 ** min(j, n - j) for j in range(n + 1)]
+
+
+def test_apply_mpo_is_matvec_and_bonds_multiply():
+    rng = np.random.default_rng(1)
+    n = 5
+    mps = I.random_cores([1, 2, 4, 3, 2, 1], seed=2)
+    w = [1, 3, 2, 4, 2, 1]
+    mpo = [rng.standard_normal((w[k], 2, 2, w[k + 1])) for k in range(n)]
+    out = S.apply_mpo(mpo, mps)
+    np.testing.assert_allclose(S.to_dense(out), M.to_dense(mpo) @ S.to_dense(mps), atol=1e-12)
+    assert S.bonds(out) == [a * b for a, b in zip(S.bonds(mps), w)]
+
+
+def test_add_is_dense_add_and_bonds_add():
+    a = I.random_cores([1, 2, 3, 2, 1], seed=4)
+    b = I.random_cores([1, 2, 2, 2, 1], seed=5)
+    out = S.add(a, b, 0.7, -1.3)
+    np.testing.assert_allclose(S.to_dense(out), 0.7 * S.to_dense(a) - 1.3 * S.to_dense(b), atol=1e-13)
+    assert S.bonds(out)[1:-1] == [x + y for x, y in zip(S.bonds(a)[1:-1], S.bonds(b)[1:-1])]
+
+
+def test_qr_sweep_left_canonical():
+    cores = I.random_cores([1, 2, 4, 8, 4, 2, 1], seed=6)
+    q = S.qr_sweep(cores)
+    np.testing.assert_allclose(S.to_dense(q), S.to_dense(cores), atol=1e-12)
+    for c in q[:-1]:  # sum_{l,u} L_{l,r}(u) L_{l,r'}(u) = delta
+        m = c.reshape(-1, c.shape[2])
+        np.testing.assert_allclose(m.T @ m, np.eye(m.shape[1]), atol=1e-12)
+
+
+def test_svd_sweep_right_canonical_and_exact_without_truncation():
+    cores = I.random_cores([1, 2, 4, 8, 4, 2, 1], seed=7)
+    out, errs = S.compress(cores, 1 << 10, 0.0)
+    np.testing.assert_allclose(S.to_dense(out), S.to_dense(cores), atol=1e-12)
+    for c in out[1:]:
+        m = c.reshape(c.shape[0], -1)
+        np.testing.assert_allclose(m @ m.T, np.eye(m.shape[0]), atol=1e-12)
+    assert max(errs) == 0.0
+
+
+def test_two_site_compression_is_eckart_young():
+    rng = np.random.default_rng(8)
+    A = rng.standard_normal((2, 2)) @ np.diag([3.0, 0.01]) @ rng.standard_normal((2, 2))
+    cores = S.tt_svd(A.reshape(-1), 2)
+    out, errs = S.compress(cores, 1, 0.0)
+    u, s, vt = np.linalg.svd(A)
+    np.testing.assert_allclose(S.to_dense(out).reshape(2, 2), s[0] * np.outer(u[:, 0], vt[0]), atol=1e-12)
+    np.testing.assert_allclose(errs[0], s[1] / np.linalg.norm(s), rtol=1e-10)
+
+
+def test_truncation_error_identity_single_bond():
+    # main text, truncation-error equation: in canonical form, cutting one
+    # bond gives ||f - f_D|| / ||f|| = sqrt(sum of discarded normalised s^2)
+    cores = I.random_cores([1, 2, 3, 3, 8, 3, 3, 2, 1], seed=9)
+    x = S.to_dense(cores)
+    out, errs = S.compress(cores, 3, 0.0)  # only bond 4 (rank 8) exceeds 3
+    assert S.bonds(out) == [1, 2, 3, 3, 3, 3, 3, 2, 1]
+    assert [e > 0 for e in errs] == [False, False, False, True, False, False, False]
+    err = np.linalg.norm(S.to_dense(out) - x) / np.linalg.norm(x)
+    np.testing.assert_allclose(err, errs[3], rtol=1e-9)
+    # and it equals the best rank-3 approximation of the 16 x 16 unfolding
+    u, sv, vt = np.linalg.svd(x.reshape(16, 16))
+    np.testing.assert_allclose(S.to_dense(out), ((u[:, :3] * sv[:3]) @ vt[:3]).reshape(-1), atol=1e-12)
+
+
+def test_choose_rank_rules():
+    s = np.array([1.0, 0.5, 1e-6, 1e-11, 1e-12])
+    assert S.choose_rank(s, 10, 0.0)[0] == 5
+    assert S.choose_rank(s, 10, 1e-10)[0] == 3
+    assert S.choose_rank(s, 2, 1e-10)[0] == 2
+    assert S.choose_rank(s, 10, 1e-5)[0] == 2
+    # a degenerate pair at the cut is dropped as a whole
+    assert S.choose_rank(np.array([1.0, 0.3, 0.3, 0.1]), 2, 0.0)[0] == 1
+    assert S.choose_rank(np.zeros(4), 3, 1e-10)[0] == 1
+    r, e = S.choose_rank(np.array([3.0, 4.0 * 0 + 1e-3]), 1, 0.0)
+    assert r == 1 and abs(e - 1e-3 / np.hypot(3.0, 1e-3)) < 1e-15
