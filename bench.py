@@ -1,0 +1,265 @@
+"""Benchmark: MPS Vlasov-Poisson RK4-C1 steps/s at n = 20 (1024 x 1024), chi = 64.
+
+One "step" is one RK4 step with compression level C1 of the two-stream
+workload on a 1024 x 1024 grid (10 + 10 bit sites, sequential mapping),
+chi = 64, tol = 1e-10, dt = 0.002: four field solves (density, Poisson, E as
+an MPS), four MPO applications and seven compressions (QR sweep + truncated
+SVD sweep).  The state is the saturated-bond two-stream input of
+``paper_2205_11990_gb300.inputs.saturated_two_stream`` (seeded), whose
+middle bonds sit at the chi = 64 cap.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle on
+the same workload instead (bounded sample).  Multi-GPU runs are independent
+replicas (the path does not shard): value = steps of all ranks / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "saturated_two_stream_1024x1024_seq"
+CHI, TOL, DT = 64, 1e-10, 0.002
+FP64_PEAK_GFLOPS = 2 * 2 * 152 * 2.070  # 2 DFMA/clk/SM x 2 flop x 152 SMs x 2070 MHz (nominal 1.25 TF/s)
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+def dist_init(n):
+    rank, world = int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        dist.init_process_group("nccl")
+    return rank, world
+
+
+def workload():
+    from paper_2205_11990_gb300 import inputs as I
+    w = I.WORKLOADS[WORKLOAD]
+    lay = w["layout"]
+    return lay, I.initial_condition(w["ic"], lay)
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            idx = os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0] or "0"
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", idx, f"--query-gpu={self.FIELDS}", "--format=csv,noheader",
+                                          "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        self.proc.wait()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0].split()[0]))
+                mx.append(float(parts[1].split()[0]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def run_ours(args, rank, world):
+    import numpy as np
+    import torch
+
+    import __graft_entry__ as g
+    g.build()
+    from paper_2205_11990_gb300 import vpmps
+
+    lay, f0 = workload()
+    ctx = vpmps.Context()
+    m = ctx.mps_from_grid(lay, f0, CHI, TOL)
+    sim = ctx.sim(lay, m, DT, CHI, TOL, TOL)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > 129 MB L2
+    for _ in range(args.warmup):
+        sim.step(1)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    clocks = Clocks()
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    launches0 = ctx.kernel_launches
+    ctx.profile(True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    recs = []
+    t_wall = time.perf_counter()
+    for i in range(args.steps):
+        flush.zero_()  # evict the L2 between timed steps (outside the event pair)
+        ev[i][0].record(stream)
+        recs += sim.step(1)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    t_wall = time.perf_counter() - t_wall
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    launches = ctx.kernel_launches - launches0
+    clk = clocks.stop()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    steps_per_s = world * args.steps / (ms / 1e3)
+
+    # dominant kernel class and its roofline
+    top = max(prof, key=lambda k: prof[k][0])
+    tms, tl, work = prof[top]
+    if top == "apply":
+        achieved = work / (tms / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": 6783.1, "unit": "GB/s"}
+    else:
+        achieved = work / (tms / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS / 1e3, "unit": "TFLOP/s"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = None
+    roof["kernel"] = {"qr_factor": "k_qr_factor", "jacobi": "k_jacobi_rows", "gemm": "k_gemm",
+                      "qr_formq": "k_qr_formq", "apply": "k_site_sum", "select": "k_select"}.get(top, top)
+    roof["launches"] = tl
+    roof["share_of_step"] = tms / ms * world if ms else None
+
+    e2e = None
+    if not args.no_e2e:
+        # end to end through the public entry point vp_run: host f0 in, f(T)
+        # and the per-step records out, MPS creation included
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        fT, _ = ctx.run(lay, f0, DT, args.steps, CHI, TOL, TOL, want_f=True)
+        t1 = time.perf_counter() - t0
+        nbytes = f0.size * 8
+        e2e = {"value": world * args.steps / t1, "unit": "steps/s",
+               "h2d_bytes_per_step": nbytes / args.steps,
+               "d2h_bytes_per_step": (nbytes + 40 * args.steps) / args.steps}
+    out = {
+        "metric": "MPS VP steps/s at n=20 chi=64 (RK4-C1, 1024x1024 two-stream, seq)",
+        "value": steps_per_s, "unit": "steps/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "grid": "1024x1024", "sites": "10+10", "mapping": "seq", "chi": CHI,
+                   "tol": TOL, "dt": DT, "parallelism": f"replicas x{world}",
+                   "l2": "flushed between timed steps (256 MB write)"},
+        "roofline": roof,
+        "gpu_launches": launches,
+        "clocks": clk,
+        "e2e": e2e,
+        "diag": {"max_bond": max(r["max_bond"] for r in recs), "field_energy": recs[-1]["field_energy"],
+                 "wall_s": t_wall, "kernel_ms": {k: round(v[0], 3) for k, v in prof.items()},
+                 "flops_per_step": sim.flops / max(1, args.steps + args.warmup)},
+    }
+    if rank == 0:
+        out["cpu_baseline"] = cpu_baseline(lay, f0, budget_s=25.0)
+        print(json.dumps(out), flush=True)
+
+
+def oracle_steps(lay, f0, nsteps, budget_s):
+    """Time up to nsteps oracle RK4-C1 steps (stop once budget_s is spent)."""
+    from oracle import vp as OV
+    c = OV.mps_from_f(f0, lay, CHI, TOL)
+    done, t = 0, 0.0
+    while done < nsteps:
+        t0 = time.perf_counter()
+        c, _ = OV.rk4_step(c, lay, DT, CHI, TOL, TOL)
+        t += time.perf_counter() - t0
+        done += 1
+        if t > budget_s:
+            break
+    return done, t
+
+
+def cpu_baseline(lay, f0, budget_s):
+    done, t = oracle_steps(lay, f0, 1000, budget_s)
+    return {"value": done / t, "unit": "steps/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{done} RK4-C1 step(s) of the same workload from the same initial MPS "
+                      f"(numpy/LAPACK, all host cores), {t:.1f} s"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    lay, f0 = workload()
+    for _ in range(min(args.warmup, 1)):
+        oracle_steps(lay, f0, 1, 1e9)
+    done, t = oracle_steps(lay, f0, args.steps, 150.0)
+    v = done / t
+    print(json.dumps({
+        "impl": "reference", "metric": "MPS VP steps/s at n=20 chi=64 (RK4-C1, 1024x1024 two-stream, seq)",
+        "value": v, "unit": "steps/s", "n_gpus": world, "steps": done, "warmup": min(args.warmup, 1),
+        "ms_per_step": 1e3 * t / done, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "grid": "1024x1024", "sites": "10+10", "mapping": "seq", "chi": CHI,
+                   "tol": TOL, "dt": DT, "parallelism": "cpu"},
+        "cpu_baseline": {"value": v, "unit": "steps/s", "cores": os.cpu_count(), "kind": "oracle",
+                         "sample": f"{done} of {args.steps} requested steps (capped at 150 s of CPU work)"},
+        "e2e": {"value": v, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world = dist_init(args.gpus)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -91,6 +91,17 @@ const char* vp_last_error(const vp_ctx* ctx);
 /* Number of kernels this context has launched so far (diagnostics). */
 int64_t vp_kernel_launches(const vp_ctx* ctx);
 
+/* Kernel-class timing (diagnostics): while enabled, every launch of the
+ * classes below is bracketed by CUDA events on the context's stream.
+ * vp_profile_enable clears the counters; vp_profile_read synchronises and
+ * returns the summed event time (ms), the launch count and the algorithmic
+ * work of the class (FP64 flops for VP_K_QR..VP_K_JACOBI, bytes moved for
+ * VP_K_APPLY). */
+enum { VP_K_QR = 0, VP_K_FORMQ = 1, VP_K_GEMM = 2, VP_K_JACOBI = 3, VP_K_SELECT = 4, VP_K_APPLY = 5,
+       VP_K_OTHER = 6, VP_K_COUNT = 7 };
+int vp_profile_enable(vp_ctx* ctx, int on);
+int vp_profile_read(vp_ctx* ctx, int kclass, double* ms, int64_t* launches, double* work);
+
 /* -------------------------------------------------------------------- MPS */
 
 /* a1: f (2^(nx+nv) doubles, row-major f[ix][iv]; host if f_on_device == 0,
@@ -141,6 +152,8 @@ int mpo_create_vlasov(vp_ctx* ctx, const vp_layout* layout, const double* E_host
  * 2_in, bonds[k+1]). */
 int mpo_create_cores(vp_ctx* ctx, int n, const int* bonds, const double* cores_host, mpo_t** out);
 int mpo_destroy(mpo_t* mpo);
+int mpo_num_sites(const mpo_t* mpo);
+/* bonds_out: n+1 ints (host). */
 int mpo_bonds(const mpo_t* mpo, int* bonds_out);
 /* Dense 2^n x 2^n operator [out][in] (site-bit indices), host; n <= 12. */
 int mpo_to_dense(vp_ctx* ctx, const mpo_t* mpo, double* host_out);

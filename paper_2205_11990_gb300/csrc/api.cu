@@ -1,0 +1,1074 @@
+// C ABI of the MPS Vlasov-Poisson library: contexts, MPS/MPO objects, the
+// compression sweeps, the field solve and the RK4 stepper (compression level
+// C1).  Host code only orchestrates: every arithmetic step runs in the
+// kernels of linalg.cu / mpsops.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "mpo_build.hpp"
+
+using vp::DevBuf;
+
+namespace vp {
+
+int fail(vp_ctx* ctx, int code, const std::string& msg) {
+  if (ctx) ctx->err = msg;
+  return code;
+}
+
+int cuda_fail(vp_ctx* ctx, cudaError_t e, const char* what) {
+  return fail(ctx, VP_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+void* dev_alloc(vp_ctx* ctx, size_t bytes) {
+  if (bytes == 0) bytes = 8;
+  if (ctx->alloc) return ctx->alloc(bytes, ctx->user);
+  void* p = nullptr;
+  if (cudaMallocAsync(&p, bytes, ctx->stream) != cudaSuccess) return nullptr;
+  return p;
+}
+
+void dev_free(vp_ctx* ctx, void* p, size_t bytes) {
+  if (!p) return;
+  if (ctx->freef)
+    ctx->freef(p, bytes, ctx->user);
+  else
+    cudaFreeAsync(p, ctx->stream);
+}
+
+int reserve(vp_ctx* ctx, DevBuf& b, size_t elems) {
+  if (elems <= b.cap && b.p) return VP_OK;
+  size_t cap = std::max<size_t>(elems, 64);
+  cap = cap + cap / 4;
+  void* p = dev_alloc(ctx, cap * sizeof(double));
+  if (!p) return fail(ctx, VP_ENOMEM, "device allocation failed");
+  dev_free(ctx, b.p, b.cap * sizeof(double));
+  b.p = (double*)p;
+  b.cap = cap;
+  return VP_OK;
+}
+
+int reserve_keep(vp_ctx* ctx, DevBuf& b, size_t elems, size_t keep) {
+  if (elems <= b.cap && b.p) return VP_OK;
+  DevBuf nb;
+  VP_TRY(reserve(ctx, nb, elems));
+  if (b.p && keep) VP_TRY(launch_copy(ctx, b.p, nb.p, std::min(keep, b.cap)));
+  release(ctx, b);
+  b = nb;
+  return VP_OK;
+}
+
+void release(vp_ctx* ctx, DevBuf& b) {
+  dev_free(ctx, b.p, b.cap * sizeof(double));
+  b.p = nullptr;
+  b.cap = 0;
+}
+
+int check_launch(vp_ctx* ctx, const char* what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(ctx, e, what);
+  return VP_OK;
+}
+
+static cudaEvent_t next_event(vp_ctx* ctx) {
+  if (ctx->ev_used == ctx->ev_pool.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    ctx->ev_pool.push_back(e);
+  }
+  return ctx->ev_pool[ctx->ev_used++];
+}
+
+void prof_begin(vp_ctx* ctx, int cls) {
+  if (!ctx->prof_on) return;
+  const size_t idx = ctx->ev_used;
+  cudaEvent_t e = next_event(ctx);
+  if (!e) return;
+  cudaEventRecord(e, ctx->stream);
+  ctx->prof_marks.push_back({cls, idx});
+}
+
+void prof_end(vp_ctx* ctx, int cls, double work) {
+  if (!ctx->prof_on) return;
+  cudaEvent_t e = next_event(ctx);
+  if (!e) return;
+  cudaEventRecord(e, ctx->stream);
+  ctx->prof_work[cls] += work;
+  ctx->prof_launches[cls] += 1;
+}
+
+int sync_status(vp_ctx* ctx) {
+  VP_CUDA(ctx, cudaMemcpyAsync(ctx->h_small + 60, &ctx->status->err, sizeof(int), cudaMemcpyDeviceToHost,
+                               ctx->stream));
+  VP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  const int err = ctx->h_small[60];
+  if (err == 0) return VP_OK;
+  VP_CUDA(ctx, cudaMemsetAsync(ctx->status, 0, sizeof(DevStatus), ctx->stream));
+  if (err == 1) return fail(ctx, VP_ETIMEOUT, "a device-side grid barrier gave up waiting");
+  if (err == 2) return fail(ctx, VP_ENUMERIC, "NaN or Inf in singular values");
+  return fail(ctx, VP_ENUMERIC, "Jacobi SVD did not converge");
+}
+
+// ------------------------------------------------------------ MPS helpers
+static size_t core_elems(const mps_t* m, int k) { return (size_t)m->r[k] * 2 * m->r[k + 1]; }
+
+static int mps_init(vp_ctx* ctx, mps_t* m, int n) {
+  m->ctx = ctx;
+  m->n = n;
+  m->r.assign(n + 1, 1);
+  m->core.assign(n, DevBuf{});
+  return VP_OK;
+}
+
+static void mps_free(mps_t* m) {
+  for (auto& b : m->core) release(m->ctx, b);
+  m->core.clear();
+}
+
+static int mps_copy(vp_ctx* ctx, const mps_t* src, mps_t* dst) {
+  if (dst->n != src->n) {
+    mps_free(dst);
+    mps_init(ctx, dst, src->n);
+  }
+  dst->r = src->r;
+  for (int k = 0; k < src->n; ++k) {
+    VP_TRY(reserve(ctx, dst->core[k], core_elems(src, k)));
+    VP_TRY(launch_copy(ctx, src->core[k].p, dst->core[k].p, core_elems(src, k)));
+  }
+  return VP_OK;
+}
+
+static int read_rank(vp_ctx* ctx, int* r, double* err) {
+  VP_CUDA(ctx, cudaMemcpyAsync(ctx->h_small, ctx->d_small, 2 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  VP_CUDA(ctx, cudaMemcpyAsync(ctx->h_smalld, ctx->d_smalld, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  VP_CUDA(ctx, cudaMemcpyAsync(ctx->h_small + 61, &ctx->status->pad2, sizeof(int), cudaMemcpyDeviceToHost,
+                               ctx->stream));
+  VP_TRY(sync_status(ctx));
+  *r = ctx->h_small[0];
+  if (err) *err = ctx->h_smalld[0];
+  return VP_OK;
+}
+
+// Flop counters of the factorisations (algorithmic counts).
+struct Flops {
+  double qr = 0, formq = 0, gemm = 0, jacobi = 0;
+};
+static thread_local Flops* g_flops = nullptr;
+
+static double qr_flops(double m, double n) {
+  return m >= n ? 2 * m * n * n - 2.0 / 3.0 * n * n * n : 2 * n * m * m - 2.0 / 3.0 * m * m * m;
+}
+
+// ------------------------------------------------------------ compression
+// QR step at site k: core_k (2 r_k x r_{k+1}) = Q R; core_k <- Q, core_{k+1} <- R core_{k+1}.
+static int qr_site(vp_ctx* ctx, mps_t* s, int k) {
+  const int m = 2 * s->r[k], n = s->r[k + 1], p = std::min(m, n);
+  const int nn = 2 * s->r[k + 2];
+  VP_TRY(reserve(ctx, ctx->w_fac, (size_t)m * n));
+  VP_TRY(reserve(ctx, ctx->w_p, (size_t)2 * m + p + 8));
+  double* tau = ctx->w_p.p;
+  double* vbuf = ctx->w_p.p + p + 8;
+  VP_TRY(launch_to_colmajor(ctx, s->core[k].p, m, n, ctx->w_fac.p));
+  prof_begin(ctx, VP_K_QR);
+  VP_TRY(launch_qr_factor(ctx, ctx->w_fac.p, m, n, tau, vbuf));
+  prof_end(ctx, VP_K_QR, qr_flops(m, n));
+  prof_begin(ctx, VP_K_FORMQ);
+  VP_TRY(launch_qr_formq(ctx, ctx->w_fac.p, m, n, tau, s->core[k].p));
+  prof_end(ctx, VP_K_FORMQ, 4.0 * m * p * p - 4.0 / 3.0 * p * p * p);
+  VP_TRY(reserve(ctx, ctx->w_gemm, (size_t)p * nn));
+  prof_begin(ctx, VP_K_GEMM);
+  VP_TRY(launch_gemm_r(ctx, p, nn, n, ctx->w_fac.p, m, s->core[k + 1].p, nn, ctx->w_gemm.p, nn));
+  prof_end(ctx, VP_K_GEMM, 2.0 * p * n * nn);
+  std::swap(s->core[k + 1], ctx->w_gemm);
+  s->r[k + 1] = p;
+  if (g_flops) {
+    g_flops->qr += qr_flops(m, n);
+    g_flops->formq += 4.0 * m * p * p - 4.0 / 3.0 * p * p * p;
+    g_flops->gemm += 2.0 * p * n * nn;
+  }
+  return VP_OK;
+}
+
+// SVD step at site k >= 1 of a left-canonical MPS (right part already
+// right-canonical): M = core_k (r_k x 2 r_{k+1}); keep r singular triplets.
+static int svd_site(vp_ctx* ctx, mps_t* s, int k, int chi, double tol, double* err_out) {
+  int m = s->r[k];
+  const int c = 2 * s->r[k + 1];
+  const int pl = 2 * s->r[k - 1];  // rows of the previous core viewed as (2 r_{k-1} x r_k)
+  double* X;
+  int b;
+  if (m > c) {
+    // tall: M = Q R, previous core <- previous * Q, work on R (c x c)
+    VP_TRY(reserve(ctx, ctx->w_fac, (size_t)m * c));
+    VP_TRY(reserve(ctx, ctx->w_p, (size_t)2 * m + c + 8));
+    double* tau = ctx->w_p.p;
+    double* vbuf = ctx->w_p.p + c + 8;
+    VP_TRY(launch_to_colmajor(ctx, s->core[k].p, m, c, ctx->w_fac.p));
+    prof_begin(ctx, VP_K_QR);
+    VP_TRY(launch_qr_factor(ctx, ctx->w_fac.p, m, c, tau, vbuf));
+    prof_end(ctx, VP_K_QR, qr_flops(m, c));
+    VP_TRY(reserve(ctx, ctx->w_tmp2, (size_t)m * c));
+    prof_begin(ctx, VP_K_FORMQ);
+    VP_TRY(launch_qr_formq(ctx, ctx->w_fac.p, m, c, tau, ctx->w_tmp2.p));
+    prof_end(ctx, VP_K_FORMQ, 4.0 * m * c * c - 4.0 / 3.0 * c * c * c);
+    VP_TRY(reserve(ctx, ctx->w_gemm, (size_t)pl * c));
+    prof_begin(ctx, VP_K_GEMM);
+    VP_TRY(launch_gemm(ctx, pl, c, m, 1.0, s->core[k - 1].p, m, ctx->w_tmp2.p, c, ctx->w_gemm.p, c));
+    prof_end(ctx, VP_K_GEMM, 2.0 * pl * c * m);
+    std::swap(s->core[k - 1], ctx->w_gemm);
+    VP_TRY(reserve(ctx, ctx->w_tmp, (size_t)c * c));
+    VP_TRY(launch_qr_getr(ctx, ctx->w_fac.p, m, c, ctx->w_tmp.p));
+    if (g_flops) {
+      g_flops->qr += qr_flops(m, c);
+      g_flops->formq += 4.0 * m * c * c - 4.0 / 3.0 * c * c * c;
+      g_flops->gemm += 2.0 * pl * c * m;
+    }
+    m = c;
+    s->r[k] = c;
+    X = ctx->w_tmp.p;
+    b = c;
+  } else {
+    VP_TRY(reserve(ctx, ctx->w_tmp, (size_t)m * c));
+    VP_TRY(launch_copy(ctx, s->core[k].p, ctx->w_tmp.p, (size_t)m * c));
+    X = ctx->w_tmp.p;
+    b = m;
+  }
+  VP_TRY(reserve(ctx, ctx->w_j, (size_t)b * b));
+  VP_CUDA(ctx, cudaMemsetAsync(ctx->status->rot, 0, sizeof(ctx->status->rot), ctx->stream));
+  prof_begin(ctx, VP_K_JACOBI);
+  VP_TRY(launch_jacobi_rows(ctx, X, b, c, ctx->w_j.p));
+  prof_end(ctx, VP_K_JACOBI, 0.0);
+  VP_TRY(reserve(ctx, ctx->w_vec, (size_t)2 * b + 8));
+  int* perm = (int*)ctx->w_vec.p;               // b ints fit in b/2 doubles
+  double* sigma = ctx->w_vec.p + (b + 1) / 2 + 4;
+  prof_begin(ctx, VP_K_SELECT);
+  VP_TRY(launch_select(ctx, X, b, c, chi, tol, perm, sigma, ctx->d_small, ctx->d_smalld));
+  prof_end(ctx, VP_K_SELECT, 0.0);
+  int r = 1;
+  double err = 0.0;
+  VP_TRY(read_rank(ctx, &r, &err));
+  if (err_out) *err_out = err;
+  if (ctx->prof_on && b > 1)
+    ctx->prof_work[VP_K_JACOBI] += (double)ctx->h_small[61] * 0.5 * b * (b - 1) * (6.0 * c + 4.0 * b);
+  if (g_flops) {
+    const double sweeps = b > 1 ? ctx->h_small[61] : 0;
+    g_flops->jacobi += sweeps * 0.5 * b * (b - 1) * (6.0 * c + 4.0 * b);
+    g_flops->gemm += 2.0 * pl * b * r;
+  }
+  // core_k <- V^T (r x c); W (b x r) = U S; previous <- previous * W
+  VP_TRY(reserve(ctx, s->core[k], (size_t)r * c));
+  VP_TRY(reserve(ctx, ctx->w_tmp2, (size_t)b * r));
+  VP_TRY(launch_svd_outputs(ctx, X, ctx->w_j.p, b, c, r, perm, sigma, s->core[k].p, ctx->w_tmp2.p));
+  VP_TRY(reserve(ctx, ctx->w_gemm, (size_t)pl * r));
+  prof_begin(ctx, VP_K_GEMM);
+  VP_TRY(launch_gemm(ctx, pl, r, b, 1.0, s->core[k - 1].p, b, ctx->w_tmp2.p, r, ctx->w_gemm.p, r));
+  prof_end(ctx, VP_K_GEMM, 2.0 * pl * b * r);
+  std::swap(s->core[k - 1], ctx->w_gemm);
+  s->r[k] = r;
+  return VP_OK;
+}
+
+static int svd_sweep(vp_ctx* ctx, mps_t* s, int chi, double tol, double* errs) {
+  for (int k = s->n - 1; k >= 1; --k) VP_TRY(svd_site(ctx, s, k, chi, tol, errs ? errs + (k - 1) : nullptr));
+  return VP_OK;
+}
+
+int compress(vp_ctx* ctx, mps_t* s, int chi, double tol, double* errs) {
+  for (int k = 0; k + 1 < s->n; ++k) VP_TRY(qr_site(ctx, s, k));
+  return svd_sweep(ctx, s, chi, tol, errs);
+}
+
+// Exact left-canonical MPS of a site-ordered device vector (2^n entries, in
+// ctx->w_tmp) by a chain of QR factorisations of reshapes, then the SVD sweep.
+static int from_vector(vp_ctx* ctx, mps_t* s, int n, const double* vec, int chi, double tol) {
+  mps_init(ctx, s, n);
+  DevBuf rem;
+  const size_t N = (size_t)1 << n;
+  VP_TRY(reserve(ctx, rem, N));
+  VP_TRY(launch_copy(ctx, vec, rem.p, N));
+  int r = 1;
+  for (int k = 0; k + 1 < n; ++k) {
+    const int m = 2 * r;
+    const size_t cols = N >> (k + 1);
+    if (cols > (size_t)1 << 30) return fail(ctx, VP_ECAPACITY, "vector too long");
+    const int nc = (int)cols, p = (int)std::min<size_t>(m, cols);
+    VP_TRY(reserve(ctx, ctx->w_fac, (size_t)m * nc));
+    VP_TRY(reserve(ctx, ctx->w_p, (size_t)2 * m + p + 8));
+    VP_TRY(launch_to_colmajor(ctx, rem.p, m, nc, ctx->w_fac.p));
+    VP_TRY(launch_qr_factor(ctx, ctx->w_fac.p, m, nc, ctx->w_p.p, ctx->w_p.p + p + 8));
+    VP_TRY(reserve(ctx, s->core[k], (size_t)m * p));
+    VP_TRY(launch_qr_formq(ctx, ctx->w_fac.p, m, nc, ctx->w_p.p, s->core[k].p));
+    VP_TRY(launch_qr_getr(ctx, ctx->w_fac.p, m, nc, rem.p));
+    s->r[k + 1] = p;
+    r = p;
+  }
+  VP_TRY(reserve(ctx, s->core[n - 1], (size_t)2 * r));
+  VP_TRY(launch_copy(ctx, rem.p, s->core[n - 1].p, (size_t)2 * r));
+  release(ctx, rem);
+  if (n > 1) VP_TRY(svd_sweep(ctx, s, chi, tol, nullptr));
+  return VP_OK;
+}
+
+// Dense vector (2^n, site bits) of an MPS into dev (capacity 2^n).
+static int to_dense_dev(vp_ctx* ctx, const mps_t* s, DevBuf& out) {
+  const int n = s->n;
+  DevBuf a, b;
+  VP_TRY(reserve(ctx, a, core_elems(s, 0)));
+  VP_TRY(launch_copy(ctx, s->core[0].p, a.p, core_elems(s, 0)));
+  size_t rows = 2;
+  for (int k = 1; k < n; ++k) {
+    const int rk = s->r[k], rn = s->r[k + 1];
+    VP_TRY(reserve(ctx, b, rows * 2 * rn));
+    if (rows > (size_t)1 << 26) return fail(ctx, VP_ECAPACITY, "to_dense: too many sites");
+    VP_TRY(launch_gemm(ctx, (int)rows, 2 * rn, rk, 1.0, a.p, rk, s->core[k].p, 2 * rn, b.p, 2 * rn));
+    std::swap(a, b);
+    rows *= 2;
+  }
+  std::swap(out, a);
+  release(ctx, a);
+  release(ctx, b);
+  return VP_OK;
+}
+
+// ------------------------------------------------------------ density
+static std::vector<int> site_dims(const vp_layout* L) {
+  std::vector<int> d;
+  if (L->mapping == VP_SEQ) {
+    for (int b = 0; b < L->nx; ++b) d.push_back(0);
+    for (int b = 0; b < L->nv; ++b) d.push_back(1);
+  } else {
+    for (int b = 0; b < std::max(L->nx, L->nv); ++b) {
+      if (b < L->nx) d.push_back(0);
+      if (b < L->nv) d.push_back(1);
+    }
+  }
+  return d;
+}
+
+// rho (2^nx, device) = dv * contraction of every v site with [1, 1], then
+// expansion of the remaining x MPS (SI "Integration").
+static int density(vp_ctx* ctx, const vp_layout* L, const mps_t* f, double* rho) {
+  const std::vector<int> dims = site_dims(L);
+  const double dv = (L->vmax - L->vmin) / (double)((1 << L->nv) - 1);
+  // pending (pl x pr) matrix of contracted v sites not yet absorbed
+  DevBuf pend, tmp, T;
+  bool have_pend = false;
+  int pend_l = 1, pend_r = 1;
+  std::vector<DevBuf> xc;  // x cores after absorption
+  std::vector<int> xr;     // x bonds
+  xr.push_back(1);
+  for (int k = 0; k < f->n; ++k) {
+    const int rl = f->r[k], rr = f->r[k + 1];
+    if (dims[k] == 1) {
+      VP_TRY(reserve(ctx, T, (size_t)rl * rr));
+      VP_TRY(launch_phys_sum(ctx, f->core[k].p, rl, rr, T.p));
+      if (!have_pend) {
+        std::swap(pend, T);
+        pend_l = rl;
+        pend_r = rr;
+        have_pend = true;
+      } else {
+        VP_TRY(reserve(ctx, tmp, (size_t)pend_l * rr));
+        VP_TRY(launch_gemm(ctx, pend_l, rr, rl, 1.0, pend.p, rl, T.p, rr, tmp.p, rr));
+        std::swap(pend, tmp);
+        pend_r = rr;
+      }
+    } else {
+      DevBuf c;
+      if (have_pend) {
+        VP_TRY(reserve(ctx, c, (size_t)pend_l * 2 * rr));
+        VP_TRY(launch_gemm(ctx, pend_l, 2 * rr, rl, 1.0, pend.p, rl, f->core[k].p, 2 * rr, c.p, 2 * rr));
+        have_pend = false;
+        xr.back() = pend_l;  // left bond of this x core is the pending left bond
+      } else {
+        VP_TRY(reserve(ctx, c, (size_t)rl * 2 * rr));
+        VP_TRY(launch_copy(ctx, f->core[k].p, c.p, (size_t)rl * 2 * rr));
+      }
+      xc.push_back(c);
+      xr.push_back(rr);
+    }
+  }
+  if (have_pend) {  // trailing v sites: absorb into the last x core on its right
+    DevBuf& last = xc.back();
+    const int lx = xr[xr.size() - 2], rx = xr.back();
+    VP_TRY(reserve(ctx, tmp, (size_t)lx * 2 * pend_r));
+    VP_TRY(launch_gemm(ctx, lx * 2, pend_r, rx, 1.0, last.p, rx, pend.p, pend_r, tmp.p, pend_r));
+    std::swap(last, tmp);
+    xr.back() = pend_r;
+  }
+  // expand
+  mps_t xm;
+  mps_init(ctx, &xm, (int)xc.size());
+  xm.r = xr;
+  for (size_t i = 0; i < xc.size(); ++i) xm.core[i] = xc[i];
+  DevBuf dense;
+  VP_TRY(to_dense_dev(ctx, &xm, dense));
+  const size_t Nx = (size_t)1 << L->nx;
+  VP_TRY(launch_copy(ctx, dense.p, rho, Nx));
+  VP_TRY(launch_scale(ctx, rho, Nx, dv));
+  release(ctx, dense);
+  mps_free(&xm);
+  release(ctx, pend);
+  release(ctx, tmp);
+  release(ctx, T);
+  return VP_OK;
+}
+
+static bool layout_ok(const vp_layout* L) {
+  return L && L->nx >= 2 && L->nv >= 2 && L->nx <= 14 && L->nv <= 14 &&
+         (L->mapping == VP_SEQ || L->mapping == VP_INTERLEAVED) && L->xmax > L->xmin && L->vmax > L->vmin &&
+         std::fabs(L->vmin + L->vmax) <= 1e-12 * std::fabs(L->vmax);
+}
+
+}  // namespace vp
+
+// ====================================================================== ABI
+using namespace vp;
+
+extern "C" {
+
+int vp_ctx_create(void* cuda_stream, vp_alloc_fn alloc, vp_free_fn free_fn, void* user, vp_ctx** out) {
+  if (!out || ((alloc == nullptr) != (free_fn == nullptr))) return VP_EINVAL;
+  *out = nullptr;
+  int dev = 0, count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess || count == 0) return VP_ECUDA;
+  if (cudaGetDevice(&dev) != cudaSuccess) return VP_ECUDA;
+  vp_ctx* c = new (std::nothrow) vp_ctx();
+  if (!c) return VP_ENOMEM;
+  c->device = dev;
+  c->stream = (cudaStream_t)cuda_stream;
+  c->alloc = alloc;
+  c->freef = free_fn;
+  c->user = user;
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) {
+    delete c;
+    return VP_ECUDA;
+  }
+  c->num_sms = prop.multiProcessorCount;
+  int coop = 0;
+  cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+  if (!coop) {
+    delete c;
+    return VP_ECUDA;
+  }
+  c->status = (DevStatus*)dev_alloc(c, sizeof(DevStatus));
+  c->d_small = (int*)dev_alloc(c, 64 * sizeof(int));
+  c->d_smalld = (double*)dev_alloc(c, 64 * sizeof(double));
+  if (!c->status || !c->d_small || !c->d_smalld || cudaMallocHost(&c->h_small, 64 * sizeof(int)) != cudaSuccess ||
+      cudaMallocHost(&c->h_smalld, 64 * sizeof(double)) != cudaSuccess) {
+    delete c;
+    return VP_ENOMEM;
+  }
+  cudaMemsetAsync(c->status, 0, sizeof(DevStatus), c->stream);
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
+    delete c;
+    return VP_ECUDA;
+  }
+  *out = c;
+  return VP_OK;
+}
+
+int vp_ctx_destroy(vp_ctx* c) {
+  if (!c) return VP_EINVAL;
+  cudaStreamSynchronize(c->stream);
+  for (DevBuf* b : {&c->w_fac, &c->w_q, &c->w_gemm, &c->w_j, &c->w_p, &c->w_tmp, &c->w_tmp2, &c->w_vec})
+    release(c, *b);
+  for (auto& b : c->w_chain) release(c, b);
+  dev_free(c, c->status, sizeof(DevStatus));
+  dev_free(c, c->d_small, 64 * sizeof(int));
+  dev_free(c, c->d_smalld, 64 * sizeof(double));
+  cudaStreamSynchronize(c->stream);
+  cudaFreeHost(c->h_small);
+  cudaFreeHost(c->h_smalld);
+  for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+  delete c;
+  return VP_OK;
+}
+
+const char* vp_last_error(const vp_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+int vp_profile_enable(vp_ctx* c, int on) {
+  if (!c) return VP_EINVAL;
+  cudaStreamSynchronize(c->stream);
+  c->prof_on = on != 0;
+  c->ev_used = 0;
+  c->prof_marks.clear();
+  for (int k = 0; k < VP_K_COUNT; ++k) {
+    c->prof_work[k] = 0.0;
+    c->prof_launches[k] = 0;
+  }
+  return VP_OK;
+}
+
+int vp_profile_read(vp_ctx* c, int cls, double* ms, int64_t* launches, double* work) {
+  if (!c || cls < 0 || cls >= VP_K_COUNT) return VP_EINVAL;
+  VP_CUDA(c, cudaStreamSynchronize(c->stream));
+  double t = 0.0;
+  for (auto& m : c->prof_marks) {
+    if (m.first != cls) continue;
+    float x = 0.f;
+    VP_CUDA(c, cudaEventElapsedTime(&x, c->ev_pool[m.second], c->ev_pool[m.second + 1]));
+    t += x;
+  }
+  if (ms) *ms = t;
+  if (launches) *launches = c->prof_launches[cls];
+  if (work) *work = c->prof_work[cls];
+  return VP_OK;
+}
+
+int64_t vp_kernel_launches(const vp_ctx* c) { return c ? c->launches : 0; }
+
+// ------------------------------------------------------------------- MPS
+int mps_create(vp_ctx* ctx, const vp_layout* L, const double* f, int f_on_device, int chi, double tol,
+               mps_t** out) {
+  if (!ctx || !out || !f || chi < 1 || tol < 0) return fail(ctx, VP_EINVAL, "mps_create: bad argument");
+  if (!layout_ok(L)) return fail(ctx, VP_EINVAL, "mps_create: unsupported layout");
+  const int n = L->nx + L->nv;
+  const size_t N = (size_t)1 << n;
+  DevBuf grid, sites;
+  VP_TRY(reserve(ctx, grid, N));
+  VP_TRY(reserve(ctx, sites, N));
+  VP_CUDA(ctx, cudaMemcpyAsync(grid.p, f, N * sizeof(double),
+                               f_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->stream));
+  VP_TRY(launch_permute_to_sites(ctx, grid.p, L->nx, L->nv, L->mapping, sites.p, 0));
+  mps_t* m = new mps_t();
+  int s = from_vector(ctx, m, n, sites.p, chi, tol);
+  release(ctx, grid);
+  release(ctx, sites);
+  if (s == VP_OK) s = sync_status(ctx);
+  if (s != VP_OK) {
+    mps_free(m);
+    delete m;
+    return s;
+  }
+  *out = m;
+  return VP_OK;
+}
+
+int mps_create_cores(vp_ctx* ctx, int n, const int* ranks, const double* cores, mps_t** out) {
+  if (!ctx || n < 1 || !ranks || !cores || !out || ranks[0] != 1 || ranks[n] != 1)
+    return fail(ctx, VP_EINVAL, "mps_create_cores: bad argument");
+  mps_t* m = new mps_t();
+  mps_init(ctx, m, n);
+  size_t off = 0;
+  for (int k = 0; k < n; ++k) {
+    if (ranks[k + 1] < 1) {
+      mps_free(m);
+      delete m;
+      return fail(ctx, VP_EINVAL, "mps_create_cores: bad rank");
+    }
+    m->r[k + 1] = ranks[k + 1];
+    const size_t e = core_elems(m, k);
+    int s = reserve(ctx, m->core[k], e);
+    if (s == VP_OK) {
+      cudaError_t ce = cudaMemcpyAsync(m->core[k].p, cores + off, e * sizeof(double), cudaMemcpyHostToDevice,
+                                       ctx->stream);
+      if (ce != cudaSuccess) s = cuda_fail(ctx, ce, "mps_create_cores");
+    }
+    if (s != VP_OK) {
+      mps_free(m);
+      delete m;
+      return s;
+    }
+    off += e;
+  }
+  cudaStreamSynchronize(ctx->stream);
+  *out = m;
+  return VP_OK;
+}
+
+int mps_destroy(mps_t* m) {
+  if (!m) return VP_EINVAL;
+  mps_free(m);
+  delete m;
+  return VP_OK;
+}
+
+int mps_num_sites(const mps_t* m) { return m ? m->n : -1; }
+
+int mps_bonds(const mps_t* m, int* out) {
+  if (!m || !out) return VP_EINVAL;
+  for (int k = 0; k <= m->n; ++k) out[k] = m->r[k];
+  return VP_OK;
+}
+
+int mps_get_cores(vp_ctx* ctx, const mps_t* m, double* host, size_t capacity) {
+  if (!ctx || !m || !host) return VP_EINVAL;
+  size_t off = 0;
+  for (int k = 0; k < m->n; ++k) {
+    const size_t e = core_elems(m, k);
+    if (off + e > capacity) return fail(ctx, VP_ECAPACITY, "mps_get_cores: buffer too small");
+    VP_CUDA(ctx, cudaMemcpyAsync(host + off, m->core[k].p, e * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    off += e;
+  }
+  VP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return VP_OK;
+}
+
+int mps_to_dense(vp_ctx* ctx, const mps_t* m, double* host) {
+  if (!ctx || !m || !host || m->n > 24) return fail(ctx, VP_EINVAL, "mps_to_dense: bad argument");
+  DevBuf d;
+  VP_TRY(to_dense_dev(ctx, m, d));
+  VP_CUDA(ctx, cudaMemcpyAsync(host, d.p, ((size_t)1 << m->n) * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  VP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  release(ctx, d);
+  return VP_OK;
+}
+
+int mps_to_grid(vp_ctx* ctx, const mps_t* m, const vp_layout* L, double* host) {
+  if (!ctx || !m || !host || !layout_ok(L) || L->nx + L->nv != m->n)
+    return fail(ctx, VP_EINVAL, "mps_to_grid: bad argument");
+  DevBuf d, g;
+  VP_TRY(to_dense_dev(ctx, m, d));
+  const size_t N = (size_t)1 << m->n;
+  VP_TRY(reserve(ctx, g, N));
+  VP_TRY(launch_permute_to_sites(ctx, d.p, L->nx, L->nv, L->mapping, g.p, 1));
+  VP_CUDA(ctx, cudaMemcpyAsync(host, g.p, N * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  VP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  release(ctx, d);
+  release(ctx, g);
+  return VP_OK;
+}
+
+// ------------------------------------------------------------------- MPO
+static int mpo_from_chain(vp_ctx* ctx, const Chain& c, mpo_t** out) {
+  mpo_t* m = new mpo_t();
+  m->ctx = ctx;
+  m->n = (int)c.core.size();
+  m->w = c.w;
+  m->core.assign(m->n, DevBuf{});
+  for (int k = 0; k < m->n; ++k) {
+    int s = reserve(ctx, m->core[k], c.core[k].size());
+    if (s == VP_OK) {
+      cudaError_t e = cudaMemcpyAsync(m->core[k].p, c.core[k].data(), c.core[k].size() * sizeof(double),
+                                      cudaMemcpyHostToDevice, ctx->stream);
+      if (e != cudaSuccess) s = cuda_fail(ctx, e, "mpo upload");
+    }
+    if (s != VP_OK) {
+      for (auto& b : m->core) release(ctx, b);
+      delete m;
+      return s;
+    }
+  }
+  VP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  *out = m;
+  return VP_OK;
+}
+
+static double grid_dx(const vp_layout* L) { return (L->xmax - L->xmin) / (double)(1 << L->nx); }
+static double grid_dv(const vp_layout* L) { return (L->vmax - L->vmin) / (double)((1 << L->nv) - 1); }
+
+int mpo_create_vp(vp_ctx* ctx, const vp_layout* L, int kind, mpo_t** out) {
+  if (!ctx || !out || !layout_ok(L)) return fail(ctx, VP_EINVAL, "mpo_create_vp: bad argument");
+  const std::vector<int> dims = site_dims(L);
+  const double dx = grid_dx(L), dv = grid_dv(L);
+  Chain c;
+  switch (kind) {
+    case VP_MPO_DX_CENTERED:
+      c = place2(stencil_chain(L->nx, {{0.0, -0.5 / dx, 0.0, 0.5 / dx, 0.0}}, true), identity_chain(L->nv), dims);
+      break;
+    case VP_MPO_DX_FORWARD:
+      c = place2(stencil_chain(L->nx, {{0.0, 0.0, -1.5 / dx, 2.0 / dx, -0.5 / dx}}, true), identity_chain(L->nv),
+                 dims);
+      break;
+    case VP_MPO_DX_BACKWARD:
+      c = place2(stencil_chain(L->nx, {{0.5 / dx, -2.0 / dx, 1.5 / dx, 0.0, 0.0}}, true), identity_chain(L->nv),
+                 dims);
+      break;
+    case VP_MPO_DV_ZERO_GRAD:
+      c = place2(identity_chain(L->nx), zero_gradient_chain(L->nv, dv), dims);
+      break;
+    case VP_MPO_DXX: {
+      const double s = 1.0 / (dx * dx);
+      c = place2(stencil_chain(L->nx, {{0.0, s, -2.0 * s, s, 0.0}}, true), identity_chain(L->nv), dims);
+      break;
+    }
+    case VP_MPO_ADVECTION:
+      c = upwind_operator(L->nx, L->nv, dims, dx, L->vmin, dv);
+      break;
+    default:
+      return fail(ctx, VP_EINVAL, "mpo_create_vp: unknown kind");
+  }
+  return mpo_from_chain(ctx, c, out);
+}
+
+int mpo_create_cores(vp_ctx* ctx, int n, const int* bonds, const double* cores, mpo_t** out) {
+  if (!ctx || n < 1 || !bonds || !cores || !out || bonds[0] != 1 || bonds[n] != 1)
+    return fail(ctx, VP_EINVAL, "mpo_create_cores: bad argument");
+  Chain c;
+  c.alloc(std::vector<int>(bonds, bonds + n + 1));
+  size_t off = 0;
+  for (int k = 0; k < n; ++k) {
+    std::memcpy(c.core[k].data(), cores + off, c.core[k].size() * sizeof(double));
+    off += c.core[k].size();
+  }
+  return mpo_from_chain(ctx, c, out);
+}
+
+int mpo_destroy(mpo_t* m) {
+  if (!m) return VP_EINVAL;
+  for (auto& b : m->core) release(m->ctx, b);
+  delete m;
+  return VP_OK;
+}
+
+int mpo_num_sites(const mpo_t* m) { return m ? m->n : -1; }
+
+int mpo_bonds(const mpo_t* m, int* out) {
+  if (!m || !out) return VP_EINVAL;
+  for (int k = 0; k <= m->n; ++k) out[k] = m->w[k];
+  return VP_OK;
+}
+
+int mpo_to_dense(vp_ctx* ctx, const mpo_t* m, double* host) {
+  if (!ctx || !m || !host || m->n > 12) return fail(ctx, VP_EINVAL, "mpo_to_dense: bad argument");
+  DevBuf a, b;
+  // T[o_prev][i_prev][w] starting from the first core (1,2,2,w1)
+  VP_TRY(reserve(ctx, a, (size_t)4 * m->w[1]));
+  VP_TRY(launch_copy(ctx, m->core[0].p, a.p, (size_t)4 * m->w[1]));
+  int rows = 2;
+  for (int k = 1; k < m->n; ++k) {
+    const size_t no = (size_t)rows * 2;
+    VP_TRY(reserve(ctx, b, no * no * m->w[k + 1]));
+    VP_TRY(launch_mpo_dense_step(ctx, a.p, rows, rows, m->w[k], m->core[k].p, m->w[k + 1], b.p));
+    std::swap(a, b);
+    rows *= 2;
+  }
+  const size_t N = (size_t)1 << m->n;
+  VP_CUDA(ctx, cudaMemcpyAsync(host, a.p, N * N * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  VP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  release(ctx, a);
+  release(ctx, b);
+  return VP_OK;
+}
+
+// ------------------------------------------------------------ operations
+static int site_sum_mps(vp_ctx* ctx, double alpha, const mps_t* a, double beta, const mpo_t* B, const mps_t* b,
+                        mps_t* out) {
+  const int n = b->n;
+  if ((a && a->n != n) || (B && B->n != n)) return fail(ctx, VP_EINVAL, "site counts differ");
+  std::vector<int> r(n + 1, 1);
+  for (int k = 1; k < n; ++k) r[k] = (a ? a->r[k] : 0) + b->r[k] * (B ? B->w[k] : 1);
+  if (out->n != n) {
+    mps_free(out);
+    mps_init(ctx, out, n);
+  }
+  for (int k = 0; k < n; ++k) {
+    SiteSum s{};
+    s.a = a ? a->core[k].p : nullptr;
+    s.al = a ? a->r[k] : 0;
+    s.ar = a ? a->r[k + 1] : 0;
+    s.b = b->core[k].p;
+    s.bl = b->r[k];
+    s.br = b->r[k + 1];
+    s.B = B ? B->core[k].p : nullptr;
+    s.wl = B ? B->w[k] : 1;
+    s.wr = B ? B->w[k + 1] : 1;
+    s.alpha = (k == 0) ? alpha : 1.0;
+    s.beta = (k == 0) ? beta : 1.0;
+    s.first = (k == 0);
+    s.last = (k == n - 1);
+    VP_TRY(reserve(ctx, out->core[k], (size_t)r[k] * 2 * r[k + 1]));
+    prof_begin(ctx, VP_K_APPLY);
+    VP_TRY(launch_site_sum(ctx, s, out->core[k].p, r[k], r[k + 1]));
+    const double bytes = 8.0 * ((double)r[k] * 2 * r[k + 1] + (a ? (double)s.al * 2 * s.ar : 0.0) +
+                                (double)s.bl * 2 * s.br + (B ? (double)s.wl * 4 * s.wr : 0.0));
+    prof_end(ctx, VP_K_APPLY, bytes);
+  }
+  out->r = r;
+  return VP_OK;
+}
+
+int mps_apply_mpo(vp_ctx* ctx, const mpo_t* mpo, const mps_t* in, mps_t* out) {
+  if (!ctx || !mpo || !in || !out || in == out) return fail(ctx, VP_EINVAL, "mps_apply_mpo: bad argument");
+  VP_TRY(site_sum_mps(ctx, 0.0, nullptr, 1.0, mpo, in, out));
+  return sync_status(ctx);
+}
+
+int mps_axpby(vp_ctx* ctx, double a, const mps_t* x, double b, const mps_t* y, mps_t* out) {
+  if (!ctx || !x || !y || !out || out == x || out == y) return fail(ctx, VP_EINVAL, "mps_axpby: bad argument");
+  VP_TRY(site_sum_mps(ctx, a, x, b, nullptr, y, out));
+  return sync_status(ctx);
+}
+
+int mps_compress(vp_ctx* ctx, mps_t* m, int chi, double tol, double* errs) {
+  if (!ctx || !m || chi < 1 || tol < 0) return fail(ctx, VP_EINVAL, "mps_compress: bad argument");
+  std::vector<double> e(std::max(1, m->n - 1), 0.0);
+  VP_TRY(compress(ctx, m, chi, tol, e.data()));
+  VP_TRY(sync_status(ctx));
+  if (errs)
+    for (int k = 0; k + 1 < m->n; ++k) errs[k] = e[k];
+  return VP_OK;
+}
+
+int vp_density(vp_ctx* ctx, const vp_layout* L, const mps_t* f, double* rho_dev) {
+  if (!ctx || !f || !rho_dev || !layout_ok(L) || L->nx + L->nv != f->n)
+    return fail(ctx, VP_EINVAL, "vp_density: bad argument");
+  VP_TRY(density(ctx, L, f, rho_dev));
+  return sync_status(ctx);
+}
+
+int vp_poisson(vp_ctx* ctx, const double* rho, int nx, double dx, double* E, double* we_host) {
+  if (!ctx || !rho || !E || nx < 1 || nx > 14 || !(dx > 0)) return fail(ctx, VP_EINVAL, "vp_poisson: bad argument");
+  VP_TRY(launch_poisson(ctx, rho, 1 << nx, dx, E, ctx->d_smalld + 8));
+  VP_CUDA(ctx, cudaMemcpyAsync(ctx->h_smalld + 8, ctx->d_smalld + 8, 2 * sizeof(double), cudaMemcpyDeviceToHost,
+                               ctx->stream));
+  VP_TRY(sync_status(ctx));
+  if (we_host) *we_host = ctx->h_smalld[8];
+  return VP_OK;
+}
+
+}  // extern "C"
+
+// ====================================================================== stepper
+struct vp_sim {
+  vp_ctx* ctx = nullptr;
+  vp_layout lay{};
+  vp_config cfg{};
+  std::vector<int> dims;
+  mps_t f, fi, acc, wa, wb, em;
+  Chain U;                       // static upwind part (host copy, for bonds)
+  std::vector<DevBuf> Ud;        // device cores of U
+  Chain Dv;                      // zero-gradient v derivative chain
+  std::vector<DevBuf> Dvd;
+  mpo_t L;                       // operator of the current stage
+  DevBuf rho, E, evec;
+  double t = 0.0;
+  Flops flops;
+};
+
+namespace vp {
+
+// Assemble L(E) = U + diag(E) (x) D_v from the current field MPS.
+static int assemble_operator(vp_sim* s) {
+  vp_ctx* ctx = s->ctx;
+  const int n = (int)s->dims.size();
+  const mps_t& em = s->em;
+  // bonds of the placed field term: E channel x D_v channel
+  std::vector<int> tw(n + 1);
+  int px = 0, pv = 0;
+  tw[0] = 1;
+  for (int k = 0; k < n; ++k) {
+    if (s->dims[k] == 0) ++px; else ++pv;
+    tw[k + 1] = em.r[px] * s->Dv.w[pv];
+  }
+  std::vector<int> w(n + 1);
+  w[0] = w[n] = 1;
+  for (int k = 1; k < n; ++k) w[k] = s->U.w[k] + tw[k];
+  s->L.ctx = ctx;
+  s->L.n = n;
+  s->L.w = w;
+  if ((int)s->L.core.size() != n) s->L.core.assign(n, DevBuf{});
+  px = pv = 0;
+  for (int k = 0; k < n; ++k) {
+    ETermSite e{};
+    if (s->dims[k] == 0) {
+      e.is_x = 1;
+      e.Ecore = em.core[px].p;
+      e.el = em.r[px];
+      e.er = em.r[px + 1];
+      e.dw = s->Dv.w[pv];
+      ++px;
+    } else {
+      e.is_x = 0;
+      e.Dcore = s->Dvd[pv].p;
+      e.dl = s->Dv.w[pv];
+      e.dr = s->Dv.w[pv + 1];
+      e.ew = em.r[px];
+      ++pv;
+    }
+    VP_TRY(reserve(ctx, s->L.core[k], (size_t)w[k] * 4 * w[k + 1]));
+    VP_TRY(launch_assemble_site(ctx, s->Ud[k].p, s->U.w[k], s->U.w[k + 1], e, k == 0, k == n - 1, s->L.core[k].p,
+                                w[k], w[k + 1]));
+  }
+  return VP_OK;
+}
+
+// Field of a stage: rho -> E -> E as an MPS (tolerance e_tol) -> L(E).
+static int stage_operator(vp_sim* s, const mps_t* f, double* we_mass) {
+  vp_ctx* ctx = s->ctx;
+  const int Nx = 1 << s->lay.nx;
+  VP_TRY(density(ctx, &s->lay, f, s->rho.p));
+  VP_TRY(launch_poisson(ctx, s->rho.p, Nx, grid_dx(&s->lay), s->E.p, ctx->d_smalld + 8));
+  if (we_mass)
+    VP_CUDA(ctx, cudaMemcpyAsync(we_mass, ctx->d_smalld + 8, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  mps_free(&s->em);
+  VP_TRY(from_vector(ctx, &s->em, s->lay.nx, s->E.p, 1 << 30, s->cfg.e_tol));
+  return assemble_operator(s);
+}
+
+static int sim_step(vp_sim* s, vp_record* rec) {
+  vp_ctx* ctx = s->ctx;
+  static const double A[3] = {0.5, 0.5, 1.0};
+  static const double B[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
+  const double dt = s->cfg.dt;
+  const mps_t* fi = &s->f;
+  const mps_t* acc = &s->f;
+  double wm[2] = {0, 0};
+  std::vector<double> errs(s->f.n, 0.0);
+  g_flops = &s->flops;
+  for (int i = 0; i < 4; ++i) {
+    VP_TRY(stage_operator(s, fi, i == 0 ? s->ctx->h_smalld + 16 : nullptr));
+    if (i < 3) {
+      VP_TRY(site_sum_mps(ctx, 1.0, acc, B[i] * dt, &s->L, fi, &s->wa));
+      VP_TRY(site_sum_mps(ctx, 1.0, &s->f, A[i] * dt, &s->L, fi, &s->wb));
+      VP_TRY(compress(ctx, &s->wa, 1 << 30, s->cfg.tol, nullptr));
+      VP_TRY(compress(ctx, &s->wb, 1 << 30, s->cfg.tol, nullptr));
+      std::swap(s->acc, s->wa);
+      std::swap(s->fi, s->wb);
+      acc = &s->acc;
+      fi = &s->fi;
+    } else {
+      VP_TRY(site_sum_mps(ctx, 1.0, acc, B[3] * dt, &s->L, fi, &s->wa));
+      VP_TRY(compress(ctx, &s->wa, s->cfg.chi, s->cfg.tol, errs.data()));
+      std::swap(s->f, s->wa);
+    }
+  }
+  g_flops = nullptr;
+  VP_TRY(sync_status(ctx));
+  wm[0] = s->ctx->h_smalld[16];
+  wm[1] = s->ctx->h_smalld[17];
+  if (!std::isfinite(wm[0])) return fail(ctx, VP_ENUMERIC, "non-finite field energy");
+  if (rec) {
+    rec->t = s->t;
+    rec->field_energy = wm[0];
+    rec->mass = wm[1];
+    rec->max_bond = *std::max_element(s->f.r.begin(), s->f.r.end());
+    rec->trunc_err = errs.empty() ? 0.0 : *std::max_element(errs.begin(), errs.end());
+  }
+  s->t += dt;
+  return VP_OK;
+}
+
+static int upload_chain(vp_ctx* ctx, const Chain& c, std::vector<DevBuf>& out) {
+  out.assign(c.core.size(), DevBuf{});
+  for (size_t k = 0; k < c.core.size(); ++k) {
+    VP_TRY(reserve(ctx, out[k], std::max<size_t>(1, c.core[k].size())));
+    VP_CUDA(ctx, cudaMemcpyAsync(out[k].p, c.core[k].data(), c.core[k].size() * sizeof(double),
+                                 cudaMemcpyHostToDevice, ctx->stream));
+  }
+  VP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return VP_OK;
+}
+
+static void sim_free(vp_sim* s) {
+  vp_ctx* ctx = s->ctx;
+  for (mps_t* m : {&s->f, &s->fi, &s->acc, &s->wa, &s->wb, &s->em}) mps_free(m);
+  for (auto& b : s->Ud) release(ctx, b);
+  for (auto& b : s->Dvd) release(ctx, b);
+  for (auto& b : s->L.core) release(ctx, b);
+  release(ctx, s->rho);
+  release(ctx, s->E);
+  release(ctx, s->evec);
+}
+
+}  // namespace vp
+
+extern "C" {
+
+int vp_sim_create(vp_ctx* ctx, const vp_layout* L, const vp_config* cfg, const mps_t* f0, vp_sim** out) {
+  if (!ctx || !cfg || !f0 || !out || !layout_ok(L) || L->nx + L->nv != f0->n || cfg->chi < 1 || cfg->tol < 0 ||
+      cfg->e_tol < 0 || !(cfg->dt > 0))
+    return fail(ctx, VP_EINVAL, "vp_sim_create: bad argument");
+  const double dx = grid_dx(L);
+  if (L->vmax * cfg->dt / dx > 0.6963) return fail(ctx, VP_ECFL, "dt above the RK4 upwind stability limit");
+  vp_sim* s = new vp_sim();
+  s->ctx = ctx;
+  s->lay = *L;
+  s->cfg = *cfg;
+  s->dims = site_dims(L);
+  for (mps_t* m : {&s->f, &s->fi, &s->acc, &s->wa, &s->wb, &s->em}) mps_init(ctx, m, 0);
+  int st = mps_copy(ctx, f0, &s->f);
+  if (st == VP_OK) {
+    s->U = upwind_operator(L->nx, L->nv, s->dims, dx, L->vmin, grid_dv(L));
+    s->Dv = zero_gradient_chain(L->nv, grid_dv(L));
+    st = upload_chain(ctx, s->U, s->Ud);
+  }
+  if (st == VP_OK) st = upload_chain(ctx, s->Dv, s->Dvd);
+  if (st == VP_OK) st = reserve(ctx, s->rho, (size_t)1 << L->nx);
+  if (st == VP_OK) st = reserve(ctx, s->E, (size_t)1 << L->nx);
+  if (st == VP_OK) st = sync_status(ctx);
+  if (st != VP_OK) {
+    sim_free(s);
+    delete s;
+    return st;
+  }
+  *out = s;
+  return VP_OK;
+}
+
+int vp_sim_destroy(vp_sim* s) {
+  if (!s) return VP_EINVAL;
+  sim_free(s);
+  delete s;
+  return VP_OK;
+}
+
+int vp_step(vp_sim* s, int nsteps, vp_record* records) {
+  if (!s || nsteps < 0) return VP_EINVAL;
+  for (int i = 0; i < nsteps; ++i) VP_TRY(sim_step(s, records ? records + i : nullptr));
+  return VP_OK;
+}
+
+const mps_t* vp_sim_state(const vp_sim* s) { return s ? &s->f : nullptr; }
+
+double vp_sim_flops(const vp_sim* s) {
+  return s ? s->flops.qr + s->flops.formq + s->flops.gemm + s->flops.jacobi : 0.0;
+}
+
+int vp_run(vp_ctx* ctx, const vp_layout* L, const vp_config* cfg, const double* f0, int nsteps, double* fT,
+           vp_record* records) {
+  if (!ctx || !cfg || !f0 || nsteps < 0) return fail(ctx, VP_EINVAL, "vp_run: bad argument");
+  mps_t* m = nullptr;
+  VP_TRY(mps_create(ctx, L, f0, 0, cfg->chi, cfg->tol, &m));
+  vp_sim* s = nullptr;
+  int st = vp_sim_create(ctx, L, cfg, m, &s);
+  mps_destroy(m);
+  if (st != VP_OK) return st;
+  st = vp_step(s, nsteps, records);
+  if (st == VP_OK && fT) st = mps_to_grid(ctx, &s->f, L, fT);
+  vp_sim_destroy(s);
+  return st;
+}
+
+}  // extern "C"
+
+extern "C" int mpo_create_vlasov(vp_ctx* ctx, const vp_layout* L, const double* E_host, double e_tol, mpo_t** out) {
+  if (!ctx || !out || !E_host || !layout_ok(L) || e_tol < 0) return fail(ctx, VP_EINVAL, "mpo_create_vlasov: bad argument");
+  vp_sim s;
+  s.ctx = ctx;
+  s.lay = *L;
+  s.dims = site_dims(L);
+  for (mps_t* m : {&s.f, &s.fi, &s.acc, &s.wa, &s.wb, &s.em}) mps_init(ctx, m, 0);
+  s.U = upwind_operator(L->nx, L->nv, s.dims, grid_dx(L), L->vmin, grid_dv(L));
+  s.Dv = zero_gradient_chain(L->nv, grid_dv(L));
+  int st = upload_chain(ctx, s.U, s.Ud);
+  if (st == VP_OK) st = upload_chain(ctx, s.Dv, s.Dvd);
+  if (st == VP_OK) st = reserve(ctx, s.E, (size_t)1 << L->nx);
+  if (st == VP_OK) {
+    cudaError_t e = cudaMemcpyAsync(s.E.p, E_host, sizeof(double) << L->nx, cudaMemcpyHostToDevice, ctx->stream);
+    if (e != cudaSuccess) st = cuda_fail(ctx, e, "mpo_create_vlasov");
+  }
+  if (st == VP_OK) st = from_vector(ctx, &s.em, L->nx, s.E.p, 1 << 30, e_tol);
+  if (st == VP_OK) st = assemble_operator(&s);
+  if (st == VP_OK) st = sync_status(ctx);
+  if (st == VP_OK) {
+    mpo_t* m = new mpo_t();
+    m->ctx = ctx;
+    m->n = s.L.n;
+    m->w = s.L.w;
+    m->core = s.L.core;
+    s.L.core.clear();
+    *out = m;
+  }
+  sim_free(&s);
+  return st;
+}

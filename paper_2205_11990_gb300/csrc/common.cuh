@@ -1,0 +1,170 @@
+// Internal declarations shared by the vpmps translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/vpmps.h"
+
+namespace vp {
+
+constexpr int kThreads = 256;      // threads per block of the factorisation kernels
+constexpr int kWarps = kThreads / 32;
+constexpr long long kSpinLimit = 1ll << 24;  // iterations before a device wait gives up (~1 s)
+
+// Device-side status words.  err: 0 = ok, 1 = a grid barrier gave up
+// (timeout), 2 = NaN/Inf met, 3 = Jacobi did not converge.
+struct DevStatus {
+  unsigned int count;   // grid-barrier arrival counter
+  unsigned int gen;     // grid-barrier generation
+  int err;
+  int pad;
+  unsigned int rot[3];  // Jacobi rotation counters, one per sweep modulo 3
+  int pad2;
+};
+
+// Grow-only device buffer owned by a context.
+struct DevBuf {
+  double* p = nullptr;
+  size_t cap = 0;  // doubles
+};
+
+}  // namespace vp
+
+struct vp_ctx {
+  int device = 0;
+  int num_sms = 0;
+  cudaStream_t stream = nullptr;
+  vp_alloc_fn alloc = nullptr;
+  vp_free_fn freef = nullptr;
+  void* user = nullptr;
+  std::string err;
+  int64_t launches = 0;
+  vp::DevStatus* status = nullptr;  // device
+  int* d_small = nullptr;           // device scratch ints (ranks, flags)
+  int* h_small = nullptr;           // pinned host mirror
+  double* d_smalld = nullptr;       // device scratch doubles
+  double* h_smalld = nullptr;       // pinned host mirror
+  // kernel-class timing
+  bool prof_on = false;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  std::vector<std::pair<int, size_t>> prof_marks;  // (class, first event index)
+  double prof_work[VP_K_COUNT] = {};
+  int64_t prof_launches[VP_K_COUNT] = {};
+  // workspaces
+  vp::DevBuf w_fac, w_q, w_gemm, w_j, w_p, w_tmp, w_tmp2, w_vec;
+  std::vector<vp::DevBuf> w_chain;
+};
+
+struct mps_t {
+  vp_ctx* ctx = nullptr;
+  int n = 0;
+  std::vector<int> r;            // n+1 bonds
+  std::vector<vp::DevBuf> core;  // core k: r[k]*2*r[k+1] doubles
+};
+
+struct mpo_t {
+  vp_ctx* ctx = nullptr;
+  int n = 0;
+  std::vector<int> w;            // n+1 bonds
+  std::vector<vp::DevBuf> core;  // core k: w[k]*4*w[k+1] doubles, (wl, out, in, wr)
+};
+
+namespace vp {
+
+// ------------------------------------------------------------ host helpers
+int fail(vp_ctx* ctx, int code, const std::string& msg);
+int cuda_fail(vp_ctx* ctx, cudaError_t e, const char* what);
+#define VP_CUDA(ctx, call)                                      \
+  do {                                                          \
+    cudaError_t e_ = (call);                                    \
+    if (e_ != cudaSuccess) return ::vp::cuda_fail(ctx, e_, #call); \
+  } while (0)
+#define VP_TRY(call)          \
+  do {                        \
+    int s_ = (call);          \
+    if (s_ != VP_OK) return s_; \
+  } while (0)
+
+void* dev_alloc(vp_ctx* ctx, size_t bytes);
+void dev_free(vp_ctx* ctx, void* p, size_t bytes);
+// Make sure b holds at least `elems` doubles (contents not preserved).
+int reserve(vp_ctx* ctx, DevBuf& b, size_t elems);
+// Same, preserving the first `keep` doubles.
+int reserve_keep(vp_ctx* ctx, DevBuf& b, size_t elems, size_t keep);
+void release(vp_ctx* ctx, DevBuf& b);
+int check_launch(vp_ctx* ctx, const char* what);
+// Bracket one launch of class `cls` with events when profiling is on.
+void prof_begin(vp_ctx* ctx, int cls);
+void prof_end(vp_ctx* ctx, int cls, double work);
+// Synchronise and read the device status word; maps errors to VP codes.
+int sync_status(vp_ctx* ctx);
+
+// ------------------------------------------------------------ kernels (linalg.cu)
+// Row-major (m x n) -> column-major copy.
+int launch_to_colmajor(vp_ctx* ctx, const double* A, int m, int n, double* out);
+// In-place Householder QR of the column-major m x n matrix A (lda = m):
+// R in the upper triangle, reflectors below, tau[min(m,n)].
+int launch_qr_factor(vp_ctx* ctx, double* A, int m, int n, double* tau, double* vbuf);
+// Q (m x p, p = min(m,n)) written row-major from the factored A.
+int launch_qr_formq(vp_ctx* ctx, const double* A, int m, int n, const double* tau, double* Q);
+// Upper-trapezoidal R (p x n) of the factored A, written row-major.
+int launch_qr_getr(vp_ctx* ctx, const double* A, int m, int n, double* R);
+// C (M x N) = alpha * A (M x K) * B (K x N), all row-major with given leading dims.
+int launch_gemm(vp_ctx* ctx, int M, int N, int K, double alpha, const double* A, int lda,
+                const double* B, int ldb, double* C, int ldc);
+// C = alpha * triu(A_colmajor) (M x K) * B: the R factor read in place.
+int launch_gemm_r(vp_ctx* ctx, int M, int N, int K, const double* Acm, int lda, const double* B,
+                  int ldb, double* C, int ldc);
+// One-sided Jacobi on the b rows (length c) of X, rotations also applied to
+// the rows of J (b x b, set to the identity here).  Row-major, contiguous.
+int launch_jacobi_rows(vp_ctx* ctx, double* X, int b, int c, double* J);
+// Sort row norms of X descending, choose the kept rank (chi, tol, ties),
+// write perm/sigma/rank/truncation error into ctx scratch.  d_out[0] = rank.
+int launch_select(vp_ctx* ctx, const double* X, int b, int c, int chi, double tol, int* perm,
+                  double* sigma, int* d_rank, double* d_err);
+// Vt (r x c) = X[perm[t]] / sigma[t];  W (b x r) = J[perm[t]][i] * sigma[t].
+int launch_svd_outputs(vp_ctx* ctx, const double* X, const double* J, int b, int c, int r,
+                       const int* perm, const double* sigma, double* Vt, double* W);
+
+// ------------------------------------------------------------ kernels (mpsops.cu)
+// out = alpha*a + beta*(B b) on one site (a may be NULL: pure apply; B may be
+// NULL: identity).  See mps_axpby / mps_apply_mpo for the block layout.
+struct SiteSum {
+  const double* a; int al, ar;     // a core (al, 2, ar)
+  const double* b; int bl, br;     // b core
+  const double* B; int wl, wr;     // MPO core (wl, 2, 2, wr) or NULL
+  double alpha, beta;
+  int first, last;                 // site position flags
+};
+int launch_site_sum(vp_ctx* ctx, const SiteSum& s, double* out, int ol, int orr);
+// T (rl x rr) = core[:,0,:] + core[:,1,:]
+int launch_phys_sum(vp_ctx* ctx, const double* core, int rl, int rr, double* T);
+int launch_copy(vp_ctx* ctx, const double* src, double* dst, size_t n);
+int launch_scale(vp_ctx* ctx, double* x, size_t n, double s);
+// dense f[ix][iv] -> site-ordered vector (gather) and back.
+int launch_permute_to_sites(vp_ctx* ctx, const double* f, int nx, int nv, int mapping, double* out,
+                            int inverse);
+int launch_poisson(vp_ctx* ctx, const double* rho, int N, double dx, double* E, double* we_dev);
+// MPO core on one site for the E-term diag(E) (x) D_v (placed product).
+struct ETermSite {
+  int is_x;                 // site carries an x bit
+  const double* Ecore;      // x site: E core (el, 2, er)
+  int el, er;
+  const double* Dcore;      // v site: D_v core (dl, 2, 2, dr)
+  int dl, dr;
+  int ew, dw;               // bond of the other dimension carried through
+};
+// Fill L core = blockdiag(U core, E-term core) (first/last concatenation).
+int launch_assemble_site(vp_ctx* ctx, const double* U, int ul, int ur, const ETermSite& e, int first,
+                         int last, double* out, int ol, int orr);
+// MPO -> dense (small n), and MPS eval helpers
+int launch_mpo_dense_step(vp_ctx* ctx, const double* T, int rows, int cols, int w, const double* core,
+                          int wr, double* out);
+
+}  // namespace vp

@@ -1,0 +1,503 @@
+// FP64 dense linear algebra of the compression sweeps (SI "Canonicalization and
+// Compression"): Householder QR, explicit Q, GEMM, one-sided Jacobi SVD and the
+// truncation rule of the truncation-error equation (main text, "MPS
+// Representation").  All kernels work on one matrix at a time and spread it
+// over every SM: FP64 on GB300 issues about two FMAs per SM per clock, so no
+// factorisation may sit on a single SM.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+
+#include "common.cuh"
+
+namespace vp {
+
+// ------------------------------------------------------------------ helpers
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum over the block; every thread receives the result.  `red` holds kWarps+1.
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    double t = lane < kWarps ? red[lane] : 0.0;
+    t = warp_sum(t);
+    if (lane == 0) red[kWarps] = t;
+  }
+  __syncthreads();
+  return red[kWarps];
+}
+
+__device__ __forceinline__ int ld_volatile(const int* p) { return *(const volatile int*)p; }
+
+// Grid-wide barrier for cooperative launches.  Every wait has a clock limit
+// (~1 s): on expiry the block records err = 1 and the barrier reports
+// failure, so the kernel returns instead of hanging.
+__device__ __forceinline__ bool grid_barrier(DevStatus* st, unsigned nblocks) {
+  __syncthreads();
+  if (nblocks > 1) {
+    if (threadIdx.x == 0) {
+      volatile unsigned* vgen = &st->gen;
+      const unsigned g = *vgen;
+      __threadfence();
+      const unsigned arrived = atomicAdd(&st->count, 1u);
+      if (arrived == nblocks - 1) {
+        atomicExch(&st->count, 0u);
+        __threadfence();
+        atomicAdd(&st->gen, 1u);
+      } else {
+        const long long t0 = clock64();
+        while (*vgen == g) {
+          if (ld_volatile(&st->err) != 0) break;
+          if (clock64() - t0 > 2000000000ll) {
+            atomicExch(&st->err, 1);
+            break;
+          }
+        }
+      }
+      __threadfence();
+    }
+    __syncthreads();
+  }
+  return ld_volatile(&st->err) == 0;
+}
+
+static int coop_launch(vp_ctx* ctx, const void* fn, int blocks, int threads, void** args, size_t smem,
+                       const char* what) {
+  ctx->launches++;
+  cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(threads), args, smem, ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, what);
+  return VP_OK;
+}
+
+// ------------------------------------------------------------ transposition
+__global__ void k_to_colmajor(const double* __restrict__ A, int m, int n, double* __restrict__ out) {
+  __shared__ double tile[32][33];
+  const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+  for (int y = threadIdx.y; y < 32; y += 8) {
+    const int r = by + y, c = bx + threadIdx.x;
+    if (r < m && c < n) tile[y][threadIdx.x] = A[(size_t)r * n + c];
+  }
+  __syncthreads();
+  for (int y = threadIdx.y; y < 32; y += 8) {
+    const int c = bx + y, r = by + threadIdx.x;
+    if (r < m && c < n) out[(size_t)c * m + r] = tile[threadIdx.x][y];
+  }
+}
+
+int launch_to_colmajor(vp_ctx* ctx, const double* A, int m, int n, double* out) {
+  dim3 grid((n + 31) / 32, (m + 31) / 32);
+  ctx->launches++;
+  k_to_colmajor<<<grid, dim3(32, 8), 0, ctx->stream>>>(A, m, n, out);
+  return check_launch(ctx, "to_colmajor");
+}
+
+// ------------------------------------------------------------ Householder QR
+// Column-cyclic ownership: column k belongs to block k % gridDim.x.  Step j:
+// the owner of column j (already updated by H_0..H_{j-1}, which it applied
+// itself) forms the reflector H_j = I - tau v v^T (LAPACK dlarfg convention,
+// v_j = 1) and publishes v in a double buffer; after one grid barrier every
+// block applies H_j to the columns it owns.  One barrier per column.
+__global__ void __launch_bounds__(kThreads) k_qr_factor(double* A, int m, int n, double* tau,
+                                                        double* vbuf, DevStatus* st) {
+  __shared__ double red[kWarps + 1];
+  const int nb = gridDim.x, bid = blockIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int p = min(m, n);
+  for (int j = 0; j < p; ++j) {
+    __syncthreads();
+    double* vj = vbuf + (size_t)(j & 1) * m;
+    if (bid == j % nb) {
+      double* col = A + (size_t)j * m;
+      double s = 0.0;
+      for (int i = j + 1 + threadIdx.x; i < m; i += kThreads) {
+        const double x = col[i];
+        s = fma(x, x, s);
+      }
+      s = block_sum(s, red);
+      const double x0 = col[j];
+      double t = 0.0, beta = x0, scale = 0.0;
+      if (s > 0.0) {
+        const double nrm = sqrt(fma(x0, x0, s));
+        beta = x0 >= 0.0 ? -nrm : nrm;
+        t = (beta - x0) / beta;
+        scale = 1.0 / (x0 - beta);
+      }
+      for (int i = j + 1 + threadIdx.x; i < m; i += kThreads) {
+        const double v = col[i] * scale;
+        col[i] = v;
+        __stcg(vj + i, v);
+      }
+      if (threadIdx.x == 0) {
+        col[j] = beta;
+        __stcg(vj + j, 1.0);
+        __stcg(tau + j, t);
+      }
+      __threadfence();
+    }
+    if (!grid_barrier(st, nb)) return;
+    const double t = __ldcg(tau + j);
+    if (t == 0.0) continue;
+    // first owned column strictly right of j
+    const int k0 = (j + 1) + ((bid - (j + 1) % nb) % nb + nb) % nb;
+    for (int k = k0 + warp * nb; k < n; k += kWarps * nb) {
+      double* col = A + (size_t)k * m;
+      double w = 0.0;
+      for (int i = j + lane; i < m; i += 32) w = fma(__ldcg(vj + i), col[i], w);
+      w = warp_sum(w) * t;
+      for (int i = j + lane; i < m; i += 32) col[i] = fma(-w, __ldcg(vj + i), col[i]);
+    }
+  }
+}
+
+int launch_qr_factor(vp_ctx* ctx, double* A, int m, int n, double* tau, double* vbuf) {
+  const int p = std::min(m, n);
+  if (p <= 0) return VP_OK;
+  // enough blocks that each owns a few columns, but never more than one per SM
+  int blocks = std::min(ctx->num_sms, std::max(1, n / 2));
+  if ((long long)m * n < 8192) blocks = 1;
+  DevStatus* st = ctx->status;
+  void* args[] = {&A, &m, &n, &tau, &vbuf, &st};
+  return coop_launch(ctx, (const void*)k_qr_factor, blocks, kThreads, args, 0, "qr_factor");
+}
+
+// Q = H_0 ... H_{p-1} [I_p; 0]: one warp per column, applied right to left in
+// a column-major scratch column, then stored row-major (m x p).
+__global__ void k_qr_formq(const double* __restrict__ A, int m, int p, const double* __restrict__ tau,
+                           double* __restrict__ scratch, double* __restrict__ Q) {
+  const int lane = threadIdx.x & 31;
+  const int k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (k >= p) return;
+  double* q = scratch + (size_t)k * m;
+  for (int i = lane; i < m; i += 32) q[i] = (i == k) ? 1.0 : 0.0;
+  __syncwarp();
+  for (int j = k; j >= 0; --j) {
+    const double t = tau[j];
+    if (t == 0.0) continue;
+    const double* v = A + (size_t)j * m;
+    double w = 0.0;
+    for (int i = j + lane; i < m; i += 32) w = fma(i == j ? 1.0 : v[i], q[i], w);
+    w = warp_sum(w) * t;
+    for (int i = j + lane; i < m; i += 32) q[i] = fma(-w, i == j ? 1.0 : v[i], q[i]);
+    __syncwarp();
+  }
+  for (int i = lane; i < m; i += 32) Q[(size_t)i * p + k] = q[i];
+}
+
+int launch_qr_formq(vp_ctx* ctx, const double* A, int m, int n, const double* tau, double* Q) {
+  const int p = std::min(m, n);
+  if (p <= 0) return VP_OK;
+  VP_TRY(reserve(ctx, ctx->w_q, (size_t)m * p));
+  const int wpb = 8;
+  ctx->launches++;
+  k_qr_formq<<<(p + wpb - 1) / wpb, wpb * 32, 0, ctx->stream>>>(A, m, p, tau, ctx->w_q.p, Q);
+  return check_launch(ctx, "qr_formq");
+}
+
+__global__ void k_qr_getr(const double* __restrict__ A, int m, int n, int p, double* __restrict__ R) {
+  const size_t total = (size_t)p * n;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int j = (int)(e / n), k = (int)(e % n);
+    R[e] = (j <= k) ? A[(size_t)k * m + j] : 0.0;
+  }
+}
+
+int launch_qr_getr(vp_ctx* ctx, const double* A, int m, int n, double* R) {
+  const int p = std::min(m, n);
+  const size_t total = (size_t)p * n;
+  if (total == 0) return VP_OK;
+  const int blocks = (int)std::min<size_t>((total + 255) / 256, (size_t)ctx->num_sms * 16);
+  ctx->launches++;
+  k_qr_getr<<<blocks, 256, 0, ctx->stream>>>(A, m, n, p, R);
+  return check_launch(ctx, "qr_getr");
+}
+
+// ------------------------------------------------------------------- GEMM
+// 64 x 64 output tile per block, K step 16, 256 threads with a 4 x 4
+// register tile each.  FP64 FMA, row-major B and C.  ALoad selects the A
+// operand: row-major, or the column-major upper triangle of a QR factor.
+struct ARowMajor {
+  const double* A;
+  int lda;
+  __device__ double operator()(int r, int k) const { return A[(size_t)r * lda + k]; }
+};
+struct AUpperColMajor {
+  const double* A;
+  int lda;
+  __device__ double operator()(int r, int k) const { return r <= k ? A[(size_t)k * lda + r] : 0.0; }
+};
+
+template <class ALoad>
+__global__ void __launch_bounds__(256) k_gemm(int M, int N, int K, double alpha, ALoad a,
+                                              const double* __restrict__ B, int ldb, double* __restrict__ C,
+                                              int ldc) {
+  __shared__ double As[16][64 + 1];
+  __shared__ double Bs[16][64];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int row0 = blockIdx.x * 64, col0 = blockIdx.y * 64;
+  double acc[4][4] = {};
+  for (int k0 = 0; k0 < K; k0 += 16) {
+    for (int e = threadIdx.x; e < 64 * 16; e += 256) {
+      const int r = e / 16, kk = e % 16;
+      const int gr = row0 + r, gk = k0 + kk;
+      As[kk][r] = (gr < M && gk < K) ? a(gr, gk) : 0.0;
+    }
+    for (int e = threadIdx.x; e < 16 * 64; e += 256) {
+      const int kk = e / 64, c = e % 64;
+      const int gk = k0 + kk, gc = col0 + c;
+      Bs[kk][c] = (gk < K && gc < N) ? B[(size_t)gk * ldb + gc] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+      double av[4], bv[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) av[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) bv[i] = Bs[kk][tx + 16 * i];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) acc[i][jj] = fma(av[i], bv[jj], acc[i][jj]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int r = row0 + ty + 16 * i;
+    if (r >= M) continue;
+#pragma unroll
+    for (int jj = 0; jj < 4; ++jj) {
+      const int c = col0 + tx + 16 * jj;
+      if (c < N) C[(size_t)r * ldc + c] = alpha * acc[i][jj];
+    }
+  }
+}
+
+int launch_gemm(vp_ctx* ctx, int M, int N, int K, double alpha, const double* A, int lda, const double* B,
+                int ldb, double* C, int ldc) {
+  if (M <= 0 || N <= 0) return VP_OK;
+  dim3 grid((M + 63) / 64, (N + 63) / 64);
+  if (grid.y > 65535) return fail(ctx, VP_ECAPACITY, "gemm: N too large");
+  ctx->launches++;
+  k_gemm<ARowMajor><<<grid, 256, 0, ctx->stream>>>(M, N, K, alpha, ARowMajor{A, lda}, B, ldb, C, ldc);
+  return check_launch(ctx, "gemm");
+}
+
+int launch_gemm_r(vp_ctx* ctx, int M, int N, int K, const double* Acm, int lda, const double* B, int ldb,
+                  double* C, int ldc) {
+  if (M <= 0 || N <= 0) return VP_OK;
+  dim3 grid((M + 63) / 64, (N + 63) / 64);
+  if (grid.y > 65535) return fail(ctx, VP_ECAPACITY, "gemm: N too large");
+  ctx->launches++;
+  k_gemm<AUpperColMajor><<<grid, 256, 0, ctx->stream>>>(M, N, K, 1.0, AUpperColMajor{Acm, lda}, B, ldb, C,
+                                                        ldc);
+  return check_launch(ctx, "gemm_r");
+}
+
+// ------------------------------------------------------------ Jacobi SVD
+// One-sided (Hestenes) Jacobi on the rows of X: rotate row pairs until all
+// are mutually orthogonal; then X = diag(s) V^T and the accumulated rotation
+// G (rows of J) gives U = G^T.  Round-robin ("circle") ordering: b' - 1
+// rounds of b'/2 disjoint pairs per sweep, one warp per pair, one grid
+// barrier per round.
+__device__ __forceinline__ int rr_index(int pos, int round, int bp) {
+  return pos == 0 ? 0 : 1 + (pos - 1 + round) % (bp - 1);
+}
+
+__global__ void __launch_bounds__(kThreads) k_jacobi_rows(double* X, int b, int c, double* J, double eps,
+                                                          int max_sweeps, DevStatus* st) {
+  const int nb = gridDim.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int gw = blockIdx.x * kWarps + warp, nw = nb * kWarps;
+  const int bp = b + (b & 1), npairs = bp / 2, rounds = bp - 1;
+  int sweep = 0;
+  bool converged = false;
+  for (; sweep < max_sweeps; ++sweep) {
+    unsigned* cnt = &st->rot[sweep % 3];
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicExch(&st->rot[(sweep + 1) % 3], 0u);
+    for (int round = 0; round < rounds; ++round) {
+      for (int pr = gw; pr < npairs; pr += nw) {
+        int i = rr_index(pr, round, bp), j = rr_index(bp - 1 - pr, round, bp);
+        if (i >= b || j >= b) continue;
+        if (i > j) {
+          const int t = i;
+          i = j;
+          j = t;
+        }
+        double* xi = X + (size_t)i * c;
+        double* xj = X + (size_t)j * c;
+        double al = 0.0, be = 0.0, ga = 0.0;
+        for (int q = lane; q < c; q += 32) {
+          const double u = __ldcg(xi + q), v = __ldcg(xj + q);
+          al = fma(u, u, al);
+          be = fma(v, v, be);
+          ga = fma(u, v, ga);
+        }
+        al = warp_sum(al);
+        be = warp_sum(be);
+        ga = warp_sum(ga);
+        if (!(al > 0.0 && be > 0.0)) continue;
+        if (!(fabs(ga) > eps * sqrt(al) * sqrt(be))) continue;
+        const double zeta = (be - al) / (2.0 * ga);
+        const double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(fma(zeta, zeta, 1.0)));
+        const double cs = 1.0 / sqrt(fma(t, t, 1.0)), sn = cs * t;
+        for (int q = lane; q < c; q += 32) {
+          const double u = __ldcg(xi + q), v = __ldcg(xj + q);
+          __stcg(xi + q, cs * u - sn * v);
+          __stcg(xj + q, sn * u + cs * v);
+        }
+        double* ji = J + (size_t)i * b;
+        double* jj = J + (size_t)j * b;
+        for (int q = lane; q < b; q += 32) {
+          const double u = __ldcg(ji + q), v = __ldcg(jj + q);
+          __stcg(ji + q, cs * u - sn * v);
+          __stcg(jj + q, sn * u + cs * v);
+        }
+        if (lane == 0) atomicAdd(cnt, 1u);
+      }
+      if (!grid_barrier(st, nb)) return;
+    }
+    if (__ldcg(cnt) == 0u) {
+      converged = true;
+      break;
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    st->pad2 = sweep + 1;
+    if (!converged) atomicCAS(&st->err, 0, 3);
+  }
+}
+
+__global__ void k_identity(double* J, int b) {
+  const size_t total = (size_t)b * b;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x)
+    J[e] = (e / b == e % b) ? 1.0 : 0.0;
+}
+
+int launch_jacobi_rows(vp_ctx* ctx, double* X, int b, int c, double* J) {
+  if (b <= 0) return VP_OK;
+  ctx->launches++;
+  k_identity<<<std::min(1024, (b * b + 255) / 256 + 1), 256, 0, ctx->stream>>>(J, b);
+  VP_TRY(check_launch(ctx, "identity"));
+  if (b == 1) return VP_OK;
+  const int npairs = (b + 1) / 2;
+  int blocks = std::min(ctx->num_sms, std::max(1, (npairs + kWarps - 1) / kWarps));
+  if ((long long)b * c < 4096) blocks = 1;
+  // rotate while |<x_i,x_j>| > eps |x_i||x_j|; eps grows with the dot length
+  double eps = 1e-15 * std::sqrt((double)c);
+  int max_sweeps = 60;
+  DevStatus* st = ctx->status;
+  void* args[] = {&X, &b, &c, &J, &eps, &max_sweeps, &st};
+  return coop_launch(ctx, (const void*)k_jacobi_rows, blocks, kThreads, args, 0, "jacobi_rows");
+}
+
+// ------------------------------------------------------------ truncation
+// Single block: row norms, descending order (ties by index), kept rank by the
+// rule r = min(chi, r_tol), r_tol the smallest r with sqrt(sum_{i>=r} s_i^2)
+// <= tol ||s|| (tail summed smallest first, tol = 0: keep all), moved down
+// to the start of a cluster of values within a relative 1e-5.
+__global__ void k_select(const double* __restrict__ X, int b, int c, int chi, double tol, int* perm,
+                         double* sigma, int* d_rank, double* d_err, DevStatus* st) {
+  extern __shared__ double sm[];
+  double* s = sm;          // b
+  double* tail = sm + b;   // b + 1
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  for (int i = warp; i < b; i += nwarps) {
+    double a = 0.0;
+    for (int q = lane; q < c; q += 32) {
+      const double u = X[(size_t)i * c + q];
+      a = fma(u, u, a);
+    }
+    a = warp_sum(a);
+    if (lane == 0) s[i] = sqrt(a);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < b; i += blockDim.x) {
+    const double si = s[i];
+    if (!isfinite(si)) atomicCAS(&st->err, 0, 2);
+    int pos = 0;
+    for (int j = 0; j < b; ++j) {
+      const double sj = s[j];
+      pos += (sj > si) || (sj == si && j < i);
+    }
+    perm[pos] = i;
+    sigma[pos] = si;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double acc = 0.0;
+    tail[b] = 0.0;
+    for (int i = b - 1; i >= 0; --i) {
+      acc = fma(sigma[i], sigma[i], acc);
+      tail[i] = acc;
+    }
+    const double nrm2 = tail[0];
+    int r = 1;
+    double err = 0.0;
+    if (nrm2 > 0.0) {
+      int r_tol = b;
+      if (tol > 0.0) {
+        const double thr2 = tol * tol * nrm2;
+        for (int q = 1; q <= b; ++q)
+          if (tail[q] <= thr2) {
+            r_tol = q;
+            break;
+          }
+      }
+      r = min(min(chi, r_tol), b);
+      while (r > 1 && r < b && (sigma[r - 1] - sigma[r]) <= 1e-5 * sigma[r - 1]) --r;
+      if (r < 1) r = 1;
+      err = sqrt(tail[r] / nrm2);
+    }
+    *d_rank = r;
+    *d_err = err;
+  }
+}
+
+int launch_select(vp_ctx* ctx, const double* X, int b, int c, int chi, double tol, int* perm, double* sigma,
+                  int* d_rank, double* d_err) {
+  const size_t smem = (size_t)(2 * b + 1) * sizeof(double);
+  if (smem > 200 * 1024) return fail(ctx, VP_ECAPACITY, "select: bond too large");
+  if (smem > 48 * 1024)
+    VP_CUDA(ctx, cudaFuncSetAttribute(k_select, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  ctx->launches++;
+  k_select<<<1, 512, smem, ctx->stream>>>(X, b, c, chi, tol, perm, sigma, d_rank, d_err, ctx->status);
+  return check_launch(ctx, "select");
+}
+
+__global__ void k_svd_outputs(const double* __restrict__ X, const double* __restrict__ J, int b, int c, int r,
+                              const int* __restrict__ perm, const double* __restrict__ sigma, double* Vt,
+                              double* W) {
+  const size_t nv = (size_t)r * c, nw = (size_t)b * r;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < nv + nw; e += (size_t)gridDim.x * blockDim.x) {
+    if (e < nv) {
+      const int t = (int)(e / c), q = (int)(e % c);
+      const double s = sigma[t];
+      Vt[e] = s > 0.0 ? X[(size_t)perm[t] * c + q] / s : 0.0;
+    } else {
+      const size_t f = e - nv;
+      const int i = (int)(f / r), t = (int)(f % r);
+      W[f] = J[(size_t)perm[t] * b + i] * sigma[t];
+    }
+  }
+}
+
+int launch_svd_outputs(vp_ctx* ctx, const double* X, const double* J, int b, int c, int r, const int* perm,
+                       const double* sigma, double* Vt, double* W) {
+  const size_t total = (size_t)r * c + (size_t)b * r;
+  const int blocks = (int)std::min<size_t>((total + 255) / 256, (size_t)ctx->num_sms * 8);
+  ctx->launches++;
+  k_svd_outputs<<<std::max(1, blocks), 256, 0, ctx->stream>>>(X, J, b, c, r, perm, sigma, Vt, W);
+  return check_launch(ctx, "svd_outputs");
+}
+
+}  // namespace vp

@@ -1,0 +1,307 @@
+// Memory-bound MPS/MPO kernels: per-site MPO x MPS contraction fused with MPS
+// addition (SI "Matrix-vector multiplication", "Addition"), integration over v
+// (SI "Integration"), the periodic Poisson solve (main text Eqs. for phi and
+// E), the site permutation of the interleaved mapping, and the assembly of
+// the Vlasov operator's MPO with the field term (SI "Dot Product").
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace vp {
+
+static int grid_for(vp_ctx* ctx, size_t total, int per = 256) {
+  return (int)std::max<size_t>(1, std::min<size_t>((total + per - 1) / per, (size_t)ctx->num_sms * 16));
+}
+
+// out core (ol, 2, orr) = alpha*a (+) beta*(B b), blocks placed as in the
+// MPS sum: a occupies the leading block of each bond, (B b) the trailing one
+// with bond index (alpha, beta) = a_b * w + b_w; the first site concatenates
+// along the right bond only and the last site along the left bond only.
+__global__ void k_site_sum(SiteSum s, double* __restrict__ out, int ol, int orr) {
+  const size_t total = (size_t)ol * 2 * orr;
+  const int offl = (s.a && !s.first) ? s.al : 0;  // start of the (B b) block on the left bond
+  const int offr = (s.a && !s.last) ? s.ar : 0;
+  const int wl = s.B ? s.wl : 1, wr = s.B ? s.wr : 1;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int l = (int)(e / (2 * orr));
+    const int o = (int)((e / orr) & 1);
+    const int r = (int)(e % orr);
+    double v = 0.0;
+    // a block
+    if (s.a) {
+      const bool inl = s.first ? true : (l < s.al);
+      const bool inr = s.last ? true : (r < s.ar);
+      if (inl && inr) {
+        const int la = s.first ? 0 : l, ra = s.last ? 0 : r;
+        v = s.alpha * s.a[((size_t)la * 2 + o) * s.ar + ra];
+      }
+    }
+    // (B b) block
+    const bool inl = s.a ? (s.first ? true : l >= offl) : true;
+    const bool inr = s.a ? (s.last ? true : r >= offr) : true;
+    if (inl && inr) {
+      const int lb = s.first ? 0 : l - offl, rb = s.last ? 0 : r - offr;
+      const int al = lb / wl, bw = lb % wl, ar = rb / wr, brw = rb % wr;
+      double acc;
+      if (s.B) {
+        const double* Bc = s.B + ((size_t)bw * 4 + o * 2) * wr + brw;  // B[bw][o][i][brw], i stride wr
+        const double* bc = s.b + (size_t)al * 2 * s.br + ar;          // b[al][i][ar], i stride br
+        acc = Bc[0] * bc[0] + Bc[wr] * bc[s.br];
+      } else {
+        acc = s.b[((size_t)al * 2 + o) * s.br + ar];
+      }
+      v += s.beta * acc;
+    }
+    out[e] = v;
+  }
+}
+
+int launch_site_sum(vp_ctx* ctx, const SiteSum& s, double* out, int ol, int orr) {
+  const size_t total = (size_t)ol * 2 * orr;
+  ctx->launches++;
+  k_site_sum<<<grid_for(ctx, total), 256, 0, ctx->stream>>>(s, out, ol, orr);
+  return check_launch(ctx, "site_sum");
+}
+
+__global__ void k_phys_sum(const double* __restrict__ core, int rl, int rr, double* __restrict__ T) {
+  const size_t total = (size_t)rl * rr;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const size_t l = e / rr, r = e % rr;
+    T[e] = core[(l * 2) * rr + r] + core[(l * 2 + 1) * rr + r];
+  }
+}
+
+int launch_phys_sum(vp_ctx* ctx, const double* core, int rl, int rr, double* T) {
+  ctx->launches++;
+  k_phys_sum<<<grid_for(ctx, (size_t)rl * rr), 256, 0, ctx->stream>>>(core, rl, rr, T);
+  return check_launch(ctx, "phys_sum");
+}
+
+__global__ void k_copy(const double* __restrict__ src, double* __restrict__ dst, size_t n) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+    dst[e] = src[e];
+}
+
+int launch_copy(vp_ctx* ctx, const double* src, double* dst, size_t n) {
+  if (n == 0) return VP_OK;
+  ctx->launches++;
+  k_copy<<<grid_for(ctx, n), 256, 0, ctx->stream>>>(src, dst, n);
+  return check_launch(ctx, "copy");
+}
+
+__global__ void k_scale(double* x, size_t n, double s) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+    x[e] *= s;
+}
+
+int launch_scale(vp_ctx* ctx, double* x, size_t n, double s) {
+  if (n == 0) return VP_OK;
+  ctx->launches++;
+  k_scale<<<grid_for(ctx, n), 256, 0, ctx->stream>>>(x, n, s);
+  return check_launch(ctx, "scale");
+}
+
+// Site-ordered index <-> (ix, iv).  Site order: SEQ = x bits then v bits;
+// INTERLEAVED = x0 v0 x1 v1 ... with leftover bits of the longer dimension.
+__device__ __forceinline__ size_t site_to_grid(size_t s, int nx, int nv, int mapping) {
+  if (mapping == VP_SEQ) return s;  // already [ix][iv]
+  const int n = nx + nv;
+  size_t ix = 0, iv = 0;
+  int site = 0;
+  const int mx = max(nx, nv);
+  for (int b = 0; b < mx; ++b) {
+    if (b < nx) {
+      ix = (ix << 1) | ((s >> (n - 1 - site)) & 1);
+      ++site;
+    }
+    if (b < nv) {
+      iv = (iv << 1) | ((s >> (n - 1 - site)) & 1);
+      ++site;
+    }
+  }
+  return (ix << nv) | iv;
+}
+
+__global__ void k_permute(const double* __restrict__ f, int nx, int nv, int mapping, double* __restrict__ out,
+                          int inverse) {
+  const size_t total = (size_t)1 << (nx + nv);
+  for (size_t s = blockIdx.x * (size_t)blockDim.x + threadIdx.x; s < total; s += (size_t)gridDim.x * blockDim.x) {
+    const size_t g = site_to_grid(s, nx, nv, mapping);
+    if (inverse)
+      out[g] = f[s];
+    else
+      out[s] = f[g];
+  }
+}
+
+int launch_permute_to_sites(vp_ctx* ctx, const double* f, int nx, int nv, int mapping, double* out,
+                            int inverse) {
+  const size_t total = (size_t)1 << (nx + nv);
+  ctx->launches++;
+  k_permute<<<grid_for(ctx, total), 256, 0, ctx->stream>>>(f, nx, nv, mapping, out, inverse);
+  return check_launch(ctx, "permute");
+}
+
+// Periodic second-order Poisson on one block.  With s_i = dx^2 (rho_i -
+// mean) and d_i = phi_{i+1} - phi_i the difference equation reads d_i -
+// d_{i-1} = s_i, so d is a prefix sum fixed by sum_i d_i = 0 (periodicity),
+// and E_i = -(phi_{i+1} - phi_{i-1}) / (2 dx) = -(d_i + d_{i-1}) / (2 dx).
+// we[0] = 1/2 sum E^2 dx, we[1] = sum rho dx.
+__global__ void k_poisson(const double* __restrict__ rho, int N, double dx, double* __restrict__ E,
+                          double* __restrict__ we) {
+  extern __shared__ double sm[];
+  double* d = sm;           // N
+  double* red = sm + N;     // blockDim/32 + 1
+  double* part = red + 33;  // blockDim
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+  auto bsum = [&](double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    if (tid == 0) {
+      double t = 0.0;
+      for (int w = 0; w < nw; ++w) t += red[w];
+      red[32] = t;
+    }
+    __syncthreads();
+    return red[32];
+  };
+  double loc = 0.0;
+  for (int i = tid; i < N; i += nt) loc += rho[i];
+  const double total = bsum(loc);
+  const double mean = total / N;
+  // contiguous chunk per thread: serial prefix inside, block scan across
+  const int chunk = (N + nt - 1) / nt;
+  const int lo = min(N, tid * chunk), hi = min(N, lo + chunk);
+  double run = 0.0;
+  for (int i = lo; i < hi; ++i) {
+    // S_i = sum_{j=1}^{i} s_j (S_0 = 0)
+    if (i > 0) run += dx * dx * (rho[i] - mean);
+    d[i] = run;
+  }
+  part[tid] = run;
+  __syncthreads();
+  if (tid == 0) {
+    double acc = 0.0;
+    for (int t = 0; t < nt; ++t) {
+      const double v = part[t];
+      part[t] = acc;
+      acc += v;
+    }
+  }
+  __syncthreads();
+  double sS = 0.0;
+  for (int i = lo; i < hi; ++i) {
+    d[i] += part[tid];
+    sS += d[i];
+  }
+  const double sumS = bsum(sS);
+  const double d0 = -sumS / N;
+  for (int i = tid; i < N; i += nt) d[i] += d0;  // d_i = d_0 + S_i
+  __syncthreads();
+  double e2 = 0.0;
+  for (int i = tid; i < N; i += nt) {
+    const double dm = d[(i + N - 1) % N];
+    const double e = -(d[i] + dm) / (2.0 * dx);
+    E[i] = e;
+    e2 = fma(e, e, e2);
+  }
+  const double we_ = bsum(e2);
+  if (tid == 0) {
+    we[0] = 0.5 * we_ * dx;
+    we[1] = total * dx;
+  }
+}
+
+int launch_poisson(vp_ctx* ctx, const double* rho, int N, double dx, double* E, double* we_dev) {
+  const int nt = 256;
+  const size_t smem = (size_t)(N + 33 + nt) * sizeof(double);
+  if (smem > 200 * 1024) return fail(ctx, VP_ECAPACITY, "poisson: 2^nx too large");
+  if (smem > 48 * 1024)
+    VP_CUDA(ctx, cudaFuncSetAttribute(k_poisson, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  ctx->launches++;
+  k_poisson<<<1, nt, smem, ctx->stream>>>(rho, N, dx, E, we_dev);
+  return check_launch(ctx, "poisson");
+}
+
+// L core = blockdiag(U, T) with T the placed field term diag(E) (x) D_v.
+// Bond indices of T flatten (E channel, D_v channel) in that order.
+__global__ void k_assemble(const double* __restrict__ U, int ul, int ur, ETermSite e, int first, int last,
+                           double* __restrict__ out, int ol, int orr) {
+  const size_t total = (size_t)ol * 4 * orr;
+  const int tl = first ? 1 : ol - ul;  // T block sizes
+  const int tr = last ? 1 : orr - ur;
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < total; q += (size_t)gridDim.x * blockDim.x) {
+    const int l = (int)(q / (4 * orr));
+    const int oi = (int)((q / orr) & 3);
+    const int o = oi >> 1, i = oi & 1;
+    const int r = (int)(q % orr);
+    double v = 0.0;
+    const bool ul_in = first ? true : l < ul;
+    const bool ur_in = last ? true : r < ur;
+    if (ul_in && ur_in) {
+      const int lu = first ? 0 : l, ru = last ? 0 : r;
+      v = U[((size_t)lu * 4 + oi) * ur + ru];
+    }
+    const bool tl_in = first ? true : l >= ul;
+    const bool tr_in = last ? true : r >= ur;
+    if (tl_in && tr_in) {
+      const int lt = first ? 0 : l - ul, rt = last ? 0 : r - ur;
+      (void)tl;
+      (void)tr;
+      if (e.is_x) {
+        // (ea, d) -> (eb, d'):  E[ea][o][eb] delta_oi delta_dd'
+        const int ea = lt / e.dw, da = lt % e.dw, eb = rt / e.dw, db = rt % e.dw;
+        if (o == i && da == db) v += e.Ecore[((size_t)ea * 2 + o) * e.er + eb];
+      } else {
+        // (ea, da) -> (eb, db):  delta_ea,eb D[da][o][i][db]
+        const int ea = lt / e.dl, da = lt % e.dl, eb = rt / e.dr, db = rt % e.dr;
+        if (ea == eb) v += e.Dcore[((size_t)da * 4 + oi) * e.dr + db];
+      }
+    }
+    out[q] = v;
+  }
+}
+
+int launch_assemble_site(vp_ctx* ctx, const double* U, int ul, int ur, const ETermSite& e, int first, int last,
+                         double* out, int ol, int orr) {
+  const size_t total = (size_t)ol * 4 * orr;
+  ctx->launches++;
+  k_assemble<<<grid_for(ctx, total), 256, 0, ctx->stream>>>(U, ul, ur, e, first, last, out, ol, orr);
+  return check_launch(ctx, "assemble");
+}
+
+// Dense MPO contraction step (tests): T (rows x w) with rows = (out, in)
+// pairs of the sites so far, times core (w, 2, 2, wr) -> (rows*4 x wr) with
+// the new (out, in) bits appended: new row index = ((o_prev*2+o) , (i_prev*2+i)).
+__global__ void k_mpo_dense_step(const double* __restrict__ T, int nrow_o, int w, const double* __restrict__ core,
+                                 int wr, double* __restrict__ out) {
+  // T layout: [o_prev][i_prev][w], o_prev, i_prev in [0, nrow_o)
+  const size_t no = (size_t)nrow_o * 2;
+  const size_t total = no * no * wr;
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < total; q += (size_t)gridDim.x * blockDim.x) {
+    const size_t oo = q / (no * wr), ii = (q / wr) % no;
+    const int r = (int)(q % wr);
+    const size_t op = oo >> 1, ip = ii >> 1;
+    const int o = (int)(oo & 1), i = (int)(ii & 1);
+    double acc = 0.0;
+    for (int a = 0; a < w; ++a)
+      acc += T[(op * nrow_o + ip) * w + a] * core[((size_t)a * 4 + o * 2 + i) * wr + r];
+    out[q] = acc;
+  }
+}
+
+int launch_mpo_dense_step(vp_ctx* ctx, const double* T, int rows, int cols, int w, const double* core, int wr,
+                          double* out) {
+  (void)cols;
+  const size_t no = (size_t)rows * 2;
+  ctx->launches++;
+  k_mpo_dense_step<<<grid_for(ctx, no * no * wr), 256, 0, ctx->stream>>>(T, rows, w, core, wr, out);
+  return check_launch(ctx, "mpo_dense");
+}
+
+}  // namespace vp

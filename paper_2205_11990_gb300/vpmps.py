@@ -1,0 +1,387 @@
+"""Python binding of libvpmps (ctypes; argument marshalling only).
+
+Every operation runs in the CUDA library; this module converts numpy arrays
+and torch tensors to pointers and sizes.  PyTorch supplies the CUDA stream
+and, by default, device memory (its caching allocator, through the
+allocator hooks of ``vp_ctx_create``).  There is no CPU fallback: without
+the built library or a CUDA device the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from .inputs import Layout
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libvpmps.so")
+
+VP_SEQ, VP_INTERLEAVED = 0, 1
+MPO_DX_CENTERED, MPO_DX_FORWARD, MPO_DX_BACKWARD, MPO_DV_ZERO_GRAD, MPO_DXX, MPO_ADVECTION = range(6)
+KCLASSES = ["qr_factor", "qr_formq", "gemm", "jacobi", "select", "apply", "other"]
+ERRORS = {1: "VP_EINVAL", 2: "VP_ENOMEM", 3: "VP_ECAPACITY", 4: "VP_ECUDA", 5: "VP_ETIMEOUT",
+          6: "VP_ENUMERIC", 7: "VP_ECFL", 8: "VP_EBUSY"}
+
+EXPORTS = [
+    "vp_ctx_create", "vp_ctx_destroy", "vp_last_error", "vp_kernel_launches", "vp_profile_enable",
+    "vp_profile_read",
+    "mps_create", "mps_create_cores", "mps_destroy", "mps_num_sites", "mps_bonds", "mps_get_cores",
+    "mps_to_dense", "mps_to_grid",
+    "mpo_create_vp", "mpo_create_vlasov", "mpo_create_cores", "mpo_destroy", "mpo_num_sites", "mpo_bonds",
+    "mpo_to_dense",
+    "mps_apply_mpo", "mps_axpby", "mps_compress", "vp_density", "vp_poisson",
+    "vp_sim_create", "vp_sim_destroy", "vp_step", "vp_sim_state", "vp_sim_flops", "vp_run",
+]
+
+
+class VpError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class CLayout(C.Structure):
+    _fields_ = [("nx", C.c_int), ("nv", C.c_int), ("mapping", C.c_int), ("xmin", C.c_double),
+                ("xmax", C.c_double), ("vmin", C.c_double), ("vmax", C.c_double)]
+
+
+class CConfig(C.Structure):
+    _fields_ = [("dt", C.c_double), ("chi", C.c_int), ("tol", C.c_double), ("e_tol", C.c_double)]
+
+
+class CRecord(C.Structure):
+    _fields_ = [("t", C.c_double), ("field_energy", C.c_double), ("mass", C.c_double), ("max_bond", C.c_int),
+                ("trunc_err", C.c_double)]
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p)
+
+_lib = None
+
+
+def load():
+    """Load the shared library (raises if it was not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libvpmps.so not built ({LIB_PATH}); run __graft_entry__.build()")
+    lib = C.CDLL(LIB_PATH)
+    P, I, D, S = C.c_void_p, C.c_int, C.c_double, C.c_size_t
+    DP, IP = C.POINTER(C.c_double), C.POINTER(C.c_int)
+    sig = {
+        "vp_ctx_create": (I, [P, ALLOC_FN, FREE_FN, P, C.POINTER(P)]),
+        "vp_ctx_destroy": (I, [P]),
+        "vp_last_error": (C.c_char_p, [P]),
+        "vp_kernel_launches": (C.c_int64, [P]),
+        "vp_profile_enable": (I, [P, I]),
+        "vp_profile_read": (I, [P, I, DP, C.POINTER(C.c_int64), DP]),
+        "mps_create": (I, [P, C.POINTER(CLayout), P, I, I, D, C.POINTER(P)]),
+        "mps_create_cores": (I, [P, I, IP, DP, C.POINTER(P)]),
+        "mps_destroy": (I, [P]),
+        "mps_num_sites": (I, [P]),
+        "mps_bonds": (I, [P, IP]),
+        "mps_get_cores": (I, [P, P, DP, S]),
+        "mps_to_dense": (I, [P, P, DP]),
+        "mps_to_grid": (I, [P, P, C.POINTER(CLayout), DP]),
+        "mpo_create_vp": (I, [P, C.POINTER(CLayout), I, C.POINTER(P)]),
+        "mpo_create_vlasov": (I, [P, C.POINTER(CLayout), DP, D, C.POINTER(P)]),
+        "mpo_create_cores": (I, [P, I, IP, DP, C.POINTER(P)]),
+        "mpo_destroy": (I, [P]),
+        "mpo_num_sites": (I, [P]),
+        "mpo_bonds": (I, [P, IP]),
+        "mpo_to_dense": (I, [P, P, DP]),
+        "mps_apply_mpo": (I, [P, P, P, P]),
+        "mps_axpby": (I, [P, D, P, D, P, P]),
+        "mps_compress": (I, [P, P, I, D, DP]),
+        "vp_density": (I, [P, C.POINTER(CLayout), P, P]),
+        "vp_poisson": (I, [P, P, I, D, P, DP]),
+        "vp_sim_create": (I, [P, C.POINTER(CLayout), C.POINTER(CConfig), P, C.POINTER(P)]),
+        "vp_sim_destroy": (I, [P]),
+        "vp_step": (I, [P, I, C.POINTER(CRecord)]),
+        "vp_sim_state": (P, [P]),
+        "vp_sim_flops": (D, [P]),
+        "vp_run": (I, [P, C.POINTER(CLayout), C.POINTER(CConfig), DP, I, DP, C.POINTER(CRecord)]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype, fn.argtypes = res, args
+    _lib = lib
+    return lib
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _ip(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(C.c_int))
+
+
+def clayout(lay: Layout) -> CLayout:
+    return CLayout(lay.nx, lay.nv, lay.mapping, lay.xmin, lay.xmax, lay.vmin, lay.vmax)
+
+
+class Context:
+    """A library context on torch's current CUDA stream and allocator."""
+
+    def __init__(self, use_torch_allocator: bool = True):
+        import torch
+        if not torch.cuda.is_available():
+            raise VpError(4, "no CUDA device")
+        self.lib = load()
+        self.torch = torch
+        self.device = torch.cuda.current_device()
+        self.stream = torch.cuda.current_stream()
+        if use_torch_allocator:
+            dev, stream = self.device, self.stream
+
+            def _alloc(nbytes, _user):
+                try:
+                    return torch.cuda.caching_allocator_alloc(int(nbytes), dev, stream)
+                except RuntimeError:
+                    return None
+
+            def _free(ptr, _nbytes, _user):
+                torch.cuda.caching_allocator_delete(ptr)
+
+            self._alloc, self._free = ALLOC_FN(_alloc), FREE_FN(_free)
+        else:
+            self._alloc, self._free = ALLOC_FN(), FREE_FN()
+        h = C.c_void_p()
+        self._check(self.lib.vp_ctx_create(C.c_void_p(self.stream.cuda_stream), self._alloc, self._free, None,
+                                           C.byref(h)), ctx=None)
+        self.h = h
+
+    def _check(self, code, ctx="self"):
+        if code != 0:
+            h = self.h if ctx == "self" else None
+            msg = self.lib.vp_last_error(h).decode() if h is not None else "context creation failed"
+            raise VpError(code, msg)
+
+    @property
+    def kernel_launches(self) -> int:
+        return int(self.lib.vp_kernel_launches(self.h))
+
+    def profile(self, on: bool = True):
+        self._check(self.lib.vp_profile_enable(self.h, int(on)))
+
+    def profile_read(self):
+        """{class: (ms, launches, work)} for the kernel classes timed since profile()."""
+        out = {}
+        for k, name in enumerate(KCLASSES):
+            ms, n, w = C.c_double(), C.c_int64(), C.c_double()
+            self._check(self.lib.vp_profile_read(self.h, k, C.byref(ms), C.byref(n), C.byref(w)))
+            out[name] = (ms.value, int(n.value), w.value)
+        return out
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.vp_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------- MPS
+    def mps_from_grid(self, lay: Layout, f, chi: int, tol: float) -> "MPS":
+        """a1: dense f[ix, iv] (numpy host array or CUDA torch tensor) -> MPS."""
+        h = C.c_void_p()
+        if isinstance(f, np.ndarray):
+            f = np.ascontiguousarray(f, dtype=np.float64)
+            assert f.size == lay.Nx * lay.Nv
+            self._check(self.lib.mps_create(self.h, C.byref(clayout(lay)), f.ctypes.data_as(C.c_void_p), 0, chi, tol,
+                                            C.byref(h)))
+        else:
+            assert f.is_cuda and f.dtype == self.torch.float64 and f.is_contiguous()
+            self._check(self.lib.mps_create(self.h, C.byref(clayout(lay)), C.c_void_p(f.data_ptr()), 1, chi, tol,
+                                            C.byref(h)))
+        return MPS(self, h)
+
+    def mps_from_cores(self, cores) -> "MPS":
+        ranks = np.array([1] + [c.shape[2] for c in cores], dtype=np.int32)
+        flat = np.ascontiguousarray(np.concatenate([np.asarray(c, dtype=np.float64).reshape(-1) for c in cores]))
+        h = C.c_void_p()
+        self._check(self.lib.mps_create_cores(self.h, len(cores), _ip(ranks), _dp(flat), C.byref(h)))
+        return MPS(self, h)
+
+    def mpo_vp(self, lay: Layout, kind: int) -> "MPO":
+        h = C.c_void_p()
+        self._check(self.lib.mpo_create_vp(self.h, C.byref(clayout(lay)), kind, C.byref(h)))
+        return MPO(self, h)
+
+    def mpo_vlasov(self, lay: Layout, E: np.ndarray, e_tol: float) -> "MPO":
+        E = np.ascontiguousarray(E, dtype=np.float64)
+        h = C.c_void_p()
+        self._check(self.lib.mpo_create_vlasov(self.h, C.byref(clayout(lay)), _dp(E), e_tol, C.byref(h)))
+        return MPO(self, h)
+
+    def mpo_from_cores(self, cores) -> "MPO":
+        bonds = np.array([1] + [c.shape[3] for c in cores], dtype=np.int32)
+        flat = np.ascontiguousarray(np.concatenate([np.asarray(c, dtype=np.float64).reshape(-1) for c in cores]))
+        h = C.c_void_p()
+        self._check(self.lib.mpo_create_cores(self.h, len(cores), _ip(bonds), _dp(flat), C.byref(h)))
+        return MPO(self, h)
+
+    def empty_mps(self) -> "MPS":
+        return self.mps_from_cores([np.zeros((1, 2, 1))])
+
+    # ------------------------------------------------------- operations
+    def apply_mpo(self, mpo: "MPO", x: "MPS", out: "MPS" = None) -> "MPS":
+        out = out or self.empty_mps()
+        self._check(self.lib.mps_apply_mpo(self.h, mpo.h, x.h, out.h))
+        return out
+
+    def axpby(self, a: float, x: "MPS", b: float, y: "MPS", out: "MPS" = None) -> "MPS":
+        out = out or self.empty_mps()
+        self._check(self.lib.mps_axpby(self.h, a, x.h, b, y.h, out.h))
+        return out
+
+    def compress(self, x: "MPS", chi: int, tol: float) -> np.ndarray:
+        errs = np.zeros(max(1, x.n - 1))
+        self._check(self.lib.mps_compress(self.h, x.h, chi, tol, _dp(errs)))
+        return errs[: x.n - 1]
+
+    def density(self, lay: Layout, f: "MPS"):
+        rho = self.torch.empty(lay.Nx, dtype=self.torch.float64, device="cuda")
+        self._check(self.lib.vp_density(self.h, C.byref(clayout(lay)), f.h, C.c_void_p(rho.data_ptr())))
+        return rho
+
+    def poisson(self, rho, nx: int, dx: float):
+        E = self.torch.empty(1 << nx, dtype=self.torch.float64, device="cuda")
+        we = C.c_double()
+        self._check(self.lib.vp_poisson(self.h, C.c_void_p(rho.data_ptr()), nx, dx, C.c_void_p(E.data_ptr()),
+                                        C.byref(we)))
+        return E, we.value
+
+    def sim(self, lay: Layout, f0: "MPS", dt: float, chi: int, tol: float = 1e-10, e_tol: float = 1e-10) -> "Sim":
+        h = C.c_void_p()
+        cfg = CConfig(dt, chi, tol, e_tol)
+        self._check(self.lib.vp_sim_create(self.h, C.byref(clayout(lay)), C.byref(cfg), f0.h, C.byref(h)))
+        return Sim(self, h, lay)
+
+    def run(self, lay: Layout, f0: np.ndarray, dt: float, nsteps: int, chi: int, tol: float = 1e-10,
+            e_tol: float = 1e-10, want_f: bool = True):
+        f0 = np.ascontiguousarray(f0, dtype=np.float64)
+        fT = np.zeros((lay.Nx, lay.Nv)) if want_f else None
+        recs = (CRecord * max(1, nsteps))()
+        cfg = CConfig(dt, chi, tol, e_tol)
+        self._check(self.lib.vp_run(self.h, C.byref(clayout(lay)), C.byref(cfg), _dp(f0), nsteps,
+                                    _dp(fT) if want_f else None, recs))
+        return fT, _records(recs, nsteps)
+
+
+def _records(recs, n):
+    return [dict(t=r.t, field_energy=r.field_energy, mass=r.mass, max_bond=r.max_bond, trunc_err=r.trunc_err)
+            for r in list(recs)[:n]]
+
+
+class MPS:
+    def __init__(self, ctx: Context, h, owned: bool = True):
+        self.ctx, self.h, self.owned = ctx, h, owned
+
+    @property
+    def n(self) -> int:
+        return int(self.ctx.lib.mps_num_sites(self.h))
+
+    def bonds(self):
+        out = np.zeros(self.n + 1, dtype=np.int32)
+        self.ctx._check(self.ctx.lib.mps_bonds(self.h, _ip(out)))
+        return [int(x) for x in out]
+
+    def cores(self):
+        r = self.bonds()
+        sizes = [r[k] * 2 * r[k + 1] for k in range(self.n)]
+        flat = np.zeros(sum(sizes))
+        self.ctx._check(self.ctx.lib.mps_get_cores(self.ctx.h, self.h, _dp(flat), flat.size))
+        out, off = [], 0
+        for k, s in enumerate(sizes):
+            out.append(flat[off:off + s].reshape(r[k], 2, r[k + 1]))
+            off += s
+        return out
+
+    def to_dense(self) -> np.ndarray:
+        out = np.zeros(1 << self.n)
+        self.ctx._check(self.ctx.lib.mps_to_dense(self.ctx.h, self.h, _dp(out)))
+        return out
+
+    def to_grid(self, lay: Layout) -> np.ndarray:
+        out = np.zeros((lay.Nx, lay.Nv))
+        self.ctx._check(self.ctx.lib.mps_to_grid(self.ctx.h, self.h, C.byref(clayout(lay)), _dp(out)))
+        return out
+
+    def close(self):
+        if self.owned and self.h:
+            self.ctx.lib.mps_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class MPO:
+    def __init__(self, ctx: Context, h):
+        self.ctx, self.h = ctx, h
+
+    @property
+    def n(self) -> int:
+        return int(self.ctx.lib.mpo_num_sites(self.h))
+
+    def bonds(self):
+        out = np.zeros(self.n + 1, dtype=np.int32)
+        self.ctx._check(self.ctx.lib.mpo_bonds(self.h, _ip(out)))
+        return [int(x) for x in out]
+
+    def to_dense(self) -> np.ndarray:
+        n = self.n
+        out = np.zeros((1 << n, 1 << n))
+        self.ctx._check(self.ctx.lib.mpo_to_dense(self.ctx.h, self.h, _dp(out)))
+        return out
+
+    def close(self):
+        if self.h:
+            self.ctx.lib.mpo_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Sim:
+    def __init__(self, ctx: Context, h, lay: Layout):
+        self.ctx, self.h, self.lay = ctx, h, lay
+
+    def step(self, nsteps: int = 1):
+        recs = (CRecord * max(1, nsteps))()
+        self.ctx._check(self.ctx.lib.vp_step(self.h, nsteps, recs))
+        return _records(recs, nsteps)
+
+    def state(self) -> MPS:
+        return MPS(self.ctx, C.c_void_p(self.ctx.lib.vp_sim_state(self.h)), owned=False)
+
+    @property
+    def flops(self) -> float:
+        return float(self.ctx.lib.vp_sim_flops(self.h))
+
+    def close(self):
+        if self.h:
+            self.ctx.lib.vp_sim_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
