@@ -37,6 +37,7 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline (profiling runs)")
     return p.parse_args()
 
 
@@ -202,7 +203,7 @@ def run_ours(args, rank, world):
                  "flops_per_step": sim.flops / max(1, args.steps + args.warmup)},
     }
     if rank == 0:
-        out["cpu_baseline"] = cpu_baseline(lay, f0, budget_s=25.0)
+        out["cpu_baseline"] = None if args.no_cpu else cpu_baseline(lay, f0, budget_s=25.0)
         print(json.dumps(out), flush=True)
 
 

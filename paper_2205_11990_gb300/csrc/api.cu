@@ -196,82 +196,110 @@ static int qr_site(vp_ctx* ctx, mps_t* s, int k) {
   return VP_OK;
 }
 
-// SVD step at site k >= 1 of a left-canonical MPS (right part already
-// right-canonical): M = core_k (r_k x 2 r_{k+1}); keep r singular triplets.
+// SVD step at site k >= 1 of a left-canonical MPS whose right part is
+// already right-canonical: M = core_k (r_k x 2 r_{k+1}); keep r singular
+// triplets (truncation rule of the truncation-error equation).
+//
+// The SVD is one-sided Jacobi on a preconditioned square factor.  With A = M
+// (tall) or M^T (wide), q = min(r_k, 2 r_{k+1}):  A Pi = Q1 R1 (columns
+// ordered by decreasing norm, Householder QR), R1^T = Q2 L^T (second QR),
+// then Jacobi on the rows of the lower-triangular L (graded, so it converges
+// in far fewer sweeps than on M itself).  L = U_L S V_L^T gives
+//   tall: M = Q1 U_L S (Pi Q2 V_L)^T  ->  core_{k-1} <- P Q1 U_L S,
+//         core_k <- (V_L^T Q2^T) with columns scattered back by Pi;
+//   wide: M = Pi Q2 V_L S (Q1 U_L)^T ->  core_k <- U_L^T Q1^T,
+//         core_{k-1} <- P Pi (Q2 V_L S).
 static int svd_site(vp_ctx* ctx, mps_t* s, int k, int chi, double tol, double* err_out) {
-  int m = s->r[k];
+  const int m = s->r[k];
   const int c = 2 * s->r[k + 1];
   const int pl = 2 * s->r[k - 1];  // rows of the previous core viewed as (2 r_{k-1} x r_k)
-  double* X;
-  int b;
-  if (m > c) {
-    // tall: M = Q R, previous core <- previous * Q, work on R (c x c)
-    VP_TRY(reserve(ctx, ctx->w_fac, (size_t)m * c));
-    VP_TRY(reserve(ctx, ctx->w_p, (size_t)2 * m + c + 8));
-    double* tau = ctx->w_p.p;
-    double* vbuf = ctx->w_p.p + c + 8;
-    VP_TRY(launch_to_colmajor(ctx, s->core[k].p, m, c, ctx->w_fac.p));
-    prof_begin(ctx, VP_K_QR);
-    VP_TRY(launch_qr_factor(ctx, ctx->w_fac.p, m, c, tau, vbuf));
-    prof_end(ctx, VP_K_QR, qr_flops(m, c));
-    VP_TRY(reserve(ctx, ctx->w_tmp2, (size_t)m * c));
-    prof_begin(ctx, VP_K_FORMQ);
-    VP_TRY(launch_qr_formq(ctx, ctx->w_fac.p, m, c, tau, ctx->w_tmp2.p));
-    prof_end(ctx, VP_K_FORMQ, 4.0 * m * c * c - 4.0 / 3.0 * c * c * c);
-    VP_TRY(reserve(ctx, ctx->w_gemm, (size_t)pl * c));
-    prof_begin(ctx, VP_K_GEMM);
-    VP_TRY(launch_gemm(ctx, pl, c, m, 1.0, s->core[k - 1].p, m, ctx->w_tmp2.p, c, ctx->w_gemm.p, c));
-    prof_end(ctx, VP_K_GEMM, 2.0 * pl * c * m);
-    std::swap(s->core[k - 1], ctx->w_gemm);
-    VP_TRY(reserve(ctx, ctx->w_tmp, (size_t)c * c));
-    VP_TRY(launch_qr_getr(ctx, ctx->w_fac.p, m, c, ctx->w_tmp.p));
-    if (g_flops) {
-      g_flops->qr += qr_flops(m, c);
-      g_flops->formq += 4.0 * m * c * c - 4.0 / 3.0 * c * c * c;
-      g_flops->gemm += 2.0 * pl * c * m;
-    }
-    m = c;
-    s->r[k] = c;
-    X = ctx->w_tmp.p;
-    b = c;
-  } else {
-    VP_TRY(reserve(ctx, ctx->w_tmp, (size_t)m * c));
-    VP_TRY(launch_copy(ctx, s->core[k].p, ctx->w_tmp.p, (size_t)m * c));
-    X = ctx->w_tmp.p;
-    b = m;
-  }
-  VP_TRY(reserve(ctx, ctx->w_j, (size_t)b * b));
+  const bool tall = m >= c;
+  const int q = tall ? c : m;  // square factor size
+  const int p = tall ? m : c;  // long side of A
+  VP_TRY(reserve(ctx, ctx->w_piv, (size_t)q / 2 + 8));
+  int* piv = (int*)ctx->w_piv.p;
+  VP_TRY(launch_norm_order(ctx, s->core[k].p, m, c, tall ? 1 : 0, piv));
+  // first QR: A Pi = Q1 R1
+  VP_TRY(reserve(ctx, ctx->w_fac, (size_t)p * q));
+  VP_TRY(reserve(ctx, ctx->w_p, (size_t)2 * p + q + 8));
+  VP_TRY(launch_gather_cm(ctx, s->core[k].p, m, c, piv, tall ? 1 : 0, ctx->w_fac.p));
+  prof_begin(ctx, VP_K_QR);
+  VP_TRY(launch_qr_factor(ctx, ctx->w_fac.p, p, q, ctx->w_p.p, ctx->w_p.p + q + 8));
+  prof_end(ctx, VP_K_QR, qr_flops(p, q));
+  VP_TRY(reserve(ctx, ctx->w_q1, (size_t)p * q));
+  prof_begin(ctx, VP_K_FORMQ);
+  VP_TRY(launch_qr_formq(ctx, ctx->w_fac.p, p, q, ctx->w_p.p, ctx->w_q1.p));
+  prof_end(ctx, VP_K_FORMQ, 4.0 * p * q * q - 4.0 / 3.0 * q * q * q);
+  // second QR: R1^T = Q2 L^T (R1 row-major is R1^T column-major)
+  VP_TRY(reserve(ctx, ctx->w_r, (size_t)q * q));
+  VP_TRY(launch_qr_getr(ctx, ctx->w_fac.p, p, q, ctx->w_r.p));
+  VP_TRY(reserve(ctx, ctx->w_p2, (size_t)3 * q + 8));
+  prof_begin(ctx, VP_K_QR);
+  VP_TRY(launch_qr_factor(ctx, ctx->w_r.p, q, q, ctx->w_p2.p, ctx->w_p2.p + q + 8));
+  prof_end(ctx, VP_K_QR, qr_flops(q, q));
+  VP_TRY(reserve(ctx, ctx->w_q2, (size_t)q * q));
+  prof_begin(ctx, VP_K_FORMQ);
+  VP_TRY(launch_qr_formq(ctx, ctx->w_r.p, q, q, ctx->w_p2.p, ctx->w_q2.p));
+  prof_end(ctx, VP_K_FORMQ, 8.0 / 3.0 * q * q * q);
+  VP_TRY(reserve(ctx, ctx->w_tmp, (size_t)q * q));
+  double* X = ctx->w_tmp.p;
+  VP_TRY(launch_lower_from_upper(ctx, ctx->w_r.p, q, X));
+  // Jacobi on the rows of L
+  VP_TRY(reserve(ctx, ctx->w_j, (size_t)q * q));
   VP_CUDA(ctx, cudaMemsetAsync(ctx->status->rot, 0, sizeof(ctx->status->rot), ctx->stream));
   prof_begin(ctx, VP_K_JACOBI);
-  VP_TRY(launch_jacobi_rows(ctx, X, b, c, ctx->w_j.p));
+  VP_TRY(launch_jacobi_rows(ctx, X, q, q, ctx->w_j.p));
   prof_end(ctx, VP_K_JACOBI, 0.0);
-  VP_TRY(reserve(ctx, ctx->w_vec, (size_t)2 * b + 8));
-  int* perm = (int*)ctx->w_vec.p;               // b ints fit in b/2 doubles
-  double* sigma = ctx->w_vec.p + (b + 1) / 2 + 4;
+  VP_TRY(reserve(ctx, ctx->w_vec, (size_t)2 * q + 8));
+  int* perm = (int*)ctx->w_vec.p;
+  double* sigma = ctx->w_vec.p + (q + 1) / 2 + 4;
   prof_begin(ctx, VP_K_SELECT);
-  VP_TRY(launch_select(ctx, X, b, c, chi, tol, perm, sigma, ctx->d_small, ctx->d_smalld));
+  VP_TRY(launch_select(ctx, X, q, q, chi, tol, perm, sigma, ctx->d_small, ctx->d_smalld));
   prof_end(ctx, VP_K_SELECT, 0.0);
   int r = 1;
   double err = 0.0;
   VP_TRY(read_rank(ctx, &r, &err));
   if (err_out) *err_out = err;
-  if (ctx->prof_on && b > 1)
-    ctx->prof_work[VP_K_JACOBI] += (double)ctx->h_small[61] * 0.5 * b * (b - 1) * (6.0 * c + 4.0 * b);
-  if (g_flops) {
-    const double sweeps = b > 1 ? ctx->h_small[61] : 0;
-    g_flops->jacobi += sweeps * 0.5 * b * (b - 1) * (6.0 * c + 4.0 * b);
-    g_flops->gemm += 2.0 * pl * b * r;
-  }
-  // core_k <- V^T (r x c); W (b x r) = U S; previous <- previous * W
-  VP_TRY(reserve(ctx, s->core[k], (size_t)r * c));
-  VP_TRY(reserve(ctx, ctx->w_tmp2, (size_t)b * r));
-  VP_TRY(launch_svd_outputs(ctx, X, ctx->w_j.p, b, c, r, perm, sigma, s->core[k].p, ctx->w_tmp2.p));
-  VP_TRY(reserve(ctx, ctx->w_gemm, (size_t)pl * r));
+  const double jac = q > 1 ? (double)ctx->h_small[61] * 0.5 * q * (q - 1) * (6.0 * q + 4.0 * q) : 0.0;
+  if (ctx->prof_on) ctx->prof_work[VP_K_JACOBI] += jac;
+  double gem = 0.0;
+  VP_TRY(reserve(ctx, ctx->w_a, (size_t)r * q + 8));
+  VP_TRY(reserve(ctx, ctx->w_b, (size_t)q * r + 8));
   prof_begin(ctx, VP_K_GEMM);
-  VP_TRY(launch_gemm(ctx, pl, r, b, 1.0, s->core[k - 1].p, b, ctx->w_tmp2.p, r, ctx->w_gemm.p, r));
-  prof_end(ctx, VP_K_GEMM, 2.0 * pl * b * r);
+  if (tall) {
+    // P1 = P Q1 (pl x q); core_{k-1} <- P1 (U_L S); core_k <- scatter(V_L^T Q2^T)
+    VP_TRY(launch_svd_outputs(ctx, X, ctx->w_j.p, q, q, r, perm, sigma, ctx->w_a.p, ctx->w_b.p));
+    VP_TRY(reserve(ctx, ctx->w_tmp2, (size_t)pl * q));
+    VP_TRY(launch_gemm(ctx, pl, q, m, 1.0, s->core[k - 1].p, m, ctx->w_q1.p, q, ctx->w_tmp2.p, q));
+    VP_TRY(reserve(ctx, ctx->w_gemm, (size_t)pl * r));
+    VP_TRY(launch_gemm(ctx, pl, r, q, 1.0, ctx->w_tmp2.p, q, ctx->w_b.p, r, ctx->w_gemm.p, r));
+    VP_TRY(reserve(ctx, ctx->w_c, (size_t)r * q));
+    VP_TRY(launch_gemm_bt(ctx, r, q, q, ctx->w_a.p, q, ctx->w_q2.p, q, ctx->w_c.p, q));
+    VP_TRY(reserve(ctx, s->core[k], (size_t)r * c));
+    VP_TRY(launch_scatter(ctx, ctx->w_c.p, r, q, piv, 1, s->core[k].p));
+    gem = 2.0 * pl * q * m + 2.0 * pl * r * q + 2.0 * r * q * q;
+  } else {
+    // core_k <- U_L^T Q1^T (r x c); core_{k-1} <- P Pi (Q2 V_L S)
+    VP_TRY(launch_svd_outputs_wide(ctx, X, ctx->w_j.p, q, r, perm, ctx->w_a.p, ctx->w_b.p));
+    VP_TRY(reserve(ctx, s->core[k], (size_t)r * c));
+    VP_TRY(launch_gemm_bt(ctx, r, c, m, ctx->w_a.p, m, ctx->w_q1.p, m, s->core[k].p, c));
+    VP_TRY(reserve(ctx, ctx->w_c, (size_t)m * r));
+    VP_TRY(launch_gemm(ctx, m, r, m, 1.0, ctx->w_q2.p, m, ctx->w_b.p, r, ctx->w_c.p, r));
+    VP_TRY(reserve(ctx, ctx->w_tmp2, (size_t)m * r));
+    VP_TRY(launch_scatter(ctx, ctx->w_c.p, m, r, piv, 0, ctx->w_tmp2.p));
+    VP_TRY(reserve(ctx, ctx->w_gemm, (size_t)pl * r));
+    VP_TRY(launch_gemm(ctx, pl, r, m, 1.0, s->core[k - 1].p, m, ctx->w_tmp2.p, r, ctx->w_gemm.p, r));
+    gem = 2.0 * r * c * m + 2.0 * m * r * m + 2.0 * pl * r * m;
+  }
+  prof_end(ctx, VP_K_GEMM, gem);
   std::swap(s->core[k - 1], ctx->w_gemm);
   s->r[k] = r;
+  if (g_flops) {
+    g_flops->qr += qr_flops(p, q) + qr_flops(q, q);
+    g_flops->formq += 4.0 * p * q * q - 4.0 / 3.0 * q * q * q + 8.0 / 3.0 * q * q * q;
+    g_flops->jacobi += jac;
+    g_flops->gemm += gem;
+  }
   return VP_OK;
 }
 
@@ -453,6 +481,7 @@ int vp_ctx_create(void* cuda_stream, vp_alloc_fn alloc, vp_free_fn free_fn, void
     return VP_ECUDA;
   }
   c->num_sms = prop.multiProcessorCount;
+  c->cluster_size = vp::probe_cluster_size();
   int coop = 0;
   cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
   if (!coop) {
@@ -479,7 +508,8 @@ int vp_ctx_create(void* cuda_stream, vp_alloc_fn alloc, vp_free_fn free_fn, void
 int vp_ctx_destroy(vp_ctx* c) {
   if (!c) return VP_EINVAL;
   cudaStreamSynchronize(c->stream);
-  for (DevBuf* b : {&c->w_fac, &c->w_q, &c->w_gemm, &c->w_j, &c->w_p, &c->w_tmp, &c->w_tmp2, &c->w_vec})
+  for (DevBuf* b : {&c->w_fac, &c->w_q, &c->w_gemm, &c->w_j, &c->w_p, &c->w_tmp, &c->w_tmp2, &c->w_vec, &c->w_split,
+                    &c->w_piv, &c->w_q1, &c->w_q2, &c->w_r, &c->w_p2, &c->w_a, &c->w_b, &c->w_c})
     release(c, *b);
   for (auto& b : c->w_chain) release(c, b);
   dev_free(c, c->status, sizeof(DevStatus));

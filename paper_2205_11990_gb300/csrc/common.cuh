@@ -19,12 +19,12 @@ constexpr long long kSpinLimit = 1ll << 24;  // iterations before a device wait 
 // Device-side status words.  err: 0 = ok, 1 = a grid barrier gave up
 // (timeout), 2 = NaN/Inf met, 3 = Jacobi did not converge.
 struct DevStatus {
-  unsigned int count;   // grid-barrier arrival counter
-  unsigned int gen;     // grid-barrier generation
+  unsigned long long bar_count;  // grid-barrier arrivals (monotonic)
+  unsigned long long bar_base;   // bar_count when the next cooperative kernel starts
   int err;
   int pad;
   unsigned int rot[3];  // Jacobi rotation counters, one per sweep modulo 3
-  int pad2;
+  int pad2;             // sweeps taken by the last Jacobi launch
 };
 
 // Grow-only device buffer owned by a context.
@@ -38,6 +38,7 @@ struct DevBuf {
 struct vp_ctx {
   int device = 0;
   int num_sms = 0;
+  int cluster_size = 0;  // CTAs per cluster for the cluster-resident kernels (16, or 8)
   cudaStream_t stream = nullptr;
   vp_alloc_fn alloc = nullptr;
   vp_free_fn freef = nullptr;
@@ -57,7 +58,8 @@ struct vp_ctx {
   double prof_work[VP_K_COUNT] = {};
   int64_t prof_launches[VP_K_COUNT] = {};
   // workspaces
-  vp::DevBuf w_fac, w_q, w_gemm, w_j, w_p, w_tmp, w_tmp2, w_vec;
+  vp::DevBuf w_fac, w_q, w_gemm, w_j, w_p, w_tmp, w_tmp2, w_vec, w_split;
+  vp::DevBuf w_piv, w_q1, w_q2, w_r, w_p2, w_a, w_b, w_c;  // preconditioned SVD
   std::vector<vp::DevBuf> w_chain;
 };
 
@@ -118,12 +120,25 @@ int launch_qr_getr(vp_ctx* ctx, const double* A, int m, int n, double* R);
 // C (M x N) = alpha * A (M x K) * B (K x N), all row-major with given leading dims.
 int launch_gemm(vp_ctx* ctx, int M, int N, int K, double alpha, const double* A, int lda,
                 const double* B, int ldb, double* C, int ldc);
+// C (M x N) = A (M x K) * Bt^T, Bt given row-major (N x K).
+int launch_gemm_bt(vp_ctx* ctx, int M, int N, int K, const double* A, int lda, const double* Bt, int ldbt,
+                   double* C, int ldc);
+// SVD preconditioning helpers (static pivoting by norm, see linalg.cu).
+int launch_norm_order(vp_ctx* ctx, const double* M, int m, int c, int by_cols, int* piv);
+int launch_gather_cm(vp_ctx* ctx, const double* M, int m, int c, const int* piv, int tall, double* out);
+int launch_lower_from_upper(vp_ctx* ctx, const double* Rcm, int q, double* L);
+int launch_scatter(vp_ctx* ctx, const double* Y, int rows, int cols_n, const int* piv, int cols, double* out);
+int launch_svd_outputs_wide(vp_ctx* ctx, const double* X, const double* J, int b, int r, const int* perm,
+                            double* Urows, double* Wv);
 // C = alpha * triu(A_colmajor) (M x K) * B: the R factor read in place.
 int launch_gemm_r(vp_ctx* ctx, int M, int N, int K, const double* Acm, int lda, const double* B,
                   int ldb, double* C, int ldc);
 // One-sided Jacobi on the b rows (length c) of X, rotations also applied to
 // the rows of J (b x b, set to the identity here).  Row-major, contiguous.
 int launch_jacobi_rows(vp_ctx* ctx, double* X, int b, int c, double* J);
+// Largest cluster (16 or 8 CTAs, one per SM) the cluster-resident kernels
+// can use on this device; 0 if none.
+int probe_cluster_size();
 // Sort row norms of X descending, choose the kept rank (chi, tol, ties),
 // write perm/sigma/rank/truncation error into ctx scratch.  d_out[0] = rank.
 int launch_select(vp_ctx* ctx, const double* X, int b, int c, int chi, double tol, int* perm,

@@ -9,7 +9,12 @@
 #include <algorithm>
 #include <cmath>
 
+#include <cooperative_groups.h>
+#include <cuda/atomic>
+
 #include "common.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace vp {
 
@@ -38,24 +43,28 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 
 __device__ __forceinline__ int ld_volatile(const int* p) { return *(const volatile int*)p; }
 
-// Grid-wide barrier for cooperative launches.  Every wait has a clock limit
-// (~1 s): on expiry the block records err = 1 and the barrier reports
-// failure, so the kernel returns instead of hanging.
-__device__ __forceinline__ bool grid_barrier(DevStatus* st, unsigned nblocks) {
-  __syncthreads();
-  if (nblocks > 1) {
-    if (threadIdx.x == 0) {
-      volatile unsigned* vgen = &st->gen;
-      const unsigned g = *vgen;
-      __threadfence();
-      const unsigned arrived = atomicAdd(&st->count, 1u);
-      if (arrived == nblocks - 1) {
-        atomicExch(&st->count, 0u);
-        __threadfence();
-        atomicAdd(&st->gen, 1u);
-      } else {
+// Grid-wide barrier for cooperative launches: one monotonic 64-bit arrival
+// counter, a release add per block and acquire polling (no reset, no
+// generation word).  Every block starts from the counter value the previous
+// cooperative kernel left in bar_base.  Waits have a clock limit (~1 s): on
+// expiry the block records err = 1 and the barrier reports failure, so the
+// kernel returns instead of hanging.
+struct GridSync {
+  DevStatus* st;
+  unsigned nb;
+  unsigned long long target;
+  __device__ GridSync(DevStatus* s, unsigned n) : st(s), nb(n), target(0) {
+    if (nb > 1) target = *(volatile unsigned long long*)&st->bar_base;
+  }
+  __device__ bool sync() {
+    __syncthreads();
+    if (nb > 1) {
+      target += nb;
+      if (threadIdx.x == 0) {
+        cuda::atomic_ref<unsigned long long, cuda::thread_scope_device> cnt(st->bar_count);
+        cnt.fetch_add(1ull, cuda::memory_order_release);
         const long long t0 = clock64();
-        while (*vgen == g) {
+        while (cnt.load(cuda::memory_order_acquire) < target) {
           if (ld_volatile(&st->err) != 0) break;
           if (clock64() - t0 > 2000000000ll) {
             atomicExch(&st->err, 1);
@@ -63,12 +72,15 @@ __device__ __forceinline__ bool grid_barrier(DevStatus* st, unsigned nblocks) {
           }
         }
       }
-      __threadfence();
+      __syncthreads();
     }
-    __syncthreads();
+    return ld_volatile(&st->err) == 0;
   }
-  return ld_volatile(&st->err) == 0;
-}
+  // Called by every block after its last sync(); block 0 publishes the base.
+  __device__ void finish() {
+    if (nb > 1 && blockIdx.x == 0 && threadIdx.x == 0) st->bar_base = target;
+  }
+};
 
 static int coop_launch(vp_ctx* ctx, const void* fn, int blocks, int threads, void** args, size_t smem,
                        const char* what) {
@@ -112,6 +124,7 @@ __global__ void __launch_bounds__(kThreads) k_qr_factor(double* A, int m, int n,
   const int nb = gridDim.x, bid = blockIdx.x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int p = min(m, n);
+  GridSync gs(st, nb);
   for (int j = 0; j < p; ++j) {
     __syncthreads();
     double* vj = vbuf + (size_t)(j & 1) * m;
@@ -143,7 +156,7 @@ __global__ void __launch_bounds__(kThreads) k_qr_factor(double* A, int m, int n,
       }
       __threadfence();
     }
-    if (!grid_barrier(st, nb)) return;
+    if (!gs.sync()) return;
     const double t = __ldcg(tau + j);
     if (t == 0.0) continue;
     // first owned column strictly right of j
@@ -156,6 +169,7 @@ __global__ void __launch_bounds__(kThreads) k_qr_factor(double* A, int m, int n,
       for (int i = j + lane; i < m; i += 32) col[i] = fma(-w, __ldcg(vj + i), col[i]);
     }
   }
+  gs.finish();
 }
 
 int launch_qr_factor(vp_ctx* ctx, double* A, int m, int n, double* tau, double* vbuf) {
@@ -235,25 +249,40 @@ struct AUpperColMajor {
   __device__ double operator()(int r, int k) const { return r <= k ? A[(size_t)k * lda + r] : 0.0; }
 };
 
-template <class ALoad>
-__global__ void __launch_bounds__(256) k_gemm(int M, int N, int K, double alpha, ALoad a,
-                                              const double* __restrict__ B, int ldb, double* __restrict__ C,
-                                              int ldc) {
+// blockIdx.z selects a K slice of `kslice` columns (split-K); slice s writes
+// its partial product to C + s * slice_stride.
+// B operand: row-major (K x N), or given as its transpose (N x K row-major).
+struct BRowMajor {
+  const double* B;
+  int ldb;
+  __device__ double operator()(int k, int n) const { return B[(size_t)k * ldb + n]; }
+};
+struct BTransposed {
+  const double* B;
+  int ldb;
+  __device__ double operator()(int k, int n) const { return B[(size_t)n * ldb + k]; }
+};
+
+template <class ALoad, class BLoad>
+__global__ void __launch_bounds__(256) k_gemm(int M, int N, int K, double alpha, ALoad a, BLoad bl,
+                                              double* __restrict__ C, int ldc, int kslice, size_t slice_stride) {
   __shared__ double As[16][64 + 1];
   __shared__ double Bs[16][64];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const int row0 = blockIdx.x * 64, col0 = blockIdx.y * 64;
+  const int kbeg = blockIdx.z * kslice, kend = min(K, kbeg + kslice);
+  C += blockIdx.z * slice_stride;
   double acc[4][4] = {};
-  for (int k0 = 0; k0 < K; k0 += 16) {
+  for (int k0 = kbeg; k0 < kend; k0 += 16) {
     for (int e = threadIdx.x; e < 64 * 16; e += 256) {
       const int r = e / 16, kk = e % 16;
       const int gr = row0 + r, gk = k0 + kk;
-      As[kk][r] = (gr < M && gk < K) ? a(gr, gk) : 0.0;
+      As[kk][r] = (gr < M && gk < kend) ? a(gr, gk) : 0.0;
     }
     for (int e = threadIdx.x; e < 16 * 64; e += 256) {
       const int kk = e / 64, c = e % 64;
       const int gk = k0 + kk, gc = col0 + c;
-      Bs[kk][c] = (gk < K && gc < N) ? B[(size_t)gk * ldb + gc] : 0.0;
+      Bs[kk][c] = (gk < kend && gc < N) ? bl(gk, gc) : 0.0;
     }
     __syncthreads();
 #pragma unroll
@@ -282,25 +311,58 @@ __global__ void __launch_bounds__(256) k_gemm(int M, int N, int K, double alpha,
   }
 }
 
+// Sum of `slices` partial products (fixed order: deterministic).
+__global__ void k_sum_slices(const double* __restrict__ P, int M, int N, int slices, size_t stride, double* C,
+                             int ldc) {
+  const size_t total = (size_t)M * N;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int s = 0; s < slices; ++s) acc += P[s * stride + e];
+    C[(e / N) * ldc + e % N] = acc;
+  }
+}
+
+// Split K when the output has too few 64 x 64 tiles to occupy the SMs.
+template <class ALoad, class BLoad>
+static int gemm_dispatch(vp_ctx* ctx, int M, int N, int K, double alpha, ALoad a, BLoad b, double* C, int ldc,
+                         const char* what) {
+  if (M <= 0 || N <= 0) return VP_OK;
+  dim3 grid((M + 63) / 64, (N + 63) / 64, 1);
+  if (grid.y > 65535) return fail(ctx, VP_ECAPACITY, "gemm: N too large");
+  const int tiles = (int)(grid.x * grid.y);
+  int slices = 1;
+  if (tiles < ctx->num_sms && K >= 128) slices = std::min(std::min(2 * ctx->num_sms / tiles, K / 64), 32);
+  if (slices <= 1) {
+    ctx->launches++;
+    k_gemm<ALoad, BLoad><<<grid, 256, 0, ctx->stream>>>(M, N, K, alpha, a, b, C, ldc, K, 0);
+    return check_launch(ctx, what);
+  }
+  const int kslice = ((K + slices - 1) / slices + 15) / 16 * 16;
+  slices = (K + kslice - 1) / kslice;
+  const size_t stride = (size_t)M * N;
+  VP_TRY(reserve(ctx, ctx->w_split, stride * slices));
+  grid.z = slices;
+  ctx->launches += 2;
+  k_gemm<ALoad, BLoad><<<grid, 256, 0, ctx->stream>>>(M, N, K, alpha, a, b, ctx->w_split.p, N, kslice, stride);
+  VP_TRY(check_launch(ctx, what));
+  const int blocks = (int)std::min<size_t>((stride + 255) / 256, (size_t)ctx->num_sms * 8);
+  k_sum_slices<<<blocks, 256, 0, ctx->stream>>>(ctx->w_split.p, M, N, slices, stride, C, ldc);
+  return check_launch(ctx, what);
+}
+
 int launch_gemm(vp_ctx* ctx, int M, int N, int K, double alpha, const double* A, int lda, const double* B,
                 int ldb, double* C, int ldc) {
-  if (M <= 0 || N <= 0) return VP_OK;
-  dim3 grid((M + 63) / 64, (N + 63) / 64);
-  if (grid.y > 65535) return fail(ctx, VP_ECAPACITY, "gemm: N too large");
-  ctx->launches++;
-  k_gemm<ARowMajor><<<grid, 256, 0, ctx->stream>>>(M, N, K, alpha, ARowMajor{A, lda}, B, ldb, C, ldc);
-  return check_launch(ctx, "gemm");
+  return gemm_dispatch(ctx, M, N, K, alpha, ARowMajor{A, lda}, BRowMajor{B, ldb}, C, ldc, "gemm");
+}
+
+int launch_gemm_bt(vp_ctx* ctx, int M, int N, int K, const double* A, int lda, const double* Bt, int ldbt, double* C,
+                   int ldc) {
+  return gemm_dispatch(ctx, M, N, K, 1.0, ARowMajor{A, lda}, BTransposed{Bt, ldbt}, C, ldc, "gemm_bt");
 }
 
 int launch_gemm_r(vp_ctx* ctx, int M, int N, int K, const double* Acm, int lda, const double* B, int ldb,
                   double* C, int ldc) {
-  if (M <= 0 || N <= 0) return VP_OK;
-  dim3 grid((M + 63) / 64, (N + 63) / 64);
-  if (grid.y > 65535) return fail(ctx, VP_ECAPACITY, "gemm: N too large");
-  ctx->launches++;
-  k_gemm<AUpperColMajor><<<grid, 256, 0, ctx->stream>>>(M, N, K, 1.0, AUpperColMajor{Acm, lda}, B, ldb, C,
-                                                        ldc);
-  return check_launch(ctx, "gemm_r");
+  return gemm_dispatch(ctx, M, N, K, 1.0, AUpperColMajor{Acm, lda}, BRowMajor{B, ldb}, C, ldc, "gemm_r");
 }
 
 // ------------------------------------------------------------ Jacobi SVD
@@ -321,6 +383,7 @@ __global__ void __launch_bounds__(kThreads) k_jacobi_rows(double* X, int b, int 
   const int bp = b + (b & 1), npairs = bp / 2, rounds = bp - 1;
   int sweep = 0;
   bool converged = false;
+  GridSync gs(st, nb);
   for (; sweep < max_sweeps; ++sweep) {
     unsigned* cnt = &st->rot[sweep % 3];
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicExch(&st->rot[(sweep + 1) % 3], 0u);
@@ -364,17 +427,101 @@ __global__ void __launch_bounds__(kThreads) k_jacobi_rows(double* X, int b, int 
         }
         if (lane == 0) atomicAdd(cnt, 1u);
       }
-      if (!grid_barrier(st, nb)) return;
+      if (!gs.sync()) return;
     }
     if (__ldcg(cnt) == 0u) {
       converged = true;
       break;
     }
   }
+  gs.finish();
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     st->pad2 = sweep + 1;
     if (!converged) atomicCAS(&st->err, 0, 3);
   }
+}
+
+// Cluster-resident variant: the b rows of X (length c) and of the rotation
+// accumulator J (length b) live in the distributed shared memory of one
+// thread-block cluster (row x in CTA x % CS, slot x / CS, X and J parts
+// contiguous), one CTA per SM.  A pair is processed by one warp through
+// DSMEM pointers; rounds are separated by the hardware cluster barrier
+// (about 0.2 us on GB300, against 2 us for a grid-wide software barrier).
+__global__ void __launch_bounds__(kThreads) k_jacobi_cluster(double* X, int b, int c, double* J, double eps,
+                                                             int max_sweeps, DevStatus* st) {
+  cg::cluster_group cl = cg::this_cluster();
+  extern __shared__ double sm[];
+  const int CS = (int)cl.num_blocks(), rank = (int)cl.block_rank();
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int rpc = (b + CS - 1) / CS, stride = c + b;
+  unsigned* cnt = reinterpret_cast<unsigned*>(sm + (size_t)rpc * stride);
+  for (int sl = 0; sl < rpc; ++sl) {
+    const int x = sl * CS + rank;
+    if (x >= b) break;
+    double* row = sm + (size_t)sl * stride;
+    for (int q = tid; q < c; q += kThreads) row[q] = X[(size_t)x * c + q];
+    for (int q = tid; q < b; q += kThreads) row[c + q] = (q == x) ? 1.0 : 0.0;
+  }
+  if (tid < 4) cnt[tid] = 0u;
+  cl.sync();
+  unsigned* c0 = cl.map_shared_rank(cnt, 0);
+  const int bp = b + (b & 1), npairs = bp / 2, rounds = bp - 1;
+  int sweep = 0;
+  bool converged = false;
+  for (; sweep < max_sweeps; ++sweep) {
+    if (rank == 0 && tid == 0) cnt[(sweep + 1) % 3] = 0u;
+    for (int round = 0; round < rounds; ++round) {
+      for (int pr = rank + warp * CS; pr < npairs; pr += CS * kWarps) {
+        int i = rr_index(pr, round, bp), j = rr_index(bp - 1 - pr, round, bp);
+        if (i >= b || j >= b) continue;
+        if (i > j) {
+          const int t = i;
+          i = j;
+          j = t;
+        }
+        double* xi = cl.map_shared_rank(sm + (size_t)(i / CS) * stride, i % CS);
+        double* xj = cl.map_shared_rank(sm + (size_t)(j / CS) * stride, j % CS);
+        double al = 0.0, be = 0.0, ga = 0.0;
+        for (int q = lane; q < c; q += 32) {
+          const double u = xi[q], v = xj[q];
+          al = fma(u, u, al);
+          be = fma(v, v, be);
+          ga = fma(u, v, ga);
+        }
+        al = warp_sum(al);
+        be = warp_sum(be);
+        ga = warp_sum(ga);
+        if (!(al > 0.0 && be > 0.0)) continue;
+        if (!(fabs(ga) > eps * sqrt(al) * sqrt(be))) continue;
+        const double zeta = (be - al) / (2.0 * ga);
+        const double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(fma(zeta, zeta, 1.0)));
+        const double cs = 1.0 / sqrt(fma(t, t, 1.0)), sn = cs * t;
+        for (int q = lane; q < stride; q += 32) {
+          const double u = xi[q], v = xj[q];
+          xi[q] = cs * u - sn * v;
+          xj[q] = sn * u + cs * v;
+        }
+        if (lane == 0) atomicAdd(&c0[sweep % 3], 1u);
+      }
+      cl.sync();
+    }
+    if (*(volatile unsigned*)&c0[sweep % 3] == 0u) {
+      converged = true;
+      break;
+    }
+  }
+  for (int sl = 0; sl < rpc; ++sl) {
+    const int x = sl * CS + rank;
+    if (x >= b) break;
+    const double* row = sm + (size_t)sl * stride;
+    for (int q = tid; q < c; q += kThreads) X[(size_t)x * c + q] = row[q];
+    for (int q = tid; q < b; q += kThreads) J[(size_t)x * b + q] = row[c + q];
+  }
+  if (rank == 0 && tid == 0) {
+    st->pad2 = sweep + 1;
+    if (!converged) atomicCAS(&st->err, 0, 3);
+  }
+  cl.sync();  // keep every CTA's shared memory alive until all remote accesses are done
 }
 
 __global__ void k_identity(double* J, int b) {
@@ -383,8 +530,64 @@ __global__ void k_identity(double* J, int b) {
     J[e] = (e / b == e % b) ? 1.0 : 0.0;
 }
 
+int probe_cluster_size() {
+  if (cudaFuncSetAttribute(k_jacobi_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) != cudaSuccess)
+    return 0;
+  cudaFuncSetAttribute(k_jacobi_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  for (int cs : {16, 8}) {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    cfg.gridDim = dim3(cs);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = 120 * 1024;
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = cs;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, k_jacobi_cluster, &cfg) == cudaSuccess && n >= 1) return cs;
+    cudaGetLastError();
+  }
+  return 0;
+}
+
+static size_t cluster_jacobi_smem(int b, int c, int CS) {
+  const size_t rpc = (size_t)(b + CS - 1) / CS;
+  return rpc * (size_t)(c + b) * sizeof(double) + 4 * sizeof(unsigned);
+}
+
 int launch_jacobi_rows(vp_ctx* ctx, double* X, int b, int c, double* J) {
   if (b <= 0) return VP_OK;
+  const int CS = ctx->cluster_size;
+  if (CS > 0 && b > 1 && cluster_jacobi_smem(b, c, CS) <= 200 * 1024) {
+    static bool attr_done = false;
+    // at least 120 KB per CTA, so no two CTAs of the cluster share an SM
+    const size_t smem = std::max<size_t>(cluster_jacobi_smem(b, c, CS), 120 * 1024);
+    if (!attr_done) {
+      VP_CUDA(ctx, cudaFuncSetAttribute(k_jacobi_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+      VP_CUDA(ctx, cudaFuncSetAttribute(k_jacobi_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+      attr_done = true;
+    }
+    double eps = 1e-15 * std::sqrt((double)c);
+    int max_sweeps = 60;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    cfg.gridDim = dim3(CS);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = ctx->stream;
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = CS;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    ctx->launches++;
+    VP_CUDA(ctx, cudaLaunchKernelEx(&cfg, k_jacobi_cluster, X, b, c, J, eps, max_sweeps, ctx->status));
+    return VP_OK;
+  }
   ctx->launches++;
   k_identity<<<std::min(1024, (b * b + 255) / 256 + 1), 256, 0, ctx->stream>>>(J, b);
   VP_TRY(check_launch(ctx, "identity"));
@@ -498,6 +701,133 @@ int launch_svd_outputs(vp_ctx* ctx, const double* X, const double* J, int b, int
   ctx->launches++;
   k_svd_outputs<<<std::max(1, blocks), 256, 0, ctx->stream>>>(X, J, b, c, r, perm, sigma, Vt, W);
   return check_launch(ctx, "svd_outputs");
+}
+
+// ------------------------------------------------------ SVD preconditioning
+// Static pivoting for the Jacobi SVD: order the columns (tall) or rows (wide)
+// of M by decreasing norm, so that the triangular factor of the reordered
+// matrix is graded and one-sided Jacobi on it converges in fewer sweeps.
+__global__ void k_norm_order(const double* __restrict__ M, int m, int c, int by_cols, int* __restrict__ piv) {
+  extern __shared__ double nrm[];
+  const int q = by_cols ? c : m, len = by_cols ? m : c;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int j = warp; j < q; j += nw) {
+    double a = 0.0;
+    for (int i = lane; i < len; i += 32) {
+      const double u = by_cols ? M[(size_t)i * c + j] : M[(size_t)j * c + i];
+      a = fma(u, u, a);
+    }
+    a = warp_sum(a);
+    if (lane == 0) nrm[j] = a;
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < q; j += blockDim.x) {
+    const double v = nrm[j];
+    int pos = 0;
+    for (int k = 0; k < q; ++k) pos += (nrm[k] > v) || (nrm[k] == v && k < j);
+    piv[pos] = j;
+  }
+}
+
+int launch_norm_order(vp_ctx* ctx, const double* M, int m, int c, int by_cols, int* piv) {
+  const int q = by_cols ? c : m;
+  const size_t smem = (size_t)q * sizeof(double);
+  if (smem > 200 * 1024) return fail(ctx, VP_ECAPACITY, "norm_order: too many columns");
+  if (smem > 48 * 1024)
+    VP_CUDA(ctx, cudaFuncSetAttribute(k_norm_order, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  ctx->launches++;
+  k_norm_order<<<1, 512, smem, ctx->stream>>>(M, m, c, by_cols, piv);
+  return check_launch(ctx, "norm_order");
+}
+
+// Column-major copy of the reordered matrix: tall, A = M[:, piv] (m x c);
+// wide, A = (M[piv, :])^T (c x m).
+__global__ void k_gather_cm(const double* __restrict__ M, int m, int c, const int* __restrict__ piv, int tall,
+                            double* __restrict__ out) {
+  const size_t total = (size_t)m * c;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    if (tall) {
+      const size_t j = e / m, i = e % m;  // out[j*m + i] = M[i][piv[j]]
+      out[e] = M[i * c + piv[j]];
+    } else {
+      const size_t j = e / c, i = e % c;  // out[j*c + i] = M[piv[j]][i]
+      out[e] = M[(size_t)piv[j] * c + i];
+    }
+  }
+}
+
+int launch_gather_cm(vp_ctx* ctx, const double* M, int m, int c, const int* piv, int tall, double* out) {
+  const size_t total = (size_t)m * c;
+  const int blocks = (int)std::max<size_t>(1, std::min<size_t>((total + 255) / 256, (size_t)ctx->num_sms * 16));
+  ctx->launches++;
+  k_gather_cm<<<blocks, 256, 0, ctx->stream>>>(M, m, c, piv, tall, out);
+  return check_launch(ctx, "gather_cm");
+}
+
+// L = R^T, row-major, from a factored column-major q x q matrix whose upper
+// triangle holds R (the reflectors below are dropped).
+__global__ void k_lower_from_upper(const double* __restrict__ Rcm, int q, double* __restrict__ L) {
+  const size_t total = (size_t)q * q;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const size_t i = e / q, j = e % q;
+    L[e] = (j <= i) ? Rcm[e] : 0.0;
+  }
+}
+
+int launch_lower_from_upper(vp_ctx* ctx, const double* Rcm, int q, double* L) {
+  const size_t total = (size_t)q * q;
+  const int blocks = (int)std::max<size_t>(1, std::min<size_t>((total + 255) / 256, (size_t)ctx->num_sms * 8));
+  ctx->launches++;
+  k_lower_from_upper<<<blocks, 256, 0, ctx->stream>>>(Rcm, q, L);
+  return check_launch(ctx, "lower_from_upper");
+}
+
+// Undo the static pivoting: cols = 1: out[t][piv[j]] = Y[t][j] (rows x q);
+// cols = 0: out[piv[j]][t] = Y[j][t] (q x rows_len).
+__global__ void k_scatter(const double* __restrict__ Y, int rows, int cols_n, const int* __restrict__ piv, int cols,
+                          double* __restrict__ out) {
+  const size_t total = (size_t)rows * cols_n;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const size_t a = e / cols_n, b = e % cols_n;
+    if (cols)
+      out[a * cols_n + piv[b]] = Y[e];
+    else
+      out[(size_t)piv[a] * cols_n + b] = Y[e];
+  }
+}
+
+int launch_scatter(vp_ctx* ctx, const double* Y, int rows, int cols_n, const int* piv, int cols, double* out) {
+  const size_t total = (size_t)rows * cols_n;
+  const int blocks = (int)std::max<size_t>(1, std::min<size_t>((total + 255) / 256, (size_t)ctx->num_sms * 8));
+  ctx->launches++;
+  k_scatter<<<blocks, 256, 0, ctx->stream>>>(Y, rows, cols_n, piv, cols, out);
+  return check_launch(ctx, "scatter");
+}
+
+// Wide-case outputs: Urows (r x b) = J[perm[t]] (rows of the accumulated
+// rotation), Wv (b x r) = X[perm[t]][i] (= V diag(s) of the factor).
+__global__ void k_svd_outputs_wide(const double* __restrict__ X, const double* __restrict__ J, int b, int r,
+                                   const int* __restrict__ perm, double* Urows, double* Wv) {
+  const size_t nu = (size_t)r * b;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < 2 * nu; e += (size_t)gridDim.x * blockDim.x) {
+    if (e < nu) {
+      const int t = (int)(e / b), q = (int)(e % b);
+      Urows[e] = J[(size_t)perm[t] * b + q];
+    } else {
+      const size_t f = e - nu;
+      const int i = (int)(f / r), t = (int)(f % r);
+      Wv[f] = X[(size_t)perm[t] * b + i];
+    }
+  }
+}
+
+int launch_svd_outputs_wide(vp_ctx* ctx, const double* X, const double* J, int b, int r, const int* perm,
+                            double* Urows, double* Wv) {
+  const size_t total = 2 * (size_t)r * b;
+  const int blocks = (int)std::max<size_t>(1, std::min<size_t>((total + 255) / 256, (size_t)ctx->num_sms * 8));
+  ctx->launches++;
+  k_svd_outputs_wide<<<blocks, 256, 0, ctx->stream>>>(X, J, b, r, perm, Urows, Wv);
+  return check_launch(ctx, "svd_outputs_wide");
 }
 
 }  // namespace vp

@@ -8,8 +8,10 @@ the built library or a CUDA device the calls raise.
 """
 from __future__ import annotations
 
+import atexit
 import ctypes as C
 import os
+import weakref
 
 import numpy as np
 
@@ -60,6 +62,17 @@ ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p)
 
 _lib = None
+_live_contexts = weakref.WeakSet()
+
+
+@atexit.register
+def _close_all():
+    # close while torch (whose allocator frees the memory) is still alive
+    for ctx in list(_live_contexts):
+        try:
+            ctx.close()
+        except Exception:
+            pass
 
 
 def load():
@@ -151,10 +164,12 @@ class Context:
             self._alloc, self._free = ALLOC_FN(_alloc), FREE_FN(_free)
         else:
             self._alloc, self._free = ALLOC_FN(), FREE_FN()
+        self._children = weakref.WeakSet()
         h = C.c_void_p()
         self._check(self.lib.vp_ctx_create(C.c_void_p(self.stream.cuda_stream), self._alloc, self._free, None,
                                            C.byref(h)), ctx=None)
         self.h = h
+        _live_contexts.add(self)
 
     def _check(self, code, ctx="self"):
         if code != 0:
@@ -179,7 +194,10 @@ class Context:
         return out
 
     def close(self):
+        """Destroy every live MPS/MPO/Sim of this context, then the context."""
         if getattr(self, "h", None):
+            for child in list(self._children):
+                child.close()
             self.lib.vp_ctx_destroy(self.h)
             self.h = None
 
@@ -285,6 +303,7 @@ def _records(recs, n):
 class MPS:
     def __init__(self, ctx: Context, h, owned: bool = True):
         self.ctx, self.h, self.owned = ctx, h, owned
+        ctx._children.add(self)
 
     @property
     def n(self) -> int:
@@ -317,7 +336,7 @@ class MPS:
         return out
 
     def close(self):
-        if self.owned and self.h:
+        if self.owned and self.h and self.ctx.h:
             self.ctx.lib.mps_destroy(self.h)
         self.h = None
 
@@ -331,6 +350,7 @@ class MPS:
 class MPO:
     def __init__(self, ctx: Context, h):
         self.ctx, self.h = ctx, h
+        ctx._children.add(self)
 
     @property
     def n(self) -> int:
@@ -348,7 +368,7 @@ class MPO:
         return out
 
     def close(self):
-        if self.h:
+        if self.h and self.ctx.h:
             self.ctx.lib.mpo_destroy(self.h)
         self.h = None
 
@@ -362,6 +382,7 @@ class MPO:
 class Sim:
     def __init__(self, ctx: Context, h, lay: Layout):
         self.ctx, self.h, self.lay = ctx, h, lay
+        ctx._children.add(self)
 
     def step(self, nsteps: int = 1):
         recs = (CRecord * max(1, nsteps))()
@@ -376,7 +397,7 @@ class Sim:
         return float(self.ctx.lib.vp_sim_flops(self.h))
 
     def close(self):
-        if self.h:
+        if self.h and self.ctx.h:
             self.ctx.lib.vp_sim_destroy(self.h)
         self.h = None
 

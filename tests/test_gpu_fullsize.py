@@ -1,0 +1,63 @@
+"""Parity at the benchmark's full size (1024 x 1024, chi = 64), GPU vs oracle.
+
+The benchmark times RK4-C1 steps of the saturated two-stream state on a
+1024 x 1024 grid (10 + 10 sites, sequential mapping).  Here one step of the
+same workload, launched the same way (vp_sim), is compared with one oracle
+step from the same initial condition: the dense f (2^20 values) to 1e-10
+relative L2 and the field energy to 1e-9.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import vp as OV
+from paper_2205_11990_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import __graft_entry__ as g
+    g.build()
+    from paper_2205_11990_gb300 import vpmps
+    c = vpmps.Context()
+    yield c
+    c.close()
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.mark.parametrize("name", ["saturated_two_stream_1024x1024_seq", "two_stream_1024x1024_seq"])
+def test_full_size_step(ctx, name):
+    w = I.WORKLOADS[name]
+    lay = w["layout"]
+    f0 = I.initial_condition(w["ic"], lay)
+    chi, dt = w["chi"], w["dt"]
+    m = ctx.mps_from_grid(lay, f0, chi, 1e-10)
+    ref = OV.mps_from_f(f0, lay, chi, 1e-10)
+    assert m.bonds() == [int(x) for x in [1] + [c.shape[2] for c in ref]]
+    assert rel(m.to_grid(lay), OV.mps_to_f(ref, lay)) < 1e-10
+    sim = ctx.sim(lay, m, dt, chi)
+    rec = sim.step(1)[0]
+    ref, d = OV.rk4_step(ref, lay, dt, chi)
+    assert abs(rec["field_energy"] - d["field_energy"]) <= 1e-9 * d["field_energy"]
+    assert sim.state().bonds() == d["bonds"]
+    assert rel(sim.state().to_grid(lay), OV.mps_to_f(ref, lay)) < 1e-10
+
+
+def test_interleaved_mid_size_steps(ctx):
+    lay = I.Layout(7, 7, 0.0, 10 * math.pi, -8.0, 8.0, I.INTERLEAVED)
+    f0 = I.saturated_two_stream(lay, modes=8)
+    dt = OV.stable_dt(lay, 0.01)
+    m = ctx.mps_from_grid(lay, f0, 32, 1e-10)
+    sim = ctx.sim(lay, m, dt, 32)
+    ref = OV.mps_from_f(f0, lay, 32, 1e-10)
+    for _ in range(2):
+        rec = sim.step(1)[0]
+        ref, d = OV.rk4_step(ref, lay, dt, 32)
+        assert abs(rec["field_energy"] - d["field_energy"]) <= 1e-9 * d["field_energy"]
+    assert rel(sim.state().to_grid(lay), OV.mps_to_f(ref, lay)) < 1e-10
