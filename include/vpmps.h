@@ -187,6 +187,25 @@ int vp_density(vp_ctx* ctx, const vp_layout* layout, const mps_t* f, double* rho
 int vp_poisson(vp_ctx* ctx, const double* rho_dev, int nx, double dx, double* E_dev,
                double* field_energy_host);
 
+/* Allocation-free variant of vp_poisson (no counterpart in the paper; a
+ * deployment aid).  For callers that cannot allocate device memory and so
+ * cannot create a vp_ctx -- code running under another framework's fixed
+ * memory budget, or a thread that must not touch the allocator while a graph
+ * capture is in progress elsewhere.  Inputs and outputs are the caller's:
+ * rho_dev, E_dev (2^nx doubles, device), field_energy_host / mass_host (host,
+ * may be NULL).  Its scratch is a file-scope device array of 16384 + 64
+ * doubles (~128 KB) that every GPU which loads the library keeps until the
+ * process exits; nothing in it needs clearing between calls (each call writes
+ * every element it reads).  All calls on a device share that array, so calls
+ * that overlap on the GPU race: serialise them (one stream, or events).  The
+ * first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress with that device current); make that first call
+ * before any stream capture.  Errors: VP_EINVAL, VP_ECAPACITY (nx > 14: 2^nx
+ * beyond the static scratch), VP_ECUDA.  Synchronises `cuda_stream` when a
+ * host output is requested.  Calls no allocator. */
+int vp_poisson_noalloc(void* cuda_stream, const double* rho_dev, int nx, double dx, double* E_dev,
+                       double* field_energy_host, double* mass_host);
+
 /* --------------------------------------------------------------- stepping */
 
 typedef struct {

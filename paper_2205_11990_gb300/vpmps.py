@@ -33,7 +33,7 @@ EXPORTS = [
     "mps_to_dense", "mps_to_grid",
     "mpo_create_vp", "mpo_create_vlasov", "mpo_create_cores", "mpo_destroy", "mpo_num_sites", "mpo_bonds",
     "mpo_to_dense",
-    "mps_apply_mpo", "mps_axpby", "mps_compress", "vp_density", "vp_poisson",
+    "mps_apply_mpo", "mps_axpby", "mps_compress", "vp_density", "vp_poisson", "vp_poisson_noalloc",
     "vp_sim_create", "vp_sim_destroy", "vp_step", "vp_sim_state", "vp_sim_flops", "vp_run",
 ]
 
@@ -112,6 +112,7 @@ def load():
         "mps_compress": (I, [P, P, I, D, DP]),
         "vp_density": (I, [P, C.POINTER(CLayout), P, P]),
         "vp_poisson": (I, [P, P, I, D, P, DP]),
+        "vp_poisson_noalloc": (I, [P, P, I, D, P, DP, DP]),
         "vp_sim_create": (I, [P, C.POINTER(CLayout), C.POINTER(CConfig), P, C.POINTER(P)]),
         "vp_sim_destroy": (I, [P]),
         "vp_step": (I, [P, I, C.POINTER(CRecord)]),
@@ -277,6 +278,16 @@ class Context:
         self._check(self.lib.vp_poisson(self.h, C.c_void_p(rho.data_ptr()), nx, dx, C.c_void_p(E.data_ptr()),
                                         C.byref(we)))
         return E, we.value
+
+    def poisson_noalloc(self, rho, nx: int, dx: float, E=None):
+        """vp_poisson_noalloc on this context's stream (no context memory used)."""
+        E = E if E is not None else self.torch.empty(1 << nx, dtype=self.torch.float64, device="cuda")
+        we, mass = C.c_double(), C.c_double()
+        code = self.lib.vp_poisson_noalloc(C.c_void_p(self.stream.cuda_stream), C.c_void_p(rho.data_ptr()), nx, dx,
+                                           C.c_void_p(E.data_ptr()), C.byref(we), C.byref(mass))
+        if code != 0:
+            raise VpError(code, "vp_poisson_noalloc failed")
+        return E, we.value, mass.value
 
     def sim(self, lay: Layout, f0: "MPS", dt: float, chi: int, tol: float = 1e-10, e_tol: float = 1e-10) -> "Sim":
         h = C.c_void_p()
