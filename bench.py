@@ -38,7 +38,24 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline (profiling runs)")
-    return p.parse_args()
+    p.add_argument("--mode", default="step", choices=["step", "batch", "serve"],
+                   help="step: the headline single-run steps/s; batch / serve: many runs on one GPU")
+    p.add_argument("--instances", type=int, default=32)
+    p.add_argument("--concurrency", type=int, default=8)
+    p.add_argument("--rate", type=float, default=20.0, help="serve: mean Poisson arrival rate (req/s)")
+    p.add_argument("--window", type=float, default=20.0, help="serve: arrival window (s)")
+    p.add_argument("--workload", default=WORKLOAD,
+                   help="named workload of paper_2205_11990_gb300.inputs.WORKLOADS (profiling of smaller cases)")
+    args = p.parse_args()
+    set_workload(args.workload)
+    return args
+
+
+def set_workload(name):
+    global WORKLOAD, CHI, DT
+    from paper_2205_11990_gb300 import inputs as I
+    w = I.WORKLOADS[name]
+    WORKLOAD, CHI, DT = name, w["chi"], w["dt"]
 
 
 def dist_init(n):
@@ -49,6 +66,11 @@ def dist_init(n):
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
         dist.init_process_group("nccl")
     return rank, world
+
+
+def metric_name(lay):
+    mp = "seq" if lay.mapping == 0 else "interleaved"
+    return f"MPS VP steps/s at n={lay.n} chi={CHI} (RK4-C1, {lay.Nx}x{lay.Nv} two-stream, {mp})"
 
 
 def workload():
@@ -187,11 +209,12 @@ def run_ours(args, rank, world):
                "h2d_bytes_per_step": nbytes / args.steps,
                "d2h_bytes_per_step": (nbytes + 40 * args.steps) / args.steps}
     out = {
-        "metric": "MPS VP steps/s at n=20 chi=64 (RK4-C1, 1024x1024 two-stream, seq)",
+        "metric": metric_name(lay),
         "value": steps_per_s, "unit": "steps/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "grid": "1024x1024", "sites": "10+10", "mapping": "seq", "chi": CHI,
+        "config": {"workload": WORKLOAD, "grid": f"{lay.Nx}x{lay.Nv}", "sites": f"{lay.nx}+{lay.nv}",
+                   "mapping": "seq" if lay.mapping == 0 else "interleaved", "chi": CHI,
                    "tol": TOL, "dt": DT, "parallelism": f"replicas x{world}",
                    "l2": "flushed between timed steps (256 MB write)"},
         "roofline": roof,
@@ -238,20 +261,127 @@ def run_reference(args, rank, world):
     done, t = oracle_steps(lay, f0, args.steps, 150.0)
     v = done / t
     print(json.dumps({
-        "impl": "reference", "metric": "MPS VP steps/s at n=20 chi=64 (RK4-C1, 1024x1024 two-stream, seq)",
+        "impl": "reference", "metric": metric_name(lay),
         "value": v, "unit": "steps/s", "n_gpus": world, "steps": done, "warmup": min(args.warmup, 1),
         "ms_per_step": 1e3 * t / done, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "grid": "1024x1024", "sites": "10+10", "mapping": "seq", "chi": CHI,
-                   "tol": TOL, "dt": DT, "parallelism": "cpu"},
+        "config": {"workload": WORKLOAD, "grid": f"{lay.Nx}x{lay.Nv}", "sites": f"{lay.nx}+{lay.nv}",
+                   "mapping": "seq" if lay.mapping == 0 else "interleaved", "chi": CHI, "tol": TOL, "dt": DT,
+                   "parallelism": "cpu"},
         "cpu_baseline": {"value": v, "unit": "steps/s", "cores": os.cpu_count(), "kind": "oracle",
                          "sample": f"{done} of {args.steps} requested steps (capped at 150 s of CPU work)"},
         "e2e": {"value": v, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 
 
+def mixed_request(rng):
+    """One seeded request of the batching/serving mix: Landau or bump-on-tail,
+    sequential or interleaved, grid bits per dimension 6..9, chi in {16, 32, 64}."""
+    import math
+    from paper_2205_11990_gb300 import inputs as I
+    nb = int(rng.integers(6, 10))
+    mapping = I.SEQ if rng.random() < 0.5 else I.INTERLEAVED
+    if rng.random() < 0.5:
+        k = float(rng.uniform(0.3, 0.6))
+        amp = float(math.exp(rng.uniform(math.log(1e-3), math.log(0.5))))
+        lay = I.Layout(nb, nb, 0.0, 2 * math.pi / k, -6.0, 6.0, mapping)
+        f0 = I.landau(lay, amp, k)
+    else:
+        k = float(rng.uniform(0.3, 0.6))
+        lay = I.Layout(nb, nb, 0.0, 2 * math.pi / k, -8.0, 8.0, mapping)
+        f0 = I.bump_on_tail(lay, 1e-3, k)
+    dx = (lay.xmax - lay.xmin) / lay.Nx
+    dt = 0.6 * dx / lay.vmax
+    chi = int(rng.choice([16, 32, 64]))
+    return lay, f0, dt, chi
+
+
+def run_batch(args):
+    import numpy as np
+    import __graft_entry__ as g
+    g.build()
+    from paper_2205_11990_gb300 import vpmps
+    ctx = vpmps.Context()
+    rng = np.random.Generator(np.random.PCG64(0))
+    reqs = [mixed_request(rng) for _ in range(args.instances)]
+    steps = max(1, args.steps)
+    out = {}
+    for label, conc in (("batched", args.concurrency), ("sequential", 1)):
+        b = vpmps.Batch(ctx, conc, 200 << 30)
+        for lay, f0, dt, chi in reqs:
+            b.submit(lay, f0, dt, steps, chi)
+        t0 = time.perf_counter()
+        b.start()
+        b.wait()
+        t = time.perf_counter() - t0
+        res = b.poll(4 * len(reqs))
+        assert all(r["status"] == 0 for r in res), res
+        out[label] = {"sims_per_s": len(reqs) / t, "wall_s": t,
+                      "step_ms_p50": float(np.median([r["step_ms_p50"] for r in res])),
+                      "step_ms_p99": float(np.max([r["step_ms_p99"] for r in res]))}
+        b.close()
+    print(json.dumps({
+        "metric": "batched sims/s (RK4-C1 runs, mixed sizes/chi/mappings)", "value": out["batched"]["sims_per_s"],
+        "unit": "sims/s", "n_gpus": 1, "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "mixed Landau/bump-on-tail, grid bits 6..9 per dim, chi 16/32/64, seq/interleaved",
+                   "instances": args.instances, "steps_per_run": steps, "concurrency": args.concurrency,
+                   "seed": 0},
+        "batched": out["batched"], "sequential_fp64_per_instance": out["sequential"],
+        "speedup_vs_sequential": out["batched"]["sims_per_s"] / out["sequential"]["sims_per_s"],
+        "gpu_launches": ctx.kernel_launches}), flush=True)
+
+
+def run_serve(args):
+    import numpy as np
+    import __graft_entry__ as g
+    g.build()
+    from paper_2205_11990_gb300 import vpmps
+    ctx = vpmps.Context()
+    rng = np.random.Generator(np.random.PCG64(1))
+    arrivals, t = [], 0.0
+    while True:
+        t += float(rng.exponential(1.0 / args.rate))
+        if t > args.window:
+            break
+        lay, f0, dt, chi = mixed_request(rng)
+        arrivals.append((t, lay, f0, dt, chi, int(rng.integers(max(2, args.steps // 4), args.steps + 1))))
+    b = vpmps.Batch(ctx, args.concurrency, 200 << 30)
+    b.start()
+    t0 = time.perf_counter()
+    done, i = [], 0
+    while len(done) < len(arrivals):
+        now = time.perf_counter() - t0
+        while i < len(arrivals) and arrivals[i][0] <= now:
+            _, lay, f0, dt, chi, n = arrivals[i]
+            b.submit(lay, f0, dt, n, chi)
+            i += 1
+        done += b.poll(256)
+        time.sleep(0.002)
+    wall = time.perf_counter() - t0
+    steps_ms = []
+    for r in done:
+        recs, ms, _ = b.records(r["id"])
+        steps_ms += list(ms)
+    run_lat = [r["queue_ms"] + r["run_ms"] for r in done]
+    b.close()
+    print(json.dumps({
+        "metric": "served sims/s with p50/p99 step and run latency (continuous batching)",
+        "value": len(done) / wall, "unit": "sims/s", "n_gpus": 1, "higher_is_better": True, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"arrivals": "Poisson", "rate_per_s": args.rate, "window_s": args.window, "requests": len(done),
+                   "steps_per_run": f"U[{max(2, args.steps // 4)}, {args.steps}]", "concurrency": args.concurrency,
+                   "seed": 1},
+        "step_ms_p50": float(np.percentile(steps_ms, 50)), "step_ms_p99": float(np.percentile(steps_ms, 99)),
+        "run_ms_p50": float(np.percentile(run_lat, 50)), "run_ms_p99": float(np.percentile(run_lat, 99)),
+        "wall_s": wall, "gpu_launches": ctx.kernel_launches}), flush=True)
+
+
 def main():
     args = parse()
+    if args.mode == "batch":
+        return run_batch(args)
+    if args.mode == "serve":
+        return run_serve(args)
     rank, world = dist_init(args.gpus)
     if args.impl == "reference":
         run_reference(args, rank, world)

@@ -213,6 +213,8 @@ typedef struct {
   int chi;          /* bond cap of f_{n+1} */
   double tol;       /* truncation tolerance of every compression (1e-10) */
   double e_tol;     /* tolerance of the E-field MPS (1e-10) */
+  int streams;      /* 1: one stream; 0 or 2: the two independent compressions of
+                       each RK stage run concurrently on a second stream */
 } vp_config;
 
 typedef struct {
@@ -238,6 +240,48 @@ double vp_sim_flops(const vp_sim* sim);
  * records[nsteps] (host, may be NULL). */
 int vp_run(vp_ctx* ctx, const vp_layout* layout, const vp_config* cfg, const double* f0_host,
            int nsteps, double* fT_host, vp_record* records);
+
+/* ------------------------------------------------- batching and serving */
+
+/* Many independent runs on one GPU (no counterpart in the paper: the
+ * serving/batching layer around its time stepper).  A pool of
+ * `max_concurrent` worker threads, each with its own context and CUDA stream;
+ * a request is admitted first-in first-out when a worker is free and its
+ * footprint fits `mem_budget_bytes`; requests submitted while others run
+ * join as slots free up, and the runs' kernels overlap on the device.  Each
+ * run's result is independent of what else runs (own buffers and stream). */
+typedef struct vp_batch vp_batch;
+
+typedef struct {
+  uint64_t id;
+  int status;           /* VP_OK or the run's error code */
+  int nsteps;
+  double queue_ms;      /* submit -> start */
+  double run_ms;        /* start -> finish (MPS creation, steps, readback) */
+  double step_ms_p50;   /* per-step latency percentiles of this run (host wall time) */
+  double step_ms_p99;
+  double field_energy;  /* W_E at the start of the last step */
+  int max_bond;
+} vp_result;
+
+/* Device bytes a run needs (states, pre-compression sums, factorisation
+ * workspaces), used for admission. */
+size_t vp_footprint_bytes(const vp_layout* layout, const vp_config* cfg);
+int vp_batch_create(vp_ctx* ctx, int max_concurrent, size_t mem_budget_bytes, vp_batch** out);
+/* Copies f0 (host, dense 2^(nx+nv)); keep_f != 0 keeps f(T) for
+ * vp_batch_records.  Errors: VP_ECAPACITY (footprint above the budget). */
+int vp_batch_submit(vp_batch* b, const vp_layout* layout, const vp_config* cfg, const double* f0_host,
+                    int nsteps, int keep_f, uint64_t* id_out);
+/* Start the workers (non-blocking); submission stays open. */
+int vp_batch_start(vp_batch* b);
+/* Block until every submitted run has finished. */
+int vp_batch_wait(vp_batch* b);
+/* Non-blocking: up to `max` runs finished since the last poll. */
+int vp_batch_poll(vp_batch* b, vp_result* out, int max, int* n_out);
+/* Per-step records[nsteps], per-step wall times step_ms[nsteps] (host, may be
+ * NULL) and f(T) on the grid (host, needs keep_f) of a finished run. */
+int vp_batch_records(vp_batch* b, uint64_t id, vp_record* records, double* step_ms, double* fT_host);
+int vp_batch_destroy(vp_batch* b);
 
 #ifdef __cplusplus
 }

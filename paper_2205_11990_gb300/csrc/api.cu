@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <thread>
 #include <string>
 #include <vector>
 
@@ -457,6 +458,25 @@ static bool layout_ok(const vp_layout* L) {
 
 }  // namespace vp
 
+extern "C" int vp_ctx_create(void* cuda_stream, vp_alloc_fn alloc, vp_free_fn free_fn, void* user, vp_ctx** out);
+
+namespace vp {
+// A context on its own non-blocking stream with the library's stream-ordered
+// allocator, for work that runs concurrently with the parent's stream.
+static vp_ctx* ctx_child(vp_ctx* parent) {
+  cudaStream_t st = nullptr;
+  if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return nullptr;
+  vp_ctx* c = nullptr;
+  if (vp_ctx_create(st, nullptr, nullptr, nullptr, &c) != VP_OK) {
+    cudaStreamDestroy(st);
+    return nullptr;
+  }
+  c->owns_stream = true;
+  parent->children.push_back(c);
+  return c;
+}
+}  // namespace vp
+
 // ====================================================================== ABI
 using namespace vp;
 
@@ -519,6 +539,7 @@ int vp_ctx_destroy(vp_ctx* c) {
   cudaFreeHost(c->h_small);
   cudaFreeHost(c->h_smalld);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+  if (c->owns_stream) cudaStreamDestroy(c->stream);
   delete c;
   return VP_OK;
 }
@@ -527,6 +548,7 @@ const char* vp_last_error(const vp_ctx* c) { return c ? c->err.c_str() : "null c
 
 int vp_profile_enable(vp_ctx* c, int on) {
   if (!c) return VP_EINVAL;
+  for (vp_ctx* ch : c->children) vp_profile_enable(ch, on);
   cudaStreamSynchronize(c->stream);
   c->prof_on = on != 0;
   c->ev_used = 0;
@@ -548,13 +570,28 @@ int vp_profile_read(vp_ctx* c, int cls, double* ms, int64_t* launches, double* w
     VP_CUDA(c, cudaEventElapsedTime(&x, c->ev_pool[m.second], c->ev_pool[m.second + 1]));
     t += x;
   }
+  double wk = c->prof_work[cls];
+  int64_t nl = c->prof_launches[cls];
+  for (vp_ctx* ch : c->children) {
+    double t2 = 0.0, w2 = 0.0;
+    int64_t n2 = 0;
+    VP_TRY(vp_profile_read(ch, cls, &t2, &n2, &w2));
+    t += t2;
+    wk += w2;
+    nl += n2;
+  }
   if (ms) *ms = t;
-  if (launches) *launches = c->prof_launches[cls];
-  if (work) *work = c->prof_work[cls];
+  if (launches) *launches = nl;
+  if (work) *work = wk;
   return VP_OK;
 }
 
-int64_t vp_kernel_launches(const vp_ctx* c) { return c ? c->launches : 0; }
+int64_t vp_kernel_launches(const vp_ctx* c) {
+  if (!c) return 0;
+  int64_t n = c->launches;
+  for (const vp_ctx* ch : c->children) n += ch->launches;
+  return n;
+}
 
 // ------------------------------------------------------------------- MPS
 int mps_create(vp_ctx* ctx, const vp_layout* L, const double* f, int f_on_device, int chi, double tol,
@@ -873,6 +910,8 @@ struct vp_sim {
   DevBuf rho, E, evec;
   double t = 0.0;
   Flops flops;
+  vp_ctx* ctxB = nullptr;  // second stream: the f_{i+1} compressions run beside the acc ones
+  cudaEvent_t evA = nullptr, evB = nullptr;
 };
 
 namespace vp {
@@ -947,7 +986,43 @@ static int sim_step(vp_sim* s, vp_record* rec) {
   g_flops = &s->flops;
   for (int i = 0; i < 4; ++i) {
     VP_TRY(stage_operator(s, fi, i == 0 ? s->ctx->h_smalld + 16 : nullptr));
-    if (i < 3) {
+    if (i < 3 && s->ctxB) {
+      // The two tolerance compressions of a stage are independent: acc_i on
+      // this context's stream, f_{i+1} on the second stream from a second
+      // host thread.  Each MPS keeps its buffers on the context that
+      // compresses it (acc, wa, f: first; fi, wb: second).
+      vp_ctx* cb = s->ctxB;
+      VP_CUDA(ctx, cudaEventRecord(s->evA, ctx->stream));
+      VP_CUDA(ctx, cudaStreamWaitEvent(cb->stream, s->evA, 0));
+      VP_TRY(site_sum_mps(ctx, 1.0, acc, B[i] * dt, &s->L, fi, &s->wa));
+      VP_TRY(site_sum_mps(cb, 1.0, &s->f, A[i] * dt, &s->L, fi, &s->wb));
+      const int cap0 = ctx->coop_cap;
+      ctx->coop_cap = cb->coop_cap = ctx->num_sms / 2;
+      int stB = VP_OK;
+      Flops fB;
+      const bool prof = ctx->prof_on;
+      std::thread worker([&] {
+        cb->prof_on = prof;
+        g_flops = &fB;
+        stB = compress(cb, &s->wb, 1 << 30, s->cfg.tol, nullptr);
+        g_flops = nullptr;
+      });
+      const int stA = compress(ctx, &s->wa, 1 << 30, s->cfg.tol, nullptr);
+      worker.join();
+      ctx->coop_cap = cap0;
+      if (stA != VP_OK) return stA;
+      if (stB != VP_OK) return fail(ctx, stB, cb->err);
+      VP_CUDA(ctx, cudaEventRecord(s->evB, cb->stream));
+      VP_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, s->evB, 0));
+      s->flops.qr += fB.qr;
+      s->flops.formq += fB.formq;
+      s->flops.gemm += fB.gemm;
+      s->flops.jacobi += fB.jacobi;
+      std::swap(s->acc, s->wa);
+      std::swap(s->fi, s->wb);
+      acc = &s->acc;
+      fi = &s->fi;
+    } else if (i < 3) {
       VP_TRY(site_sum_mps(ctx, 1.0, acc, B[i] * dt, &s->L, fi, &s->wa));
       VP_TRY(site_sum_mps(ctx, 1.0, &s->f, A[i] * dt, &s->L, fi, &s->wb));
       VP_TRY(compress(ctx, &s->wa, 1 << 30, s->cfg.tol, nullptr));
@@ -991,6 +1066,20 @@ static int upload_chain(vp_ctx* ctx, const Chain& c, std::vector<DevBuf>& out) {
 
 static void sim_free(vp_sim* s) {
   vp_ctx* ctx = s->ctx;
+  if (s->ctxB) {
+    cudaStreamSynchronize(s->ctxB->stream);
+    cudaStreamSynchronize(ctx->stream);
+    for (mps_t* m : {&s->fi, &s->wb}) {
+      m->ctx = s->ctxB;  // these buffers belong to the second context
+      mps_free(m);
+    }
+    auto& ch = ctx->children;
+    ch.erase(std::remove(ch.begin(), ch.end(), s->ctxB), ch.end());
+    vp_ctx_destroy(s->ctxB);
+    s->ctxB = nullptr;
+  }
+  if (s->evA) cudaEventDestroy(s->evA);
+  if (s->evB) cudaEventDestroy(s->evB);
   for (mps_t* m : {&s->f, &s->fi, &s->acc, &s->wa, &s->wb, &s->em}) mps_free(m);
   for (auto& b : s->Ud) release(ctx, b);
   for (auto& b : s->Dvd) release(ctx, b);
@@ -1025,6 +1114,15 @@ int vp_sim_create(vp_ctx* ctx, const vp_layout* L, const vp_config* cfg, const m
   if (st == VP_OK) st = upload_chain(ctx, s->Dv, s->Dvd);
   if (st == VP_OK) st = reserve(ctx, s->rho, (size_t)1 << L->nx);
   if (st == VP_OK) st = reserve(ctx, s->E, (size_t)1 << L->nx);
+  if (st == VP_OK && cfg->streams != 1) {
+    s->ctxB = ctx_child(ctx);
+    if (s->ctxB) {
+      s->fi.ctx = s->wb.ctx = s->ctxB;
+      if (cudaEventCreateWithFlags(&s->evA, cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&s->evB, cudaEventDisableTiming) != cudaSuccess)
+        st = fail(ctx, VP_ECUDA, "vp_sim_create: event creation failed");
+    }
+  }
   if (st == VP_OK) st = sync_status(ctx);
   if (st != VP_OK) {
     sim_free(s);

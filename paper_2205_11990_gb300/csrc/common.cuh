@@ -39,6 +39,9 @@ struct vp_ctx {
   int device = 0;
   int num_sms = 0;
   int cluster_size = 0;  // CTAs per cluster for the cluster-resident kernels (16, or 8)
+  int coop_cap = 0;      // max blocks of a cooperative grid launch (0: one per SM)
+  bool owns_stream = false;
+  std::vector<vp_ctx*> children;  // contexts created for concurrent work
   cudaStream_t stream = nullptr;
   vp_alloc_fn alloc = nullptr;
   vp_free_fn freef = nullptr;

@@ -82,6 +82,17 @@ struct GridSync {
   }
 };
 
+// The same interface over one thread-block cluster (the whole grid is one
+// cluster): hardware barrier, about 0.2 us.
+struct ClusterSync {
+  __device__ ClusterSync(DevStatus*, unsigned) {}
+  __device__ bool sync() {
+    cg::this_cluster().sync();
+    return true;
+  }
+  __device__ void finish() {}
+};
+
 static int coop_launch(vp_ctx* ctx, const void* fn, int blocks, int threads, void** args, size_t smem,
                        const char* what) {
   ctx->launches++;
@@ -118,13 +129,14 @@ int launch_to_colmajor(vp_ctx* ctx, const double* A, int m, int n, double* out) 
 // itself) forms the reflector H_j = I - tau v v^T (LAPACK dlarfg convention,
 // v_j = 1) and publishes v in a double buffer; after one grid barrier every
 // block applies H_j to the columns it owns.  One barrier per column.
+template <class Sync>
 __global__ void __launch_bounds__(kThreads) k_qr_factor(double* A, int m, int n, double* tau,
                                                         double* vbuf, DevStatus* st) {
   __shared__ double red[kWarps + 1];
   const int nb = gridDim.x, bid = blockIdx.x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int p = min(m, n);
-  GridSync gs(st, nb);
+  Sync gs(st, nb);
   for (int j = 0; j < p; ++j) {
     __syncthreads();
     double* vj = vbuf + (size_t)(j & 1) * m;
@@ -175,12 +187,40 @@ __global__ void __launch_bounds__(kThreads) k_qr_factor(double* A, int m, int n,
 int launch_qr_factor(vp_ctx* ctx, double* A, int m, int n, double* tau, double* vbuf) {
   const int p = std::min(m, n);
   if (p <= 0) return VP_OK;
+  // Small and medium matrices: one cluster (per-column barrier ~0.2 us); the
+  // FP64 work per column and CTA stays below ~1 us while n * m <= 32K.
+  const int CS = ctx->cluster_size;
+  if (CS > 0 && (long long)m * n <= 32768 && (long long)m * n >= 2048 && n >= CS) {
+    static bool attr_done = false;
+    if (!attr_done) {
+      VP_CUDA(ctx, cudaFuncSetAttribute(k_qr_factor<ClusterSync>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+      VP_CUDA(ctx, cudaFuncSetAttribute(k_qr_factor<ClusterSync>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        120 * 1024));
+      attr_done = true;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    cfg.gridDim = dim3(CS);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = 120 * 1024;  // one CTA per SM
+    cfg.stream = ctx->stream;
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = CS;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    ctx->launches++;
+    VP_CUDA(ctx, cudaLaunchKernelEx(&cfg, k_qr_factor<ClusterSync>, A, m, n, tau, vbuf, ctx->status));
+    return VP_OK;
+  }
   // enough blocks that each owns a few columns, but never more than one per SM
-  int blocks = std::min(ctx->num_sms, std::max(1, n / 2));
+  const int cap = ctx->coop_cap > 0 ? std::min(ctx->coop_cap, ctx->num_sms) : ctx->num_sms;
+  int blocks = std::min(cap, std::max(1, n / 2));
   if ((long long)m * n < 8192) blocks = 1;
   DevStatus* st = ctx->status;
   void* args[] = {&A, &m, &n, &tau, &vbuf, &st};
-  return coop_launch(ctx, (const void*)k_qr_factor, blocks, kThreads, args, 0, "qr_factor");
+  return coop_launch(ctx, (const void*)k_qr_factor<GridSync>, blocks, kThreads, args, 0, "qr_factor");
 }
 
 // Q = H_0 ... H_{p-1} [I_p; 0]: one warp per column, applied right to left in
@@ -447,6 +487,8 @@ __global__ void __launch_bounds__(kThreads) k_jacobi_rows(double* X, int b, int 
 // contiguous), one CTA per SM.  A pair is processed by one warp through
 // DSMEM pointers; rounds are separated by the hardware cluster barrier
 // (about 0.2 us on GB300, against 2 us for a grid-wide software barrier).
+constexpr int kJacRegs = 16;  // row elements per lane kept in registers (row length <= 512)
+
 __global__ void __launch_bounds__(kThreads) k_jacobi_cluster(double* X, int b, int c, double* J, double eps,
                                                              int max_sweeps, DevStatus* st) {
   cg::cluster_group cl = cg::this_cluster();
@@ -470,6 +512,7 @@ __global__ void __launch_bounds__(kThreads) k_jacobi_cluster(double* X, int b, i
   bool converged = false;
   for (; sweep < max_sweeps; ++sweep) {
     if (rank == 0 && tid == 0) cnt[(sweep + 1) % 3] = 0u;
+    unsigned rotated = 0;
     for (int round = 0; round < rounds; ++round) {
       for (int pr = rank + warp * CS; pr < npairs; pr += CS * kWarps) {
         int i = rr_index(pr, round, bp), j = rr_index(bp - 1 - pr, round, bp);
@@ -481,28 +524,62 @@ __global__ void __launch_bounds__(kThreads) k_jacobi_cluster(double* X, int b, i
         }
         double* xi = cl.map_shared_rank(sm + (size_t)(i / CS) * stride, i % CS);
         double* xj = cl.map_shared_rank(sm + (size_t)(j / CS) * stride, j % CS);
-        double al = 0.0, be = 0.0, ga = 0.0;
-        for (int q = lane; q < c; q += 32) {
-          const double u = xi[q], v = xj[q];
-          al = fma(u, u, al);
-          be = fma(v, v, be);
-          ga = fma(u, v, ga);
+        if (stride <= 32 * kJacRegs) {
+          // both rows in registers: one DSMEM read and one write per element
+          double ri[kJacRegs], rj[kJacRegs];
+          double al = 0.0, be = 0.0, ga = 0.0;
+#pragma unroll
+          for (int e = 0; e < kJacRegs; ++e) {
+            const int q = lane + 32 * e;
+            ri[e] = q < stride ? xi[q] : 0.0;
+            rj[e] = q < stride ? xj[q] : 0.0;
+            if (q < c) {
+              al = fma(ri[e], ri[e], al);
+              be = fma(rj[e], rj[e], be);
+              ga = fma(ri[e], rj[e], ga);
+            }
+          }
+          al = warp_sum(al);
+          be = warp_sum(be);
+          ga = warp_sum(ga);
+          if (!(al > 0.0 && be > 0.0)) continue;
+          if (!(fabs(ga) > eps * sqrt(al) * sqrt(be))) continue;
+          const double zeta = (be - al) / (2.0 * ga);
+          const double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(fma(zeta, zeta, 1.0)));
+          const double cs = 1.0 / sqrt(fma(t, t, 1.0)), sn = cs * t;
+#pragma unroll
+          for (int e = 0; e < kJacRegs; ++e) {
+            const int q = lane + 32 * e;
+            if (q < stride) {
+              xi[q] = cs * ri[e] - sn * rj[e];
+              xj[q] = sn * ri[e] + cs * rj[e];
+            }
+          }
+        } else {
+          double al = 0.0, be = 0.0, ga = 0.0;
+          for (int q = lane; q < c; q += 32) {
+            const double u = xi[q], v = xj[q];
+            al = fma(u, u, al);
+            be = fma(v, v, be);
+            ga = fma(u, v, ga);
+          }
+          al = warp_sum(al);
+          be = warp_sum(be);
+          ga = warp_sum(ga);
+          if (!(al > 0.0 && be > 0.0)) continue;
+          if (!(fabs(ga) > eps * sqrt(al) * sqrt(be))) continue;
+          const double zeta = (be - al) / (2.0 * ga);
+          const double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(fma(zeta, zeta, 1.0)));
+          const double cs = 1.0 / sqrt(fma(t, t, 1.0)), sn = cs * t;
+          for (int q = lane; q < stride; q += 32) {
+            const double u = xi[q], v = xj[q];
+            xi[q] = cs * u - sn * v;
+            xj[q] = sn * u + cs * v;
+          }
         }
-        al = warp_sum(al);
-        be = warp_sum(be);
-        ga = warp_sum(ga);
-        if (!(al > 0.0 && be > 0.0)) continue;
-        if (!(fabs(ga) > eps * sqrt(al) * sqrt(be))) continue;
-        const double zeta = (be - al) / (2.0 * ga);
-        const double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(fma(zeta, zeta, 1.0)));
-        const double cs = 1.0 / sqrt(fma(t, t, 1.0)), sn = cs * t;
-        for (int q = lane; q < stride; q += 32) {
-          const double u = xi[q], v = xj[q];
-          xi[q] = cs * u - sn * v;
-          xj[q] = sn * u + cs * v;
-        }
-        if (lane == 0) atomicAdd(&c0[sweep % 3], 1u);
+        ++rotated;
       }
+      if (round == rounds - 1 && lane == 0 && rotated) atomicAdd(&c0[sweep % 3], rotated);
       cl.sync();
     }
     if (*(volatile unsigned*)&c0[sweep % 3] == 0u) {

@@ -128,6 +128,10 @@ WORKLOADS = {
                                      ic="two_stream", chi=64, dt=0.002),
     "saturated_two_stream_1024x1024_seq": dict(layout=Layout(10, 10, 0.0, 10 * math.pi, -8.0, 8.0, SEQ),
                                                ic="saturated_two_stream", chi=64, dt=0.002),
+    "saturated_two_stream_1024x1024_int": dict(layout=Layout(10, 10, 0.0, 10 * math.pi, -8.0, 8.0, INTERLEAVED),
+                                               ic="saturated_two_stream", chi=64, dt=0.002),
+    "saturated_two_stream_256x256_seq": dict(layout=Layout(8, 8, 0.0, 10 * math.pi, -8.0, 8.0, SEQ),
+                                             ic="saturated_two_stream", chi=32, dt=0.008),
 }
 
 

@@ -35,6 +35,8 @@ EXPORTS = [
     "mpo_to_dense",
     "mps_apply_mpo", "mps_axpby", "mps_compress", "vp_density", "vp_poisson", "vp_poisson_noalloc",
     "vp_sim_create", "vp_sim_destroy", "vp_step", "vp_sim_state", "vp_sim_flops", "vp_run",
+    "vp_footprint_bytes", "vp_batch_create", "vp_batch_submit", "vp_batch_start", "vp_batch_wait", "vp_batch_poll",
+    "vp_batch_records", "vp_batch_destroy",
 ]
 
 
@@ -50,7 +52,14 @@ class CLayout(C.Structure):
 
 
 class CConfig(C.Structure):
-    _fields_ = [("dt", C.c_double), ("chi", C.c_int), ("tol", C.c_double), ("e_tol", C.c_double)]
+    _fields_ = [("dt", C.c_double), ("chi", C.c_int), ("tol", C.c_double), ("e_tol", C.c_double),
+                ("streams", C.c_int)]
+
+
+class CResult(C.Structure):
+    _fields_ = [("id", C.c_uint64), ("status", C.c_int), ("nsteps", C.c_int), ("queue_ms", C.c_double),
+                ("run_ms", C.c_double), ("step_ms_p50", C.c_double), ("step_ms_p99", C.c_double),
+                ("field_energy", C.c_double), ("max_bond", C.c_int)]
 
 
 class CRecord(C.Structure):
@@ -119,6 +128,14 @@ def load():
         "vp_sim_state": (P, [P]),
         "vp_sim_flops": (D, [P]),
         "vp_run": (I, [P, C.POINTER(CLayout), C.POINTER(CConfig), DP, I, DP, C.POINTER(CRecord)]),
+        "vp_footprint_bytes": (S, [C.POINTER(CLayout), C.POINTER(CConfig)]),
+        "vp_batch_create": (I, [P, I, S, C.POINTER(P)]),
+        "vp_batch_submit": (I, [P, C.POINTER(CLayout), C.POINTER(CConfig), DP, I, I, C.POINTER(C.c_uint64)]),
+        "vp_batch_start": (I, [P]),
+        "vp_batch_wait": (I, [P]),
+        "vp_batch_poll": (I, [P, C.POINTER(CResult), I, C.POINTER(I)]),
+        "vp_batch_records": (I, [P, C.c_uint64, C.POINTER(CRecord), DP, DP]),
+        "vp_batch_destroy": (I, [P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -289,9 +306,10 @@ class Context:
             raise VpError(code, "vp_poisson_noalloc failed")
         return E, we.value, mass.value
 
-    def sim(self, lay: Layout, f0: "MPS", dt: float, chi: int, tol: float = 1e-10, e_tol: float = 1e-10) -> "Sim":
+    def sim(self, lay: Layout, f0: "MPS", dt: float, chi: int, tol: float = 1e-10, e_tol: float = 1e-10,
+            streams: int = 2) -> "Sim":
         h = C.c_void_p()
-        cfg = CConfig(dt, chi, tol, e_tol)
+        cfg = CConfig(dt, chi, tol, e_tol, streams)
         self._check(self.lib.vp_sim_create(self.h, C.byref(clayout(lay)), C.byref(cfg), f0.h, C.byref(h)))
         return Sim(self, h, lay)
 
@@ -300,10 +318,67 @@ class Context:
         f0 = np.ascontiguousarray(f0, dtype=np.float64)
         fT = np.zeros((lay.Nx, lay.Nv)) if want_f else None
         recs = (CRecord * max(1, nsteps))()
-        cfg = CConfig(dt, chi, tol, e_tol)
+        cfg = CConfig(dt, chi, tol, e_tol, 2)
         self._check(self.lib.vp_run(self.h, C.byref(clayout(lay)), C.byref(cfg), _dp(f0), nsteps,
                                     _dp(fT) if want_f else None, recs))
         return fT, _records(recs, nsteps)
+
+
+class Batch:
+    """Concurrent independent runs (vp_batch_*): submit, start, wait/poll."""
+
+    def __init__(self, ctx: Context, max_concurrent: int, mem_budget_bytes: int):
+        self.ctx = ctx
+        h = C.c_void_p()
+        ctx._check(ctx.lib.vp_batch_create(ctx.h, max_concurrent, mem_budget_bytes, C.byref(h)))
+        self.h = h
+        self.nsteps = {}
+        ctx._children.add(self)
+
+    def submit(self, lay: Layout, f0: np.ndarray, dt: float, nsteps: int, chi: int, tol: float = 1e-10,
+               e_tol: float = 1e-10, keep_f: bool = False) -> int:
+        f0 = np.ascontiguousarray(f0, dtype=np.float64)
+        rid = C.c_uint64()
+        cfg = CConfig(dt, chi, tol, e_tol, 1)
+        self.ctx._check(self.ctx.lib.vp_batch_submit(self.h, C.byref(clayout(lay)), C.byref(cfg), _dp(f0), nsteps,
+                                                     int(keep_f), C.byref(rid)))
+        self.nsteps[rid.value] = (nsteps, lay)
+        return rid.value
+
+    def start(self):
+        self.ctx._check(self.ctx.lib.vp_batch_start(self.h))
+
+    def wait(self):
+        self.ctx._check(self.ctx.lib.vp_batch_wait(self.h))
+
+    def poll(self, max_n: int = 1024):
+        out = (CResult * max_n)()
+        n = C.c_int()
+        self.ctx._check(self.ctx.lib.vp_batch_poll(self.h, out, max_n, C.byref(n)))
+        return [{k: getattr(r, k) for k, _ in CResult._fields_} for r in list(out)[: n.value]]
+
+    def records(self, rid: int, want_f: bool = False):
+        nsteps, lay = self.nsteps[rid]
+        recs = (CRecord * max(1, nsteps))()
+        ms = np.zeros(max(1, nsteps))
+        fT = np.zeros((lay.Nx, lay.Nv)) if want_f else None
+        self.ctx._check(self.ctx.lib.vp_batch_records(self.h, rid, recs, _dp(ms), _dp(fT) if want_f else None))
+        return _records(recs, nsteps), ms[:nsteps], fT
+
+    def close(self):
+        if self.h and self.ctx.h:
+            self.ctx.lib.vp_batch_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def footprint_bytes(lay: Layout, chi: int, dt: float = 0.01) -> int:
+    return int(load().vp_footprint_bytes(C.byref(clayout(lay)), C.byref(CConfig(dt, chi, 1e-10, 1e-10, 1))))
 
 
 def _records(recs, n):
