@@ -27,10 +27,12 @@
  *  - Work is enqueued on the context's CUDA stream.  Functions that return
  *    host data synchronise that stream before returning.  A context is not
  *    re-entrant: use one context per host thread / stream.
- *  - Site ordering: site 0 is the most significant (coarsest) bit.  With
- *    VP_SEQ the sites are x_0..x_{nx-1}, v_0..v_{nv-1} (ordering S1); with
- *    VP_INTERLEAVED they are x_0, v_0, x_1, v_1, ... (ordering IF), leftover
- *    bits of the longer dimension last.
+ *  - Site ordering (main text, "State Compressibility"): x_0 / v_0 is the most
+ *    significant (coarsest) bit of a dimension.  VP_SEQ (S1): x_0..x_{nx-1},
+ *    v_0..v_{nv-1}; VP_SEQ_S2: x_{nx-1}..x_0 (fine to coarse), then
+ *    v_0..v_{nv-1}; VP_SEQ_S3: x_0..x_{nx-1}, then v_{nv-1}..v_0;
+ *    VP_INTERLEAVED (IF): x_0, v_0, x_1, v_1, ..., leftover bits of the longer
+ *    dimension last.
  *  - Grid: x_i = xmin + i dx, dx = (xmax - xmin)/2^nx (periodic, right end
  *    excluded); v_j = vmin + j dv, dv = (vmax - vmin)/(2^nv - 1) (both ends
  *    included, zero-gradient boundaries).  The v domain must be symmetric
@@ -56,10 +58,11 @@ enum {
   VP_ETIMEOUT = 5,   /* a device-side wait gave up after its iteration limit */
   VP_ENUMERIC = 6,   /* NaN/Inf in singular values or the field */
   VP_ECFL = 7,       /* time step above the RK4 stability limit */
-  VP_EBUSY = 8       /* object in use by another operation */
+  VP_EBUSY = 8,      /* object in use by another operation */
+  VP_EIO = 9         /* checkpoint file missing, unreadable or malformed */
 };
 
-enum { VP_SEQ = 0, VP_INTERLEAVED = 1 };
+enum { VP_SEQ = 0, VP_INTERLEAVED = 1, VP_SEQ_S2 = 2, VP_SEQ_S3 = 3 };
 
 /* Opaque handles. */
 typedef struct vp_ctx vp_ctx;
@@ -74,7 +77,7 @@ typedef void (*vp_free_fn)(void* ptr, size_t bytes, void* user);
 
 typedef struct {
   int nx, nv;      /* bits per dimension, each in [2, 14] */
-  int mapping;     /* VP_SEQ or VP_INTERLEAVED */
+  int mapping;     /* VP_SEQ, VP_INTERLEAVED, VP_SEQ_S2 or VP_SEQ_S3 */
   double xmin, xmax, vmin, vmax;
 } vp_layout;
 
@@ -123,6 +126,15 @@ int mps_num_sites(const mps_t* mps);
 int mps_bonds(const mps_t* mps, int* ranks_out);
 /* Packed cores to host (layout as mps_create_cores); `capacity` doubles. */
 int mps_get_cores(vp_ctx* ctx, const mps_t* mps, double* host_out, size_t capacity);
+/* Checkpoint an MPS to a file / restore it (the state is the whole of a
+ * simulation's f, so a run can resume from it).  File: 8-byte magic
+ * "VPMPS01\0", int32 n, int32 0, int32 ranks[n+1], zero padding to 8 bytes,
+ * then the cores packed as in mps_get_cores (FP64), little-endian.  mps_save
+ * writes `path`.tmp and renames it over `path`; mps_load rejects a file whose
+ * size disagrees with its bond ranks.  Errors: VP_EIO (open/read/write or
+ * format), VP_EINVAL, VP_ENOMEM. */
+int mps_save(vp_ctx* ctx, const mps_t* mps, const char* path);
+int mps_load(vp_ctx* ctx, const char* path, mps_t** out);
 /* Contract to the dense 2^n vector indexed by site bits (site 0 = MSB), host
  * output.  n <= 24. */
 int mps_to_dense(vp_ctx* ctx, const mps_t* mps, double* host_out);
@@ -206,6 +218,15 @@ int vp_poisson(vp_ctx* ctx, const double* rho_dev, int nx, double dx, double* E_
 int vp_poisson_noalloc(void* cuda_stream, const double* rho_dev, int nx, double dx, double* E_dev,
                        double* field_energy_host, double* mass_host);
 
+/* Dense contraction C (M x N) = alpha * A (M x K) * B (K x N), row-major
+ * device buffers with leading dimensions lda >= K, ldb >= N, ldc >= N, in
+ * the arithmetic of `precision` (VP_PREC_*, see vp_config): the kernel the
+ * sweeps use for their GEMM-shaped contractions (R x next core, U S
+ * products).  K = 0 gives C = 0.  Synchronises the context stream; a device
+ * wait that gave up is reported as VP_ETIMEOUT.  Errors: VP_EINVAL. */
+int vp_gemm(vp_ctx* ctx, int precision, int M, int N, int K, double alpha, const double* A, int lda,
+            const double* B, int ldb, double* C, int ldc);
+
 /* --------------------------------------------------------------- stepping */
 
 typedef struct {
@@ -215,7 +236,37 @@ typedef struct {
   double e_tol;     /* tolerance of the E-field MPS (1e-10) */
   int streams;      /* 1: one stream; 0 or 2: the two independent compressions of
                        each RK stage run concurrently on a second stream */
+  int level;        /* compression level (SI "Compressed time evolution
+                       algorithm"), 0 or 1: C1; 2..5: C2..C5 -- C2 also caps the
+                       intermediate states at chi, C3 also the running sum of
+                       derivatives (D = k1, D <- C(D + w_i k_i), w = 2, 2, 1;
+                       f_{n+1} = C(f_n + dt/6 D)), C4 also each derivative,
+                       C5 also the advection and field terms of each
+                       derivative before they are added */
+  int e_chi;        /* bond cap D_F of the field MPS (main text, "Approximation
+                       of the nonlinear term"); 0: no cap */
+  int precision;    /* VP_PREC_*: arithmetic of the dense contractions of the
+                       sweeps (R x next core, the Q and U S products).  QR,
+                       Jacobi SVD, truncation, the MPO application and the
+                       Poisson solve stay FP64 in every mode.
+                         FP64          FP64 FMA;
+                         FP32_CONTRACT FP32 FMA, FP32 accumulation (CUDA cores);
+                         TF32          tensor cores, operands rounded to TF32,
+                                       FP32 accumulation in tensor memory;
+                         BF16          tensor cores, BF16 operands, FP32
+                                       accumulation;
+                         TF32X3        tensor cores, split products
+                                       a_hi b_hi + a_hi b_lo + a_lo b_hi of
+                                       TF32 halves, FP32 accumulation. */
 } vp_config;
+
+enum {
+  VP_PREC_FP64 = 0,
+  VP_PREC_FP32_CONTRACT = 1,
+  VP_PREC_TF32 = 2,
+  VP_PREC_BF16 = 3,
+  VP_PREC_TF32X3 = 4
+};
 
 typedef struct {
   double t;             /* time at the start of the step */
@@ -233,6 +284,10 @@ int vp_sim_destroy(vp_sim* sim);
 int vp_step(vp_sim* sim, int nsteps, vp_record* records);
 /* The current state (owned by the sim; valid until the next vp_step). */
 const mps_t* vp_sim_state(const vp_sim* sim);
+/* Entanglement entropy per bond (main text, EE equation: -sum p log2 p over
+ * the normalised squared singular values kept at that bond) of the last step's
+ * final compression; S_out: n-1 doubles (host).  Zero before the first step. */
+int vp_sim_entropy(const vp_sim* sim, double* S_out);
 /* Algorithmic FP64 flop count of the factorisations since creation. */
 double vp_sim_flops(const vp_sim* sim);
 

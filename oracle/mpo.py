@@ -152,20 +152,28 @@ def diag_from_mps(cores):
     return out
 
 
+def reverse(chain):
+    """The same operator (or MPS) with its sites in the opposite order: core k
+    of the result is core L-1-k with its two bonds exchanged."""
+    if chain[0].ndim == 3:
+        return [c.transpose(2, 1, 0).copy() for c in chain[::-1]]
+    return [c.transpose(3, 1, 2, 0).copy() for c in chain[::-1]]
+
+
 def place(factors, sitemap):
     """Tensor product of per-dimension MPOs placed on an MPS site ordering.
 
-    ``factors[d]`` is the MPO acting on the bits of dimension d (most
-    significant first); ``sitemap[k] = (d, b)`` says that site k carries bit b
-    of dimension d.  A dimension that is not yet entered or already left
-    carries its bond through the site unchanged, so the bond at a cut is the
-    product of the per-dimension bonds there.
+    ``factors[d]`` is the MPO acting on the bits of dimension d, its cores in
+    the order in which the site map meets that dimension's bits
+    (``sitemap[k] = (d, b)``: site k carries bit b of dimension d).  A
+    dimension that is not yet entered or already left carries its bond
+    through the site unchanged, so the bond at a cut is the product of the
+    per-dimension bonds there.
     """
     ndim = len(factors)
     pos = [0] * ndim
     out = []
     for (d, b) in sitemap:
-        assert b == pos[d], "bits of each dimension must appear most significant first"
         left = [factors[e][pos[e]].shape[0] if pos[e] < len(factors[e]) else factors[e][-1].shape[3]
                 for e in range(ndim)]
         core = factors[d][pos[d]]

@@ -178,6 +178,24 @@ def compress(cores, chi, tol):
     return out, errs
 
 
+def entanglement_entropy(s, r):
+    """Main text, EE equation: -sum p log2 p, p_i = s_i^2 / sum_{i<r} s^2 over
+    the r kept singular values of one bond."""
+    p = np.asarray(s[:r], dtype=np.float64) ** 2
+    tot = p.sum()
+    if tot <= 0:
+        return 0.0
+    p = p[p > 0] / tot
+    return float(-np.sum(p * np.log2(p)))
+
+
+def compress_with_entropy(cores, chi, tol):
+    """compress() that also returns the entropy of the kept values per bond."""
+    out, errs, svals = svd_sweep(qr_sweep(cores), chi, tol)
+    ee = [entanglement_entropy(svals[j], out[j + 1].shape[0]) for j in range(len(out) - 1)]
+    return out, errs, ee
+
+
 def from_dense(vec, n, chi, tol):
     """Exact TT-SVD followed by :func:`compress` (used for f0 and for E)."""
     return compress(tt_svd(vec, n), chi, tol)[0]

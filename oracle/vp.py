@@ -43,13 +43,19 @@ def grid_steps(layout):
 def sitemap(layout):
     """Site -> (dimension, bit).  0 = x, 1 = v; bits most significant first.
 
-    SEQ (S1): all x bits then all v bits.  INTERLEAVED (IF): x_0, v_0, x_1,
+    SEQ (S1): all x bits then all v bits, each coarse to fine; S2: x fine to
+    coarse, then v coarse to fine; S3: x coarse to fine, then v fine to coarse
+    (main text, "State Compressibility").  INTERLEAVED (IF): x_0, v_0, x_1,
     v_1, ...; when nx != nv the leftover bits of the longer dimension follow
     in their own order.
     """
     nx, nv = layout.nx, layout.nv
     if layout.mapping == 0:
         return [(0, b) for b in range(nx)] + [(1, b) for b in range(nv)]
+    if layout.mapping == 2:
+        return [(0, nx - 1 - b) for b in range(nx)] + [(1, b) for b in range(nv)]
+    if layout.mapping == 3:
+        return [(0, b) for b in range(nx)] + [(1, nv - 1 - b) for b in range(nv)]
     out = []
     for b in range(max(nx, nv)):
         if b < nx:
@@ -73,6 +79,24 @@ def sites_to_dense(vec, layout):
     return vec.reshape([2] * (nx + nv)).transpose(inv).reshape(layout.Nx, layout.Nv)
 
 
+def descending(layout, dim):
+    """True when the bits of `dim` appear fine to coarse in the site order."""
+    return (layout.mapping == 2 and dim == 0) or (layout.mapping == 3 and dim == 1)
+
+
+def orient(chain, layout, dim):
+    """An MPO/MPS chain built coarse-to-fine, put in the site order of `dim`."""
+    return M.reverse(chain) if descending(layout, dim) else chain
+
+
+def bitrev(n_bits):
+    idx = np.arange(1 << n_bits)
+    out = np.zeros_like(idx)
+    for b in range(n_bits):
+        out |= ((idx >> b) & 1) << (n_bits - 1 - b)
+    return out
+
+
 def mps_from_f(f, layout, chi, tol=TOL):
     return S.from_dense(dense_to_sites(f, layout), layout.n, chi, tol)
 
@@ -90,7 +114,8 @@ def density(cores, layout):
     vsites = {k for k, (d, _) in enumerate(sm) if d == 1}
     vecs = {k: np.ones(2) for k in vsites}
     xm = S.contract_sites(cores, vsites, vecs)
-    return S.to_dense(xm) * dv
+    rho = S.to_dense(xm) * dv  # indexed by the x bits in site order
+    return rho[bitrev(layout.nx)] if descending(layout, 0) else rho
 
 
 # ---------------------------------------------------------------- Poisson (a4)
@@ -147,9 +172,10 @@ def _static_parts(layout):
     vp = M.diag_from_mps(_vh_mps(layout, True))
     vm = M.diag_from_mps(_vh_mps(layout, False))
     # -v+ D_b  -v- D_f  (v > 0 takes the backward stencil, v < 0 the forward one)
-    up = M.mpo_sum(M.place([M.mpo_scale(M.backward_periodic(layout.nx, dx), -1.0), vp], sm),
-                   M.place([M.mpo_scale(M.forward_periodic(layout.nx, dx), -1.0), vm], sm))
-    dvz = M.centered_zero_gradient(layout.nv, dv)
+    bwd = orient(M.mpo_scale(M.backward_periodic(layout.nx, dx), -1.0), layout, 0)
+    fwd = orient(M.mpo_scale(M.forward_periodic(layout.nx, dx), -1.0), layout, 0)
+    up = M.mpo_sum(M.place([bwd, orient(vp, layout, 1)], sm), M.place([fwd, orient(vm, layout, 1)], sm))
+    dvz = orient(M.centered_zero_gradient(layout.nv, dv), layout, 1)
     return up, dvz
 
 
@@ -160,9 +186,14 @@ def operator(E_cores, layout):
     return M.mpo_sum(up, et)
 
 
-def field_mps(E, layout, tol=TOL):
-    """E(x) as an MPS on the x bits, tolerance-truncated (no D_F cap)."""
-    return S.from_dense(E, layout.nx, 1 << layout.nx, tol)
+def field_mps(E, layout, tol=TOL, e_chi=None):
+    """E(x) as an MPS on the x bits in their site order, tolerance-truncated;
+    e_chi caps its bond (the field compression D_F of the main text,
+    "Approximation of the nonlinear term"; None: no cap)."""
+    E = np.asarray(E, dtype=np.float64)
+    if descending(layout, 0):
+        E = E[bitrev(layout.nx)]
+    return S.from_dense(E, layout.nx, e_chi if e_chi else 1 << layout.nx, tol)
 
 
 # ------------------------------------------------------------------ step (a10)
@@ -183,8 +214,21 @@ def rhs(cores, layout, e_tol=TOL):
     return S.apply_mpo(L, cores), we, rho
 
 
-def rk4_step(f, layout, dt, chi, tol=TOL, e_tol=TOL):
-    """One RK4 step with compression level C1; returns (f_{n+1}, diagnostics)."""
+def rk4_step(f, layout, dt, chi, tol=TOL, e_tol=TOL, level=1, e_chi=None):
+    """One RK4 step; returns (f_{n+1}, diagnostics).
+
+    Compression levels (SI "Compressed time evolution algorithm"); every
+    compression also applies the tolerance:
+      C1  f_{n+1} to chi; intermediate states and the running sum to tol only;
+      C2  C1 + the intermediate states f_n + a_i dt k_i to chi;
+      C3  C2 + the sum of derivatives: D = k_1, D <- C_chi(D + w_i k_i) with
+          w = (2, 2, 1), f_{n+1} = C_chi(f_n + dt/6 D);
+      C4  C3 + each derivative k_i = C_chi(L f_i);
+      C5  C4 + the terms of each derivative: k_i = C_chi(C_chi(U f_i) +
+          C_chi(T f_i)), U the advection operator, T the field term.
+    """
+    if level != 1 or e_chi:
+        return _rk4_step_levels(f, layout, dt, chi, tol, e_tol, level, e_chi)
     acc = f
     fi = f
     diag = {}
@@ -199,7 +243,8 @@ def rk4_step(f, layout, dt, chi, tol=TOL, e_tol=TOL):
             fi, _ = S.compress(S.add(f, k, 1.0, A_RK[i] * dt), 1 << 30, tol)
             acc, _ = S.compress(S.add(acc, k, 1.0, B_RK[i] * dt), 1 << 30, tol)
         else:
-            acc, errs = S.compress(S.add(acc, k, 1.0, B_RK[3] * dt), chi, tol)
+            acc, errs, ee = S.compress_with_entropy(S.add(acc, k, 1.0, B_RK[3] * dt), chi, tol)
+            diag["entropy"] = ee
     diag["trunc_err"] = errs
     diag["bonds"] = S.bonds(acc)
     return acc, diag
@@ -226,3 +271,44 @@ def run(f0, layout, dt, nsteps, chi, tol=TOL, e_tol=TOL, every=1):
         if step % every == 0:
             hist.append((step * dt, d["field_energy"], d["mass"], max(d["bonds"])))
     return cores, hist
+
+
+W_RK = (1.0, 2.0, 2.0, 1.0)
+
+
+def _rk4_step_levels(f, layout, dt, chi, tol, e_tol, level, e_chi):
+    big = 1 << 30
+    up, dvz = _static_parts(layout)
+    sm = sitemap(layout)
+    acc, D, fi, k = f, None, f, None
+    diag = {}
+    errs = None
+    for i in range(4):
+        E, we, rho = stage_field(fi, layout, e_tol)
+        if i == 0:
+            dx, _ = grid_steps(layout)
+            diag["field_energy"] = we
+            diag["mass"] = float(np.sum(rho)) * dx
+        Em = field_mps(E, layout, e_tol, e_chi)
+        if level >= 5:
+            ku, _ = S.compress(S.apply_mpo(up, fi), chi, tol)
+            kt, _ = S.compress(S.apply_mpo(M.place([M.diag_from_mps(Em), dvz], sm), fi), chi, tol)
+            k, _ = S.compress(S.add(ku, kt), chi, tol)
+        else:
+            k = S.apply_mpo(M.mpo_sum(up, M.place([M.diag_from_mps(Em), dvz], sm)), fi)
+            if level >= 4:
+                k, _ = S.compress(k, chi, tol)
+        if level >= 3:
+            D = k if i == 0 else S.compress(S.add(D, k, 1.0, W_RK[i]), chi, tol)[0]
+        elif i < 3:
+            acc, _ = S.compress(S.add(acc, k, 1.0, B_RK[i] * dt), big, tol)
+        if i < 3:
+            fi, _ = S.compress(S.add(f, k, 1.0, A_RK[i] * dt), chi if level >= 2 else big, tol)
+    if level >= 3:
+        out, errs, ee = S.compress_with_entropy(S.add(f, D, 1.0, dt / 6.0), chi, tol)
+    else:
+        out, errs, ee = S.compress_with_entropy(S.add(acc, k, 1.0, B_RK[3] * dt), chi, tol)
+    diag["entropy"] = ee
+    diag["trunc_err"] = errs
+    diag["bonds"] = S.bonds(out)
+    return out, diag

@@ -148,7 +148,7 @@ static int mps_copy(vp_ctx* ctx, const mps_t* src, mps_t* dst) {
 
 static int read_rank(vp_ctx* ctx, int* r, double* err) {
   VP_CUDA(ctx, cudaMemcpyAsync(ctx->h_small, ctx->d_small, 2 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
-  VP_CUDA(ctx, cudaMemcpyAsync(ctx->h_smalld, ctx->d_smalld, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  VP_CUDA(ctx, cudaMemcpyAsync(ctx->h_smalld, ctx->d_smalld, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   VP_CUDA(ctx, cudaMemcpyAsync(ctx->h_small + 61, &ctx->status->pad2, sizeof(int), cudaMemcpyDeviceToHost,
                                ctx->stream));
   VP_TRY(sync_status(ctx));
@@ -162,6 +162,7 @@ struct Flops {
   double qr = 0, formq = 0, gemm = 0, jacobi = 0;
 };
 static thread_local Flops* g_flops = nullptr;
+static thread_local double* g_entropy = nullptr;  // per-bond entanglement entropy of the compression running
 
 static double qr_flops(double m, double n) {
   return m >= n ? 2 * m * n * n - 2.0 / 3.0 * n * n * n : 2 * n * m * m - 2.0 / 3.0 * m * m * m;
@@ -197,6 +198,28 @@ static int qr_site(vp_ctx* ctx, mps_t* s, int k) {
   return VP_OK;
 }
 
+static int ensure_side(vp_ctx* ctx) {
+  if (ctx->side) return VP_OK;
+  VP_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking));
+  VP_CUDA(ctx, cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
+  VP_CUDA(ctx, cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming));
+  return VP_OK;
+}
+
+// Launches inside the scope go to the side stream with the side scratch.
+struct SideScope {
+  vp_ctx* c;
+  explicit SideScope(vp_ctx* ctx) : c(ctx) { swap_all(); }
+  ~SideScope() { swap_all(); }
+  void swap_all() {
+    std::swap(c->stream, c->side);
+    std::swap(c->w_q, c->w_q_side);
+    std::swap(c->w_split, c->w_split_side);
+    std::swap(c->w_tca, c->w_tca_side);
+    std::swap(c->w_tcb, c->w_tcb_side);
+  }
+};
+
 // SVD step at site k >= 1 of a left-canonical MPS whose right part is
 // already right-canonical: M = core_k (r_k x 2 r_{k+1}); keep r singular
 // triplets (truncation rule of the truncation-error equation).
@@ -228,9 +251,6 @@ static int svd_site(vp_ctx* ctx, mps_t* s, int k, int chi, double tol, double* e
   VP_TRY(launch_qr_factor(ctx, ctx->w_fac.p, p, q, ctx->w_p.p, ctx->w_p.p + q + 8));
   prof_end(ctx, VP_K_QR, qr_flops(p, q));
   VP_TRY(reserve(ctx, ctx->w_q1, (size_t)p * q));
-  prof_begin(ctx, VP_K_FORMQ);
-  VP_TRY(launch_qr_formq(ctx, ctx->w_fac.p, p, q, ctx->w_p.p, ctx->w_q1.p));
-  prof_end(ctx, VP_K_FORMQ, 4.0 * p * q * q - 4.0 / 3.0 * q * q * q);
   // second QR: R1^T = Q2 L^T (R1 row-major is R1^T column-major)
   VP_TRY(reserve(ctx, ctx->w_r, (size_t)q * q));
   VP_TRY(launch_qr_getr(ctx, ctx->w_fac.p, p, q, ctx->w_r.p));
@@ -239,17 +259,42 @@ static int svd_site(vp_ctx* ctx, mps_t* s, int k, int chi, double tol, double* e
   VP_TRY(launch_qr_factor(ctx, ctx->w_r.p, q, q, ctx->w_p2.p, ctx->w_p2.p + q + 8));
   prof_end(ctx, VP_K_QR, qr_flops(q, q));
   VP_TRY(reserve(ctx, ctx->w_q2, (size_t)q * q));
-  prof_begin(ctx, VP_K_FORMQ);
-  VP_TRY(launch_qr_formq(ctx, ctx->w_r.p, q, q, ctx->w_p2.p, ctx->w_q2.p));
-  prof_end(ctx, VP_K_FORMQ, 8.0 / 3.0 * q * q * q);
+  // Q1, Q2 (and, tall, P Q1) only feed the outputs: form them on the side
+  // stream while the Jacobi SVD runs.  Their scratch is reserved up front so
+  // nothing is reallocated while the two streams run.
+  if (tall) VP_TRY(reserve(ctx, ctx->w_tmp2, (size_t)pl * q));
+  VP_TRY(ensure_side(ctx));
+  VP_TRY(reserve(ctx, ctx->w_q_side, (size_t)std::max(p, q) * q));
+  VP_TRY(reserve(ctx, ctx->w_split_side, (size_t)pl * q * 33));
+  VP_CUDA(ctx, cudaEventRecord(ctx->ev_fork, ctx->stream));
+  VP_CUDA(ctx, cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0));
+  {
+    SideScope side(ctx);
+    prof_begin(ctx, VP_K_FORMQ);
+    VP_TRY(launch_qr_formq(ctx, ctx->w_fac.p, p, q, ctx->w_p.p, ctx->w_q1.p));
+    prof_end(ctx, VP_K_FORMQ, 4.0 * p * q * q - 4.0 / 3.0 * q * q * q);
+    prof_begin(ctx, VP_K_FORMQ);
+    VP_TRY(launch_qr_formq(ctx, ctx->w_r.p, q, q, ctx->w_p2.p, ctx->w_q2.p));
+    prof_end(ctx, VP_K_FORMQ, 8.0 / 3.0 * q * q * q);
+    if (tall) VP_TRY(launch_gemm(ctx, pl, q, m, 1.0, s->core[k - 1].p, m, ctx->w_q1.p, q, ctx->w_tmp2.p, q));
+  }
+  VP_CUDA(ctx, cudaEventRecord(ctx->ev_join, ctx->side));
   VP_TRY(reserve(ctx, ctx->w_tmp, (size_t)q * q));
   double* X = ctx->w_tmp.p;
   VP_TRY(launch_lower_from_upper(ctx, ctx->w_r.p, q, X));
-  // Jacobi on the rows of L
-  VP_TRY(reserve(ctx, ctx->w_j, (size_t)q * q));
+  // Jacobi on the rows of L.  Tall case: no rotation accumulator; U_L S = L V_L
+  // is recovered afterwards from a saved copy of L.
+  double* Lsave = nullptr;
+  if (tall) {
+    VP_TRY(reserve(ctx, ctx->w_l, (size_t)q * q));
+    VP_TRY(launch_copy(ctx, X, ctx->w_l.p, (size_t)q * q));
+    Lsave = ctx->w_l.p;
+  } else {
+    VP_TRY(reserve(ctx, ctx->w_j, (size_t)q * q));
+  }
   VP_CUDA(ctx, cudaMemsetAsync(ctx->status->rot, 0, sizeof(ctx->status->rot), ctx->stream));
   prof_begin(ctx, VP_K_JACOBI);
-  VP_TRY(launch_jacobi_rows(ctx, X, q, q, ctx->w_j.p));
+  VP_TRY(launch_jacobi_rows(ctx, X, q, q, tall ? nullptr : ctx->w_j.p));
   prof_end(ctx, VP_K_JACOBI, 0.0);
   VP_TRY(reserve(ctx, ctx->w_vec, (size_t)2 * q + 8));
   int* perm = (int*)ctx->w_vec.p;
@@ -261,24 +306,25 @@ static int svd_site(vp_ctx* ctx, mps_t* s, int k, int chi, double tol, double* e
   double err = 0.0;
   VP_TRY(read_rank(ctx, &r, &err));
   if (err_out) *err_out = err;
-  const double jac = q > 1 ? (double)ctx->h_small[61] * 0.5 * q * (q - 1) * (6.0 * q + 4.0 * q) : 0.0;
+  if (g_entropy) g_entropy[k - 1] = ctx->h_smalld[1];
+  const double jac = q > 1 ? (double)ctx->h_small[61] * 0.5 * q * (q - 1) * (6.0 * q + (tall ? 0.0 : 4.0 * q)) : 0.0;
   if (ctx->prof_on) ctx->prof_work[VP_K_JACOBI] += jac;
   double gem = 0.0;
   VP_TRY(reserve(ctx, ctx->w_a, (size_t)r * q + 8));
   VP_TRY(reserve(ctx, ctx->w_b, (size_t)q * r + 8));
+  VP_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0));
   prof_begin(ctx, VP_K_GEMM);
   if (tall) {
     // P1 = P Q1 (pl x q); core_{k-1} <- P1 (U_L S); core_k <- scatter(V_L^T Q2^T)
-    VP_TRY(launch_svd_outputs(ctx, X, ctx->w_j.p, q, q, r, perm, sigma, ctx->w_a.p, ctx->w_b.p));
-    VP_TRY(reserve(ctx, ctx->w_tmp2, (size_t)pl * q));
-    VP_TRY(launch_gemm(ctx, pl, q, m, 1.0, s->core[k - 1].p, m, ctx->w_q1.p, q, ctx->w_tmp2.p, q));
+    VP_TRY(launch_svd_outputs(ctx, X, nullptr, q, q, r, perm, sigma, ctx->w_a.p, nullptr));
+    VP_TRY(launch_gemm_bt(ctx, q, r, q, Lsave, q, ctx->w_a.p, q, ctx->w_b.p, r));  // U_L S = L V_L
     VP_TRY(reserve(ctx, ctx->w_gemm, (size_t)pl * r));
     VP_TRY(launch_gemm(ctx, pl, r, q, 1.0, ctx->w_tmp2.p, q, ctx->w_b.p, r, ctx->w_gemm.p, r));
     VP_TRY(reserve(ctx, ctx->w_c, (size_t)r * q));
     VP_TRY(launch_gemm_bt(ctx, r, q, q, ctx->w_a.p, q, ctx->w_q2.p, q, ctx->w_c.p, q));
     VP_TRY(reserve(ctx, s->core[k], (size_t)r * c));
     VP_TRY(launch_scatter(ctx, ctx->w_c.p, r, q, piv, 1, s->core[k].p));
-    gem = 2.0 * pl * q * m + 2.0 * pl * r * q + 2.0 * r * q * q;
+    gem = 2.0 * pl * q * m + 2.0 * pl * r * q + 2.0 * r * q * q + 2.0 * q * q * r;
   } else {
     // core_k <- U_L^T Q1^T (r x c); core_{k-1} <- P Pi (Q2 V_L S)
     VP_TRY(launch_svd_outputs_wide(ctx, X, ctx->w_j.p, q, r, perm, ctx->w_a.p, ctx->w_b.p));
@@ -367,9 +413,12 @@ static int to_dense_dev(vp_ctx* ctx, const mps_t* s, DevBuf& out) {
 }
 
 // ------------------------------------------------------------ density
+static bool xdesc(const vp_layout* L) { return L->mapping == VP_SEQ_S2; }
+static bool vdesc(const vp_layout* L) { return L->mapping == VP_SEQ_S3; }
+
 static std::vector<int> site_dims(const vp_layout* L) {
   std::vector<int> d;
-  if (L->mapping == VP_SEQ) {
+  if (L->mapping != VP_INTERLEAVED) {
     for (int b = 0; b < L->nx; ++b) d.push_back(0);
     for (int b = 0; b < L->nv; ++b) d.push_back(1);
   } else {
@@ -440,7 +489,10 @@ static int density(vp_ctx* ctx, const vp_layout* L, const mps_t* f, double* rho)
   DevBuf dense;
   VP_TRY(to_dense_dev(ctx, &xm, dense));
   const size_t Nx = (size_t)1 << L->nx;
-  VP_TRY(launch_copy(ctx, dense.p, rho, Nx));
+  if (xdesc(L))  // the expansion is indexed by the x bits in site order: undo the bit reversal
+    VP_TRY(launch_permute_to_sites(ctx, dense.p, L->nx, 0, VP_SEQ_S2, rho, 1));
+  else
+    VP_TRY(launch_copy(ctx, dense.p, rho, Nx));
   VP_TRY(launch_scale(ctx, rho, Nx, dv));
   release(ctx, dense);
   mps_free(&xm);
@@ -452,7 +504,7 @@ static int density(vp_ctx* ctx, const vp_layout* L, const mps_t* f, double* rho)
 
 static bool layout_ok(const vp_layout* L) {
   return L && L->nx >= 2 && L->nv >= 2 && L->nx <= 14 && L->nv <= 14 &&
-         (L->mapping == VP_SEQ || L->mapping == VP_INTERLEAVED) && L->xmax > L->xmin && L->vmax > L->vmin &&
+         L->mapping >= VP_SEQ && L->mapping <= VP_SEQ_S3 && L->xmax > L->xmin && L->vmax > L->vmin &&
          std::fabs(L->vmin + L->vmax) <= 1e-12 * std::fabs(L->vmax);
 }
 
@@ -529,7 +581,8 @@ int vp_ctx_destroy(vp_ctx* c) {
   if (!c) return VP_EINVAL;
   cudaStreamSynchronize(c->stream);
   for (DevBuf* b : {&c->w_fac, &c->w_q, &c->w_gemm, &c->w_j, &c->w_p, &c->w_tmp, &c->w_tmp2, &c->w_vec, &c->w_split,
-                    &c->w_piv, &c->w_q1, &c->w_q2, &c->w_r, &c->w_p2, &c->w_a, &c->w_b, &c->w_c})
+                    &c->w_piv, &c->w_q1, &c->w_q2, &c->w_r, &c->w_p2, &c->w_a, &c->w_b, &c->w_c, &c->w_l,
+                    &c->w_q_side, &c->w_split_side})
     release(c, *b);
   for (auto& b : c->w_chain) release(c, b);
   dev_free(c, c->status, sizeof(DevStatus));
@@ -539,6 +592,9 @@ int vp_ctx_destroy(vp_ctx* c) {
   cudaFreeHost(c->h_small);
   cudaFreeHost(c->h_smalld);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+  if (c->side) cudaStreamDestroy(c->side);
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
   if (c->owns_stream) cudaStreamDestroy(c->stream);
   delete c;
   return VP_OK;
@@ -737,29 +793,31 @@ int mpo_create_vp(vp_ctx* ctx, const vp_layout* L, int kind, mpo_t** out) {
   if (!ctx || !out || !layout_ok(L)) return fail(ctx, VP_EINVAL, "mpo_create_vp: bad argument");
   const std::vector<int> dims = site_dims(L);
   const double dx = grid_dx(L), dv = grid_dv(L);
+  auto ox = [&](Chain ch) { return xdesc(L) ? reverse_chain(ch) : ch; };
+  auto ov = [&](Chain ch) { return vdesc(L) ? reverse_chain(ch) : ch; };
   Chain c;
   switch (kind) {
     case VP_MPO_DX_CENTERED:
-      c = place2(stencil_chain(L->nx, {{0.0, -0.5 / dx, 0.0, 0.5 / dx, 0.0}}, true), identity_chain(L->nv), dims);
+      c = place2(ox(stencil_chain(L->nx, {{0.0, -0.5 / dx, 0.0, 0.5 / dx, 0.0}}, true)), identity_chain(L->nv), dims);
       break;
     case VP_MPO_DX_FORWARD:
-      c = place2(stencil_chain(L->nx, {{0.0, 0.0, -1.5 / dx, 2.0 / dx, -0.5 / dx}}, true), identity_chain(L->nv),
-                 dims);
+      c = place2(ox(stencil_chain(L->nx, {{0.0, 0.0, -1.5 / dx, 2.0 / dx, -0.5 / dx}}, true)),
+                 identity_chain(L->nv), dims);
       break;
     case VP_MPO_DX_BACKWARD:
-      c = place2(stencil_chain(L->nx, {{0.5 / dx, -2.0 / dx, 1.5 / dx, 0.0, 0.0}}, true), identity_chain(L->nv),
-                 dims);
+      c = place2(ox(stencil_chain(L->nx, {{0.5 / dx, -2.0 / dx, 1.5 / dx, 0.0, 0.0}}, true)),
+                 identity_chain(L->nv), dims);
       break;
     case VP_MPO_DV_ZERO_GRAD:
-      c = place2(identity_chain(L->nx), zero_gradient_chain(L->nv, dv), dims);
+      c = place2(identity_chain(L->nx), ov(zero_gradient_chain(L->nv, dv)), dims);
       break;
     case VP_MPO_DXX: {
       const double s = 1.0 / (dx * dx);
-      c = place2(stencil_chain(L->nx, {{0.0, s, -2.0 * s, s, 0.0}}, true), identity_chain(L->nv), dims);
+      c = place2(ox(stencil_chain(L->nx, {{0.0, s, -2.0 * s, s, 0.0}}, true)), identity_chain(L->nv), dims);
       break;
     }
     case VP_MPO_ADVECTION:
-      c = upwind_operator(L->nx, L->nv, dims, dx, L->vmin, dv);
+      c = upwind_operator(L->nx, L->nv, dims, dx, L->vmin, dv, xdesc(L), vdesc(L));
       break;
     default:
       return fail(ctx, VP_EINVAL, "mpo_create_vp: unknown kind");
@@ -883,6 +941,20 @@ int vp_density(vp_ctx* ctx, const vp_layout* L, const mps_t* f, double* rho_dev)
   return sync_status(ctx);
 }
 
+int vp_gemm(vp_ctx* ctx, int precision, int M, int N, int K, double alpha, const double* A, int lda,
+            const double* B, int ldb, double* C, int ldc) {
+  if (!ctx || M < 0 || N < 0 || K < 0 || (M > 0 && N > 0 && (!C || ldc < N)) ||
+      (M > 0 && N > 0 && K > 0 && (!A || !B || lda < K || ldb < N)) || precision < VP_PREC_FP64 ||
+      precision > VP_PREC_TF32X3)
+    return fail(ctx, VP_EINVAL, "vp_gemm: bad argument");
+  const int p0 = ctx->precision;
+  ctx->precision = precision;
+  const int st = launch_gemm(ctx, M, N, K, alpha, A, lda, B, ldb, C, ldc);
+  ctx->precision = p0;
+  VP_TRY(st);
+  return sync_status(ctx);
+}
+
 int vp_poisson(vp_ctx* ctx, const double* rho, int nx, double dx, double* E, double* we_host) {
   if (!ctx || !rho || !E || nx < 1 || nx > 14 || !(dx > 0)) return fail(ctx, VP_EINVAL, "vp_poisson: bad argument");
   VP_TRY(launch_poisson(ctx, rho, 1 << nx, dx, E, ctx->d_smalld + 8));
@@ -902,6 +974,8 @@ struct vp_sim {
   vp_config cfg{};
   std::vector<int> dims;
   mps_t f, fi, acc, wa, wb, em;
+  mps_t kd, ku, kt;              // derivative and its two terms (levels C4, C5)
+  mpo_t LT;                      // field term alone (level C5)
   Chain U;                       // static upwind part (host copy, for bonds)
   std::vector<DevBuf> Ud;        // device cores of U
   Chain Dv;                      // zero-gradient v derivative chain
@@ -910,6 +984,7 @@ struct vp_sim {
   DevBuf rho, E, evec;
   double t = 0.0;
   Flops flops;
+  std::vector<double> entropy;  // per-bond EE of the last final compression
   vp_ctx* ctxB = nullptr;  // second stream: the f_{i+1} compressions run beside the acc ones
   cudaEvent_t evA = nullptr, evB = nullptr;
 };
@@ -917,8 +992,9 @@ struct vp_sim {
 namespace vp {
 
 // Assemble L(E) = U + diag(E) (x) D_v from the current field MPS.
-static int assemble_operator(vp_sim* s) {
+static int assemble_operator(vp_sim* s, bool with_upwind = true, mpo_t* dst = nullptr) {
   vp_ctx* ctx = s->ctx;
+  mpo_t& L = dst ? *dst : s->L;
   const int n = (int)s->dims.size();
   const mps_t& em = s->em;
   // bonds of the placed field term: E channel x D_v channel
@@ -929,13 +1005,14 @@ static int assemble_operator(vp_sim* s) {
     if (s->dims[k] == 0) ++px; else ++pv;
     tw[k + 1] = em.r[px] * s->Dv.w[pv];
   }
-  std::vector<int> w(n + 1);
+  std::vector<int> w(n + 1), uw(n + 1, 0);
+  if (with_upwind) uw = s->U.w;
   w[0] = w[n] = 1;
-  for (int k = 1; k < n; ++k) w[k] = s->U.w[k] + tw[k];
-  s->L.ctx = ctx;
-  s->L.n = n;
-  s->L.w = w;
-  if ((int)s->L.core.size() != n) s->L.core.assign(n, DevBuf{});
+  for (int k = 1; k < n; ++k) w[k] = uw[k] + tw[k];
+  L.ctx = ctx;
+  L.n = n;
+  L.w = w;
+  if ((int)L.core.size() != n) L.core.assign(n, DevBuf{});
   px = pv = 0;
   for (int k = 0; k < n; ++k) {
     ETermSite e{};
@@ -954,9 +1031,9 @@ static int assemble_operator(vp_sim* s) {
       e.ew = em.r[px];
       ++pv;
     }
-    VP_TRY(reserve(ctx, s->L.core[k], (size_t)w[k] * 4 * w[k + 1]));
-    VP_TRY(launch_assemble_site(ctx, s->Ud[k].p, s->U.w[k], s->U.w[k + 1], e, k == 0, k == n - 1, s->L.core[k].p,
-                                w[k], w[k + 1]));
+    VP_TRY(reserve(ctx, L.core[k], (size_t)w[k] * 4 * w[k + 1]));
+    VP_TRY(launch_assemble_site(ctx, s->Ud[k].p, with_upwind ? s->U.w[k] : 0, with_upwind ? s->U.w[k + 1] : 0, e,
+                                k == 0, k == n - 1, L.core[k].p, w[k], w[k + 1]));
   }
   return VP_OK;
 }
@@ -970,11 +1047,108 @@ static int stage_operator(vp_sim* s, const mps_t* f, double* we_mass) {
   if (we_mass)
     VP_CUDA(ctx, cudaMemcpyAsync(we_mass, ctx->d_smalld + 8, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   mps_free(&s->em);
-  VP_TRY(from_vector(ctx, &s->em, s->lay.nx, s->E.p, 1 << 30, s->cfg.e_tol));
+  const double* Ev = s->E.p;
+  if (xdesc(&s->lay)) {  // field MPS in the site order of the x bits
+    VP_TRY(reserve(ctx, s->evec, (size_t)Nx));
+    VP_TRY(launch_permute_to_sites(ctx, s->E.p, s->lay.nx, 0, VP_SEQ_S2, s->evec.p, 0));
+    Ev = s->evec.p;
+  }
+  VP_TRY(from_vector(ctx, &s->em, s->lay.nx, Ev, s->cfg.e_chi > 0 ? s->cfg.e_chi : 1 << 30, s->cfg.e_tol));
   return assemble_operator(s);
 }
 
+// Compression levels C2..C5 (and a capped field bond): one stream, the
+// schedule spelled out in vp_config.level.
+static int sim_step_levels(vp_sim* s, vp_record* rec) {
+  vp_ctx* ctx = s->ctx;
+  static const double A[3] = {0.5, 0.5, 1.0};
+  static const double B[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
+  static const double Wt[4] = {1.0, 2.0, 2.0, 1.0};
+  const int level = std::max(1, s->cfg.level), chi = s->cfg.chi, big = 1 << 30;
+  const double dt = s->cfg.dt, tol = s->cfg.tol;
+  const mps_t* fi = &s->f;
+  const mps_t* acc = &s->f;
+  std::vector<double> errs(s->f.n, 0.0);
+  g_flops = &s->flops;
+  mpo_t Uview;
+  Uview.ctx = ctx;
+  Uview.n = (int)s->dims.size();
+  Uview.w = s->U.w;
+  for (int i = 0; i < 4; ++i) {
+    VP_TRY(stage_operator(s, fi, i == 0 ? s->ctx->h_smalld + 16 : nullptr));
+    if (level >= 5) {
+      Uview.core = s->Ud;
+      VP_TRY(site_sum_mps(ctx, 0.0, nullptr, 1.0, &Uview, fi, &s->ku));
+      Uview.core.clear();
+      VP_TRY(compress(ctx, &s->ku, chi, tol, nullptr));
+      VP_TRY(assemble_operator(s, false, &s->LT));
+      VP_TRY(site_sum_mps(ctx, 0.0, nullptr, 1.0, &s->LT, fi, &s->kt));
+      VP_TRY(compress(ctx, &s->kt, chi, tol, nullptr));
+      VP_TRY(site_sum_mps(ctx, 1.0, &s->ku, 1.0, nullptr, &s->kt, &s->kd));
+      VP_TRY(compress(ctx, &s->kd, chi, tol, nullptr));
+    } else {
+      VP_TRY(site_sum_mps(ctx, 0.0, nullptr, 1.0, &s->L, fi, &s->kd));
+      if (level >= 4) VP_TRY(compress(ctx, &s->kd, chi, tol, nullptr));
+    }
+    if (level >= 3) {
+      if (i == 0) {
+        VP_TRY(mps_copy(ctx, &s->kd, &s->acc));
+      } else {
+        VP_TRY(site_sum_mps(ctx, 1.0, &s->acc, Wt[i], nullptr, &s->kd, &s->wa));
+        VP_TRY(compress(ctx, &s->wa, chi, tol, nullptr));
+        std::swap(s->acc, s->wa);
+      }
+    } else if (i < 3) {
+      VP_TRY(site_sum_mps(ctx, 1.0, acc, B[i] * dt, nullptr, &s->kd, &s->wa));
+      VP_TRY(compress(ctx, &s->wa, big, tol, nullptr));
+      std::swap(s->acc, s->wa);
+      acc = &s->acc;
+    }
+    if (i < 3) {
+      VP_TRY(site_sum_mps(ctx, 1.0, &s->f, A[i] * dt, nullptr, &s->kd, &s->wb));
+      VP_TRY(compress(ctx, &s->wb, level >= 2 ? chi : big, tol, nullptr));
+      std::swap(s->fi, s->wb);
+      fi = &s->fi;
+    }
+  }
+  if (level >= 3)
+    VP_TRY(site_sum_mps(ctx, 1.0, &s->f, dt / 6.0, nullptr, &s->acc, &s->wa));
+  else
+    VP_TRY(site_sum_mps(ctx, 1.0, acc, B[3] * dt, nullptr, &s->kd, &s->wa));
+  s->entropy.assign(std::max(1, s->f.n - 1), 0.0);
+  g_entropy = s->entropy.data();
+  const int stc = compress(ctx, &s->wa, chi, tol, errs.data());
+  g_entropy = nullptr;
+  VP_TRY(stc);
+  std::swap(s->f, s->wa);
+  g_flops = nullptr;
+  VP_TRY(sync_status(ctx));
+  const double we = s->ctx->h_smalld[16], mass = s->ctx->h_smalld[17];
+  if (!std::isfinite(we)) return fail(ctx, VP_ENUMERIC, "non-finite field energy");
+  if (rec) {
+    rec->t = s->t;
+    rec->field_energy = we;
+    rec->mass = mass;
+    rec->max_bond = *std::max_element(s->f.r.begin(), s->f.r.end());
+    rec->trunc_err = errs.empty() ? 0.0 : *std::max_element(errs.begin(), errs.end());
+  }
+  s->t += dt;
+  return VP_OK;
+}
+
+static int sim_step_impl(vp_sim* s, vp_record* rec);
+
+// The contraction precision applies to this sim's steps only.
 static int sim_step(vp_sim* s, vp_record* rec) {
+  const int p0 = s->ctx->precision;
+  s->ctx->precision = s->cfg.precision;
+  if (s->ctxB) s->ctxB->precision = s->cfg.precision;
+  const int st = s->cfg.level > 1 ? sim_step_levels(s, rec) : sim_step_impl(s, rec);
+  s->ctx->precision = p0;
+  return st;
+}
+
+static int sim_step_impl(vp_sim* s, vp_record* rec) {
   vp_ctx* ctx = s->ctx;
   static const double A[3] = {0.5, 0.5, 1.0};
   static const double B[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
@@ -1033,7 +1207,11 @@ static int sim_step(vp_sim* s, vp_record* rec) {
       fi = &s->fi;
     } else {
       VP_TRY(site_sum_mps(ctx, 1.0, acc, B[3] * dt, &s->L, fi, &s->wa));
-      VP_TRY(compress(ctx, &s->wa, s->cfg.chi, s->cfg.tol, errs.data()));
+      s->entropy.assign(std::max(1, s->f.n - 1), 0.0);
+      g_entropy = s->entropy.data();
+      const int stc = compress(ctx, &s->wa, s->cfg.chi, s->cfg.tol, errs.data());
+      g_entropy = nullptr;
+      VP_TRY(stc);
       std::swap(s->f, s->wa);
     }
   }
@@ -1080,7 +1258,8 @@ static void sim_free(vp_sim* s) {
   }
   if (s->evA) cudaEventDestroy(s->evA);
   if (s->evB) cudaEventDestroy(s->evB);
-  for (mps_t* m : {&s->f, &s->fi, &s->acc, &s->wa, &s->wb, &s->em}) mps_free(m);
+  for (mps_t* m : {&s->f, &s->fi, &s->acc, &s->wa, &s->wb, &s->em, &s->kd, &s->ku, &s->kt}) mps_free(m);
+  for (auto& b : s->LT.core) release(ctx, b);
   for (auto& b : s->Ud) release(ctx, b);
   for (auto& b : s->Dvd) release(ctx, b);
   for (auto& b : s->L.core) release(ctx, b);
@@ -1104,17 +1283,20 @@ int vp_sim_create(vp_ctx* ctx, const vp_layout* L, const vp_config* cfg, const m
   s->lay = *L;
   s->cfg = *cfg;
   s->dims = site_dims(L);
-  for (mps_t* m : {&s->f, &s->fi, &s->acc, &s->wa, &s->wb, &s->em}) mps_init(ctx, m, 0);
+  for (mps_t* m : {&s->f, &s->fi, &s->acc, &s->wa, &s->wb, &s->em, &s->kd, &s->ku, &s->kt}) mps_init(ctx, m, 0);
   int st = mps_copy(ctx, f0, &s->f);
   if (st == VP_OK) {
-    s->U = upwind_operator(L->nx, L->nv, s->dims, dx, L->vmin, grid_dv(L));
+    s->U = upwind_operator(L->nx, L->nv, s->dims, dx, L->vmin, grid_dv(L), xdesc(L), vdesc(L));
     s->Dv = zero_gradient_chain(L->nv, grid_dv(L));
+    if (vdesc(L)) s->Dv = reverse_chain(s->Dv);
     st = upload_chain(ctx, s->U, s->Ud);
   }
   if (st == VP_OK) st = upload_chain(ctx, s->Dv, s->Dvd);
   if (st == VP_OK) st = reserve(ctx, s->rho, (size_t)1 << L->nx);
   if (st == VP_OK) st = reserve(ctx, s->E, (size_t)1 << L->nx);
-  if (st == VP_OK && cfg->streams != 1) {
+  if (cfg->level < 0 || cfg->level > 5 || cfg->e_chi < 0 || cfg->precision < VP_PREC_FP64 || cfg->precision > VP_PREC_TF32X3)
+    st = fail(ctx, VP_EINVAL, "vp_sim_create: bad level/e_chi/precision");
+  if (st == VP_OK && cfg->streams != 1 && cfg->level <= 1) {
     s->ctxB = ctx_child(ctx);
     if (s->ctxB) {
       s->fi.ctx = s->wb.ctx = s->ctxB;
@@ -1148,6 +1330,12 @@ int vp_step(vp_sim* s, int nsteps, vp_record* records) {
 
 const mps_t* vp_sim_state(const vp_sim* s) { return s ? &s->f : nullptr; }
 
+int vp_sim_entropy(const vp_sim* s, double* out) {
+  if (!s || !out) return VP_EINVAL;
+  for (int k = 0; k + 1 < s->f.n; ++k) out[k] = k < (int)s->entropy.size() ? s->entropy[k] : 0.0;
+  return VP_OK;
+}
+
 double vp_sim_flops(const vp_sim* s) {
   return s ? s->flops.qr + s->flops.formq + s->flops.gemm + s->flops.jacobi : 0.0;
 }
@@ -1176,8 +1364,9 @@ extern "C" int mpo_create_vlasov(vp_ctx* ctx, const vp_layout* L, const double* 
   s.lay = *L;
   s.dims = site_dims(L);
   for (mps_t* m : {&s.f, &s.fi, &s.acc, &s.wa, &s.wb, &s.em}) mps_init(ctx, m, 0);
-  s.U = upwind_operator(L->nx, L->nv, s.dims, grid_dx(L), L->vmin, grid_dv(L));
+  s.U = upwind_operator(L->nx, L->nv, s.dims, grid_dx(L), L->vmin, grid_dv(L), xdesc(L), vdesc(L));
   s.Dv = zero_gradient_chain(L->nv, grid_dv(L));
+  if (vdesc(L)) s.Dv = reverse_chain(s.Dv);
   int st = upload_chain(ctx, s.U, s.Ud);
   if (st == VP_OK) st = upload_chain(ctx, s.Dv, s.Dvd);
   if (st == VP_OK) st = reserve(ctx, s.E, (size_t)1 << L->nx);
@@ -1185,7 +1374,11 @@ extern "C" int mpo_create_vlasov(vp_ctx* ctx, const vp_layout* L, const double* 
     cudaError_t e = cudaMemcpyAsync(s.E.p, E_host, sizeof(double) << L->nx, cudaMemcpyHostToDevice, ctx->stream);
     if (e != cudaSuccess) st = cuda_fail(ctx, e, "mpo_create_vlasov");
   }
-  if (st == VP_OK) st = from_vector(ctx, &s.em, L->nx, s.E.p, 1 << 30, e_tol);
+  if (st == VP_OK && xdesc(L)) {
+    st = reserve(ctx, s.evec, (size_t)1 << L->nx);
+    if (st == VP_OK) st = launch_permute_to_sites(ctx, s.E.p, L->nx, 0, VP_SEQ_S2, s.evec.p, 0);
+  }
+  if (st == VP_OK) st = from_vector(ctx, &s.em, L->nx, xdesc(L) ? s.evec.p : s.E.p, 1 << 30, e_tol);
   if (st == VP_OK) st = assemble_operator(&s);
   if (st == VP_OK) st = sync_status(ctx);
   if (st == VP_OK) {

@@ -40,8 +40,11 @@ struct vp_ctx {
   int num_sms = 0;
   int cluster_size = 0;  // CTAs per cluster for the cluster-resident kernels (16, or 8)
   int coop_cap = 0;      // max blocks of a cooperative grid launch (0: one per SM)
+  int precision = 0;     // VP_PREC_* of the GEMM contractions (factorisations stay FP64)
   bool owns_stream = false;
   std::vector<vp_ctx*> children;  // contexts created for concurrent work
+  cudaStream_t side = nullptr;     // side stream: Q formation beside the Jacobi SVD
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   cudaStream_t stream = nullptr;
   vp_alloc_fn alloc = nullptr;
   vp_free_fn freef = nullptr;
@@ -62,7 +65,10 @@ struct vp_ctx {
   int64_t prof_launches[VP_K_COUNT] = {};
   // workspaces
   vp::DevBuf w_fac, w_q, w_gemm, w_j, w_p, w_tmp, w_tmp2, w_vec, w_split;
-  vp::DevBuf w_piv, w_q1, w_q2, w_r, w_p2, w_a, w_b, w_c;  // preconditioned SVD
+  vp::DevBuf w_piv, w_q1, w_q2, w_r, w_p2, w_a, w_b, w_c, w_l;  // preconditioned SVD
+  vp::DevBuf w_tca, w_tcb;            // packed operands of the tensor-core contractions
+  vp::DevBuf w_q_side, w_split_side;  // scratch of the side-stream phase
+  vp::DevBuf w_tca_side, w_tcb_side;
   std::vector<vp::DevBuf> w_chain;
 };
 
@@ -133,6 +139,17 @@ int launch_lower_from_upper(vp_ctx* ctx, const double* Rcm, int q, double* L);
 int launch_scatter(vp_ctx* ctx, const double* Y, int rows, int cols_n, const int* piv, int cols, double* out);
 int launch_svd_outputs_wide(vp_ctx* ctx, const double* X, const double* J, int b, int r, const int* perm,
                             double* Urows, double* Wv);
+// Operand of a tensor-core contraction as (row, k) -> value: kind 0
+// p[r * ld + k]; kind 1 p[k * ld + r]; kind 2 the upper triangle of a
+// column-major factor, r <= k ? p[k * ld + r] : 0.
+struct TcOperand {
+  const double* p;
+  int ld;
+  int kind;
+};
+// C (M x N) = alpha * A (M x K) * B^T with B given as (N x K) operand, on the
+// tensor cores in the context's reduced-precision mode (tcgemm.cu).
+int launch_tc_gemm(vp_ctx* ctx, int M, int N, int K, double alpha, TcOperand a, TcOperand b, double* C, int ldc);
 // C = alpha * triu(A_colmajor) (M x K) * B: the R factor read in place.
 int launch_gemm_r(vp_ctx* ctx, int M, int N, int K, const double* Acm, int lda, const double* B,
                   int ldb, double* C, int ldc);

@@ -303,31 +303,31 @@ struct BTransposed {
   __device__ double operator()(int k, int n) const { return B[(size_t)n * ldb + k]; }
 };
 
-template <class ALoad, class BLoad>
+template <class ALoad, class BLoad, class T = double>
 __global__ void __launch_bounds__(256) k_gemm(int M, int N, int K, double alpha, ALoad a, BLoad bl,
                                               double* __restrict__ C, int ldc, int kslice, size_t slice_stride) {
-  __shared__ double As[16][64 + 1];
-  __shared__ double Bs[16][64];
+  __shared__ T As[16][64 + 1];
+  __shared__ T Bs[16][64];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const int row0 = blockIdx.x * 64, col0 = blockIdx.y * 64;
   const int kbeg = blockIdx.z * kslice, kend = min(K, kbeg + kslice);
   C += blockIdx.z * slice_stride;
-  double acc[4][4] = {};
+  T acc[4][4] = {};
   for (int k0 = kbeg; k0 < kend; k0 += 16) {
     for (int e = threadIdx.x; e < 64 * 16; e += 256) {
       const int r = e / 16, kk = e % 16;
       const int gr = row0 + r, gk = k0 + kk;
-      As[kk][r] = (gr < M && gk < kend) ? a(gr, gk) : 0.0;
+      As[kk][r] = (T)((gr < M && gk < kend) ? a(gr, gk) : 0.0);
     }
     for (int e = threadIdx.x; e < 16 * 64; e += 256) {
       const int kk = e / 64, c = e % 64;
       const int gk = k0 + kk, gc = col0 + c;
-      Bs[kk][c] = (gk < kend && gc < N) ? bl(gk, gc) : 0.0;
+      Bs[kk][c] = (T)((gk < kend && gc < N) ? bl(gk, gc) : 0.0);
     }
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < 16; ++kk) {
-      double av[4], bv[4];
+      T av[4], bv[4];
 #pragma unroll
       for (int i = 0; i < 4; ++i) av[i] = As[kk][ty + 16 * i];
 #pragma unroll
@@ -346,7 +346,7 @@ __global__ void __launch_bounds__(256) k_gemm(int M, int N, int K, double alpha,
 #pragma unroll
     for (int jj = 0; jj < 4; ++jj) {
       const int c = col0 + tx + 16 * jj;
-      if (c < N) C[(size_t)r * ldc + c] = alpha * acc[i][jj];
+      if (c < N) C[(size_t)r * ldc + c] = alpha * (double)acc[i][jj];
     }
   }
 }
@@ -362,19 +362,28 @@ __global__ void k_sum_slices(const double* __restrict__ P, int M, int N, int sli
   }
 }
 
+// The same operands as (row, k) maps for the tensor-core path.
+static TcOperand tc_a(const ARowMajor& a) { return {a.A, a.lda, 0}; }
+static TcOperand tc_a(const AUpperColMajor& a) { return {a.A, a.lda, 2}; }
+static TcOperand tc_b(const BRowMajor& b) { return {b.B, b.ldb, 1}; }
+static TcOperand tc_b(const BTransposed& b) { return {b.B, b.ldb, 0}; }
+
 // Split K when the output has too few 64 x 64 tiles to occupy the SMs.
 template <class ALoad, class BLoad>
 static int gemm_dispatch(vp_ctx* ctx, int M, int N, int K, double alpha, ALoad a, BLoad b, double* C, int ldc,
                          const char* what) {
   if (M <= 0 || N <= 0) return VP_OK;
+  if (ctx->precision >= VP_PREC_TF32 && K > 0) return launch_tc_gemm(ctx, M, N, K, alpha, tc_a(a), tc_b(b), C, ldc);
   dim3 grid((M + 63) / 64, (N + 63) / 64, 1);
   if (grid.y > 65535) return fail(ctx, VP_ECAPACITY, "gemm: N too large");
   const int tiles = (int)(grid.x * grid.y);
   int slices = 1;
   if (tiles < ctx->num_sms && K >= 128) slices = std::min(std::min(2 * ctx->num_sms / tiles, K / 64), 32);
+  // FP32 contraction mode: inputs rounded to FP32, FP32 FMA and accumulation
+  auto kern = ctx->precision == VP_PREC_FP32_CONTRACT ? k_gemm<ALoad, BLoad, float> : k_gemm<ALoad, BLoad, double>;
   if (slices <= 1) {
     ctx->launches++;
-    k_gemm<ALoad, BLoad><<<grid, 256, 0, ctx->stream>>>(M, N, K, alpha, a, b, C, ldc, K, 0);
+    kern<<<grid, 256, 0, ctx->stream>>>(M, N, K, alpha, a, b, C, ldc, K, 0);
     return check_launch(ctx, what);
   }
   const int kslice = ((K + slices - 1) / slices + 15) / 16 * 16;
@@ -383,7 +392,7 @@ static int gemm_dispatch(vp_ctx* ctx, int M, int N, int K, double alpha, ALoad a
   VP_TRY(reserve(ctx, ctx->w_split, stride * slices));
   grid.z = slices;
   ctx->launches += 2;
-  k_gemm<ALoad, BLoad><<<grid, 256, 0, ctx->stream>>>(M, N, K, alpha, a, b, ctx->w_split.p, N, kslice, stride);
+  kern<<<grid, 256, 0, ctx->stream>>>(M, N, K, alpha, a, b, ctx->w_split.p, N, kslice, stride);
   VP_TRY(check_launch(ctx, what));
   const int blocks = (int)std::min<size_t>((stride + 255) / 256, (size_t)ctx->num_sms * 8);
   k_sum_slices<<<blocks, 256, 0, ctx->stream>>>(ctx->w_split.p, M, N, slices, stride, C, ldc);
@@ -413,6 +422,18 @@ int launch_gemm_r(vp_ctx* ctx, int M, int N, int K, const double* Acm, int lda, 
 // barrier per round.
 __device__ __forceinline__ int rr_index(int pos, int round, int bp) {
   return pos == 0 ? 0 : 1 + (pos - 1 + round) % (bp - 1);
+}
+
+// Plane rotation that zeroes the Gram entry gamma of a row pair with squared
+// norms alpha, beta: tan(theta) = t is the smaller root of
+// t^2 + 2 t d / gamma - 1 = 0, d = (beta - alpha) / 2, written without the
+// quotient d / gamma as t = sign(d) gamma / (|d| + sqrt(d^2 + gamma^2)); then
+// cos = 1 / sqrt(1 + t^2), sin = t cos.  Three long-latency operations.
+__device__ __forceinline__ void jacobi_rotation(double al, double be, double ga, double& t, double& cs, double& sn) {
+  const double d = 0.5 * (be - al);
+  t = copysign(1.0, d) * ga / (fabs(d) + sqrt(fma(d, d, ga * ga)));
+  cs = rsqrt(fma(t, t, 1.0));
+  sn = cs * t;
 }
 
 __global__ void __launch_bounds__(kThreads) k_jacobi_rows(double* X, int b, int c, double* J, double eps,
@@ -449,21 +470,22 @@ __global__ void __launch_bounds__(kThreads) k_jacobi_rows(double* X, int b, int 
         be = warp_sum(be);
         ga = warp_sum(ga);
         if (!(al > 0.0 && be > 0.0)) continue;
-        if (!(fabs(ga) > eps * sqrt(al) * sqrt(be))) continue;
-        const double zeta = (be - al) / (2.0 * ga);
-        const double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(fma(zeta, zeta, 1.0)));
-        const double cs = 1.0 / sqrt(fma(t, t, 1.0)), sn = cs * t;
+        if (!(ga * ga > eps * eps * al * be)) continue;
+        double t, cs, sn;
+        jacobi_rotation(al, be, ga, t, cs, sn);
         for (int q = lane; q < c; q += 32) {
           const double u = __ldcg(xi + q), v = __ldcg(xj + q);
           __stcg(xi + q, cs * u - sn * v);
           __stcg(xj + q, sn * u + cs * v);
         }
-        double* ji = J + (size_t)i * b;
-        double* jj = J + (size_t)j * b;
-        for (int q = lane; q < b; q += 32) {
-          const double u = __ldcg(ji + q), v = __ldcg(jj + q);
-          __stcg(ji + q, cs * u - sn * v);
-          __stcg(jj + q, sn * u + cs * v);
+        if (J) {
+          double* ji = J + (size_t)i * b;
+          double* jj = J + (size_t)j * b;
+          for (int q = lane; q < b; q += 32) {
+            const double u = __ldcg(ji + q), v = __ldcg(jj + q);
+            __stcg(ji + q, cs * u - sn * v);
+            __stcg(jj + q, sn * u + cs * v);
+          }
         }
         if (lane == 0) atomicAdd(cnt, 1u);
       }
@@ -487,31 +509,42 @@ __global__ void __launch_bounds__(kThreads) k_jacobi_rows(double* X, int b, int 
 // contiguous), one CTA per SM.  A pair is processed by one warp through
 // DSMEM pointers; rounds are separated by the hardware cluster barrier
 // (about 0.2 us on GB300, against 2 us for a grid-wide software barrier).
-constexpr int kJacRegs = 16;  // row elements per lane kept in registers (row length <= 512)
-
 __global__ void __launch_bounds__(kThreads) k_jacobi_cluster(double* X, int b, int c, double* J, double eps,
                                                              int max_sweeps, DevStatus* st) {
   cg::cluster_group cl = cg::this_cluster();
   extern __shared__ double sm[];
   const int CS = (int)cl.num_blocks(), rank = (int)cl.block_rank();
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int rpc = (b + CS - 1) / CS, stride = c + b;
-  unsigned* cnt = reinterpret_cast<unsigned*>(sm + (size_t)rpc * stride);
+  const int jb = J ? b : 0;  // accumulate the rotations only when J is wanted
+  const int rpc = (b + CS - 1) / CS, stride = c + jb;
+  double* nrm = sm + (size_t)rpc * stride;                   // squared row norms, one per local row
+  unsigned* cnt = reinterpret_cast<unsigned*>(nrm + rpc);
   for (int sl = 0; sl < rpc; ++sl) {
     const int x = sl * CS + rank;
     if (x >= b) break;
     double* row = sm + (size_t)sl * stride;
     for (int q = tid; q < c; q += kThreads) row[q] = X[(size_t)x * c + q];
-    for (int q = tid; q < b; q += kThreads) row[c + q] = (q == x) ? 1.0 : 0.0;
+    for (int q = tid; q < jb; q += kThreads) row[c + q] = (q == x) ? 1.0 : 0.0;
   }
   if (tid < 4) cnt[tid] = 0u;
-  cl.sync();
   unsigned* c0 = cl.map_shared_rank(cnt, 0);
   const int bp = b + (b & 1), npairs = bp / 2, rounds = bp - 1;
   int sweep = 0;
   bool converged = false;
   for (; sweep < max_sweeps; ++sweep) {
+    // exact squared norms of the local rows once per sweep; a rotation then
+    // updates them as alpha' = alpha - t gamma, beta' = beta + t gamma
+    __syncthreads();
+    for (int sl = warp; sl < rpc; sl += kWarps) {
+      if (sl * CS + rank >= b) break;
+      const double* row = sm + (size_t)sl * stride;
+      double a = 0.0;
+      for (int q = lane; q < c; q += 32) a = fma(row[q], row[q], a);
+      a = warp_sum(a);
+      if (lane == 0) nrm[sl] = a;
+    }
     if (rank == 0 && tid == 0) cnt[(sweep + 1) % 3] = 0u;
+    cl.sync();
     unsigned rotated = 0;
     for (int round = 0; round < rounds; ++round) {
       for (int pr = rank + warp * CS; pr < npairs; pr += CS * kWarps) {
@@ -524,58 +557,24 @@ __global__ void __launch_bounds__(kThreads) k_jacobi_cluster(double* X, int b, i
         }
         double* xi = cl.map_shared_rank(sm + (size_t)(i / CS) * stride, i % CS);
         double* xj = cl.map_shared_rank(sm + (size_t)(j / CS) * stride, j % CS);
-        if (stride <= 32 * kJacRegs) {
-          // both rows in registers: one DSMEM read and one write per element
-          double ri[kJacRegs], rj[kJacRegs];
-          double al = 0.0, be = 0.0, ga = 0.0;
-#pragma unroll
-          for (int e = 0; e < kJacRegs; ++e) {
-            const int q = lane + 32 * e;
-            ri[e] = q < stride ? xi[q] : 0.0;
-            rj[e] = q < stride ? xj[q] : 0.0;
-            if (q < c) {
-              al = fma(ri[e], ri[e], al);
-              be = fma(rj[e], rj[e], be);
-              ga = fma(ri[e], rj[e], ga);
-            }
-          }
-          al = warp_sum(al);
-          be = warp_sum(be);
-          ga = warp_sum(ga);
-          if (!(al > 0.0 && be > 0.0)) continue;
-          if (!(fabs(ga) > eps * sqrt(al) * sqrt(be))) continue;
-          const double zeta = (be - al) / (2.0 * ga);
-          const double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(fma(zeta, zeta, 1.0)));
-          const double cs = 1.0 / sqrt(fma(t, t, 1.0)), sn = cs * t;
-#pragma unroll
-          for (int e = 0; e < kJacRegs; ++e) {
-            const int q = lane + 32 * e;
-            if (q < stride) {
-              xi[q] = cs * ri[e] - sn * rj[e];
-              xj[q] = sn * ri[e] + cs * rj[e];
-            }
-          }
-        } else {
-          double al = 0.0, be = 0.0, ga = 0.0;
-          for (int q = lane; q < c; q += 32) {
-            const double u = xi[q], v = xj[q];
-            al = fma(u, u, al);
-            be = fma(v, v, be);
-            ga = fma(u, v, ga);
-          }
-          al = warp_sum(al);
-          be = warp_sum(be);
-          ga = warp_sum(ga);
-          if (!(al > 0.0 && be > 0.0)) continue;
-          if (!(fabs(ga) > eps * sqrt(al) * sqrt(be))) continue;
-          const double zeta = (be - al) / (2.0 * ga);
-          const double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(fma(zeta, zeta, 1.0)));
-          const double cs = 1.0 / sqrt(fma(t, t, 1.0)), sn = cs * t;
-          for (int q = lane; q < stride; q += 32) {
-            const double u = xi[q], v = xj[q];
-            xi[q] = cs * u - sn * v;
-            xj[q] = sn * u + cs * v;
-          }
+        double* ni = cl.map_shared_rank(nrm + i / CS, i % CS);
+        double* nj = cl.map_shared_rank(nrm + j / CS, j % CS);
+        const double al = *ni, be = *nj;
+        double ga = 0.0;
+        for (int q = lane; q < c; q += 32) ga = fma(xi[q], xj[q], ga);
+        ga = warp_sum(ga);
+        if (!(al > 0.0 && be > 0.0)) continue;
+        if (!(ga * ga > eps * eps * al * be)) continue;
+        double t, cs, sn;
+        jacobi_rotation(al, be, ga, t, cs, sn);
+        for (int q = lane; q < stride; q += 32) {
+          const double u = xi[q], v = xj[q];
+          xi[q] = cs * u - sn * v;
+          xj[q] = sn * u + cs * v;
+        }
+        if (lane == 0) {
+          *ni = fma(-t, ga, al);
+          *nj = fma(t, ga, be);
         }
         ++rotated;
       }
@@ -592,7 +591,7 @@ __global__ void __launch_bounds__(kThreads) k_jacobi_cluster(double* X, int b, i
     if (x >= b) break;
     const double* row = sm + (size_t)sl * stride;
     for (int q = tid; q < c; q += kThreads) X[(size_t)x * c + q] = row[q];
-    for (int q = tid; q < b; q += kThreads) J[(size_t)x * b + q] = row[c + q];
+    for (int q = tid; q < jb; q += kThreads) J[(size_t)x * b + q] = row[c + q];
   }
   if (rank == 0 && tid == 0) {
     st->pad2 = sweep + 1;
@@ -630,18 +629,18 @@ int probe_cluster_size() {
   return 0;
 }
 
-static size_t cluster_jacobi_smem(int b, int c, int CS) {
+static size_t cluster_jacobi_smem(int b, int c, int CS, bool withJ) {
   const size_t rpc = (size_t)(b + CS - 1) / CS;
-  return rpc * (size_t)(c + b) * sizeof(double) + 4 * sizeof(unsigned);
+  return rpc * (size_t)(c + (withJ ? b : 0) + 1) * sizeof(double) + 4 * sizeof(unsigned);
 }
 
 int launch_jacobi_rows(vp_ctx* ctx, double* X, int b, int c, double* J) {
   if (b <= 0) return VP_OK;
   const int CS = ctx->cluster_size;
-  if (CS > 0 && b > 1 && cluster_jacobi_smem(b, c, CS) <= 200 * 1024) {
+  if (CS > 0 && b > 1 && cluster_jacobi_smem(b, c, CS, J != nullptr) <= 200 * 1024) {
     static bool attr_done = false;
     // at least 120 KB per CTA, so no two CTAs of the cluster share an SM
-    const size_t smem = std::max<size_t>(cluster_jacobi_smem(b, c, CS), 120 * 1024);
+    const size_t smem = std::max<size_t>(cluster_jacobi_smem(b, c, CS, J != nullptr), 120 * 1024);
     if (!attr_done) {
       VP_CUDA(ctx, cudaFuncSetAttribute(k_jacobi_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
       VP_CUDA(ctx, cudaFuncSetAttribute(k_jacobi_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
@@ -665,9 +664,11 @@ int launch_jacobi_rows(vp_ctx* ctx, double* X, int b, int c, double* J) {
     VP_CUDA(ctx, cudaLaunchKernelEx(&cfg, k_jacobi_cluster, X, b, c, J, eps, max_sweeps, ctx->status));
     return VP_OK;
   }
-  ctx->launches++;
-  k_identity<<<std::min(1024, (b * b + 255) / 256 + 1), 256, 0, ctx->stream>>>(J, b);
-  VP_TRY(check_launch(ctx, "identity"));
+  if (J) {
+    ctx->launches++;
+    k_identity<<<std::min(1024, (b * b + 255) / 256 + 1), 256, 0, ctx->stream>>>(J, b);
+    VP_TRY(check_launch(ctx, "identity"));
+  }
   if (b == 1) return VP_OK;
   const int npairs = (b + 1) / 2;
   int blocks = std::min(ctx->num_sms, std::max(1, (npairs + kWarps - 1) / kWarps));
@@ -738,8 +739,18 @@ __global__ void k_select(const double* __restrict__ X, int b, int c, int chi, do
       if (r < 1) r = 1;
       err = sqrt(tail[r] / nrm2);
     }
+    // entanglement entropy of the kept values (main text, EE equation):
+    // -sum p log2 p with p_i = s_i^2 / sum_{kept} s^2
+    double ee = 0.0;
+    const double kept2 = tail[0] - tail[r];
+    if (kept2 > 0.0)
+      for (int q = 0; q < r; ++q) {
+        const double pq = sigma[q] * sigma[q] / kept2;
+        if (pq > 0.0) ee -= pq * log2(pq);
+      }
     *d_rank = r;
-    *d_err = err;
+    d_err[0] = err;
+    d_err[1] = ee;
   }
 }
 
@@ -757,7 +768,7 @@ int launch_select(vp_ctx* ctx, const double* X, int b, int c, int chi, double to
 __global__ void k_svd_outputs(const double* __restrict__ X, const double* __restrict__ J, int b, int c, int r,
                               const int* __restrict__ perm, const double* __restrict__ sigma, double* Vt,
                               double* W) {
-  const size_t nv = (size_t)r * c, nw = (size_t)b * r;
+  const size_t nv = (size_t)r * c, nw = J ? (size_t)b * r : 0;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < nv + nw; e += (size_t)gridDim.x * blockDim.x) {
     if (e < nv) {
       const int t = (int)(e / c), q = (int)(e % c);

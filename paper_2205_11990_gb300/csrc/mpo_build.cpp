@@ -133,6 +133,22 @@ Chain identity_chain(int L) {
   return c;
 }
 
+Chain reverse_chain(const Chain& a) {
+  const int L = (int)a.core.size();
+  std::vector<int> w(L + 1);
+  for (int k = 0; k <= L; ++k) w[k] = a.w[L - k];
+  Chain c;
+  c.alloc(w);
+  for (int k = 0; k < L; ++k) {
+    const int src = L - 1 - k;
+    const int al = a.w[src], ar = a.w[src + 1];
+    for (int l = 0; l < al; ++l)
+      for (int r = 0; r < ar; ++r)
+        for (int oi = 0; oi < 4; ++oi) c.core[k][((size_t)r * 4 + oi) * al + l] = a.core[src][((size_t)l * 4 + oi) * ar + r];
+  }
+  return c;
+}
+
 Chain scaled(const Chain& a, double s) {
   Chain c = a;
   for (double& x : c.core[0]) x *= s;
@@ -205,16 +221,19 @@ Chain chain_sum(const Chain& a, const Chain& b) {
   return c;
 }
 
-Chain upwind_operator(int nx, int nv, const std::vector<int>& sitedim, double dx, double vmin, double dv) {
+Chain upwind_operator(int nx, int nv, const std::vector<int>& sitedim, double dx, double vmin, double dv,
+                      bool xdesc, bool vdesc) {
   // v > 0: backward stencil (3 f_n - 4 f_{n-1} + f_{n-2}) / (2 dx);
   // v < 0: forward stencil (-3 f_n + 4 f_{n+1} - f_{n+2}) / (2 dx)
   const std::vector<double> cb = {0.5 / dx, -2.0 / dx, 1.5 / dx, 0.0, 0.0};
   const std::vector<double> cf = {0.0, 0.0, -1.5 / dx, 2.0 / dx, -0.5 / dx};
-  bool seq = true;
+  bool seq = !xdesc && !vdesc;
   for (int k = 0; k < (int)sitedim.size(); ++k) seq = seq && (sitedim[k] == (k < nx ? 0 : 1));
   if (!seq) {
-    Chain b = place2(stencil_chain(nx, {cb}, true), scaled(velocity_chain(nv, vmin, dv, +1), -1.0), sitedim);
-    Chain f = place2(stencil_chain(nx, {cf}, true), scaled(velocity_chain(nv, vmin, dv, -1), -1.0), sitedim);
+    auto ox = [&](Chain c) { return xdesc ? reverse_chain(c) : c; };
+    auto ov = [&](Chain c) { return vdesc ? reverse_chain(c) : c; };
+    Chain b = place2(ox(stencil_chain(nx, {cb}, true)), ov(scaled(velocity_chain(nv, vmin, dv, +1), -1.0)), sitedim);
+    Chain f = place2(ox(stencil_chain(nx, {cf}, true)), ov(scaled(velocity_chain(nv, vmin, dv, -1), -1.0)), sitedim);
     return chain_sum(b, f);
   }
   // Sequential sites: the two stencils share the x carry channels and end on

@@ -34,13 +34,17 @@ Chain velocity_chain(int L, double vmin, double dv, int which);
 
 // Upwind advection -v+ D_b^x - v- D_f^x on the full site chain.
 // sitemap[k] = 0 for an x bit, 1 for a v bit (bits in order).
-Chain upwind_operator(int nx, int nv, const std::vector<int>& sitedim, double dx, double vmin, double dv);
+Chain upwind_operator(int nx, int nv, const std::vector<int>& sitedim, double dx, double vmin, double dv,
+                      bool xdesc = false, bool vdesc = false);
 
 // Generic placement of per-dimension chains on the site order (tensor
 // product; bonds multiply, dimension 0 index major).
 Chain place2(const Chain& X, const Chain& V, const std::vector<int>& sitedim);
 Chain chain_sum(const Chain& a, const Chain& b);
 Chain identity_chain(int L);
+// The same operator with its sites in the opposite order (core k <- core L-1-k,
+// bonds exchanged): for a dimension whose bits appear fine to coarse.
+Chain reverse_chain(const Chain& a);
 Chain scaled(const Chain& a, double s);
 
 }  // namespace vp

@@ -105,8 +105,16 @@ int launch_scale(vp_ctx* ctx, double* x, size_t n, double s) {
 
 // Site-ordered index <-> (ix, iv).  Site order: SEQ = x bits then v bits;
 // INTERLEAVED = x0 v0 x1 v1 ... with leftover bits of the longer dimension.
+__device__ __forceinline__ size_t bitrev_n(size_t x, int n) { return n > 0 ? __brevll(x) >> (64 - n) : 0; }
+
 __device__ __forceinline__ size_t site_to_grid(size_t s, int nx, int nv, int mapping) {
   if (mapping == VP_SEQ) return s;  // already [ix][iv]
+  if (mapping == VP_SEQ_S2 || mapping == VP_SEQ_S3) {
+    size_t ix = s >> nv, iv = s & ((size_t(1) << nv) - 1);
+    if (mapping == VP_SEQ_S2) ix = bitrev_n(ix, nx);  // x bits fine to coarse
+    else iv = bitrev_n(iv, nv);                        // v bits fine to coarse
+    return (ix << nv) | iv;
+  }
   const int n = nx + nv;
   size_t ix = 0, iv = 0;
   int site = 0;

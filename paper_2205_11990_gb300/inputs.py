@@ -24,6 +24,8 @@ import numpy as np
 
 SEQ = 0          # S1: x bits coarse->fine, then v bits coarse->fine
 INTERLEAVED = 1  # IF: x_1, v_1, x_2, v_2, ... (coarse first)
+SEQ_S2 = 2       # S2: x bits fine->coarse, then v bits coarse->fine
+SEQ_S3 = 3       # S3: x bits coarse->fine, then v bits fine->coarse
 
 
 @dataclasses.dataclass(frozen=True)
@@ -63,6 +65,11 @@ def landau(layout: Layout, amp=0.01, k=0.5):
     """f0 = (1 + A cos kx) exp(-v^2/2)/sqrt(2 pi)."""
     x, v = layout.x(), layout.v()
     return np.outer(1.0 + amp * np.cos(k * x), maxwellian(v))
+
+
+def nonlinear_landau(layout: Layout):
+    """Landau initial condition at amplitude 0.5 (k = 0.5): the nonlinear case."""
+    return landau(layout, amp=0.5, k=0.5)
 
 
 def two_stream(layout: Layout, amp=1e-3, k=0.2, v0=3.0):
@@ -132,9 +139,18 @@ WORKLOADS = {
                                                ic="saturated_two_stream", chi=64, dt=0.002),
     "saturated_two_stream_256x256_seq": dict(layout=Layout(8, 8, 0.0, 10 * math.pi, -8.0, 8.0, SEQ),
                                              ic="saturated_two_stream", chi=32, dt=0.008),
+    # 4096 x 4096 (12 + 12 sites): dt = 0.6 dx / vmax
+    "nonlinear_landau_4096x4096_seq": dict(layout=Layout(12, 12, 0.0, 4 * math.pi, -6.0, 6.0, SEQ),
+                                           ic="nonlinear_landau", chi=128, dt=0.6 * (4 * math.pi / 4096) / 6.0),
+    "saturated_two_stream_4096x4096_seq": dict(layout=Layout(12, 12, 0.0, 10 * math.pi, -8.0, 8.0, SEQ),
+                                               ic="saturated_two_stream_64", chi=128,
+                                               dt=0.6 * (10 * math.pi / 4096) / 8.0),
+    "two_stream_4096x4096_seq": dict(layout=Layout(12, 12, 0.0, 10 * math.pi, -8.0, 8.0, SEQ),
+                                     ic="two_stream", chi=128, dt=0.6 * (10 * math.pi / 4096) / 8.0),
 }
 
 
 def initial_condition(name: str, layout: Layout) -> np.ndarray:
-    return {"landau": landau, "two_stream": two_stream, "bump_on_tail": bump_on_tail,
-            "saturated_two_stream": saturated_two_stream}[name](layout)
+    return {"landau": landau, "nonlinear_landau": nonlinear_landau, "two_stream": two_stream,
+            "bump_on_tail": bump_on_tail, "saturated_two_stream": saturated_two_stream,
+            "saturated_two_stream_64": lambda lay: saturated_two_stream(lay, modes=64)}[name](layout)

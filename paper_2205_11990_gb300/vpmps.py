@@ -22,19 +22,23 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libvpmps.so")
 
 VP_SEQ, VP_INTERLEAVED = 0, 1
 MPO_DX_CENTERED, MPO_DX_FORWARD, MPO_DX_BACKWARD, MPO_DV_ZERO_GRAD, MPO_DXX, MPO_ADVECTION = range(6)
+# contraction precision modes (vp_config.precision, vp_gemm)
+PREC_FP64, PREC_FP32, PREC_TF32, PREC_BF16, PREC_TF32X3 = 0, 1, 2, 3, 4
+PRECISIONS = {"fp64": PREC_FP64, "fp32": PREC_FP32, "tf32": PREC_TF32, "bf16": PREC_BF16, "tf32x3": PREC_TF32X3}
+
 KCLASSES = ["qr_factor", "qr_formq", "gemm", "jacobi", "select", "apply", "other"]
 ERRORS = {1: "VP_EINVAL", 2: "VP_ENOMEM", 3: "VP_ECAPACITY", 4: "VP_ECUDA", 5: "VP_ETIMEOUT",
-          6: "VP_ENUMERIC", 7: "VP_ECFL", 8: "VP_EBUSY"}
+          6: "VP_ENUMERIC", 7: "VP_ECFL", 8: "VP_EBUSY", 9: "VP_EIO"}
 
 EXPORTS = [
     "vp_ctx_create", "vp_ctx_destroy", "vp_last_error", "vp_kernel_launches", "vp_profile_enable",
     "vp_profile_read",
     "mps_create", "mps_create_cores", "mps_destroy", "mps_num_sites", "mps_bonds", "mps_get_cores",
-    "mps_to_dense", "mps_to_grid",
+    "mps_to_dense", "mps_to_grid", "mps_save", "mps_load",
     "mpo_create_vp", "mpo_create_vlasov", "mpo_create_cores", "mpo_destroy", "mpo_num_sites", "mpo_bonds",
     "mpo_to_dense",
-    "mps_apply_mpo", "mps_axpby", "mps_compress", "vp_density", "vp_poisson", "vp_poisson_noalloc",
-    "vp_sim_create", "vp_sim_destroy", "vp_step", "vp_sim_state", "vp_sim_flops", "vp_run",
+    "mps_apply_mpo", "mps_axpby", "mps_compress", "vp_density", "vp_poisson", "vp_poisson_noalloc", "vp_gemm",
+    "vp_sim_create", "vp_sim_destroy", "vp_step", "vp_sim_state", "vp_sim_entropy", "vp_sim_flops", "vp_run",
     "vp_footprint_bytes", "vp_batch_create", "vp_batch_submit", "vp_batch_start", "vp_batch_wait", "vp_batch_poll",
     "vp_batch_records", "vp_batch_destroy",
 ]
@@ -53,7 +57,7 @@ class CLayout(C.Structure):
 
 class CConfig(C.Structure):
     _fields_ = [("dt", C.c_double), ("chi", C.c_int), ("tol", C.c_double), ("e_tol", C.c_double),
-                ("streams", C.c_int)]
+                ("streams", C.c_int), ("level", C.c_int), ("e_chi", C.c_int), ("precision", C.c_int)]
 
 
 class CResult(C.Structure):
@@ -109,6 +113,8 @@ def load():
         "mps_get_cores": (I, [P, P, DP, S]),
         "mps_to_dense": (I, [P, P, DP]),
         "mps_to_grid": (I, [P, P, C.POINTER(CLayout), DP]),
+        "mps_save": (I, [P, P, C.c_char_p]),
+        "mps_load": (I, [P, C.c_char_p, C.POINTER(P)]),
         "mpo_create_vp": (I, [P, C.POINTER(CLayout), I, C.POINTER(P)]),
         "mpo_create_vlasov": (I, [P, C.POINTER(CLayout), DP, D, C.POINTER(P)]),
         "mpo_create_cores": (I, [P, I, IP, DP, C.POINTER(P)]),
@@ -122,11 +128,13 @@ def load():
         "vp_density": (I, [P, C.POINTER(CLayout), P, P]),
         "vp_poisson": (I, [P, P, I, D, P, DP]),
         "vp_poisson_noalloc": (I, [P, P, I, D, P, DP, DP]),
+        "vp_gemm": (I, [P, I, I, I, I, D, P, I, P, I, P, I]),
         "vp_sim_create": (I, [P, C.POINTER(CLayout), C.POINTER(CConfig), P, C.POINTER(P)]),
         "vp_sim_destroy": (I, [P]),
         "vp_step": (I, [P, I, C.POINTER(CRecord)]),
         "vp_sim_state": (P, [P]),
         "vp_sim_flops": (D, [P]),
+        "vp_sim_entropy": (I, [P, DP]),
         "vp_run": (I, [P, C.POINTER(CLayout), C.POINTER(CConfig), DP, I, DP, C.POINTER(CRecord)]),
         "vp_footprint_bytes": (S, [C.POINTER(CLayout), C.POINTER(CConfig)]),
         "vp_batch_create": (I, [P, I, S, C.POINTER(P)]),
@@ -247,6 +255,11 @@ class Context:
         self._check(self.lib.mps_create_cores(self.h, len(cores), _ip(ranks), _dp(flat), C.byref(h)))
         return MPS(self, h)
 
+    def mps_load(self, path: str) -> "MPS":
+        h = C.c_void_p()
+        self._check(self.lib.mps_load(self.h, os.fsencode(path), C.byref(h)))
+        return MPS(self, h)
+
     def mpo_vp(self, lay: Layout, kind: int) -> "MPO":
         h = C.c_void_p()
         self._check(self.lib.mpo_create_vp(self.h, C.byref(clayout(lay)), kind, C.byref(h)))
@@ -306,10 +319,24 @@ class Context:
             raise VpError(code, "vp_poisson_noalloc failed")
         return E, we.value, mass.value
 
+    def gemm(self, A, B, alpha: float = 1.0, precision: int = 0):
+        """vp_gemm: alpha * A @ B for 2-D float64 CUDA tensors (row-major)."""
+        t = self.torch
+        A = A.contiguous()
+        B = B.contiguous()
+        M, K = A.shape
+        K2, N = B.shape
+        if K2 != K:
+            raise ValueError("gemm: inner dimensions differ")
+        Cout = t.empty((M, N), dtype=t.float64, device=A.device)
+        self._check(self.lib.vp_gemm(self.h, precision, M, N, K, alpha, C.c_void_p(A.data_ptr()), max(K, 1),
+                                     C.c_void_p(B.data_ptr()), max(N, 1), C.c_void_p(Cout.data_ptr()), max(N, 1)))
+        return Cout
+
     def sim(self, lay: Layout, f0: "MPS", dt: float, chi: int, tol: float = 1e-10, e_tol: float = 1e-10,
-            streams: int = 2) -> "Sim":
+            streams: int = 2, level: int = 1, e_chi: int = 0, precision: int = 0) -> "Sim":
         h = C.c_void_p()
-        cfg = CConfig(dt, chi, tol, e_tol, streams)
+        cfg = CConfig(dt, chi, tol, e_tol, streams, level, e_chi, precision)
         self._check(self.lib.vp_sim_create(self.h, C.byref(clayout(lay)), C.byref(cfg), f0.h, C.byref(h)))
         return Sim(self, h, lay)
 
@@ -318,7 +345,7 @@ class Context:
         f0 = np.ascontiguousarray(f0, dtype=np.float64)
         fT = np.zeros((lay.Nx, lay.Nv)) if want_f else None
         recs = (CRecord * max(1, nsteps))()
-        cfg = CConfig(dt, chi, tol, e_tol, 2)
+        cfg = CConfig(dt, chi, tol, e_tol, 2, 1, 0, 0)
         self._check(self.lib.vp_run(self.h, C.byref(clayout(lay)), C.byref(cfg), _dp(f0), nsteps,
                                     _dp(fT) if want_f else None, recs))
         return fT, _records(recs, nsteps)
@@ -339,7 +366,7 @@ class Batch:
                e_tol: float = 1e-10, keep_f: bool = False) -> int:
         f0 = np.ascontiguousarray(f0, dtype=np.float64)
         rid = C.c_uint64()
-        cfg = CConfig(dt, chi, tol, e_tol, 1)
+        cfg = CConfig(dt, chi, tol, e_tol, 1, 1, 0, 0)
         self.ctx._check(self.ctx.lib.vp_batch_submit(self.h, C.byref(clayout(lay)), C.byref(cfg), _dp(f0), nsteps,
                                                      int(keep_f), C.byref(rid)))
         self.nsteps[rid.value] = (nsteps, lay)
@@ -378,7 +405,7 @@ class Batch:
 
 
 def footprint_bytes(lay: Layout, chi: int, dt: float = 0.01) -> int:
-    return int(load().vp_footprint_bytes(C.byref(clayout(lay)), C.byref(CConfig(dt, chi, 1e-10, 1e-10, 1))))
+    return int(load().vp_footprint_bytes(C.byref(clayout(lay)), C.byref(CConfig(dt, chi, 1e-10, 1e-10, 1, 1, 0, 0))))
 
 
 def _records(recs, n):
@@ -410,6 +437,9 @@ class MPS:
             out.append(flat[off:off + s].reshape(r[k], 2, r[k + 1]))
             off += s
         return out
+
+    def save(self, path: str) -> None:
+        self.ctx._check(self.ctx.lib.mps_save(self.ctx.h, self.h, os.fsencode(path)))
 
     def to_dense(self) -> np.ndarray:
         out = np.zeros(1 << self.n)
@@ -481,6 +511,11 @@ class Sim:
     @property
     def flops(self) -> float:
         return float(self.ctx.lib.vp_sim_flops(self.h))
+
+    def entropy(self) -> np.ndarray:
+        out = np.zeros(max(1, self.lay.n - 1))
+        self.ctx._check(self.ctx.lib.vp_sim_entropy(self.h, _dp(out)))
+        return out[: self.lay.n - 1]
 
     def close(self):
         if self.h and self.ctx.h:

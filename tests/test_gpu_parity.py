@@ -40,7 +40,9 @@ def rel(a, b):
 
 LAYS = [I.Layout(3, 4, 0.0, 2 * math.pi, -5.0, 5.0, I.SEQ),
         I.Layout(4, 4, 0.0, 4 * math.pi, -6.0, 6.0, I.INTERLEAVED),
-        I.Layout(3, 5, 0.0, 3.0, -4.0, 4.0, I.INTERLEAVED)]
+        I.Layout(3, 5, 0.0, 3.0, -4.0, 4.0, I.INTERLEAVED),
+        I.Layout(4, 3, 0.0, 4 * math.pi, -6.0, 6.0, I.SEQ_S2),
+        I.Layout(3, 4, 0.0, 4 * math.pi, -6.0, 6.0, I.SEQ_S3)]
 
 
 # ----------------------------------------------------------------- MPOs (a2)
@@ -51,12 +53,13 @@ def test_mpo_builders_match_printed_operators(ctx, lay):
     sm = OV.sitemap(lay)
     idx, idv = OM.identity(lay.nx), OM.identity(lay.nv)
     nx = lay.nx
+    ox = lambda ch: OV.orient(ch, lay, 0)  # noqa: E731
     cases = {
-        V.MPO_DX_CENTERED: OM.place([OM.centered_periodic(nx, dx), idv], sm),
-        V.MPO_DX_FORWARD: OM.place([OM.forward_periodic(nx, dx), idv], sm),
-        V.MPO_DX_BACKWARD: OM.place([OM.backward_periodic(nx, dx), idv], sm),
-        V.MPO_DV_ZERO_GRAD: OM.place([idx, OM.centered_zero_gradient(lay.nv, dv)], sm),
-        V.MPO_DXX: OM.place([OM.second_periodic(nx, dx), idv], sm),
+        V.MPO_DX_CENTERED: OM.place([ox(OM.centered_periodic(nx, dx)), idv], sm),
+        V.MPO_DX_FORWARD: OM.place([ox(OM.forward_periodic(nx, dx)), idv], sm),
+        V.MPO_DX_BACKWARD: OM.place([ox(OM.backward_periodic(nx, dx)), idv], sm),
+        V.MPO_DV_ZERO_GRAD: OM.place([idx, OV.orient(OM.centered_zero_gradient(lay.nv, dv), lay, 1)], sm),
+        V.MPO_DXX: OM.place([ox(OM.second_periodic(nx, dx)), idv], sm),
         V.MPO_ADVECTION: OV._static_parts(lay)[0],
     }
     for kind, ref in cases.items():
@@ -181,6 +184,8 @@ def test_poisson_large_grid(ctx):
 # --------------------------------------------------------------- step (a10)
 STEP_CASES = [
     (I.Layout(5, 5, 0.0, 4 * math.pi, -6.0, 6.0, I.SEQ), "landau", 0.02, 16, 3),
+    (I.Layout(5, 5, 0.0, 4 * math.pi, -6.0, 6.0, I.SEQ_S2), "landau", 0.02, 16, 2),
+    (I.Layout(5, 5, 0.0, 10 * math.pi, -8.0, 8.0, I.SEQ_S3), "two_stream", 0.05, 16, 2),
     (I.Layout(4, 4, 0.0, 4 * math.pi, -6.0, 6.0, I.INTERLEAVED), "landau", 0.05, 8, 3),
     (I.Layout(5, 6, 0.0, 10 * math.pi, -8.0, 8.0, I.INTERLEAVED), "two_stream", 0.05, 12, 2),
     (I.Layout(6, 6, 0.0, 4 * math.pi, -6.0, 6.0, I.SEQ), "landau", 0.02, 64, 2),
@@ -202,6 +207,7 @@ def test_rk4_c1_steps(ctx, lay, ic, dt, chi, nsteps):
         assert abs(rec["mass"] - d["mass"]) <= 1e-12 * abs(d["mass"])
         assert sim.state().bonds() == d["bonds"]
         assert rel(sim.state().to_grid(lay), OV.mps_to_f(ref, lay)) < F_TOL
+        np.testing.assert_allclose(sim.entropy(), d["entropy"], rtol=1e-8, atol=1e-12)
 
 
 def test_exact_mode_matches_dense_grid(ctx):
@@ -236,3 +242,51 @@ def test_cfl_guard(ctx):
     with pytest.raises(vpmps.VpError) as e:
         ctx.sim(lay, m, 1.0, 8)
     assert e.value.code == 7
+
+
+# ---------------------------------------------- compression levels C2-C5, D_F
+@pytest.mark.parametrize("level,e_chi", [(2, 0), (3, 0), (4, 0), (5, 0), (1, 3), (4, 2)])
+def test_compression_levels_and_field_cap(ctx, level, e_chi):
+    lay = I.Layout(5, 5, 0.0, 10 * math.pi, -8.0, 8.0, I.SEQ)
+    f0 = I.saturated_two_stream(lay, modes=6)
+    chi, dt = 10, 0.02
+    m = ctx.mps_from_grid(lay, f0, chi, 1e-10)
+    sim = ctx.sim(lay, m, dt, chi, level=level, e_chi=e_chi)
+    ref = OV.mps_from_f(f0, lay, chi, 1e-10)
+    for _ in range(2):
+        rec = sim.step(1)[0]
+        ref, d = OV.rk4_step(ref, lay, dt, chi, level=level, e_chi=e_chi or None)
+        assert abs(rec["field_energy"] - d["field_energy"]) <= WE_TOL * d["field_energy"]
+        assert sim.state().bonds() == d["bonds"]
+        assert rel(sim.state().to_grid(lay), OV.mps_to_f(ref, lay)) < F_TOL
+
+
+# --------------------------------------------------- precision configuration
+# contraction precision modes against the FP64 path (which matches the
+# oracle): field-energy error (absolute, normalised units) and f error.
+# FP32 and split TF32x3 keep FP32-level accuracy: |dW_E| <= 1e-6 (relative to
+# W_E that is ~1e-5, since W_E comes from the O(1e-2) perturbation of f and
+# the FP32 sums carry ~1e-7 of the whole of f).  Plain TF32 and BF16 round
+# every operand to 10 / 7 mantissa bits: their bounds are those of that
+# rounding, checked so that a broken kernel (errors of order one) fails.
+PREC_BOUNDS = {1: (1e-6, 2e-4, 1e-5), 4: (1e-6, 2e-4, 1e-5), 2: (1e-4, 5e-2, 5e-3), 3: (1e-3, 5e-1, 5e-2)}
+
+
+@pytest.mark.parametrize("prec", [1, 4, 2, 3])
+def test_reduced_precision_contractions_vs_fp64(ctx, prec):
+    lay = I.Layout(6, 6, 0.0, 10 * math.pi, -8.0, 8.0, I.SEQ)
+    f0 = I.saturated_two_stream(lay, modes=8)
+    chi, dt = 24, 0.02
+    runs = {}
+    for p in (0, prec):
+        m = ctx.mps_from_grid(lay, f0, chi, 1e-10)
+        sim = ctx.sim(lay, m, dt, chi, precision=p)
+        recs = sim.step(4)
+        runs[p] = (np.array([r["field_energy"] for r in recs]), sim.state().to_grid(lay))
+        sim.close()
+    we64, f64 = runs[0]
+    wep, fp = runs[prec]
+    we_abs, we_rel, f_rel = PREC_BOUNDS[prec]
+    assert np.max(np.abs(wep - we64)) < we_abs
+    assert np.max(np.abs(wep - we64) / we64) < we_rel
+    assert 0 < rel(fp, f64) < f_rel

@@ -90,3 +90,13 @@ def test_choose_rank_rules():
     assert S.choose_rank(np.zeros(4), 3, 1e-10)[0] == 1
     r, e = S.choose_rank(np.array([3.0, 4.0 * 0 + 1e-3]), 1, 0.0)
     assert r == 1 and abs(e - 1e-3 / np.hypot(3.0, 1e-3)) < 1e-15
+
+
+def test_entanglement_entropy_closed_forms():
+    # maximally entangled: r equal values -> log2 r; product state -> 0
+    assert abs(S.entanglement_entropy(np.ones(8), 8) - 3.0) < 1e-14
+    assert S.entanglement_entropy(np.array([2.0, 0.0]), 1) == 0.0
+    # a Bell-like two-site state (|00> + |11>)/sqrt2 has EE 1 at its bond
+    v = np.array([1.0, 0.0, 0.0, 1.0]) / np.sqrt(2)
+    _, _, ee = S.compress_with_entropy(S.tt_svd(v, 2), 4, 0.0)
+    assert abs(ee[0] - 1.0) < 1e-12

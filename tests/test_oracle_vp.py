@@ -138,3 +138,70 @@ def test_dense_solver_two_stream_growth_rate():
     sel = (ts > 8) & (ts < 22)
     g = 0.5 * np.polyfit(ts[sel], np.log(wes[sel]), 1)[0]
     assert abs(g - DS.two_stream_root(0.2).imag) / DS.two_stream_root(0.2).imag < 0.05
+
+
+@pytest.mark.parametrize("level", [1, 2, 3, 4, 5])
+def test_compression_levels_exact_mode_match_dense_grid(level):
+    # with chi = 2^(n/2) and tol = 0 every compression is exact, so all five
+    # schedules reproduce the plain RK4 step of the dense solver
+    lay = I.Layout(4, 4, 0.0, 4 * math.pi, -6.0, 6.0, I.SEQ)
+    f = I.landau(lay, 0.3, 0.5)
+    cores = V.mps_from_f(f, lay, 1 << 10, 0.0)
+    fd = f.copy()
+    for _ in range(3):
+        fd, _, _ = DF.rk4_step(fd, lay, 0.05)
+        cores, _ = V.rk4_step(cores, lay, 0.05, 1 << 10, 0.0, 0.0, level=level)
+    assert np.linalg.norm(V.mps_to_f(cores, lay) - fd) / np.linalg.norm(fd) < 1e-12
+
+
+@pytest.mark.parametrize("level", [2, 3, 4, 5])
+def test_higher_levels_compress_more(level):
+    lay = I.Layout(5, 5, 0.0, 10 * math.pi, -8.0, 8.0, I.SEQ)
+    f = I.saturated_two_stream(lay, modes=6)
+    c = V.mps_from_f(f, lay, 8, 1e-10)
+    out, d = V.rk4_step(c, lay, 0.02, 8, level=level)
+    out1, d1 = V.rk4_step(c, lay, 0.02, 8, level=1)
+    assert max(d["bonds"]) <= 8
+    # the extra truncations move the result by at most a small fraction
+    ref = V.mps_to_f(out1, lay)
+    assert np.linalg.norm(V.mps_to_f(out, lay) - ref) / np.linalg.norm(ref) < 1e-2
+
+
+def test_field_bond_cap():
+    lay = I.Layout(6, 5, 0.0, 10 * math.pi, -8.0, 8.0, I.SEQ)
+    x = lay.x()
+    E = sum(np.cos(m * 0.2 * x + m) / m for m in range(1, 12))
+    for cap in (2, 4):
+        em = V.field_mps(E, lay, 1e-10, cap)
+        assert max(S.bonds(em)) <= cap
+    # the cap is the best rank-cap approximation: error decreases with the cap
+    errs = [np.linalg.norm(S.to_dense(V.field_mps(E, lay, 1e-10, c)) - E) for c in (1, 2, 4, 8)]
+    assert errs == sorted(errs, reverse=True)
+
+
+@pytest.mark.parametrize("mapping", [I.SEQ_S2, I.SEQ_S3])
+def test_s2_s3_orderings(mapping):
+    lay = I.Layout(4, 4, 0.0, 4 * math.pi, -6.0, 6.0, mapping)
+    f = I.landau(lay, 0.4, 0.5) + 0.1 * I.random_vector(lay.n, 3).reshape(lay.Nx, lay.Nv)
+    np.testing.assert_array_equal(V.sites_to_dense(V.dense_to_sites(f, lay), lay), f)
+    cores = V.mps_from_f(f, lay, 1 << 10, 0.0)
+    _, dv = V.grid_steps(lay)
+    np.testing.assert_allclose(V.density(cores, lay), f.sum(axis=1) * dv, atol=1e-13)
+    E, _, _ = V.stage_field(cores, lay)
+    L = V.operator(V.field_mps(E, lay, 0.0), lay)
+    got = V.sites_to_dense(M.to_dense(L) @ V.dense_to_sites(f, lay), lay)
+    ref, _, _ = DF.rhs(f, lay)
+    np.testing.assert_allclose(got, ref, atol=1e-12 * np.abs(ref).max())
+    # the untruncated step still equals the dense FD step
+    fd, _, _ = DF.rk4_step(f, lay, 0.05)
+    out, _ = V.rk4_step(cores, lay, 0.05, 1 << 10, 0.0, 0.0)
+    assert np.linalg.norm(V.mps_to_f(out, lay) - fd) / np.linalg.norm(fd) < 1e-12
+
+
+def test_reverse_chain_is_same_operator():
+    X = M.forward_periodic(4, 0.3)
+    D = M.to_dense(X)
+    Dr = M.to_dense(M.reverse(X))
+    # reversing the site order permutes the basis by bit reversal
+    br = V.bitrev(4)
+    np.testing.assert_allclose(Dr, D[np.ix_(br, br)], atol=1e-13)
