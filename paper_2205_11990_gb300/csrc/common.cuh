@@ -25,6 +25,10 @@ struct DevStatus {
   int pad;
   unsigned int rot[3];  // Jacobi rotation counters, one per sweep modulo 3
   int pad2;             // sweeps taken by the last Jacobi launch
+  unsigned long long pub_count;  // Householder reflectors published (monotonic)
+  unsigned long long pub_base;   // pub_count when the next QR launch starts
+  unsigned int pub_done;         // blocks of the current QR launch that have finished
+  int pad3;
 };
 
 // Grow-only device buffer owned by a context.

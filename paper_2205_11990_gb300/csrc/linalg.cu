@@ -184,6 +184,116 @@ __global__ void __launch_bounds__(kThreads) k_qr_factor(double* A, int m, int n,
   gs.finish();
 }
 
+// Look-ahead variant for the cooperative grid: no grid barrier.  Reflector j
+// (v in column j of A below the diagonal, v_j = 1 implicit, tau[j]) is
+// published by a release increment of a monotonic counter.  At step j every
+// block waits only for reflector j; the owner of column j+1 first applies H_j
+// to that column with the whole block, forms and publishes reflector j+1, and
+// only then applies H_j to the rest of its columns.  The critical path per
+// column is one column update, one reflector and one publication; the bulk
+// trailing update runs behind it.  The counter base carries over between
+// launches: the last block to finish records the new base.
+__global__ void __launch_bounds__(kThreads) k_qr_factor_la(double* A, int m, int n, double* tau, DevStatus* st) {
+  __shared__ double red[kWarps + 1];
+  __shared__ int s_ok;
+  const int nb = gridDim.x, bid = blockIdx.x, tid = threadIdx.x;
+  const int lane = tid & 31, warp = tid >> 5;
+  const int p = min(m, n);
+  const unsigned long long base = *(volatile unsigned long long*)&st->pub_base;
+  cuda::atomic_ref<unsigned long long, cuda::thread_scope_device> pub(st->pub_count);
+
+  // reflector of column j (which already carries H_0 .. H_{j-1})
+  auto reflect = [&](int j) {
+    double* col = A + (size_t)j * m;
+    double s = 0.0;
+    for (int i = j + 1 + tid; i < m; i += kThreads) {
+      const double x = col[i];
+      s = fma(x, x, s);
+    }
+    s = block_sum(s, red);
+    const double x0 = col[j];
+    double t = 0.0, beta = x0, scale = 0.0;
+    if (s > 0.0) {
+      const double nrm = sqrt(fma(x0, x0, s));
+      beta = x0 >= 0.0 ? -nrm : nrm;
+      t = (beta - x0) / beta;
+      scale = 1.0 / (x0 - beta);
+    }
+    for (int i = j + 1 + tid; i < m; i += kThreads) col[i] *= scale;
+    if (tid == 0) {
+      col[j] = beta;
+      tau[j] = t;
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) pub.store(base + j + 1, cuda::memory_order_release);
+  };
+  auto wait = [&](int j) -> bool {
+    if (tid == 0) {
+      int ok = 1;
+      const long long t0 = clock64();
+      while (pub.load(cuda::memory_order_acquire) < base + j + 1) {
+        if (ld_volatile(&st->err) != 0) {
+          ok = 0;
+          break;
+        }
+        if (clock64() - t0 > 2000000000ll) {
+          atomicExch(&st->err, 1);
+          ok = 0;
+          break;
+        }
+      }
+      s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+  };
+
+  if (bid == 0) reflect(0);
+  bool ok = true;
+  for (int j = 0; j < p && ok; ++j) {
+    if (!wait(j)) {
+      ok = false;
+      break;
+    }
+    const double t = __ldcg(tau + j);
+    const double* v = A + (size_t)j * m;
+    if (j + 1 < p && bid == (j + 1) % nb) {
+      if (t != 0.0) {
+        double* col = A + (size_t)(j + 1) * m;
+        double w = tid == 0 ? col[j] : 0.0;
+        for (int i = j + 1 + tid; i < m; i += kThreads) w = fma(__ldcg(v + i), col[i], w);
+        w = block_sum(w, red) * t;
+        if (tid == 0) col[j] -= w;
+        for (int i = j + 1 + tid; i < m; i += kThreads) col[i] = fma(-w, __ldcg(v + i), col[i]);
+        __syncthreads();
+      }
+      reflect(j + 1);
+    }
+    if (t == 0.0) continue;
+    const int first = j + 2;
+    const int k0 = first + ((bid - first % nb) % nb + nb) % nb;
+    for (int k = k0 + warp * nb; k < n; k += kWarps * nb) {
+      double* col = A + (size_t)k * m;
+      double w = lane == 0 ? col[j] : 0.0;
+      for (int i = j + 1 + lane; i < m; i += 32) w = fma(__ldcg(v + i), col[i], w);
+      w = warp_sum(w) * t;
+      if (lane == 0) col[j] -= w;
+      for (int i = j + 1 + lane; i < m; i += 32) col[i] = fma(-w, __ldcg(v + i), col[i]);
+    }
+  }
+  // the last block to finish publishes the base of the next launch
+  __syncthreads();
+  if (tid == 0 && ok) {
+    __threadfence();
+    if (atomicAdd(&st->pub_done, 1u) == (unsigned)nb - 1) {
+      st->pub_base = base + p;
+      st->pub_done = 0u;
+      __threadfence();
+    }
+  }
+}
+
 int launch_qr_factor(vp_ctx* ctx, double* A, int m, int n, double* tau, double* vbuf) {
   const int p = std::min(m, n);
   if (p <= 0) return VP_OK;
@@ -219,6 +329,10 @@ int launch_qr_factor(vp_ctx* ctx, double* A, int m, int n, double* tau, double* 
   int blocks = std::min(cap, std::max(1, n / 2));
   if ((long long)m * n < 8192) blocks = 1;
   DevStatus* st = ctx->status;
+  if (blocks > 1) {
+    void* args[] = {&A, &m, &n, &tau, &st};
+    return coop_launch(ctx, (const void*)k_qr_factor_la, blocks, kThreads, args, 0, "qr_factor");
+  }
   void* args[] = {&A, &m, &n, &tau, &vbuf, &st};
   return coop_launch(ctx, (const void*)k_qr_factor<GridSync>, blocks, kThreads, args, 0, "qr_factor");
 }
