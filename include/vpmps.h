@@ -104,6 +104,19 @@ enum { VP_K_QR = 0, VP_K_FORMQ = 1, VP_K_GEMM = 2, VP_K_JACOBI = 3, VP_K_SELECT 
        VP_K_OTHER = 6, VP_K_COUNT = 7 };
 int vp_profile_enable(vp_ctx* ctx, int on);
 int vp_profile_read(vp_ctx* ctx, int kclass, double* ms, int64_t* launches, double* work);
+/* Launch trace of the same profiling window: one record per bracketed
+ * launch, in issue order (this context first, then the contexts it created
+ * for concurrent work).  m, n, k: the shape of the launch (QR: rows, columns;
+ * Jacobi: rows, row length, sweeps taken; GEMM: M, N, K; apply: the site).
+ * With concurrent streams an event interval also counts time spent queued
+ * behind the other stream's kernels; with one stream it is the kernel's own
+ * time.  Writes up to `cap` records, *n_out = the total available. */
+typedef struct {
+  int kclass;
+  int m, n, k;
+  double ms;
+} vp_trace_rec;
+int vp_profile_trace(vp_ctx* ctx, vp_trace_rec* out, int cap, int* n_out);
 
 /* -------------------------------------------------------------------- MPS */
 

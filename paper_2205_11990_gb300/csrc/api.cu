@@ -93,14 +93,20 @@ void prof_begin(vp_ctx* ctx, int cls) {
   cudaEvent_t e = next_event(ctx);
   if (!e) return;
   cudaEventRecord(e, ctx->stream);
-  ctx->prof_marks.push_back({cls, idx});
+  ctx->prof_marks.push_back({cls, idx, 0, 0, 0});
 }
 
-void prof_end(vp_ctx* ctx, int cls, double work) {
+void prof_end(vp_ctx* ctx, int cls, double work, int m, int n, int k) {
   if (!ctx->prof_on) return;
   cudaEvent_t e = next_event(ctx);
   if (!e) return;
   cudaEventRecord(e, ctx->stream);
+  if (!ctx->prof_marks.empty()) {
+    auto& mk = ctx->prof_marks.back();
+    mk.m = m;
+    mk.n = n;
+    mk.k = k;
+  }
   ctx->prof_work[cls] += work;
   ctx->prof_launches[cls] += 1;
 }
@@ -180,14 +186,14 @@ static int qr_site(vp_ctx* ctx, mps_t* s, int k) {
   VP_TRY(launch_to_colmajor(ctx, s->core[k].p, m, n, ctx->w_fac.p));
   prof_begin(ctx, VP_K_QR);
   VP_TRY(launch_qr_factor(ctx, ctx->w_fac.p, m, n, tau, vbuf));
-  prof_end(ctx, VP_K_QR, qr_flops(m, n));
+  prof_end(ctx, VP_K_QR, qr_flops(m, n), m, n);
   prof_begin(ctx, VP_K_FORMQ);
   VP_TRY(launch_qr_formq(ctx, ctx->w_fac.p, m, n, tau, s->core[k].p));
-  prof_end(ctx, VP_K_FORMQ, 4.0 * m * p * p - 4.0 / 3.0 * p * p * p);
+  prof_end(ctx, VP_K_FORMQ, 4.0 * m * p * p - 4.0 / 3.0 * p * p * p, m, p);
   VP_TRY(reserve(ctx, ctx->w_gemm, (size_t)p * nn));
   prof_begin(ctx, VP_K_GEMM);
   VP_TRY(launch_gemm_r(ctx, p, nn, n, ctx->w_fac.p, m, s->core[k + 1].p, nn, ctx->w_gemm.p, nn));
-  prof_end(ctx, VP_K_GEMM, 2.0 * p * n * nn);
+  prof_end(ctx, VP_K_GEMM, 2.0 * p * n * nn, p, nn, n);
   std::swap(s->core[k + 1], ctx->w_gemm);
   s->r[k + 1] = p;
   if (g_flops) {
@@ -249,7 +255,7 @@ static int svd_site(vp_ctx* ctx, mps_t* s, int k, int chi, double tol, double* e
   VP_TRY(launch_gather_cm(ctx, s->core[k].p, m, c, piv, tall ? 1 : 0, ctx->w_fac.p));
   prof_begin(ctx, VP_K_QR);
   VP_TRY(launch_qr_factor(ctx, ctx->w_fac.p, p, q, ctx->w_p.p, ctx->w_p.p + q + 8));
-  prof_end(ctx, VP_K_QR, qr_flops(p, q));
+  prof_end(ctx, VP_K_QR, qr_flops(p, q), p, q);
   VP_TRY(reserve(ctx, ctx->w_q1, (size_t)p * q));
   // second QR: R1^T = Q2 L^T (R1 row-major is R1^T column-major)
   VP_TRY(reserve(ctx, ctx->w_r, (size_t)q * q));
@@ -257,7 +263,7 @@ static int svd_site(vp_ctx* ctx, mps_t* s, int k, int chi, double tol, double* e
   VP_TRY(reserve(ctx, ctx->w_p2, (size_t)3 * q + 8));
   prof_begin(ctx, VP_K_QR);
   VP_TRY(launch_qr_factor(ctx, ctx->w_r.p, q, q, ctx->w_p2.p, ctx->w_p2.p + q + 8));
-  prof_end(ctx, VP_K_QR, qr_flops(q, q));
+  prof_end(ctx, VP_K_QR, qr_flops(q, q), q, q);
   VP_TRY(reserve(ctx, ctx->w_q2, (size_t)q * q));
   // Q1, Q2 (and, tall, P Q1) only feed the outputs: form them on the side
   // stream while the Jacobi SVD runs.  Their scratch is reserved up front so
@@ -272,10 +278,10 @@ static int svd_site(vp_ctx* ctx, mps_t* s, int k, int chi, double tol, double* e
     SideScope side(ctx);
     prof_begin(ctx, VP_K_FORMQ);
     VP_TRY(launch_qr_formq(ctx, ctx->w_fac.p, p, q, ctx->w_p.p, ctx->w_q1.p));
-    prof_end(ctx, VP_K_FORMQ, 4.0 * p * q * q - 4.0 / 3.0 * q * q * q);
+    prof_end(ctx, VP_K_FORMQ, 4.0 * p * q * q - 4.0 / 3.0 * q * q * q, p, q);
     prof_begin(ctx, VP_K_FORMQ);
     VP_TRY(launch_qr_formq(ctx, ctx->w_r.p, q, q, ctx->w_p2.p, ctx->w_q2.p));
-    prof_end(ctx, VP_K_FORMQ, 8.0 / 3.0 * q * q * q);
+    prof_end(ctx, VP_K_FORMQ, 8.0 / 3.0 * q * q * q, q, q);
     if (tall) VP_TRY(launch_gemm(ctx, pl, q, m, 1.0, s->core[k - 1].p, m, ctx->w_q1.p, q, ctx->w_tmp2.p, q));
   }
   VP_CUDA(ctx, cudaEventRecord(ctx->ev_join, ctx->side));
@@ -295,13 +301,14 @@ static int svd_site(vp_ctx* ctx, mps_t* s, int k, int chi, double tol, double* e
   VP_CUDA(ctx, cudaMemsetAsync(ctx->status->rot, 0, sizeof(ctx->status->rot), ctx->stream));
   prof_begin(ctx, VP_K_JACOBI);
   VP_TRY(launch_jacobi_rows(ctx, X, q, q, tall ? nullptr : ctx->w_j.p));
-  prof_end(ctx, VP_K_JACOBI, 0.0);
+  prof_end(ctx, VP_K_JACOBI, 0.0, q, q);
+  const size_t jac_mark = ctx->prof_on && !ctx->prof_marks.empty() ? ctx->prof_marks.size() - 1 : (size_t)-1;
   VP_TRY(reserve(ctx, ctx->w_vec, (size_t)2 * q + 8));
   int* perm = (int*)ctx->w_vec.p;
   double* sigma = ctx->w_vec.p + (q + 1) / 2 + 4;
   prof_begin(ctx, VP_K_SELECT);
   VP_TRY(launch_select(ctx, X, q, q, chi, tol, perm, sigma, ctx->d_small, ctx->d_smalld));
-  prof_end(ctx, VP_K_SELECT, 0.0);
+  prof_end(ctx, VP_K_SELECT, 0.0, q, q);
   int r = 1;
   double err = 0.0;
   VP_TRY(read_rank(ctx, &r, &err));
@@ -309,6 +316,7 @@ static int svd_site(vp_ctx* ctx, mps_t* s, int k, int chi, double tol, double* e
   if (g_entropy) g_entropy[k - 1] = ctx->h_smalld[1];
   const double jac = q > 1 ? (double)ctx->h_small[61] * 0.5 * q * (q - 1) * (6.0 * q + (tall ? 0.0 : 4.0 * q)) : 0.0;
   if (ctx->prof_on) ctx->prof_work[VP_K_JACOBI] += jac;
+  if (jac_mark != (size_t)-1 && jac_mark < ctx->prof_marks.size()) ctx->prof_marks[jac_mark].k = ctx->h_small[61];
   double gem = 0.0;
   VP_TRY(reserve(ctx, ctx->w_a, (size_t)r * q + 8));
   VP_TRY(reserve(ctx, ctx->w_b, (size_t)q * r + 8));
@@ -338,7 +346,7 @@ static int svd_site(vp_ctx* ctx, mps_t* s, int k, int chi, double tol, double* e
     VP_TRY(launch_gemm(ctx, pl, r, m, 1.0, s->core[k - 1].p, m, ctx->w_tmp2.p, r, ctx->w_gemm.p, r));
     gem = 2.0 * r * c * m + 2.0 * m * r * m + 2.0 * pl * r * m;
   }
-  prof_end(ctx, VP_K_GEMM, gem);
+  prof_end(ctx, VP_K_GEMM, gem, q, r, pl);
   std::swap(s->core[k - 1], ctx->w_gemm);
   s->r[k] = r;
   if (g_flops) {
@@ -621,9 +629,9 @@ int vp_profile_read(vp_ctx* c, int cls, double* ms, int64_t* launches, double* w
   VP_CUDA(c, cudaStreamSynchronize(c->stream));
   double t = 0.0;
   for (auto& m : c->prof_marks) {
-    if (m.first != cls) continue;
+    if (m.cls != cls) continue;
     float x = 0.f;
-    VP_CUDA(c, cudaEventElapsedTime(&x, c->ev_pool[m.second], c->ev_pool[m.second + 1]));
+    VP_CUDA(c, cudaEventElapsedTime(&x, c->ev_pool[m.ev], c->ev_pool[m.ev + 1]));
     t += x;
   }
   double wk = c->prof_work[cls];
@@ -639,6 +647,28 @@ int vp_profile_read(vp_ctx* c, int cls, double* ms, int64_t* launches, double* w
   if (ms) *ms = t;
   if (launches) *launches = nl;
   if (work) *work = wk;
+  return VP_OK;
+}
+
+int vp_profile_trace(vp_ctx* c, vp_trace_rec* out, int cap, int* n_out) {
+  if (!c || (!out && cap > 0) || cap < 0 || !n_out) return VP_EINVAL;
+  VP_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (c->side) VP_CUDA(c, cudaStreamSynchronize(c->side));
+  int n = 0;
+  for (auto& m : c->prof_marks) {
+    if (n < cap) {
+      float x = 0.f;
+      VP_CUDA(c, cudaEventElapsedTime(&x, c->ev_pool[m.ev], c->ev_pool[m.ev + 1]));
+      out[n] = vp_trace_rec{m.cls, m.m, m.n, m.k, (double)x};
+    }
+    ++n;
+  }
+  for (vp_ctx* ch : c->children) {
+    int n2 = 0;
+    VP_TRY(vp_profile_trace(ch, out ? out + std::min(n, cap) : nullptr, std::max(0, cap - n), &n2));
+    n += n2;
+  }
+  *n_out = n;
   return VP_OK;
 }
 

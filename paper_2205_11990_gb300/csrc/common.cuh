@@ -64,7 +64,12 @@ struct vp_ctx {
   bool prof_on = false;
   std::vector<cudaEvent_t> ev_pool;
   size_t ev_used = 0;
-  std::vector<std::pair<int, size_t>> prof_marks;  // (class, first event index)
+  struct ProfMark {
+    int cls;
+    size_t ev;    // index of the begin event (the end event follows it)
+    int m, n, k;  // shape of the launch (trace records)
+  };
+  std::vector<ProfMark> prof_marks;
   double prof_work[VP_K_COUNT] = {};
   int64_t prof_launches[VP_K_COUNT] = {};
   // workspaces
@@ -116,7 +121,7 @@ void release(vp_ctx* ctx, DevBuf& b);
 int check_launch(vp_ctx* ctx, const char* what);
 // Bracket one launch of class `cls` with events when profiling is on.
 void prof_begin(vp_ctx* ctx, int cls);
-void prof_end(vp_ctx* ctx, int cls, double work);
+void prof_end(vp_ctx* ctx, int cls, double work, int m = 0, int n = 0, int k = 0);
 // Synchronise and read the device status word; maps errors to VP codes.
 int sync_status(vp_ctx* ctx);
 

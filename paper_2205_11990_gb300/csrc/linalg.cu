@@ -748,9 +748,231 @@ static size_t cluster_jacobi_smem(int b, int c, int CS, bool withJ) {
   return rpc * (size_t)(c + (withJ ? b : 0) + 1) * sizeof(double) + 4 * sizeof(unsigned);
 }
 
+// Block-local variant.  The b rows are split into 2 CS blocks of nb rows (nb
+// even, padding rows zero); CTA c of a CS-CTA cluster holds two blocks, "top"
+// and "bottom", in its own shared memory.  One block round rotates every
+// pair between the two local blocks (nb inner rounds of nb disjoint pairs,
+// separated by __syncthreads only); the first block round of a sweep also
+// rotates the pairs inside each block.  Then the blocks move on the circle
+// schedule (block positions 0..2CS-1, top of CTA c = c, bottom = 2CS-1-c;
+// position 0 stays, every other position advances by one), by DSMEM copies
+// into the other half of a double buffer and one cluster barrier.  After
+// 2CS-1 block rounds every pair of rows has met once (one sweep) and every
+// block is back home.
+//
+// Rotations are applied in scaled form: a row is stored as x~ with a scale
+// d (x = d x~), its squared norm alpha kept beside it.  The rotation with
+// tan t and cos c becomes x~_i <- x~_i - (t d_j / d_i) x~_j,
+// x~_j <- x~_j + (t d_i / d_j) x~_i, d <- c d: two FMAs per element pair
+// instead of four operations, with the same rounding bound.  Each sweep
+// starts by folding d back into the rows and recomputing alpha exactly.
+// Row layout (stride c + jb + 2 doubles): x~ (c), accumulated rotation row
+// (jb, when J is wanted), alpha, d.
+struct JacBlockCfg {
+  int CS, nb, stride;
+};
+
+__device__ __forceinline__ int jac_pos_cta(int pos, int CS) { return pos < CS ? pos : 2 * CS - 1 - pos; }
+__device__ __forceinline__ int jac_pos_slot(int pos, int CS) { return pos < CS ? 0 : 1; }
+__device__ __forceinline__ int jac_next_pos(int pos, int CS) {
+  return pos == 0 ? 0 : (pos == 2 * CS - 1 ? 1 : pos + 1);
+}
+
+// One scaled rotation of rows ri, rj (local shared memory) by one warp.
+// Returns true when the pair was rotated.
+__device__ __forceinline__ bool jac_pair(double* ri, double* rj, int c, int w, double eps2, int lane) {
+  double* ei = ri + w;  // alpha, d of row i
+  double* ej = rj + w;
+  const double al = ei[0], be = ej[0], di = ei[1], dj = ej[1];
+  double g = 0.0;
+  for (int q = lane; q < c; q += 32) g = fma(ri[q], rj[q], g);
+  g = warp_sum(g);
+  if (!(al > 0.0 && be > 0.0)) return false;
+  const double ga = di * dj * g;
+  if (!(ga * ga > eps2 * al * be)) return false;
+  double t, cs, sn;
+  jacobi_rotation(al, be, ga, t, cs, sn);
+  const double inv = 1.0 / (di * dj);
+  const double a = t * dj * dj * inv, bb = t * di * di * inv;
+  for (int q = lane; q < w; q += 32) {
+    const double u = ri[q], v = rj[q];
+    ri[q] = fma(-a, v, u);
+    rj[q] = fma(bb, u, v);
+  }
+  __syncwarp();
+  if (lane == 0) {
+    ei[0] = fma(-t, ga, al);
+    ej[0] = fma(t, ga, be);
+    ei[1] = cs * di;
+    ej[1] = cs * dj;
+  }
+  return true;
+}
+
+__global__ void __launch_bounds__(kThreads) k_jacobi_block(double* X, int b, int c, double* J, double eps,
+                                                           int max_sweeps, int nb, DevStatus* st) {
+  cg::cluster_group cl = cg::this_cluster();
+  extern __shared__ double sm[];
+  const int CS = (int)cl.num_blocks(), rank = (int)cl.block_rank();
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int jb = J ? b : 0;
+  const int w = c + jb, stride = w + 2;
+  const size_t slot_sz = (size_t)nb * stride;
+  // buffer set s, slot (0 top, 1 bottom), row r
+  auto row = [&](int s, int slot, int r) { return sm + ((size_t)(s * 2 + slot)) * slot_sz + (size_t)r * stride; };
+  unsigned* cnt = reinterpret_cast<unsigned*>(sm + 4 * slot_sz);
+  const double eps2 = eps * eps;
+
+  // home placement: top = block rank, bottom = block 2 CS - 1 - rank
+  for (int slot = 0; slot < 2; ++slot) {
+    const int blk = slot == 0 ? rank : 2 * CS - 1 - rank;
+    for (int r = 0; r < nb; ++r) {
+      const int x = blk * nb + r;
+      double* d = row(0, slot, r);
+      for (int q = tid; q < stride; q += kThreads) {
+        double v = 0.0;
+        if (x < b) {
+          if (q < c) v = X[(size_t)x * c + q];
+          else if (q < w) v = (q - c == x) ? 1.0 : 0.0;
+        }
+        if (q == w + 1) v = 1.0;  // scale d
+        d[q] = v;
+      }
+    }
+  }
+  if (tid < 4) cnt[tid] = 0u;
+  unsigned* c0 = cl.map_shared_rank(cnt, 0);
+  int cur = 0, sweep = 0;
+  bool converged = false;
+  const int brounds = 2 * CS - 1;
+  for (; sweep < max_sweeps; ++sweep) {
+    // fold the scales into the rows, exact squared norms
+    __syncthreads();
+    for (int rr = warp; rr < 2 * nb; rr += kWarps) {
+      double* d = row(cur, rr / nb, rr % nb);
+      const double sc = d[w + 1];
+      double a = 0.0;
+      for (int q = lane; q < w; q += 32) {
+        const double v = d[q] * sc;
+        d[q] = v;
+        if (q < c) a = fma(v, v, a);
+      }
+      a = warp_sum(a);
+      __syncwarp();
+      if (lane == 0) {
+        d[w] = a;
+        d[w + 1] = 1.0;
+      }
+    }
+    if (rank == 0 && tid == 0) cnt[(sweep + 1) % 3] = 0u;
+    cl.sync();
+    unsigned rotated = 0;
+    for (int br = 0; br < brounds; ++br) {
+      if (br == 0) {
+        // pairs inside each local block: round robin over nb rows
+        for (int ir = 0; ir < nb - 1; ++ir) {
+          for (int pi = warp; pi < nb; pi += kWarps) {
+            const int slot = pi / (nb / 2), pos = pi % (nb / 2);
+            const int i = rr_index(pos, ir, nb), j = rr_index(nb - 1 - pos, ir, nb);
+            if (jac_pair(row(cur, slot, i), row(cur, slot, j), c, w, eps2, lane)) ++rotated;
+          }
+          __syncthreads();
+        }
+      }
+      // pairs between the two local blocks
+      for (int s = 0; s < nb; ++s) {
+        for (int pi = warp; pi < nb; pi += kWarps)
+          if (jac_pair(row(cur, 0, pi), row(cur, 1, (pi + s) % nb), c, w, eps2, lane)) ++rotated;
+        __syncthreads();
+      }
+      if (br == brounds - 1 && lane == 0 && rotated) atomicAdd(&c0[sweep % 3], rotated);
+      // move both blocks to their next positions (other half of the buffer)
+      if (CS > 1) {
+        for (int slot = 0; slot < 2; ++slot) {
+          const int pos = slot == 0 ? rank : 2 * CS - 1 - rank;
+          const int np = jac_next_pos(pos, CS);
+          double* dst = cl.map_shared_rank(row(cur ^ 1, jac_pos_slot(np, CS), 0), jac_pos_cta(np, CS));
+          const double* src = row(cur, slot, 0);
+          for (size_t e = tid; e < slot_sz; e += kThreads) dst[e] = src[e];
+        }
+        cur ^= 1;
+      }
+      cl.sync();
+    }
+    if (*(volatile unsigned*)&c0[sweep % 3] == 0u) {
+      converged = true;
+      break;
+    }
+  }
+  // blocks are home after a whole number of sweeps: write back x = d x~
+  __syncthreads();
+  for (int slot = 0; slot < 2; ++slot) {
+    const int blk = slot == 0 ? rank : 2 * CS - 1 - rank;
+    for (int r = 0; r < nb; ++r) {
+      const int x = blk * nb + r;
+      if (x >= b) continue;
+      const double* d = row(cur, slot, r);
+      const double sc = d[w + 1];
+      for (int q = tid; q < c; q += kThreads) X[(size_t)x * c + q] = sc * d[q];
+      for (int q = tid; q < jb; q += kThreads) J[(size_t)x * b + q] = sc * d[c + q];
+    }
+  }
+  if (rank == 0 && tid == 0) {
+    st->pad2 = sweep + 1;
+    if (!converged) atomicCAS(&st->err, 0, 3);
+  }
+  cl.sync();  // keep every CTA's shared memory alive until all remote accesses are done
+}
+
+static JacBlockCfg jac_block_cfg(int b, int c, bool withJ, int cs_max) {
+  JacBlockCfg g{1, 2, 0};
+  int cs = 1;
+  while (cs < 16 && cs < cs_max && cs * 8 < b) cs *= 2;
+  int nb = (b + 2 * cs - 1) / (2 * cs);
+  nb += nb & 1;
+  if (nb < 2) nb = 2;
+  g.CS = cs;
+  g.nb = nb;
+  g.stride = c + (withJ ? b : 0) + 2;
+  return g;
+}
+
+static size_t jac_block_smem(const JacBlockCfg& g) {
+  return 4 * (size_t)g.nb * g.stride * sizeof(double) + 4 * sizeof(unsigned);
+}
+
 int launch_jacobi_rows(vp_ctx* ctx, double* X, int b, int c, double* J) {
   if (b <= 0) return VP_OK;
   const int CS = ctx->cluster_size;
+  const JacBlockCfg bc = jac_block_cfg(b, c, J != nullptr, std::max(1, CS));
+  if (b > 1 && jac_block_smem(bc) <= 200 * 1024) {
+    static bool battr_done = false;
+    if (!battr_done) {
+      VP_CUDA(ctx, cudaFuncSetAttribute(k_jacobi_block, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+      VP_CUDA(ctx, cudaFuncSetAttribute(k_jacobi_block, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+      battr_done = true;
+    }
+    // one CTA per SM: the FP64 pipe of each SM is the limit
+    const size_t smem = std::max<size_t>(jac_block_smem(bc), 120 * 1024);
+    double eps = 1e-15 * std::sqrt((double)c);
+    int max_sweeps = 60;
+    int nb = bc.nb;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    cfg.gridDim = dim3(bc.CS);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = ctx->stream;
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = bc.CS;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    ctx->launches++;
+    VP_CUDA(ctx, cudaLaunchKernelEx(&cfg, k_jacobi_block, X, b, c, J, eps, max_sweeps, nb, ctx->status));
+    return VP_OK;
+  }
   if (CS > 0 && b > 1 && cluster_jacobi_smem(b, c, CS, J != nullptr) <= 200 * 1024) {
     static bool attr_done = false;
     // at least 120 KB per CTA, so no two CTAs of the cluster share an SM

@@ -32,7 +32,7 @@ ERRORS = {1: "VP_EINVAL", 2: "VP_ENOMEM", 3: "VP_ECAPACITY", 4: "VP_ECUDA", 5: "
 
 EXPORTS = [
     "vp_ctx_create", "vp_ctx_destroy", "vp_last_error", "vp_kernel_launches", "vp_profile_enable",
-    "vp_profile_read",
+    "vp_profile_read", "vp_profile_trace",
     "mps_create", "mps_create_cores", "mps_destroy", "mps_num_sites", "mps_bonds", "mps_get_cores",
     "mps_to_dense", "mps_to_grid", "mps_save", "mps_load",
     "mpo_create_vp", "mpo_create_vlasov", "mpo_create_cores", "mpo_destroy", "mpo_num_sites", "mpo_bonds",
@@ -48,6 +48,10 @@ class VpError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"{ERRORS.get(code, code)}: {msg}")
         self.code = code
+
+
+class CTraceRec(C.Structure):
+    _fields_ = [("kclass", C.c_int), ("m", C.c_int), ("n", C.c_int), ("k", C.c_int), ("ms", C.c_double)]
 
 
 class CLayout(C.Structure):
@@ -105,6 +109,7 @@ def load():
         "vp_kernel_launches": (C.c_int64, [P]),
         "vp_profile_enable": (I, [P, I]),
         "vp_profile_read": (I, [P, I, DP, C.POINTER(C.c_int64), DP]),
+        "vp_profile_trace": (I, [P, C.POINTER(CTraceRec), I, IP]),
         "mps_create": (I, [P, C.POINTER(CLayout), P, I, I, D, C.POINTER(P)]),
         "mps_create_cores": (I, [P, I, IP, DP, C.POINTER(P)]),
         "mps_destroy": (I, [P]),
@@ -218,6 +223,14 @@ class Context:
             self._check(self.lib.vp_profile_read(self.h, k, C.byref(ms), C.byref(n), C.byref(w)))
             out[name] = (ms.value, int(n.value), w.value)
         return out
+
+    def profile_trace(self):
+        """Per-launch records of the profiling window: [{class, m, n, k, ms}]."""
+        n = C.c_int()
+        self._check(self.lib.vp_profile_trace(self.h, None, 0, C.byref(n)))
+        buf = (CTraceRec * max(1, n.value))()
+        self._check(self.lib.vp_profile_trace(self.h, buf, n.value, C.byref(n)))
+        return [{"class": KCLASSES[r.kclass], "m": r.m, "n": r.n, "k": r.k, "ms": r.ms} for r in buf[:n.value]]
 
     def close(self):
         """Destroy every live MPS/MPO/Sim of this context, then the context."""

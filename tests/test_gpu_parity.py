@@ -293,3 +293,26 @@ def test_reduced_precision_contractions_vs_fp64(ctx, prec):
     assert np.max(np.abs(wep - we64)) < we_abs
     assert np.max(np.abs(wep - we64) / we64) < we_rel
     assert 0 < rel(fp, f64) < f_rel
+
+
+def test_profile_trace_records(ctx):
+    # the launch trace carries one record per bracketed launch with its shape,
+    # and its per-class counts agree with the class totals
+    lay = I.Layout(5, 5, 0.0, 4 * math.pi, -6.0, 6.0, I.SEQ)
+    m = ctx.mps_from_grid(lay, I.landau(lay), 16, 1e-10)
+    sim = ctx.sim(lay, m, 0.02, 16, streams=1)
+    ctx.profile(True)
+    sim.step(1)
+    tr = ctx.profile_trace()
+    tot = ctx.profile_read()
+    ctx.profile(False)
+    sim.close()
+    assert tr and all(r["ms"] >= 0 for r in tr)
+    for cls, (ms, n, _) in tot.items():
+        recs = [r for r in tr if r["class"] == cls]
+        assert len(recs) == n
+        assert abs(sum(r["ms"] for r in recs) - ms) <= 1e-6 * max(1.0, ms)
+    qr = [r for r in tr if r["class"] == "qr_factor"]
+    assert qr and all(r["m"] >= 1 and r["n"] >= 1 for r in qr)
+    jac = [r for r in tr if r["class"] == "jacobi"]
+    assert jac and all(r["m"] == r["n"] and r["k"] >= 1 for r in jac)
