@@ -300,7 +300,7 @@ static int svd_site(vp_ctx* ctx, mps_t* s, int k, int chi, double tol, double* e
   }
   VP_CUDA(ctx, cudaMemsetAsync(ctx->status->rot, 0, sizeof(ctx->status->rot), ctx->stream));
   prof_begin(ctx, VP_K_JACOBI);
-  VP_TRY(launch_jacobi_rows(ctx, X, q, q, tall ? nullptr : ctx->w_j.p));
+  VP_TRY(launch_jacobi_rows(ctx, X, q, q, tall ? nullptr : ctx->w_j.p, tol >= 1e-13));
   prof_end(ctx, VP_K_JACOBI, 0.0, q, q);
   const size_t jac_mark = ctx->prof_on && !ctx->prof_marks.empty() ? ctx->prof_marks.size() - 1 : (size_t)-1;
   VP_TRY(reserve(ctx, ctx->w_vec, (size_t)2 * q + 8));

@@ -164,7 +164,10 @@ int launch_gemm_r(vp_ctx* ctx, int M, int N, int K, const double* Acm, int lda, 
                   int ldb, double* C, int ldc);
 // One-sided Jacobi on the b rows (length c) of X, rotations also applied to
 // the rows of J (b x b, set to the identity here).  Row-major, contiguous.
-int launch_jacobi_rows(vp_ctx* ctx, double* X, int b, int c, double* J);
+// floor_ok: the caller truncates every singular value below 1e-13 of the
+// largest (tol >= 1e-13), so the double-word kernel, which leaves rows under
+// 1e-15 of the largest unrotated, may be used.
+int launch_jacobi_rows(vp_ctx* ctx, double* X, int b, int c, double* J, bool floor_ok);
 // Largest cluster (16 or 8 CTAs, one per SM) the cluster-resident kernels
 // can use on this device; 0 if none.
 int probe_cluster_size();

@@ -13,6 +13,7 @@
 #include <cuda/atomic>
 
 #include "common.cuh"
+#include "dw.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -80,17 +81,6 @@ struct GridSync {
   __device__ void finish() {
     if (nb > 1 && blockIdx.x == 0 && threadIdx.x == 0) st->bar_base = target;
   }
-};
-
-// The same interface over one thread-block cluster (the whole grid is one
-// cluster): hardware barrier, about 0.2 us.
-struct ClusterSync {
-  __device__ ClusterSync(DevStatus*, unsigned) {}
-  __device__ bool sync() {
-    cg::this_cluster().sync();
-    return true;
-  }
-  __device__ void finish() {}
 };
 
 static int coop_launch(vp_ctx* ctx, const void* fn, int blocks, int threads, void** args, size_t smem,
@@ -186,15 +176,15 @@ __global__ void __launch_bounds__(kThreads) k_qr_factor(double* A, int m, int n,
 
 // Look-ahead variant for the cooperative grid: no grid barrier.  Reflector j
 // (v in column j of A below the diagonal, v_j = 1 implicit, tau[j]) is
-// published by a release increment of a monotonic counter.  At step j every
-// block waits only for reflector j; the owner of column j+1 first applies H_j
-// to that column with the whole block, forms and publishes reflector j+1, and
-// only then applies H_j to the rest of its columns.  The critical path per
-// column is one column update, one reflector and one publication; the bulk
-// trailing update runs behind it.  The counter base carries over between
-// launches: the last block to finish records the new base.
+// published by a release store of a monotonic counter.  At step j every
+// block waits only for reflector j; in the owner of column j+1, warp 0
+// applies H_j to that column, forms and publishes reflector j+1 while the
+// other warps apply H_j to the rest of the block's columns.  The critical path
+// per column is one warp's column update, reflector and publication (a whole
+// block would only add barriers: the FP64 pipe is per SM); the bulk trailing
+// update runs beside it.  The counter base carries over between launches:
+// the last block to finish records the new base.
 __global__ void __launch_bounds__(kThreads) k_qr_factor_la(double* A, int m, int n, double* tau, DevStatus* st) {
-  __shared__ double red[kWarps + 1];
   __shared__ int s_ok;
   const int nb = gridDim.x, bid = blockIdx.x, tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
@@ -202,15 +192,27 @@ __global__ void __launch_bounds__(kThreads) k_qr_factor_la(double* A, int m, int
   const unsigned long long base = *(volatile unsigned long long*)&st->pub_base;
   cuda::atomic_ref<unsigned long long, cuda::thread_scope_device> pub(st->pub_count);
 
-  // reflector of column j (which already carries H_0 .. H_{j-1})
-  auto reflect = [&](int j) {
+  // One warp: apply H_{j-1} (when j > 0) to column j, form reflector j in
+  // place and publish it.  Column j already carries H_0 .. H_{j-2}.
+  auto critical = [&](int j) {
     double* col = A + (size_t)j * m;
+    if (j > 0) {
+      const double t = __ldcg(tau + j - 1);
+      if (t != 0.0) {
+        const double* v = A + (size_t)(j - 1) * m;
+        double w = lane == 0 ? col[j - 1] : 0.0;
+        for (int i = j + lane; i < m; i += 32) w = fma(__ldcg(v + i), col[i], w);
+        w = warp_sum(w) * t;
+        if (lane == 0) col[j - 1] -= w;
+        for (int i = j + lane; i < m; i += 32) col[i] = fma(-w, __ldcg(v + i), col[i]);
+      }
+    }
     double s = 0.0;
-    for (int i = j + 1 + tid; i < m; i += kThreads) {
+    for (int i = j + 1 + lane; i < m; i += 32) {
       const double x = col[i];
       s = fma(x, x, s);
     }
-    s = block_sum(s, red);
+    s = warp_sum(s);
     const double x0 = col[j];
     double t = 0.0, beta = x0, scale = 0.0;
     if (s > 0.0) {
@@ -219,14 +221,14 @@ __global__ void __launch_bounds__(kThreads) k_qr_factor_la(double* A, int m, int
       t = (beta - x0) / beta;
       scale = 1.0 / (x0 - beta);
     }
-    for (int i = j + 1 + tid; i < m; i += kThreads) col[i] *= scale;
-    if (tid == 0) {
+    for (int i = j + 1 + lane; i < m; i += 32) col[i] *= scale;
+    if (lane == 0) {
       col[j] = beta;
       tau[j] = t;
     }
     __threadfence();
-    __syncthreads();
-    if (tid == 0) pub.store(base + j + 1, cuda::memory_order_release);
+    __syncwarp();
+    if (lane == 0) pub.store(base + j + 1, cuda::memory_order_release);
   };
   auto wait = [&](int j) -> bool {
     if (tid == 0) {
@@ -249,31 +251,27 @@ __global__ void __launch_bounds__(kThreads) k_qr_factor_la(double* A, int m, int
     return s_ok != 0;
   };
 
-  if (bid == 0) reflect(0);
+  if (bid == 0 && warp == 0) critical(0);
   bool ok = true;
-  for (int j = 0; j < p && ok; ++j) {
+  for (int j = 0; j < p; ++j) {
     if (!wait(j)) {
       ok = false;
       break;
     }
-    const double t = __ldcg(tau + j);
-    const double* v = A + (size_t)j * m;
-    if (j + 1 < p && bid == (j + 1) % nb) {
-      if (t != 0.0) {
-        double* col = A + (size_t)(j + 1) * m;
-        double w = tid == 0 ? col[j] : 0.0;
-        for (int i = j + 1 + tid; i < m; i += kThreads) w = fma(__ldcg(v + i), col[i], w);
-        w = block_sum(w, red) * t;
-        if (tid == 0) col[j] -= w;
-        for (int i = j + 1 + tid; i < m; i += kThreads) col[i] = fma(-w, __ldcg(v + i), col[i]);
-        __syncthreads();
-      }
-      reflect(j + 1);
+    // the owner of column j+1 hands it to warp 0 (critical path); the
+    // remaining warps apply H_j to the block's columns from j+2 on
+    const bool owner = j + 1 < p && bid == (j + 1) % nb;
+    if (owner && warp == 0) {
+      critical(j + 1);
+      continue;
     }
+    const double t = __ldcg(tau + j);
     if (t == 0.0) continue;
+    const double* v = A + (size_t)j * m;
+    const int wk = owner ? warp - 1 : warp, nwk = owner ? kWarps - 1 : kWarps;
     const int first = j + 2;
     const int k0 = first + ((bid - first % nb) % nb + nb) % nb;
-    for (int k = k0 + warp * nb; k < n; k += kWarps * nb) {
+    for (int k = k0 + wk * nb; k < n; k += nwk * nb) {
       double* col = A + (size_t)k * m;
       double w = lane == 0 ? col[j] : 0.0;
       for (int i = j + 1 + lane; i < m; i += 32) w = fma(__ldcg(v + i), col[i], w);
@@ -294,40 +292,87 @@ __global__ void __launch_bounds__(kThreads) k_qr_factor_la(double* A, int m, int
   }
 }
 
+// Small matrices: one block, the matrix in shared memory (leading dimension
+// m | 1, odd, so that lanes walking different columns hit different banks).
+// Step j: warp 0 forms reflector j; then each thread owns one trailing column
+// and applies H_j to it with a serial dot product over the rows, so one FMA
+// instruction serves 32 columns (a warp per column would spend a five-step
+// shuffle reduction on every column, and FP64 issues at two lanes per clock
+// per SM).
+__global__ void __launch_bounds__(kThreads) k_qr_factor_small(double* A, int m, int n, double* tau) {
+  extern __shared__ double sa[];
+  __shared__ double s_t;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int ld = m | 1, p = min(m, n);
+  for (int e = tid; e < m * n; e += kThreads) sa[(size_t)(e / m) * ld + e % m] = A[e];
+  __syncthreads();
+  for (int j = 0; j < p; ++j) {
+    double* col = sa + (size_t)j * ld;
+    if (warp == 0) {
+      double s = 0.0;
+      for (int i = j + 1 + lane; i < m; i += 32) s = fma(col[i], col[i], s);
+      s = warp_sum(s);
+      const double x0 = col[j];
+      double t = 0.0, beta = x0, scale = 0.0;
+      if (s > 0.0) {
+        const double nrm = sqrt(fma(x0, x0, s));
+        beta = x0 >= 0.0 ? -nrm : nrm;
+        t = (beta - x0) / beta;
+        scale = 1.0 / (x0 - beta);
+      }
+      for (int i = j + 1 + lane; i < m; i += 32) col[i] *= scale;
+      __syncwarp();
+      if (lane == 0) {
+        col[j] = beta;
+        s_t = t;
+        tau[j] = t;
+      }
+    }
+    __syncthreads();
+    const double t = s_t;
+    if (t != 0.0) {
+      for (int k = j + 1 + tid; k < n; k += kThreads) {
+        double* ck = sa + (size_t)k * ld;
+        double w = ck[j];
+        for (int i = j + 1; i < m; ++i) w = fma(col[i], ck[i], w);
+        w *= t;
+        ck[j] -= w;
+        for (int i = j + 1; i < m; ++i) ck[i] = fma(-w, col[i], ck[i]);
+      }
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < m * n; e += kThreads) A[e] = sa[(size_t)(e / m) * ld + e % m];
+}
+
+// Cost model (SM clocks) of the two factorisations: FP64 warp instructions
+// at 16 clocks each plus the per-column reflector chain (small), or a
+// measured ~2.5 us per column on the critical path (look-ahead grid).
+static double qr_small_cost(int m, int n) {
+  const int p = std::min(m, n);
+  double c = 0.0;
+  for (int j = 0; j < p; ++j) c += 16.0 * ((n - j - 1 + 31) / 32) * 2.0 * (m - j) + 600.0;
+  return c;
+}
+static double qr_grid_cost(int m, int n) { return 5200.0 * std::min(m, n); }
+
 int launch_qr_factor(vp_ctx* ctx, double* A, int m, int n, double* tau, double* vbuf) {
   const int p = std::min(m, n);
   if (p <= 0) return VP_OK;
-  // Small and medium matrices: one cluster (per-column barrier ~0.2 us); the
-  // FP64 work per column and CTA stays below ~1 us while n * m <= 32K.
-  const int CS = ctx->cluster_size;
-  if (CS > 0 && (long long)m * n <= 32768 && (long long)m * n >= 2048 && n >= CS) {
-    static bool attr_done = false;
-    if (!attr_done) {
-      VP_CUDA(ctx, cudaFuncSetAttribute(k_qr_factor<ClusterSync>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
-      VP_CUDA(ctx, cudaFuncSetAttribute(k_qr_factor<ClusterSync>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        120 * 1024));
-      attr_done = true;
+  const size_t small_smem = (size_t)(m | 1) * n * sizeof(double);
+  if (small_smem <= 200 * 1024 && qr_small_cost(m, n) <= qr_grid_cost(m, n)) {
+    static bool sattr = false;
+    if (!sattr) {
+      VP_CUDA(ctx, cudaFuncSetAttribute(k_qr_factor_small, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+      sattr = true;
     }
-    cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute at[1];
-    cfg.gridDim = dim3(CS);
-    cfg.blockDim = dim3(kThreads);
-    cfg.dynamicSmemBytes = 120 * 1024;  // one CTA per SM
-    cfg.stream = ctx->stream;
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = CS;
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
     ctx->launches++;
-    VP_CUDA(ctx, cudaLaunchKernelEx(&cfg, k_qr_factor<ClusterSync>, A, m, n, tau, vbuf, ctx->status));
-    return VP_OK;
+    k_qr_factor_small<<<1, kThreads, small_smem, ctx->stream>>>(A, m, n, tau);
+    return check_launch(ctx, "qr_factor_small");
   }
   // enough blocks that each owns a few columns, but never more than one per SM
   const int cap = ctx->coop_cap > 0 ? std::min(ctx->coop_cap, ctx->num_sms) : ctx->num_sms;
-  int blocks = std::min(cap, std::max(1, n / 2));
-  if ((long long)m * n < 8192) blocks = 1;
+  const int blocks = std::min(cap, std::max(1, n / 2));
   DevStatus* st = ctx->status;
   if (blocks > 1) {
     void* args[] = {&A, &m, &n, &tau, &st};
@@ -778,35 +823,52 @@ __device__ __forceinline__ int jac_next_pos(int pos, int CS) {
   return pos == 0 ? 0 : (pos == 2 * CS - 1 ? 1 : pos + 1);
 }
 
-// One scaled rotation of rows ri, rj (local shared memory) by one warp.
-// Returns true when the pair was rotated.
-__device__ __forceinline__ bool jac_pair(double* ri, double* rj, int c, int w, double eps2, int lane) {
-  double* ei = ri + w;  // alpha, d of row i
-  double* ej = rj + w;
-  const double al = ei[0], be = ej[0], di = ei[1], dj = ej[1];
+// The pairs of one inner round are processed in three phases, because FP64
+// issues at two lanes per clock per SM on GB300 and the scalar work of a
+// rotation (threshold, square root, divisions) costs as much as a whole
+// 128-element update when every warp repeats it:
+//   A  one warp per pair: gamma~ = <x~_i, x~_j> (FMA + warp reduction);
+//   B  one lane per pair (warp 0): threshold, rotation, new alpha and d, the
+//      two update coefficients;
+//   C  one warp per pair: x~_i -= a x~_j, x~_j += b x~_i.
+// par[4 p + 0..3]: gamma~, a, b, rotate flag of pair p.
+__device__ __forceinline__ void jac_dot(const double* ri, const double* rj, int c, int lane, double* par) {
   double g = 0.0;
   for (int q = lane; q < c; q += 32) g = fma(ri[q], rj[q], g);
   g = warp_sum(g);
-  if (!(al > 0.0 && be > 0.0)) return false;
-  const double ga = di * dj * g;
-  if (!(ga * ga > eps2 * al * be)) return false;
+  if (lane == 0) par[0] = g;
+}
+
+// Returns 1 when the pair is rotated.
+__device__ __forceinline__ int jac_params(double* ri, double* rj, int w, double eps2, double* par) {
+  double* ei = ri + w;  // alpha, d of row i
+  double* ej = rj + w;
+  const double al = ei[0], be = ej[0], di = ei[1], dj = ej[1];
+  par[3] = 0.0;
+  if (!(al > 0.0 && be > 0.0)) return 0;
+  const double ga = di * dj * par[0];
+  if (!(ga * ga > eps2 * al * be)) return 0;
   double t, cs, sn;
   jacobi_rotation(al, be, ga, t, cs, sn);
   const double inv = 1.0 / (di * dj);
-  const double a = t * dj * dj * inv, bb = t * di * di * inv;
+  par[1] = t * dj * dj * inv;
+  par[2] = t * di * di * inv;
+  par[3] = 1.0;
+  ei[0] = fma(-t, ga, al);
+  ej[0] = fma(t, ga, be);
+  ei[1] = cs * di;
+  ej[1] = cs * dj;
+  return 1;
+}
+
+__device__ __forceinline__ void jac_update(double* ri, double* rj, int w, int lane, const double* par) {
+  if (par[3] == 0.0) return;
+  const double a = par[1], bb = par[2];
   for (int q = lane; q < w; q += 32) {
     const double u = ri[q], v = rj[q];
     ri[q] = fma(-a, v, u);
     rj[q] = fma(bb, u, v);
   }
-  __syncwarp();
-  if (lane == 0) {
-    ei[0] = fma(-t, ga, al);
-    ej[0] = fma(t, ga, be);
-    ei[1] = cs * di;
-    ej[1] = cs * dj;
-  }
-  return true;
 }
 
 __global__ void __launch_bounds__(kThreads) k_jacobi_block(double* X, int b, int c, double* J, double eps,
@@ -820,8 +882,32 @@ __global__ void __launch_bounds__(kThreads) k_jacobi_block(double* X, int b, int
   const size_t slot_sz = (size_t)nb * stride;
   // buffer set s, slot (0 top, 1 bottom), row r
   auto row = [&](int s, int slot, int r) { return sm + ((size_t)(s * 2 + slot)) * slot_sz + (size_t)r * stride; };
-  unsigned* cnt = reinterpret_cast<unsigned*>(sm + 4 * slot_sz);
+  double* par = sm + 4 * slot_sz;  // 4 doubles per pair of an inner round
+  unsigned* cnt = reinterpret_cast<unsigned*>(par + 4 * nb);
   const double eps2 = eps * eps;
+  // one inner round over nb disjoint pairs (rows given by pair_rows)
+  auto inner_round = [&](auto pair_rows, unsigned& rotated) {
+    for (int pi = warp; pi < nb; pi += kWarps) {
+      double *ri, *rj;
+      pair_rows(pi, ri, rj);
+      jac_dot(ri, rj, c, lane, par + 4 * pi);
+    }
+    __syncthreads();
+    if (warp == 0) {
+      for (int pi = lane; pi < nb; pi += 32) {
+        double *ri, *rj;
+        pair_rows(pi, ri, rj);
+        rotated += jac_params(ri, rj, w, eps2, par + 4 * pi);
+      }
+    }
+    __syncthreads();
+    for (int pi = warp; pi < nb; pi += kWarps) {
+      double *ri, *rj;
+      pair_rows(pi, ri, rj);
+      jac_update(ri, rj, w, lane, par + 4 * pi);
+    }
+    __syncthreads();
+  };
 
   // home placement: top = block rank, bottom = block 2 CS - 1 - rank
   for (int slot = 0; slot < 2; ++slot) {
@@ -870,22 +956,27 @@ __global__ void __launch_bounds__(kThreads) k_jacobi_block(double* X, int b, int
     for (int br = 0; br < brounds; ++br) {
       if (br == 0) {
         // pairs inside each local block: round robin over nb rows
-        for (int ir = 0; ir < nb - 1; ++ir) {
-          for (int pi = warp; pi < nb; pi += kWarps) {
-            const int slot = pi / (nb / 2), pos = pi % (nb / 2);
-            const int i = rr_index(pos, ir, nb), j = rr_index(nb - 1 - pos, ir, nb);
-            if (jac_pair(row(cur, slot, i), row(cur, slot, j), c, w, eps2, lane)) ++rotated;
-          }
-          __syncthreads();
-        }
+        for (int ir = 0; ir < nb - 1; ++ir)
+          inner_round(
+              [&](int pi, double*& ri, double*& rj) {
+                const int slot = pi / (nb / 2), pos = pi % (nb / 2);
+                ri = row(cur, slot, rr_index(pos, ir, nb));
+                rj = row(cur, slot, rr_index(nb - 1 - pos, ir, nb));
+              },
+              rotated);
       }
       // pairs between the two local blocks
-      for (int s = 0; s < nb; ++s) {
-        for (int pi = warp; pi < nb; pi += kWarps)
-          if (jac_pair(row(cur, 0, pi), row(cur, 1, (pi + s) % nb), c, w, eps2, lane)) ++rotated;
-        __syncthreads();
+      for (int s = 0; s < nb; ++s)
+        inner_round(
+            [&](int pi, double*& ri, double*& rj) {
+              ri = row(cur, 0, pi);
+              rj = row(cur, 1, (pi + s) % nb);
+            },
+            rotated);
+      if (br == brounds - 1 && warp == 0) {
+        const unsigned tot = __reduce_add_sync(0xffffffffu, rotated);
+        if (lane == 0 && tot) atomicAdd(&c0[sweep % 3], tot);
       }
-      if (br == brounds - 1 && lane == 0 && rotated) atomicAdd(&c0[sweep % 3], rotated);
       // move both blocks to their next positions (other half of the buffer)
       if (CS > 1) {
         for (int slot = 0; slot < 2; ++slot) {
@@ -924,6 +1015,210 @@ __global__ void __launch_bounds__(kThreads) k_jacobi_block(double* X, int b, int
   cl.sync();  // keep every CTA's shared memory alive until all remote accesses are done
 }
 
+// Double-word variant of k_jacobi_block (the production path): the same
+// block-local circle schedule, with the rows held as double-word FP32 pairs
+// (dw.cuh), so that the dot products, rotation parameters and updates run on
+// the FP32 pipe.  The matrix is first scaled by a power of two common to the
+// whole cluster (exact) so that its largest entry is ~1; rows whose squared
+// norm falls below 1e-30 of that (singular values under 1e-15 of the
+// largest) are left alone.  A rotation uses the standard form
+// x_i <- c x_i - s x_j, x_j <- s x_i + c x_j with c = 1/sqrt(1 + t^2) and
+// s = c t computed to double-word accuracy from an FP32 tangent t: the angle
+// need not be the exact Jacobi angle, the rotation is orthogonal to ~1e-14
+// either way.  Pairs rotate while |gamma| > eps sqrt(alpha beta) with eps
+// above the ~1e-14 noise of a double-word dot product.  Row layout (stride
+// w + 1, w = c + jb, in double-word units): x (c), rotation row (jb), alpha.
+__global__ void __launch_bounds__(kThreads) k_jacobi_dw(double* X, int b, int c, double* J, float eps,
+                                                        int max_sweeps, int nb, DevStatus* st) {
+  cg::cluster_group cl = cg::this_cluster();
+  extern __shared__ double smd[];
+  dw* sm = reinterpret_cast<dw*>(smd);
+  const int CS = (int)cl.num_blocks(), rank = (int)cl.block_rank();
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int jb = J ? b : 0;
+  const int w = c + jb, stride = w + 1;
+  const size_t slot_sz = (size_t)nb * stride;
+  auto row = [&](int s, int slot, int r) { return sm + ((size_t)(s * 2 + slot)) * slot_sz + (size_t)r * stride; };
+  dw* par = sm + 4 * slot_sz;  // per pair: flag, cos, sin
+  float* red = reinterpret_cast<float*>(par + 3 * nb);  // kWarps + 1 floats
+  unsigned* cnt = reinterpret_cast<unsigned*>(red + kWarps + 2);
+
+  // common power-of-two scale: largest |x| over the cluster's rows
+  float mx = 0.f;
+  for (int slot = 0; slot < 2; ++slot) {
+    const int blk = slot == 0 ? rank : 2 * CS - 1 - rank;
+    for (int r = 0; r < nb; ++r) {
+      const int x = blk * nb + r;
+      if (x >= b) continue;
+      for (int q = tid; q < c; q += kThreads) mx = fmaxf(mx, fabsf(__double2float_rn(X[(size_t)x * c + q])));
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (lane == 0) red[warp] = mx;
+  __syncthreads();
+  if (tid == 0) {
+    float m = 0.f;
+    for (int i = 0; i < kWarps; ++i) m = fmaxf(m, red[i]);
+    red[kWarps] = m;
+  }
+  if (tid < 4) cnt[tid] = 0u;
+  cl.sync();
+  float gmax = 0.f;
+  for (int r = 0; r < CS; ++r) gmax = fmaxf(gmax, *cl.map_shared_rank(red + kWarps, r));
+  int ex = 0;
+  if (gmax > 0.f) frexpf(gmax, &ex);
+  const double sc = ldexp(1.0, -ex), inv_sc = ldexp(1.0, ex);
+
+  // home placement: top = block rank, bottom = block 2 CS - 1 - rank
+  for (int slot = 0; slot < 2; ++slot) {
+    const int blk = slot == 0 ? rank : 2 * CS - 1 - rank;
+    for (int r = 0; r < nb; ++r) {
+      const int x = blk * nb + r;
+      dw* d = row(0, slot, r);
+      for (int q = tid; q < stride; q += kThreads) {
+        dw v = {0.f, 0.f};
+        if (x < b) {
+          if (q < c) v = dw_from(X[(size_t)x * c + q] * sc);
+          else if (q < w) v.hi = (q - c == x) ? 1.0f : 0.0f;
+        }
+        d[q] = v;
+      }
+    }
+  }
+  unsigned* c0 = cl.map_shared_rank(cnt, 0);
+  const float tiny = 1e-30f;
+
+  // one inner round over nb disjoint pairs: A dot products (a warp per pair),
+  // B rotation parameters (a lane per pair), C updates (a warp per pair)
+  auto inner_round = [&](auto pair_rows, unsigned& rotated) {
+    for (int pi = warp; pi < nb; pi += kWarps) {
+      dw *ri, *rj;
+      pair_rows(pi, ri, rj);
+      dw_acc acc;
+      for (int q = lane; q < c; q += 32) dw_dot_step(acc, ri[q], rj[q]);
+      const dw g = dw_warp_sum(dw_acc_value(acc));
+      if (lane == 0) par[3 * pi] = g;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      for (int pi = lane; pi < nb; pi += 32) {
+        dw *ri, *rj;
+        pair_rows(pi, ri, rj);
+        const dw al = ri[w], be = rj[w], g = par[3 * pi];
+        float flag = 0.f;
+        if (al.hi > tiny && be.hi > tiny && fabsf(g.hi) * rsqrtf(al.hi) * rsqrtf(be.hi) > eps) {
+          // tangent in FP32 after an exact power-of-two scaling of d and
+          // gamma (their squares would leave the FP32 range for small rows)
+          const float d0 = 0.5f * dw_add(be, dw_neg(al)).hi;
+          int e2;
+          frexpf(fmaxf(fabsf(d0), fabsf(g.hi)), &e2);
+          const float d = ldexpf(d0, -e2), gs = ldexpf(g.hi, -e2);
+          const float t = copysignf(1.0f, d) * gs / (fabsf(d) + sqrtf(fmaf(d, d, gs * gs)));
+          if (t != 0.f) {
+            const dw t2 = two_prod(t, t);
+            const dw cs = dw_rsqrt(dw_add({1.0f, 0.0f}, t2));
+            const dw sn = dw_mul_f(cs, t);
+            const dw tg = dw_mul_f(g, t);
+            ri[w] = dw_add(al, dw_neg(tg));
+            rj[w] = dw_add(be, tg);
+            par[3 * pi + 1] = cs;
+            par[3 * pi + 2] = sn;
+            flag = 1.f;
+            ++rotated;
+          }
+        }
+        par[3 * pi].hi = flag;
+      }
+    }
+    __syncthreads();
+    for (int pi = warp; pi < nb; pi += kWarps) {
+      if (par[3 * pi].hi == 0.f) continue;
+      dw *ri, *rj;
+      pair_rows(pi, ri, rj);
+      const dw cs = par[3 * pi + 1], sn = par[3 * pi + 2];
+      for (int q = lane; q < w; q += 32) {
+        const dw u = ri[q], v = rj[q];
+        ri[q] = dw_add(dw_mul(cs, u), dw_neg(dw_mul(sn, v)));
+        rj[q] = dw_add(dw_mul(sn, u), dw_mul(cs, v));
+      }
+    }
+    __syncthreads();
+  };
+
+  int cur = 0, sweep = 0;
+  bool converged = false;
+  const int brounds = 2 * CS - 1;
+  for (; sweep < max_sweeps; ++sweep) {
+    // exact squared norms of the local rows
+    __syncthreads();
+    for (int rr = warp; rr < 2 * nb; rr += kWarps) {
+      dw* d = row(cur, rr / nb, rr % nb);
+      dw_acc acc;
+      for (int q = lane; q < c; q += 32) dw_dot_step(acc, d[q], d[q]);
+      const dw a = dw_warp_sum(dw_acc_value(acc));
+      if (lane == 0) d[w] = a;
+    }
+    if (rank == 0 && tid == 0) cnt[(sweep + 1) % 3] = 0u;
+    cl.sync();
+    unsigned rotated = 0;
+    for (int br = 0; br < brounds; ++br) {
+      if (br == 0) {
+        for (int ir = 0; ir < nb - 1; ++ir)
+          inner_round(
+              [&](int pi, dw*& ri, dw*& rj) {
+                const int slot = pi / (nb / 2), pos = pi % (nb / 2);
+                ri = row(cur, slot, rr_index(pos, ir, nb));
+                rj = row(cur, slot, rr_index(nb - 1 - pos, ir, nb));
+              },
+              rotated);
+      }
+      for (int s = 0; s < nb; ++s)
+        inner_round(
+            [&](int pi, dw*& ri, dw*& rj) {
+              ri = row(cur, 0, pi);
+              rj = row(cur, 1, (pi + s) % nb);
+            },
+            rotated);
+      if (br == brounds - 1 && warp == 0) {
+        const unsigned tot = __reduce_add_sync(0xffffffffu, rotated);
+        if (lane == 0 && tot) atomicAdd(&c0[sweep % 3], tot);
+      }
+      if (CS > 1) {
+        for (int slot = 0; slot < 2; ++slot) {
+          const int pos = slot == 0 ? rank : 2 * CS - 1 - rank;
+          const int np = jac_next_pos(pos, CS);
+          dw* dst = cl.map_shared_rank(row(cur ^ 1, jac_pos_slot(np, CS), 0), jac_pos_cta(np, CS));
+          const dw* src = row(cur, slot, 0);
+          for (size_t e = tid; e < slot_sz; e += kThreads) dst[e] = src[e];
+        }
+        cur ^= 1;
+      }
+      cl.sync();
+    }
+    if (*(volatile unsigned*)&c0[sweep % 3] == 0u) {
+      converged = true;
+      break;
+    }
+  }
+  __syncthreads();
+  for (int slot = 0; slot < 2; ++slot) {
+    const int blk = slot == 0 ? rank : 2 * CS - 1 - rank;
+    for (int r = 0; r < nb; ++r) {
+      const int x = blk * nb + r;
+      if (x >= b) continue;
+      const dw* d = row(cur, slot, r);
+      for (int q = tid; q < c; q += kThreads) X[(size_t)x * c + q] = dw_to(d[q]) * inv_sc;
+      for (int q = tid; q < jb; q += kThreads) J[(size_t)x * b + q] = dw_to(d[c + q]);
+    }
+  }
+  if (rank == 0 && tid == 0) {
+    st->pad2 = sweep + 1;
+    if (!converged) atomicCAS(&st->err, 0, 3);
+  }
+  cl.sync();  // keep every CTA's shared memory alive until all remote accesses are done
+}
+
 static JacBlockCfg jac_block_cfg(int b, int c, bool withJ, int cs_max) {
   JacBlockCfg g{1, 2, 0};
   int cs = 1;
@@ -937,14 +1232,49 @@ static JacBlockCfg jac_block_cfg(int b, int c, bool withJ, int cs_max) {
   return g;
 }
 
-static size_t jac_block_smem(const JacBlockCfg& g) {
-  return 4 * (size_t)g.nb * g.stride * sizeof(double) + 4 * sizeof(unsigned);
+static size_t jac_dw_smem(const JacBlockCfg& g) {
+  // rows (stride - 1 double words: no scale slot), pair parameters, reduction, counters
+  return (4 * (size_t)g.nb * (g.stride - 1) + 3 * (size_t)g.nb) * sizeof(dw) + (kWarps + 2) * sizeof(float) +
+         4 * sizeof(unsigned);
 }
 
-int launch_jacobi_rows(vp_ctx* ctx, double* X, int b, int c, double* J) {
+static size_t jac_block_smem(const JacBlockCfg& g) {
+  return (4 * (size_t)g.nb * g.stride + 4 * (size_t)g.nb) * sizeof(double) + 4 * sizeof(unsigned);
+}
+
+int launch_jacobi_rows(vp_ctx* ctx, double* X, int b, int c, double* J, bool floor_ok) {
   if (b <= 0) return VP_OK;
   const int CS = ctx->cluster_size;
   const JacBlockCfg bc = jac_block_cfg(b, c, J != nullptr, std::max(1, CS));
+  if (floor_ok && b > 1 && jac_dw_smem(bc) <= 200 * 1024) {
+    static bool dattr_done = false;
+    if (!dattr_done) {
+      VP_CUDA(ctx, cudaFuncSetAttribute(k_jacobi_dw, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+      VP_CUDA(ctx, cudaFuncSetAttribute(k_jacobi_dw, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+      dattr_done = true;
+    }
+    const size_t smem = std::max<size_t>(jac_dw_smem(bc), 120 * 1024);
+    // rotate while |gamma| > eps sqrt(alpha beta); eps above the double-word
+    // dot-product noise, which grows like sqrt(c) u^2
+    float eps = (float)(4e-13 * std::sqrt((double)c));
+    int max_sweeps = 60;
+    int nb = bc.nb;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    cfg.gridDim = dim3(bc.CS);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = ctx->stream;
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = bc.CS;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    ctx->launches++;
+    VP_CUDA(ctx, cudaLaunchKernelEx(&cfg, k_jacobi_dw, X, b, c, J, eps, max_sweeps, nb, ctx->status));
+    return VP_OK;
+  }
   if (b > 1 && jac_block_smem(bc) <= 200 * 1024) {
     static bool battr_done = false;
     if (!battr_done) {

@@ -107,6 +107,10 @@ COMPRESS_CASES = [
     ([1, 2, 3, 37, 90, 41, 7, 2, 1], 1 << 10, 0.0),
     ([1, 2, 4, 8, 16, 32, 64, 130, 64, 17, 4, 2, 1], 24, 0.0),
     ([1, 2, 4, 8, 16, 32, 70, 150, 200, 75, 31, 8, 2, 1], 1 << 10, 0.0),
+    # truncating compressions (the double-word Jacobi path)
+    ([1, 2, 4, 8, 16, 32, 70, 150, 200, 75, 31, 8, 2, 1], 1 << 10, 1e-12),
+    ([1, 2, 4, 8, 16, 32, 64, 130, 64, 17, 4, 2, 1], 24, 1e-10),
+    ([1, 2, 3, 37, 90, 41, 7, 2, 1], 1 << 10, 1e-3),
 ]
 
 
@@ -134,6 +138,22 @@ def test_compress_tolerance_on_smooth_state(ctx):
         assert m.bonds() == OS.bonds(ref), (tol, chi)
         assert rel(m.to_dense(), OS.to_dense(ref)) < F_TOL
         assert max(errs) <= max(tol, 1.0) and abs(max(errs) - max(ref_errs)) <= 1e-6 * max(ref_errs) + 1e-15
+
+
+def test_compress_rank_deficient_sum(ctx):
+    # f + f has every bond doubled with exactly dependent rows: the truncating
+    # compression must find the original ranks (singular values at round-off
+    # level are cut) and reproduce 2 f
+    lay = I.Layout(5, 6, 0.0, 4 * math.pi, -6.0, 6.0, I.INTERLEAVED)
+    f = I.landau(lay, 0.3, 0.5) + 0.05 * I.saturated_two_stream(lay, modes=4)
+    a = ctx.mps_from_grid(lay, f, 1 << 10, 1e-12)
+    s = ctx.axpby(1.0, a, 1.0, a)
+    assert s.bonds()[1:-1] == [2 * r for r in a.bonds()[1:-1]]
+    ref, _ = OS.compress(OS.add(a.cores(), a.cores(), 1.0, 1.0), 1 << 10, 1e-12)
+    ctx.compress(s, 1 << 10, 1e-12)
+    assert s.bonds() == OS.bonds(ref)
+    assert max(s.bonds()) <= max(a.bonds())
+    assert rel(s.to_grid(lay), 2 * a.to_grid(lay)) < F_TOL
 
 
 def test_compress_zero_state(ctx):
@@ -204,7 +224,9 @@ def test_rk4_c1_steps(ctx, lay, ic, dt, chi, nsteps):
         rec = sim.step(1)[0]
         ref, d = OV.rk4_step(ref, lay, dt, chi)
         assert abs(rec["field_energy"] - d["field_energy"]) <= WE_TOL * d["field_energy"]
-        assert abs(rec["mass"] - d["mass"]) <= 1e-12 * abs(d["mass"])
+        # mass to the f tolerance: the truncating factorisations run in
+        # double-word arithmetic (~1e-12)
+        assert abs(rec["mass"] - d["mass"]) <= F_TOL * abs(d["mass"])
         assert sim.state().bonds() == d["bonds"]
         assert rel(sim.state().to_grid(lay), OV.mps_to_f(ref, lay)) < F_TOL
         np.testing.assert_allclose(sim.entropy(), d["entropy"], rtol=1e-8, atol=1e-12)
