@@ -28,9 +28,36 @@ int cuda_fail(vp_ctx* ctx, cudaError_t e, const char* what) {
   return fail(ctx, VP_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
+void drain_pending(vp_ctx* ctx, bool all) {
+  size_t k = 0;
+  for (size_t i = 0; i < ctx->pending.size(); ++i) {
+    const vp_ctx::PendingFree f = ctx->pending[i];
+    bool done = true;
+    if (all) {
+      cudaEventSynchronize(f.ev);
+    } else {
+      const cudaError_t q = cudaEventQuery(f.ev);
+      if (q == cudaErrorNotReady) {
+        (void)cudaGetLastError();  // "not ready" is a status, not an error
+        done = false;
+      }
+    }
+    if (done) {
+      ctx->freef(f.p, f.bytes, ctx->user);
+      ctx->free_events.push_back(f.ev);
+    } else {
+      ctx->pending[k++] = f;
+    }
+  }
+  ctx->pending.resize(k);
+}
+
 void* dev_alloc(vp_ctx* ctx, size_t bytes) {
   if (bytes == 0) bytes = 8;
-  if (ctx->alloc) return ctx->alloc(bytes, ctx->user);
+  if (ctx->alloc) {
+    drain_pending(ctx, false);
+    return ctx->alloc(bytes, ctx->user);
+  }
   void* p = nullptr;
   if (cudaMallocAsync(&p, bytes, ctx->stream) != cudaSuccess) return nullptr;
   return p;
@@ -38,10 +65,24 @@ void* dev_alloc(vp_ctx* ctx, size_t bytes) {
 
 void dev_free(vp_ctx* ctx, void* p, size_t bytes) {
   if (!p) return;
-  if (ctx->freef)
+  if (!ctx->freef) {
+    cudaFreeAsync(p, ctx->stream);  // stream-ordered by the runtime's pool
+    return;
+  }
+  cudaEvent_t ev = nullptr;
+  if (!ctx->free_events.empty()) {
+    ev = ctx->free_events.back();
+    ctx->free_events.pop_back();
+  } else if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+    ev = nullptr;
+  }
+  if (ev && cudaEventRecord(ev, ctx->stream) == cudaSuccess) {
+    ctx->pending.push_back({p, bytes, ev});
+  } else {
+    cudaStreamSynchronize(ctx->stream);
     ctx->freef(p, bytes, ctx->user);
-  else
-    cudaFreeAsync(p, ctx->stream);
+    if (ev) ctx->free_events.push_back(ev);
+  }
 }
 
 int reserve(vp_ctx* ctx, DevBuf& b, size_t elems) {
@@ -223,6 +264,7 @@ struct SideScope {
     std::swap(c->w_split, c->w_split_side);
     std::swap(c->w_tca, c->w_tca_side);
     std::swap(c->w_tcb, c->w_tcb_side);
+    std::swap(c->w_fq, c->w_fq_side);
   }
 };
 
@@ -590,13 +632,17 @@ int vp_ctx_destroy(vp_ctx* c) {
   cudaStreamSynchronize(c->stream);
   for (DevBuf* b : {&c->w_fac, &c->w_q, &c->w_gemm, &c->w_j, &c->w_p, &c->w_tmp, &c->w_tmp2, &c->w_vec, &c->w_split,
                     &c->w_piv, &c->w_q1, &c->w_q2, &c->w_r, &c->w_p2, &c->w_a, &c->w_b, &c->w_c, &c->w_l,
-                    &c->w_q_side, &c->w_split_side})
+                    &c->w_q_side, &c->w_split_side, &c->w_tca, &c->w_tcb, &c->w_tca_side, &c->w_tcb_side,
+                    &c->w_qrv, &c->w_qrc, &c->w_fq, &c->w_fq_side})
     release(c, *b);
   for (auto& b : c->w_chain) release(c, b);
   dev_free(c, c->status, sizeof(DevStatus));
   dev_free(c, c->d_small, 64 * sizeof(int));
   dev_free(c, c->d_smalld, 64 * sizeof(double));
   cudaStreamSynchronize(c->stream);
+  if (c->side) cudaStreamSynchronize(c->side);
+  if (c->freef) drain_pending(c, true);
+  for (cudaEvent_t e : c->free_events) cudaEventDestroy(e);
   cudaFreeHost(c->h_small);
   cudaFreeHost(c->h_smalld);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);

@@ -79,6 +79,19 @@ struct vp_ctx {
   vp::DevBuf w_q_side, w_split_side;  // scratch of the side-stream phase
   vp::DevBuf w_tca_side, w_tcb_side;
   std::vector<vp::DevBuf> w_chain;
+  vp::DevBuf w_qrv;                   // double-word reflectors published by the grid QR kernel
+  vp::DevBuf w_qrc;                   // its columns when they exceed shared memory
+  vp::DevBuf w_fq, w_fq_side;         // double-word reflectors of the Q formation
+  // Blocks handed back to the caller's allocator only once the work queued
+  // before their release has finished (the allocator callbacks know no
+  // streams, and this context's kernels run on several).
+  struct PendingFree {
+    void* p;
+    size_t bytes;
+    cudaEvent_t ev;
+  };
+  std::vector<PendingFree> pending;
+  std::vector<cudaEvent_t> free_events;
 };
 
 struct mps_t {
@@ -118,6 +131,8 @@ int reserve(vp_ctx* ctx, DevBuf& b, size_t elems);
 // Same, preserving the first `keep` doubles.
 int reserve_keep(vp_ctx* ctx, DevBuf& b, size_t elems, size_t keep);
 void release(vp_ctx* ctx, DevBuf& b);
+// Return released blocks whose work has finished (all: wait for every one).
+void drain_pending(vp_ctx* ctx, bool all);
 int check_launch(vp_ctx* ctx, const char* what);
 // Bracket one launch of class `cls` with events when profiling is on.
 void prof_begin(vp_ctx* ctx, int cls);

@@ -127,4 +127,24 @@ __device__ __forceinline__ dw dw_rsqrt(dw x) {
   return fast_two_sum(y0, corr);
 }
 
+// sqrt(x) for x >= 0: FP32 root y0, then y0 + (x - y0^2) / (2 y0) with the
+// residual x - y0^2 formed in DW (Newton's step for y^2 = x).
+__device__ __forceinline__ dw dw_sqrt(dw x) {
+  if (!(x.hi > 0.f)) return {0.f, 0.f};
+  const float y0 = sqrtf(x.hi);
+  const dw r = dw_add(x, dw_neg(two_prod(y0, y0)));
+  return fast_two_sum(y0, r.hi / (2.0f * y0));
+}
+
+// a / b: FP32 quotient q0, then one step of long division on the DW
+// remainder a - q0 b.
+__device__ __forceinline__ dw dw_div(dw a, dw b) {
+  const float q0 = a.hi / b.hi;
+  const dw r = dw_add(a, dw_neg(dw_mul_f(b, q0)));
+  return fast_two_sum(q0, r.hi / b.hi);
+}
+
+// x * 2^e for a DW value (exact unless the low part leaves the FP32 range).
+__device__ __forceinline__ dw dw_ldexp(dw x, int e) { return {ldexpf(x.hi, e), ldexpf(x.lo, e)}; }
+
 }  // namespace vp

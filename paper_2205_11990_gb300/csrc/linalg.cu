@@ -174,57 +174,109 @@ __global__ void __launch_bounds__(kThreads) k_qr_factor(double* A, int m, int n,
   gs.finish();
 }
 
-// Look-ahead variant for the cooperative grid: no grid barrier.  Reflector j
-// (v in column j of A below the diagonal, v_j = 1 implicit, tau[j]) is
-// published by a release store of a monotonic counter.  At step j every
-// block waits only for reflector j; in the owner of column j+1, warp 0
-// applies H_j to that column, forms and publishes reflector j+1 while the
-// other warps apply H_j to the rest of the block's columns.  The critical path
-// per column is one warp's column update, reflector and publication (a whole
-// block would only add barriers: the FP64 pipe is per SM); the bulk trailing
-// update runs beside it.  The counter base carries over between launches:
-// the last block to finish records the new base.
-__global__ void __launch_bounds__(kThreads) k_qr_factor_la(double* A, int m, int n, double* tau, DevStatus* st) {
+// Look-ahead QR for the cooperative grid (factors too large for one cluster):
+// no grid barrier.  Reflector j is published as double words in V (column j,
+// V[j][j] = 1) and T[j] by a release store of a monotonic counter; at step j
+// every block waits only for reflector j.  In the owner of column j+1, warp
+// 0 applies H_j to that column, forms and publishes reflector j+1 while the
+// other warps apply H_j to the rest of the block's columns; the counter base
+// carries over between launches (the last block to finish records it).  The
+// block's columns are held as double-word values (dw.cuh) in shared memory
+// (in global scratch when they do not fit), the arithmetic on the FP32 pipe.
+// Column k is scaled by 2^-e_k on load (A D = Q (R D): only R changes, and
+// is unscaled on store); each reflector is formed on its column rescaled by
+// a further power of two (v and tau do not depend on the scale), so no
+// square leaves the FP32 range.  The output A, tau is the FP64 LAPACK layout
+// of k_qr_factor.
+__global__ void __launch_bounds__(kThreads) k_qr_factor_dw(double* A, int m, int n, double* tau, dw* V, dw* T,
+                                                          dw* gcols, int* gexp, DevStatus* st) {
+  extern __shared__ dw cols_sm[];
   __shared__ int s_ok;
   const int nb = gridDim.x, bid = blockIdx.x, tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
   const int p = min(m, n);
+  const int nown = bid < n ? (n - bid + nb - 1) / nb : 0;
+  const int nmax = (n + nb - 1) / nb;
+  // the block's columns (and their scale exponents) in shared memory, or in
+  // global scratch (gcols, gexp: column k at k m) when they do not fit
+  dw* cols = gcols ? gcols + (size_t)bid * m : cols_sm;
+  const size_t cstride = gcols ? (size_t)nb * m : (size_t)m;
+  int* cexp = gcols ? gexp + bid : reinterpret_cast<int*>(cols_sm + (size_t)nmax * m);
+  const int estride = gcols ? nb : 1;
   const unsigned long long base = *(volatile unsigned long long*)&st->pub_base;
   cuda::atomic_ref<unsigned long long, cuda::thread_scope_device> pub(st->pub_count);
 
-  // One warp: apply H_{j-1} (when j > 0) to column j, form reflector j in
-  // place and publish it.  Column j already carries H_0 .. H_{j-2}.
+  // load the owned columns (k = bid + lc nb), each scaled by a power of two
+  for (int lc = warp; lc < nown; lc += kWarps) {
+    const double* a = A + (size_t)(bid + lc * nb) * m;
+    float mx = 0.f;
+    for (int i = lane; i < m; i += 32) mx = fmaxf(mx, fabsf(__double2float_rn(a[i])));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    int e = 0;
+    if (mx > 0.f) frexpf(mx, &e);
+    if (lane == 0) cexp[lc * estride] = e;
+    const double sc = ldexp(1.0, -e);
+    dw* c = cols + (size_t)lc * cstride;
+    for (int i = lane; i < m; i += 32) c[i] = dw_from(a[i] * sc);
+  }
+  __syncthreads();
+
+  // H_j applied to a local column by one warp: c -= (t (v . c)) v, rows >= j
+  auto apply = [&](int j, dw* c) {
+    const dw* v = V + (size_t)j * m;
+    const float2 t2 = __ldcg(reinterpret_cast<const float2*>(T + j));
+    const dw t = {t2.x, t2.y};
+    dw_acc acc;
+    for (int i = j + lane; i < m; i += 32) {
+      const float2 vv = __ldcg(reinterpret_cast<const float2*>(v + i));
+      dw_dot_step(acc, {vv.x, vv.y}, c[i]);
+    }
+    const dw w = dw_mul(dw_warp_sum(dw_acc_value(acc)), t);
+    if (w.hi == 0.f) return;
+    for (int i = j + lane; i < m; i += 32) {
+      const float2 vv = __ldcg(reinterpret_cast<const float2*>(v + i));
+      c[i] = dw_add(c[i], dw_neg(dw_mul(w, {vv.x, vv.y})));
+    }
+  };
+  // the critical chain of column j (one warp of its owner): H_{j-1}, then
+  // reflector j formed, stored locally and published
   auto critical = [&](int j) {
-    double* col = A + (size_t)j * m;
-    if (j > 0) {
-      const double t = __ldcg(tau + j - 1);
-      if (t != 0.0) {
-        const double* v = A + (size_t)(j - 1) * m;
-        double w = lane == 0 ? col[j - 1] : 0.0;
-        for (int i = j + lane; i < m; i += 32) w = fma(__ldcg(v + i), col[i], w);
-        w = warp_sum(w) * t;
-        if (lane == 0) col[j - 1] -= w;
-        for (int i = j + lane; i < m; i += 32) col[i] = fma(-w, __ldcg(v + i), col[i]);
-      }
-    }
-    double s = 0.0;
+    dw* c = cols + (size_t)(j / nb) * cstride;
+    if (j > 0) apply(j - 1, c);
+    __syncwarp();
+    float mx = 0.f;
+    for (int i = j + lane; i < m; i += 32) mx = fmaxf(mx, fabsf(c[i].hi));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    int e = 0;
+    if (mx > 0.f) frexpf(mx, &e);
+    dw_acc acc;
     for (int i = j + 1 + lane; i < m; i += 32) {
-      const double x = col[i];
-      s = fma(x, x, s);
+      const dw x = dw_ldexp(c[i], -e);
+      dw_dot_step(acc, x, x);
     }
-    s = warp_sum(s);
-    const double x0 = col[j];
-    double t = 0.0, beta = x0, scale = 0.0;
-    if (s > 0.0) {
-      const double nrm = sqrt(fma(x0, x0, s));
-      beta = x0 >= 0.0 ? -nrm : nrm;
-      t = (beta - x0) / beta;
-      scale = 1.0 / (x0 - beta);
+    const dw s = dw_warp_sum(dw_acc_value(acc));
+    const dw x0 = dw_ldexp(c[j], -e);
+    dw t = {0.f, 0.f}, beta = x0, scale = {0.f, 0.f};
+    if (s.hi > 0.f) {
+      const dw nrm = dw_sqrt(dw_add(dw_mul(x0, x0), s));
+      beta = x0.hi >= 0.f ? dw_neg(nrm) : nrm;
+      t = dw_div(dw_add(beta, dw_neg(x0)), beta);
+      scale = dw_div({1.0f, 0.0f}, dw_add(x0, dw_neg(beta)));
     }
-    for (int i = j + 1 + lane; i < m; i += 32) col[i] *= scale;
+    dw* v = V + (size_t)j * m;
+    for (int i = j + 1 + lane; i < m; i += 32) {
+      const dw vi = dw_mul(dw_ldexp(c[i], -e), scale);
+      c[i] = vi;
+      __stcg(reinterpret_cast<float2*>(v + i), make_float2(vi.hi, vi.lo));
+    }
+    __syncwarp();
     if (lane == 0) {
-      col[j] = beta;
-      tau[j] = t;
+      c[j] = dw_ldexp(beta, e);
+      __stcg(reinterpret_cast<float2*>(v + j), make_float2(1.0f, 0.0f));
+      __stcg(reinterpret_cast<float2*>(T + j), make_float2(t.hi, t.lo));
+      tau[j] = dw_to(t);
     }
     __threadfence();
     __syncwarp();
@@ -258,29 +310,26 @@ __global__ void __launch_bounds__(kThreads) k_qr_factor_la(double* A, int m, int
       ok = false;
       break;
     }
-    // the owner of column j+1 hands it to warp 0 (critical path); the
-    // remaining warps apply H_j to the block's columns from j+2 on
     const bool owner = j + 1 < p && bid == (j + 1) % nb;
     if (owner && warp == 0) {
       critical(j + 1);
       continue;
     }
-    const double t = __ldcg(tau + j);
-    if (t == 0.0) continue;
-    const double* v = A + (size_t)j * m;
     const int wk = owner ? warp - 1 : warp, nwk = owner ? kWarps - 1 : kWarps;
-    const int first = j + 2;
-    const int k0 = first + ((bid - first % nb) % nb + nb) % nb;
-    for (int k = k0 + wk * nb; k < n; k += nwk * nb) {
-      double* col = A + (size_t)k * m;
-      double w = lane == 0 ? col[j] : 0.0;
-      for (int i = j + 1 + lane; i < m; i += 32) w = fma(__ldcg(v + i), col[i], w);
-      w = warp_sum(w) * t;
-      if (lane == 0) col[j] -= w;
-      for (int i = j + 1 + lane; i < m; i += 32) col[i] = fma(-w, __ldcg(v + i), col[i]);
-    }
+    // owned columns k >= j + 2: local index lc with bid + lc nb >= j + 2
+    const int lc0 = (j + 2 - bid + nb - 1) / nb > 0 ? (j + 2 - bid + nb - 1) / nb : 0;
+    for (int lc = lc0 + wk; lc < nown; lc += nwk) apply(j, cols + (size_t)lc * cstride);
   }
-  // the last block to finish publishes the base of the next launch
+  __syncthreads();
+  // store: R part unscaled by 2^e_k, reflectors (below the diagonal of the
+  // first p columns) as they are
+  for (int lc = warp; lc < nown; lc += kWarps) {
+    const int k = bid + lc * nb;
+    const double sc = ldexp(1.0, cexp[lc * estride]);
+    const dw* c = cols + (size_t)lc * cstride;
+    double* a = A + (size_t)k * m;
+    for (int i = lane; i < m; i += 32) a[i] = (k < p && i > k) ? dw_to(c[i]) : dw_to(c[i]) * sc;
+  }
   __syncthreads();
   if (tid == 0 && ok) {
     __threadfence();
@@ -292,126 +341,236 @@ __global__ void __launch_bounds__(kThreads) k_qr_factor_la(double* A, int m, int
   }
 }
 
-// Small matrices: one block, the matrix in shared memory (leading dimension
-// m | 1, odd, so that lanes walking different columns hit different banks).
-// Step j: warp 0 forms reflector j; then each thread owns one trailing column
-// and applies H_j to it with a serial dot product over the rows, so one FMA
-// instruction serves 32 columns (a warp per column would spend a five-step
-// shuffle reduction on every column, and FP64 issues at two lanes per clock
-// per SM).
-__global__ void __launch_bounds__(kThreads) k_qr_factor_small(double* A, int m, int n, double* tau) {
-  extern __shared__ double sa[];
-  __shared__ double s_t;
+// Cluster-resident double-word QR (small factors).  Column k lives in CTA
+// k % CS (slot k / CS) as double words, scaled by its own power of two as in
+// k_qr_factor_dw.  Step j: in the owner of column j+1, warp 0 applies H_j to
+// that column, forms reflector j+1 in place and pushes it (rows >= j+1,
+// leading 1) with its tau into every CTA's incoming buffer (j+1) % 2 through
+// distributed shared memory; the other warps, and every other CTA, apply H_j
+// (read from the local incoming buffer j % 2) to their columns right of j+1.
+// One hardware cluster barrier per step orders the pushes.
+__global__ void __launch_bounds__(kThreads) k_qr_factor_cdw(double* A, int m, int n, double* tau) {
+  cg::cluster_group cl = cg::this_cluster();
+  const int CS = (int)cl.num_blocks(), rank = (int)cl.block_rank();
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int ld = m | 1, p = min(m, n);
-  for (int e = tid; e < m * n; e += kThreads) sa[(size_t)(e / m) * ld + e % m] = A[e];
-  __syncthreads();
-  for (int j = 0; j < p; ++j) {
-    double* col = sa + (size_t)j * ld;
-    if (warp == 0) {
-      double s = 0.0;
-      for (int i = j + 1 + lane; i < m; i += 32) s = fma(col[i], col[i], s);
-      s = warp_sum(s);
-      const double x0 = col[j];
-      double t = 0.0, beta = x0, scale = 0.0;
-      if (s > 0.0) {
-        const double nrm = sqrt(fma(x0, x0, s));
-        beta = x0 >= 0.0 ? -nrm : nrm;
-        t = (beta - x0) / beta;
-        scale = 1.0 / (x0 - beta);
-      }
-      for (int i = j + 1 + lane; i < m; i += 32) col[i] *= scale;
-      __syncwarp();
-      if (lane == 0) {
-        col[j] = beta;
-        s_t = t;
-        tau[j] = t;
-      }
-    }
-    __syncthreads();
-    const double t = s_t;
-    if (t != 0.0) {
-      for (int k = j + 1 + tid; k < n; k += kThreads) {
-        double* ck = sa + (size_t)k * ld;
-        double w = ck[j];
-        for (int i = j + 1; i < m; ++i) w = fma(col[i], ck[i], w);
-        w *= t;
-        ck[j] -= w;
-        for (int i = j + 1; i < m; ++i) ck[i] = fma(-w, col[i], ck[i]);
-      }
-    }
-    __syncthreads();
+  const int p = min(m, n);
+  const int nmax = (n + CS - 1) / CS;
+  const int nown = rank < n ? (n - rank + CS - 1) / CS : 0;
+  extern __shared__ double qsm_raw[];
+  dw* cols = reinterpret_cast<dw*>(qsm_raw);  // nmax columns of m
+  dw* vbuf = cols + (size_t)nmax * m;         // 2 x m incoming reflectors
+  dw* tbuf = vbuf + 2 * (size_t)m;            // 2 incoming taus
+  int* cexp = reinterpret_cast<int*>(tbuf + 2);
+
+  for (int lc = warp; lc < nown; lc += kWarps) {
+    const double* a = A + (size_t)(rank + lc * CS) * m;
+    float mx = 0.f;
+    for (int i = lane; i < m; i += 32) mx = fmaxf(mx, fabsf(__double2float_rn(a[i])));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    int e = 0;
+    if (mx > 0.f) frexpf(mx, &e);
+    if (lane == 0) cexp[lc] = e;
+    const double sc = ldexp(1.0, -e);
+    dw* c = cols + (size_t)lc * m;
+    for (int i = lane; i < m; i += 32) c[i] = dw_from(a[i] * sc);
   }
-  for (int e = tid; e < m * n; e += kThreads) A[e] = sa[(size_t)(e / m) * ld + e % m];
+
+  // H_j (from the local incoming buffer) applied to a local column, one warp
+  auto apply = [&](int j, dw* c) {
+    const dw* v = vbuf + (size_t)(j & 1) * m;
+    const dw t = tbuf[j & 1];
+    if (t.hi == 0.f) return;
+    dw_acc acc;
+    for (int i = j + lane; i < m; i += 32) dw_dot_step(acc, v[i], c[i]);
+    const dw w = dw_mul(dw_warp_sum(dw_acc_value(acc)), t);
+    if (w.hi == 0.f) return;
+    for (int i = j + lane; i < m; i += 32) c[i] = dw_add(c[i], dw_neg(dw_mul(w, v[i])));
+  };
+  // reflector j formed in place in local column c, pushed to every CTA
+  auto reflect_push = [&](int j, dw* c) {
+    float mx = 0.f;
+    for (int i = j + lane; i < m; i += 32) mx = fmaxf(mx, fabsf(c[i].hi));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    int e = 0;
+    if (mx > 0.f) frexpf(mx, &e);
+    dw_acc acc;
+    for (int i = j + 1 + lane; i < m; i += 32) {
+      const dw x = dw_ldexp(c[i], -e);
+      dw_dot_step(acc, x, x);
+    }
+    const dw s = dw_warp_sum(dw_acc_value(acc));
+    const dw x0 = dw_ldexp(c[j], -e);
+    dw t = {0.f, 0.f}, beta = x0, scale = {0.f, 0.f};
+    if (s.hi > 0.f) {
+      const dw nrm = dw_sqrt(dw_add(dw_mul(x0, x0), s));
+      beta = x0.hi >= 0.f ? dw_neg(nrm) : nrm;
+      t = dw_div(dw_add(beta, dw_neg(x0)), beta);
+      scale = dw_div({1.0f, 0.0f}, dw_add(x0, dw_neg(beta)));
+    }
+    for (int i = j + 1 + lane; i < m; i += 32) c[i] = dw_mul(dw_ldexp(c[i], -e), scale);
+    __syncwarp();
+    if (lane == 0) {
+      c[j] = dw_ldexp(beta, e);
+      tau[j] = dw_to(t);
+    }
+    for (int r = 0; r < CS; ++r) {
+      dw* dst = cl.map_shared_rank(vbuf + (size_t)(j & 1) * m, r);
+      for (int i = j + lane; i < m; i += 32) dst[i] = (i == j) ? dw{1.0f, 0.0f} : c[i];
+      if (lane == 0) *cl.map_shared_rank(tbuf + (j & 1), r) = t;
+    }
+  };
+
+  cl.sync();  // every CTA resident before the first remote write
+  if (rank == 0 && warp == 0 && p > 0) reflect_push(0, cols);
+  cl.sync();
+  for (int j = 0; j < p; ++j) {
+    const bool owner = j + 1 < p && rank == (j + 1) % CS;
+    if (owner && warp == 0) {
+      dw* c = cols + (size_t)((j + 1) / CS) * m;
+      apply(j, c);
+      __syncwarp();
+      reflect_push(j + 1, c);
+    } else {
+      const int wk = owner ? warp - 1 : warp, nwk = owner ? kWarps - 1 : kWarps;
+      const int lc0 = (j + 2 - rank + CS - 1) / CS > 0 ? (j + 2 - rank + CS - 1) / CS : 0;
+      for (int lc = lc0 + wk; lc < nown; lc += nwk) apply(j, cols + (size_t)lc * m);
+    }
+    cl.sync();
+  }
+  for (int lc = warp; lc < nown; lc += kWarps) {
+    const int k = rank + lc * CS;
+    const double sc = ldexp(1.0, cexp[lc]);
+    const dw* c = cols + (size_t)lc * m;
+    double* a = A + (size_t)k * m;
+    for (int i = lane; i < m; i += 32) a[i] = (k < p && i > k) ? dw_to(c[i]) : dw_to(c[i]) * sc;
+  }
 }
 
-// Cost model (SM clocks) of the two factorisations: FP64 warp instructions
-// at 16 clocks each plus the per-column reflector chain (small), or a
-// measured ~2.5 us per column on the critical path (look-ahead grid).
-static double qr_small_cost(int m, int n) {
-  const int p = std::min(m, n);
-  double c = 0.0;
-  for (int j = 0; j < p; ++j) c += 16.0 * ((n - j - 1 + 31) / 32) * 2.0 * (m - j) + 600.0;
-  return c;
+static size_t qr_cdw_smem(int m, int n, int CS) {
+  const size_t nmax = (size_t)(n + CS - 1) / CS;
+  return (nmax * m + 2 * (size_t)m + 2) * sizeof(dw) + nmax * sizeof(int);
 }
-static double qr_grid_cost(int m, int n) { return 5200.0 * std::min(m, n); }
 
 int launch_qr_factor(vp_ctx* ctx, double* A, int m, int n, double* tau, double* vbuf) {
   const int p = std::min(m, n);
   if (p <= 0) return VP_OK;
-  const size_t small_smem = (size_t)(m | 1) * n * sizeof(double);
-  if (small_smem <= 200 * 1024 && qr_small_cost(m, n) <= qr_grid_cost(m, n)) {
-    static bool sattr = false;
-    if (!sattr) {
-      VP_CUDA(ctx, cudaFuncSetAttribute(k_qr_factor_small, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-      sattr = true;
+  // Measured per column on GB300 (headline workload): the cluster kernel is
+  // faster up to ~1e4 elements (2.5-4 us against 5-13 us), the grid kernel
+  // above (its reflector pushes to every CTA would cost more than the L2
+  // flags of the grid kernel).
+  if (ctx->cluster_size > 1 && (long long)m * n <= 10000) {
+    int cs = 2;
+    while (cs < std::min(ctx->cluster_size, 4) && cs * 8 < n) cs *= 2;
+    const size_t need = qr_cdw_smem(m, n, cs);
+    if (need <= 200 * 1024) {
+      static bool cattr = false;
+      if (!cattr) {
+        VP_CUDA(ctx, cudaFuncSetAttribute(k_qr_factor_cdw, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        VP_CUDA(ctx, cudaFuncSetAttribute(k_qr_factor_cdw, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+        cattr = true;
+      }
+      cudaLaunchConfig_t cfg = {};
+      cudaLaunchAttribute at[1];
+      cfg.gridDim = dim3(cs);
+      cfg.blockDim = dim3(kThreads);
+      cfg.dynamicSmemBytes = std::max<size_t>(need, 116 * 1024);  // one CTA of the cluster per SM
+      cfg.stream = ctx->stream;
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = cs;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      ctx->launches++;
+      VP_CUDA(ctx, cudaLaunchKernelEx(&cfg, k_qr_factor_cdw, A, m, n, tau));
+      return VP_OK;
     }
-    ctx->launches++;
-    k_qr_factor_small<<<1, kThreads, small_smem, ctx->stream>>>(A, m, n, tau);
-    return check_launch(ctx, "qr_factor_small");
   }
   // enough blocks that each owns a few columns, but never more than one per SM
   const int cap = ctx->coop_cap > 0 ? std::min(ctx->coop_cap, ctx->num_sms) : ctx->num_sms;
   const int blocks = std::min(cap, std::max(1, n / 2));
   DevStatus* st = ctx->status;
   if (blocks > 1) {
-    void* args[] = {&A, &m, &n, &tau, &st};
-    return coop_launch(ctx, (const void*)k_qr_factor_la, blocks, kThreads, args, 0, "qr_factor");
+    // the same double-word arithmetic whichever the storage, so that the
+    // result does not depend on the context's block cap
+    const int nmax = (n + blocks - 1) / blocks;
+    const size_t smem = (size_t)nmax * m * sizeof(dw) + (size_t)nmax * sizeof(int);
+    static bool qattr = false;
+    if (!qattr) {
+      VP_CUDA(ctx, cudaFuncSetAttribute(k_qr_factor_dw, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+      qattr = true;
+    }
+    VP_TRY(reserve(ctx, ctx->w_qrv, (size_t)m * p + p + 8));
+    dw* V = reinterpret_cast<dw*>(ctx->w_qrv.p);
+    dw* T = V + (size_t)m * p;
+    dw* gcols = nullptr;
+    int* gexp = nullptr;
+    size_t dyn = smem;
+    if (smem > 200 * 1024) {
+      VP_TRY(reserve(ctx, ctx->w_qrc, (size_t)m * n + n / 2 + 8));
+      gcols = reinterpret_cast<dw*>(ctx->w_qrc.p);
+      gexp = reinterpret_cast<int*>(gcols + (size_t)m * n);
+      dyn = 0;
+    }
+    void* args[] = {&A, &m, &n, &tau, &V, &T, &gcols, &gexp, &st};
+    return coop_launch(ctx, (const void*)k_qr_factor_dw, blocks, kThreads, args, dyn, "qr_factor_dw");
   }
   void* args[] = {&A, &m, &n, &tau, &vbuf, &st};
   return coop_launch(ctx, (const void*)k_qr_factor<GridSync>, blocks, kThreads, args, 0, "qr_factor");
 }
 
-// Q = H_0 ... H_{p-1} [I_p; 0]: one warp per column, applied right to left in
-// a column-major scratch column, then stored row-major (m x p).
-__global__ void k_qr_formq(const double* __restrict__ A, int m, int p, const double* __restrict__ tau,
-                           double* __restrict__ scratch, double* __restrict__ Q) {
+// Q = H_0 ... H_{p-1} [I_p; 0] in double words: the reflectors (below the
+// diagonal of the factored A, leading 1 implicit) and taus are converted
+// once, then one warp per column k of Q applies H_k, ..., H_0 to e_k with
+// double-word dot products and updates (each step would otherwise be a chain
+// of FP64 FMAs at ~400 cycles apiece); Q is stored row-major (m x p).
+__global__ void k_reflectors_to_dw(const double* __restrict__ A, int m, int p, const double* __restrict__ tau,
+                                   dw* __restrict__ V, dw* __restrict__ T) {
+  const size_t total = (size_t)m * p;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int j = (int)(e / m), i = (int)(e % m);
+    V[e] = i > j ? dw_from(A[e]) : (i == j ? dw{1.0f, 0.0f} : dw{0.0f, 0.0f});
+    if (e < (size_t)p) T[e] = dw_from(tau[e]);
+  }
+}
+
+__global__ void k_qr_formq_dw(const dw* __restrict__ V, int m, int p, const dw* __restrict__ T, dw* __restrict__ scratch,
+                              double* __restrict__ Q) {
   const int lane = threadIdx.x & 31;
   const int k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (k >= p) return;
-  double* q = scratch + (size_t)k * m;
-  for (int i = lane; i < m; i += 32) q[i] = (i == k) ? 1.0 : 0.0;
+  dw* q = scratch + (size_t)k * m;
+  for (int i = lane; i < m; i += 32) q[i] = (i == k) ? dw{1.0f, 0.0f} : dw{0.0f, 0.0f};
   __syncwarp();
   for (int j = k; j >= 0; --j) {
-    const double t = tau[j];
-    if (t == 0.0) continue;
-    const double* v = A + (size_t)j * m;
-    double w = 0.0;
-    for (int i = j + lane; i < m; i += 32) w = fma(i == j ? 1.0 : v[i], q[i], w);
-    w = warp_sum(w) * t;
-    for (int i = j + lane; i < m; i += 32) q[i] = fma(-w, i == j ? 1.0 : v[i], q[i]);
+    const dw t = T[j];
+    if (t.hi == 0.f) continue;
+    const dw* v = V + (size_t)j * m;
+    dw_acc acc;
+    for (int i = j + lane; i < m; i += 32) dw_dot_step(acc, v[i], q[i]);
+    const dw w = dw_mul(dw_warp_sum(dw_acc_value(acc)), t);
+    for (int i = j + lane; i < m; i += 32) q[i] = dw_add(q[i], dw_neg(dw_mul(w, v[i])));
     __syncwarp();
   }
-  for (int i = lane; i < m; i += 32) Q[(size_t)i * p + k] = q[i];
+  for (int i = lane; i < m; i += 32) Q[(size_t)i * p + k] = dw_to(q[i]);
 }
 
 int launch_qr_formq(vp_ctx* ctx, const double* A, int m, int n, const double* tau, double* Q) {
   const int p = std::min(m, n);
   if (p <= 0) return VP_OK;
   VP_TRY(reserve(ctx, ctx->w_q, (size_t)m * p));
+  VP_TRY(reserve(ctx, ctx->w_fq, (size_t)m * p + p + 8));
+  dw* V = reinterpret_cast<dw*>(ctx->w_fq.p);
+  dw* T = V + (size_t)m * p;
+  const size_t total = (size_t)m * p;
+  const int cb = (int)std::min<size_t>((total + 255) / 256, (size_t)ctx->num_sms * 8);
+  ctx->launches += 2;
+  k_reflectors_to_dw<<<cb, 256, 0, ctx->stream>>>(A, m, p, tau, V, T);
+  VP_TRY(check_launch(ctx, "reflectors_to_dw"));
   const int wpb = 8;
-  ctx->launches++;
-  k_qr_formq<<<(p + wpb - 1) / wpb, wpb * 32, 0, ctx->stream>>>(A, m, p, tau, ctx->w_q.p, Q);
+  k_qr_formq_dw<<<(p + wpb - 1) / wpb, wpb * 32, 0, ctx->stream>>>(V, m, p, T, reinterpret_cast<dw*>(ctx->w_q.p), Q);
   return check_launch(ctx, "qr_formq");
 }
 
