@@ -28,6 +28,7 @@ sys.path.insert(0, ROOT)
 WORKLOAD = "saturated_two_stream_1024x1024_seq"
 CHI, TOL, DT = 64, 1e-10, 0.002
 FP64_PEAK_GFLOPS = 2 * 2 * 152 * 2.070  # 2 DFMA/clk/SM x 2 flop x 152 SMs x 2070 MHz (nominal 1.25 TF/s)
+NCU_TRAFFIC = {"qr_factor": 208.0e3, "jacobi": 70.3e3}  # bytes per launch, profiles/k_*_dw_*.md
 
 
 def parse():
@@ -193,9 +194,11 @@ def run_ours(args, rank, world):
         achieved = work / (tms / 1e3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS / 1e3, "unit": "TFLOP/s"}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = None
-    roof["kernel"] = {"qr_factor": "k_qr_factor", "jacobi": "k_jacobi_cluster", "gemm": "k_gemm",
-                      "qr_formq": "k_qr_formq", "apply": "k_site_sum", "select": "k_select"}.get(top, top)
+    # DRAM bytes (read + write) per launch of the dominant kernel, from the ncu
+    # captures summarised under profiles/ (two launches each, this workload)
+    roof["traffic"] = NCU_TRAFFIC.get(top) if WORKLOAD == "saturated_two_stream_1024x1024_seq" else None
+    roof["kernel"] = {"qr_factor": "k_qr_factor_dw", "jacobi": "k_jacobi_dw", "gemm": "k_gemm",
+                      "qr_formq": "k_qr_formq_dw", "apply": "k_site_sum", "select": "k_select"}.get(top, top)
     roof["launches"] = tl
     roof["share_of_step"] = tms / ms * world if ms else None
 
