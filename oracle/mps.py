@@ -222,3 +222,94 @@ def contract_sites(cores, sites, vectors):
     if pending is not None:
         keep[-1] = np.einsum("aib,bc->aic", keep[-1], pending)
     return keep
+
+
+def _lq(m):
+    """m = L Q with Q having orthonormal rows (QR of the transpose)."""
+    q, r = sla.qr(m.T, mode="economic")
+    return r.T, q.T
+
+
+def compress_modified(cores, chi, tol, split):
+    """Modified centre-bond-first compression (SI "Modified Compression
+    Scheme") of a sequentially ordered MPS whose first ``split`` sites hold
+    one dimension (x) and the rest the other (v).
+
+    1. Mixed canonical form about the centre bond: the v sites right of the
+       first v site are right-canonicalised (LQ, factor pushed left), the x
+       sites left-canonicalised (QR, R pushed right), and the first v site is
+       split as C Q by one more LQ: C is the matrix of the centre bond.
+    2. C = U S V^T, truncated by :func:`choose_rank`.
+    3. S^{-1} S is inserted between S and V^T: the last x site takes U S, the
+       first v site S V^T Q, and S^{-1} waits on the bond.  Each half then
+       sees an orthonormal other half.
+    4. Truncated-SVD sweep through the x sites, from the centre to the left
+       end (the usual right-to-left step).
+    5. The same through the v sites, from the centre to the right end
+       (left-to-right steps: SVD of the (2 r_{k-1} x r_k) reshape, U kept,
+       S V^T pushed right).
+    6. S^{-1} is absorbed into the first v site (zero where S is zero).
+    Returns (cores, truncation error per bond, singular values per bond).
+    """
+    out = [np.asarray(c, dtype=np.float64).copy() for c in cores]
+    n = len(out)
+    if not 0 < split < n:
+        raise ValueError("split must leave sites on both sides")
+    errs = [0.0] * (n - 1)
+    svals = [None] * (n - 1)
+    # 1. right-canonical v sites split+1 .. n-1
+    for k in range(n - 1, split, -1):
+        c = out[k]
+        rl, _, rr = c.shape
+        lm, q = _lq(c.reshape(rl, 2 * rr))
+        p = q.shape[0]
+        out[k] = q.reshape(p, 2, rr)
+        prev = out[k - 1]
+        out[k - 1] = (prev.reshape(-1, rl) @ lm).reshape(prev.shape[0], 2, p)
+    # left-canonical x sites 0 .. split-1
+    for k in range(split):
+        c = out[k]
+        rl, _, rr = c.shape
+        q, r = sla.qr(c.reshape(rl * 2, rr), mode="economic")
+        p = q.shape[1]
+        out[k] = q.reshape(rl, 2, p)
+        nxt = out[k + 1]
+        out[k + 1] = (r @ nxt.reshape(rr, -1)).reshape(p, 2, nxt.shape[2])
+    # the centre bond matrix
+    c = out[split]
+    rl, _, rr = c.shape
+    cm, q = _lq(c.reshape(rl, 2 * rr))
+    # 2. its SVD, truncated
+    u, s, vt = sla.svd(cm, full_matrices=False, lapack_driver="gesvd")
+    r, e = choose_rank(s, chi, tol)
+    errs[split - 1], svals[split - 1] = e, s
+    u, s, vt = u[:, :r], s[:r], vt[:r]
+    # 3. U S to the left half, S V^T to the right half, S^{-1} on the bond
+    prev = out[split - 1]
+    out[split - 1] = (prev.reshape(-1, rl) @ (u * s)).reshape(prev.shape[0], 2, r)
+    out[split] = ((s[:, None] * vt) @ q).reshape(r, 2, rr)
+    # 4. x half, centre to left end
+    for k in range(split - 1, 0, -1):
+        c = out[k]
+        a, _, b = c.shape
+        uu, ss, vv = sla.svd(c.reshape(a, 2 * b), full_matrices=False, lapack_driver="gesvd")
+        rk, ek = choose_rank(ss, chi, tol)
+        errs[k - 1], svals[k - 1] = ek, ss
+        out[k] = vv[:rk].reshape(rk, 2, b)
+        prev = out[k - 1]
+        out[k - 1] = (prev.reshape(-1, a) @ (uu[:, :rk] * ss[:rk])).reshape(prev.shape[0], 2, rk)
+    # 5. v half, centre to right end
+    for k in range(split, n - 1):
+        c = out[k]
+        a, _, b = c.shape
+        uu, ss, vv = sla.svd(c.reshape(2 * a, b), full_matrices=False, lapack_driver="gesvd")
+        rk, ek = choose_rank(ss, chi, tol)
+        errs[k], svals[k] = ek, ss
+        out[k] = uu[:, :rk].reshape(a, 2, rk)
+        nxt = out[k + 1]
+        out[k + 1] = ((ss[:rk, None] * vv[:rk]) @ nxt.reshape(b, -1)).reshape(rk, 2, nxt.shape[2])
+    # 6. S^{-1} into the first v site
+    inv = np.where(s > 0.0, 1.0 / np.where(s > 0.0, s, 1.0), 0.0)
+    c = out[split]
+    out[split] = (inv[:, None] * c.reshape(c.shape[0], -1)).reshape(c.shape)
+    return out, errs, svals

@@ -214,7 +214,29 @@ def rhs(cores, layout, e_tol=TOL):
     return S.apply_mpo(L, cores), we, rho
 
 
-def rk4_step(f, layout, dt, chi, tol=TOL, e_tol=TOL, level=1, e_chi=None):
+def _compressors(layout, modified):
+    """(compress, compress_with_entropy) of a step: the plain QR + SVD sweeps,
+    or, for a sequential ordering, the modified centre-bond-first scheme with
+    the centre at the x / v cut (SI "Modified Compression Scheme")."""
+    if not modified:
+        return S.compress, S.compress_with_entropy
+    if layout.mapping not in (0, 2, 3):
+        raise ValueError("the modified compression needs a sequential ordering")
+    split = layout.nx
+
+    def comp(c, chi, tol):
+        out, errs, _ = S.compress_modified(c, chi, tol, split)
+        return out, errs
+
+    def comp_ee(c, chi, tol):
+        out, errs, sv = S.compress_modified(c, chi, tol, split)
+        ee = [S.entanglement_entropy(sv[j], out[j + 1].shape[0]) for j in range(len(out) - 1)]
+        return out, errs, ee
+
+    return comp, comp_ee
+
+
+def rk4_step(f, layout, dt, chi, tol=TOL, e_tol=TOL, level=1, e_chi=None, modified=False):
     """One RK4 step; returns (f_{n+1}, diagnostics).
 
     Compression levels (SI "Compressed time evolution algorithm"); every
@@ -227,8 +249,9 @@ def rk4_step(f, layout, dt, chi, tol=TOL, e_tol=TOL, level=1, e_chi=None):
       C5  C4 + the terms of each derivative: k_i = C_chi(C_chi(U f_i) +
           C_chi(T f_i)), U the advection operator, T the field term.
     """
+    comp, comp_ee = _compressors(layout, modified)
     if level != 1 or e_chi:
-        return _rk4_step_levels(f, layout, dt, chi, tol, e_tol, level, e_chi)
+        return _rk4_step_levels(f, layout, dt, chi, tol, e_tol, level, e_chi, comp, comp_ee)
     acc = f
     fi = f
     diag = {}
@@ -240,10 +263,10 @@ def rk4_step(f, layout, dt, chi, tol=TOL, e_tol=TOL, level=1, e_chi=None):
             diag["field_energy"] = we
             diag["mass"] = float(np.sum(rho)) * dx
         if i < 3:
-            fi, _ = S.compress(S.add(f, k, 1.0, A_RK[i] * dt), 1 << 30, tol)
-            acc, _ = S.compress(S.add(acc, k, 1.0, B_RK[i] * dt), 1 << 30, tol)
+            fi, _ = comp(S.add(f, k, 1.0, A_RK[i] * dt), 1 << 30, tol)
+            acc, _ = comp(S.add(acc, k, 1.0, B_RK[i] * dt), 1 << 30, tol)
         else:
-            acc, errs, ee = S.compress_with_entropy(S.add(acc, k, 1.0, B_RK[3] * dt), chi, tol)
+            acc, errs, ee = comp_ee(S.add(acc, k, 1.0, B_RK[3] * dt), chi, tol)
             diag["entropy"] = ee
     diag["trunc_err"] = errs
     diag["bonds"] = S.bonds(acc)
@@ -276,7 +299,7 @@ def run(f0, layout, dt, nsteps, chi, tol=TOL, e_tol=TOL, every=1):
 W_RK = (1.0, 2.0, 2.0, 1.0)
 
 
-def _rk4_step_levels(f, layout, dt, chi, tol, e_tol, level, e_chi):
+def _rk4_step_levels(f, layout, dt, chi, tol, e_tol, level, e_chi, comp=S.compress, comp_ee=S.compress_with_entropy):
     big = 1 << 30
     up, dvz = _static_parts(layout)
     sm = sitemap(layout)
@@ -291,23 +314,23 @@ def _rk4_step_levels(f, layout, dt, chi, tol, e_tol, level, e_chi):
             diag["mass"] = float(np.sum(rho)) * dx
         Em = field_mps(E, layout, e_tol, e_chi)
         if level >= 5:
-            ku, _ = S.compress(S.apply_mpo(up, fi), chi, tol)
-            kt, _ = S.compress(S.apply_mpo(M.place([M.diag_from_mps(Em), dvz], sm), fi), chi, tol)
-            k, _ = S.compress(S.add(ku, kt), chi, tol)
+            ku, _ = comp(S.apply_mpo(up, fi), chi, tol)
+            kt, _ = comp(S.apply_mpo(M.place([M.diag_from_mps(Em), dvz], sm), fi), chi, tol)
+            k, _ = comp(S.add(ku, kt), chi, tol)
         else:
             k = S.apply_mpo(M.mpo_sum(up, M.place([M.diag_from_mps(Em), dvz], sm)), fi)
             if level >= 4:
-                k, _ = S.compress(k, chi, tol)
+                k, _ = comp(k, chi, tol)
         if level >= 3:
-            D = k if i == 0 else S.compress(S.add(D, k, 1.0, W_RK[i]), chi, tol)[0]
+            D = k if i == 0 else comp(S.add(D, k, 1.0, W_RK[i]), chi, tol)[0]
         elif i < 3:
-            acc, _ = S.compress(S.add(acc, k, 1.0, B_RK[i] * dt), big, tol)
+            acc, _ = comp(S.add(acc, k, 1.0, B_RK[i] * dt), big, tol)
         if i < 3:
-            fi, _ = S.compress(S.add(f, k, 1.0, A_RK[i] * dt), chi if level >= 2 else big, tol)
+            fi, _ = comp(S.add(f, k, 1.0, A_RK[i] * dt), chi if level >= 2 else big, tol)
     if level >= 3:
-        out, errs, ee = S.compress_with_entropy(S.add(f, D, 1.0, dt / 6.0), chi, tol)
+        out, errs, ee = comp_ee(S.add(f, D, 1.0, dt / 6.0), chi, tol)
     else:
-        out, errs, ee = S.compress_with_entropy(S.add(acc, k, 1.0, B_RK[3] * dt), chi, tol)
+        out, errs, ee = comp_ee(S.add(acc, k, 1.0, B_RK[3] * dt), chi, tol)
     diag["entropy"] = ee
     diag["trunc_err"] = errs
     diag["bonds"] = S.bonds(out)

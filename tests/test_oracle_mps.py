@@ -100,3 +100,46 @@ def test_entanglement_entropy_closed_forms():
     v = np.array([1.0, 0.0, 0.0, 1.0]) / np.sqrt(2)
     _, _, ee = S.compress_with_entropy(S.tt_svd(v, 2), 4, 0.0)
     assert abs(ee[0] - 1.0) < 1e-12
+
+
+# ------------------------------------------- modified compression (SI scheme)
+def test_modified_compression_exact_and_centre_schmidt_values():
+    # nothing truncated: the state is reproduced; the centre bond's values are
+    # the singular values of the dense state reshaped at the x / v cut
+    cores = I.random_cores([1, 2, 4, 8, 16, 8, 4, 2, 1], seed=3)
+    d = S.to_dense(cores)
+    out, errs, sv = S.compress_modified(cores, 1 << 10, 0.0, 4)
+    assert np.linalg.norm(S.to_dense(out) - d) <= 1e-13 * np.linalg.norm(d)
+    ref = np.linalg.svd(d.reshape(16, 16), compute_uv=False)
+    np.testing.assert_allclose(sv[3][:len(ref)], ref, rtol=1e-12, atol=1e-14 * ref[0])
+    assert max(errs) == 0.0
+
+
+def test_modified_compression_centre_cut_is_eckart_young():
+    # a state whose only bond above chi is the centre: the result is the best
+    # rank-chi approximation across the cut (the half sweeps cut nothing)
+    rng = np.random.default_rng(11)
+    nx = nv = 3
+    X = rng.standard_normal((8, 6))
+    V = rng.standard_normal((6, 8)) * np.exp(-np.arange(6))[:, None]
+    d = (X @ V).reshape(-1)
+    cores = S.tt_svd(d, nx + nv)
+    # bonds of a 3 + 3 site chain are at most 2, 4, (6 at the centre), 4, 2
+    out, errs, _ = S.compress_modified(cores, 4, 0.0, nx)
+    u, s, vt = np.linalg.svd(d.reshape(8, 8))
+    best = (u[:, :4] * s[:4]) @ vt[:4]
+    assert np.linalg.norm(S.to_dense(out) - best.reshape(-1)) <= 1e-12 * np.linalg.norm(d)
+    assert abs(errs[nx - 1] - np.sqrt(np.sum(s[4:] ** 2)) / np.linalg.norm(s)) <= 1e-12
+    assert [e for j, e in enumerate(errs) if j != nx - 1] == [0.0] * 4
+
+
+def test_modified_compression_error_bound():
+    # every truncation removes an orthogonal piece: the total relative error
+    # is at most the root sum of the per-bond truncation errors
+    cores = I.random_cores([1, 2, 4, 8, 16, 32, 16, 8, 4, 2, 1], seed=9)
+    d = S.to_dense(cores)
+    for chi, tol in ((6, 0.0), (1 << 10, 0.05), (4, 0.01)):
+        out, errs, _ = S.compress_modified(cores, chi, tol, 5)
+        e = np.linalg.norm(S.to_dense(out) - d) / np.linalg.norm(d)
+        assert e <= np.sqrt(np.sum(np.square(errs))) * (1 + 1e-9) + 1e-14
+        assert max(c.shape[2] for c in out) <= chi

@@ -205,3 +205,17 @@ def test_reverse_chain_is_same_operator():
     # reversing the site order permutes the basis by bit reversal
     br = V.bitrev(4)
     np.testing.assert_allclose(Dr, D[np.ix_(br, br)], atol=1e-13)
+
+
+@pytest.mark.parametrize("mapping", [I.SEQ, I.SEQ_S2, I.SEQ_S3])
+def test_modified_compression_step_exact_mode(mapping):
+    # the centre-bond-first compression truncates nothing at tol = 0: the MPS
+    # step still equals the dense finite-difference step
+    lay = I.Layout(3, 4, 0.0, 4 * math.pi, -6.0, 6.0, mapping)
+    f0 = I.landau(lay, 0.3, 0.5)
+    c = V.mps_from_f(f0, lay, 1 << 10, 0.0)
+    c, _ = V.rk4_step(c, lay, 0.05, 1 << 10, 0.0, 0.0, modified=True)
+    fd, _, _ = DF.rk4_step(f0.copy(), lay, 0.05)
+    assert np.linalg.norm(V.mps_to_f(c, lay) - fd) <= 1e-12 * np.linalg.norm(fd)
+    with pytest.raises(ValueError):
+        V.rk4_step(c, I.Layout(3, 4, 0.0, 4 * math.pi, -6.0, 6.0, I.INTERLEAVED), 0.05, 8, modified=True)
