@@ -201,6 +201,15 @@ int mps_axpby(vp_ctx* ctx, double a, const mps_t* x, double b, const mps_t* y, m
  * trunc_err_out: n-1 doubles (host) or NULL.  Errors: VP_ETIMEOUT,
  * VP_ENUMERIC. */
 int mps_compress(vp_ctx* ctx, mps_t* inout, int chi, double tol, double* trunc_err_out);
+/* Modified centre-bond-first compression (SI "Modified Compression Scheme")
+ * about the bond after site split-1 (1 <= split < n; for a sequential
+ * ordering, split = nx is the x / v cut): the bond is put at the centre of a
+ * mixed canonical form and truncated first (chi, tol as for mps_compress),
+ * S^{-1} S is inserted there, the two halves are swept outward from it with
+ * the same truncation rule, and S^{-1} is absorbed into site split.  The
+ * result is not in canonical form.  trunc_err_out as for mps_compress.
+ * Errors: VP_EINVAL. */
+int mps_compress_modified(vp_ctx* ctx, mps_t* inout, int split, int chi, double tol, double* trunc_err_out);
 
 /* a3: rho[ix] = sum_iv f(x_ix, v_iv) dv (SI "Integration", rectangle rule);
  * rho_dev: 2^nx doubles (device). */
@@ -271,7 +280,15 @@ typedef struct {
                          TF32X3        tensor cores, split products
                                        a_hi b_hi + a_hi b_lo + a_lo b_hi of
                                        TF32 halves, FP32 accumulation. */
+  int compression;  /* VP_COMPRESS_SWEEPS (0): QR sweep then truncated-SVD
+                       sweep (SI "Canonicalization and Compression");
+                       VP_COMPRESS_MODIFIED (1): the centre-bond-first scheme
+                       of SI "Modified Compression Scheme" for every
+                       compression of the step, centred on the x / v bond
+                       (sequential orderings only, else VP_EINVAL) */
 } vp_config;
+
+enum { VP_COMPRESS_SWEEPS = 0, VP_COMPRESS_MODIFIED = 1 };
 
 enum {
   VP_PREC_FP64 = 0,

@@ -281,7 +281,7 @@ struct SideScope {
 //         core_k <- (V_L^T Q2^T) with columns scattered back by Pi;
 //   wide: M = Pi Q2 V_L S (Q1 U_L)^T ->  core_k <- U_L^T Q1^T,
 //         core_{k-1} <- P Pi (Q2 V_L S).
-static int svd_site(vp_ctx* ctx, mps_t* s, int k, int chi, double tol, double* err_out) {
+static int svd_site(vp_ctx* ctx, mps_t* s, int k, int chi, double tol, double* err_out, double* sig_out = nullptr) {
   const int m = s->r[k];
   const int c = 2 * s->r[k + 1];
   const int pl = 2 * s->r[k - 1];  // rows of the previous core viewed as (2 r_{k-1} x r_k)
@@ -356,6 +356,7 @@ static int svd_site(vp_ctx* ctx, mps_t* s, int k, int chi, double tol, double* e
   VP_TRY(read_rank(ctx, &r, &err));
   if (err_out) *err_out = err;
   if (g_entropy) g_entropy[k - 1] = ctx->h_smalld[1];
+  if (sig_out) VP_TRY(launch_copy(ctx, sigma, sig_out, (size_t)r));
   const double jac = q > 1 ? (double)ctx->h_small[61] * 0.5 * q * (q - 1) * (6.0 * q + (tall ? 0.0 : 4.0 * q)) : 0.0;
   if (ctx->prof_on) ctx->prof_work[VP_K_JACOBI] += jac;
   if (jac_mark != (size_t)-1 && jac_mark < ctx->prof_marks.size()) ctx->prof_marks[jac_mark].k = ctx->h_small[61];
@@ -405,7 +406,106 @@ static int svd_sweep(vp_ctx* ctx, mps_t* s, int chi, double tol, double* errs) {
   return VP_OK;
 }
 
+// Right-canonical site k (k >= 1): M = core_k as (r_{k-1} x 2 r_k) = L Q with
+// orthonormal rows Q, from the Householder QR of M^T (whose column-major
+// layout is M's row-major one); core_k <- Q, core_{k-1} <- core_{k-1} L.
+static int lq_site(vp_ctx* ctx, mps_t* s, int k) {
+  const int m = 2 * s->r[k + 1], n = s->r[k], p = std::min(m, n);
+  const int rows = 2 * s->r[k - 1];
+  VP_TRY(reserve(ctx, ctx->w_fac, (size_t)m * n));
+  VP_TRY(reserve(ctx, ctx->w_p, (size_t)2 * m + p + 8));
+  VP_TRY(launch_copy(ctx, s->core[k].p, ctx->w_fac.p, (size_t)m * n));
+  double* tau = ctx->w_p.p;
+  prof_begin(ctx, VP_K_QR);
+  VP_TRY(launch_qr_factor(ctx, ctx->w_fac.p, m, n, tau, ctx->w_p.p + p + 8));
+  prof_end(ctx, VP_K_QR, qr_flops(m, n), m, n);
+  VP_TRY(reserve(ctx, ctx->w_q1, (size_t)m * p));
+  prof_begin(ctx, VP_K_FORMQ);
+  VP_TRY(launch_qr_formq(ctx, ctx->w_fac.p, m, n, tau, ctx->w_q1.p));
+  prof_end(ctx, VP_K_FORMQ, 4.0 * m * p * p - 4.0 / 3.0 * p * p * p, m, p);
+  VP_TRY(reserve(ctx, ctx->w_r, (size_t)p * n));
+  VP_TRY(launch_qr_getr(ctx, ctx->w_fac.p, m, n, ctx->w_r.p));
+  VP_TRY(reserve(ctx, ctx->w_tmp, (size_t)p * m));
+  VP_TRY(launch_to_colmajor(ctx, ctx->w_q1.p, m, p, ctx->w_tmp.p));  // Q^T, row-major (p x m)
+  VP_TRY(reserve(ctx, ctx->w_gemm, (size_t)rows * p));
+  prof_begin(ctx, VP_K_GEMM);
+  VP_TRY(launch_gemm_bt(ctx, rows, p, n, s->core[k - 1].p, n, ctx->w_r.p, n, ctx->w_gemm.p, p));
+  prof_end(ctx, VP_K_GEMM, 2.0 * rows * p * n, rows, p, n);
+  std::swap(s->core[k], ctx->w_tmp);
+  std::swap(s->core[k - 1], ctx->w_gemm);
+  s->r[k] = p;
+  return VP_OK;
+}
+
+// Modified centre-bond-first compression (SI "Modified Compression Scheme")
+// about the bond between sites split-1 and split (the x / v cut of a
+// sequential ordering):
+//  1. sites right of split right-canonical (LQ), sites left of it
+//     left-canonical (QR, R into core split);
+//  2. the SVD of core split truncates the centre bond: core split-1 takes
+//     U S, core split V^T -- the same U and S as the SVD of the centre bond
+//     matrix, since core split = C Q with Q orthonormal rows;
+//  3. S^{-1} S inserted: core split scaled by S (the kept values), S^{-1}
+//     held back, so each half sees an orthonormal other half;
+//  4. the x half swept from the centre to the left end (right-to-left SVD
+//     steps), 5. the v half from the centre to the right end: the same
+//     steps on the v half read back to front (cores transposed), 6. S^{-1}
+//     absorbed into core split.
+static int compress_modified(vp_ctx* ctx, mps_t* s, int split, int chi, double tol, double* errs) {
+  const int n = s->n;
+  if (split < 1 || split >= n) return fail(ctx, VP_EINVAL, "modified compression: bad split");
+  for (int k = n - 1; k > split; --k) VP_TRY(lq_site(ctx, s, k));
+  for (int k = 0; k < split; ++k) VP_TRY(qr_site(ctx, s, k));
+  VP_TRY(reserve(ctx, ctx->w_sig, (size_t)s->r[split] + 8));
+  VP_TRY(svd_site(ctx, s, split, chi, tol, errs ? errs + split - 1 : nullptr, ctx->w_sig.p));
+  const int rc = s->r[split];
+  for (int k = split - 1; k >= 1; --k) VP_TRY(svd_site(ctx, s, k, chi, tol, errs ? errs + k - 1 : nullptr));
+  VP_TRY(launch_scale_rows(ctx, s->core[split].p, rc, 2 * s->r[split + 1], ctx->w_sig.p, 0));
+  // v half: the chain split .. n-1 read back to front
+  const int mv = n - split;
+  if (mv > 1) {
+    mps_t rv;
+    rv.ctx = ctx;
+    rv.n = mv;
+    rv.r.assign(mv + 1, 1);
+    rv.core.assign(mv, DevBuf{});
+    for (int j = 0; j < mv; ++j) {
+      const int k = n - 1 - j;
+      rv.r[j + 1] = s->r[k];
+      VP_TRY(reserve(ctx, rv.core[j], (size_t)s->r[k] * 2 * s->r[k + 1]));
+      VP_TRY(launch_core_transpose(ctx, s->core[k].p, s->r[k], s->r[k + 1], rv.core[j].p));
+    }
+    rv.r[0] = s->r[n];
+    std::vector<double> e(mv, 0.0), ee(mv, 0.0);
+    double* ent = g_entropy;
+    g_entropy = ent ? ee.data() : nullptr;
+    for (int j = mv - 1; j >= 1; --j) {
+      const int st = svd_site(ctx, &rv, j, chi, tol, &e[j - 1]);
+      if (st != VP_OK) {
+        g_entropy = ent;
+        for (auto& b : rv.core) release(ctx, b);
+        return st;
+      }
+    }
+    g_entropy = ent;
+    for (int j = 1; j < mv; ++j) {  // rv bond j-1 is the bond after site n-1-j
+      if (errs) errs[n - 1 - j] = e[j - 1];
+      if (ent) ent[n - 1 - j] = ee[j - 1];
+    }
+    for (int j = 0; j < mv; ++j) {
+      const int k = n - 1 - j;
+      s->r[k] = rv.r[j + 1];
+      VP_TRY(reserve(ctx, s->core[k], (size_t)rv.r[j + 1] * 2 * rv.r[j]));
+      VP_TRY(launch_core_transpose(ctx, rv.core[j].p, rv.r[j], rv.r[j + 1], s->core[k].p));
+    }
+    for (auto& b : rv.core) release(ctx, b);
+  }
+  return launch_scale_rows(ctx, s->core[split].p, rc, 2 * s->r[split + 1], ctx->w_sig.p, 1);
+}
+
 int compress(vp_ctx* ctx, mps_t* s, int chi, double tol, double* errs) {
+  if (ctx->modified_split > 0 && ctx->modified_split < s->n)
+    return compress_modified(ctx, s, ctx->modified_split, chi, tol, errs);
   for (int k = 0; k + 1 < s->n; ++k) VP_TRY(qr_site(ctx, s, k));
   return svd_sweep(ctx, s, chi, tol, errs);
 }
@@ -1000,6 +1100,17 @@ int mps_axpby(vp_ctx* ctx, double a, const mps_t* x, double b, const mps_t* y, m
   return sync_status(ctx);
 }
 
+int mps_compress_modified(vp_ctx* ctx, mps_t* m, int split, int chi, double tol, double* errs) {
+  if (!ctx || !m || chi < 1 || tol < 0 || split < 1 || split >= m->n)
+    return fail(ctx, VP_EINVAL, "mps_compress_modified: bad argument");
+  std::vector<double> e(std::max(1, m->n - 1), 0.0);
+  VP_TRY(compress_modified(ctx, m, split, chi, tol, e.data()));
+  VP_TRY(sync_status(ctx));
+  if (errs)
+    for (int k = 0; k + 1 < m->n; ++k) errs[k] = e[k];
+  return VP_OK;
+}
+
 int mps_compress(vp_ctx* ctx, mps_t* m, int chi, double tol, double* errs) {
   if (!ctx || !m || chi < 1 || tol < 0) return fail(ctx, VP_EINVAL, "mps_compress: bad argument");
   std::vector<double> e(std::max(1, m->n - 1), 0.0);
@@ -1215,12 +1326,20 @@ static int sim_step_levels(vp_sim* s, vp_record* rec) {
 static int sim_step_impl(vp_sim* s, vp_record* rec);
 
 // The contraction precision applies to this sim's steps only.
+// So does the compression scheme (the modified one cuts first at the x / v
+// bond, after the x sites).
 static int sim_step(vp_sim* s, vp_record* rec) {
-  const int p0 = s->ctx->precision;
+  const int p0 = s->ctx->precision, m0 = s->ctx->modified_split;
+  const int split = s->cfg.compression == VP_COMPRESS_MODIFIED ? s->lay.nx : 0;
   s->ctx->precision = s->cfg.precision;
-  if (s->ctxB) s->ctxB->precision = s->cfg.precision;
+  s->ctx->modified_split = split;
+  if (s->ctxB) {
+    s->ctxB->precision = s->cfg.precision;
+    s->ctxB->modified_split = split;
+  }
   const int st = s->cfg.level > 1 ? sim_step_levels(s, rec) : sim_step_impl(s, rec);
   s->ctx->precision = p0;
+  s->ctx->modified_split = m0;
   return st;
 }
 
@@ -1372,6 +1491,9 @@ int vp_sim_create(vp_ctx* ctx, const vp_layout* L, const vp_config* cfg, const m
   if (st == VP_OK) st = reserve(ctx, s->E, (size_t)1 << L->nx);
   if (cfg->level < 0 || cfg->level > 5 || cfg->e_chi < 0 || cfg->precision < VP_PREC_FP64 || cfg->precision > VP_PREC_TF32X3)
     st = fail(ctx, VP_EINVAL, "vp_sim_create: bad level/e_chi/precision");
+  if (st == VP_OK && (cfg->compression < VP_COMPRESS_SWEEPS || cfg->compression > VP_COMPRESS_MODIFIED ||
+                      (cfg->compression == VP_COMPRESS_MODIFIED && (L->mapping == VP_INTERLEAVED || L->nx < 1 || L->nv < 1))))
+    st = fail(ctx, VP_EINVAL, "vp_sim_create: the modified compression needs a sequential ordering");
   if (st == VP_OK && cfg->streams != 1 && cfg->level <= 1) {
     s->ctxB = ctx_child(ctx);
     if (s->ctxB) {

@@ -45,6 +45,7 @@ struct vp_ctx {
   int cluster_size = 0;  // CTAs per cluster for the cluster-resident kernels (16, or 8)
   int coop_cap = 0;      // max blocks of a cooperative grid launch (0: one per SM)
   int precision = 0;     // VP_PREC_* of the GEMM contractions (factorisations stay FP64)
+  int modified_split = 0;  // > 0: compressions use the centre-bond-first scheme about this bond
   bool owns_stream = false;
   std::vector<vp_ctx*> children;  // contexts created for concurrent work
   cudaStream_t side = nullptr;     // side stream: Q formation beside the Jacobi SVD
@@ -82,6 +83,7 @@ struct vp_ctx {
   vp::DevBuf w_qrv;                   // double-word reflectors published by the grid QR kernel
   vp::DevBuf w_qrc;                   // its columns when they exceed shared memory
   vp::DevBuf w_fq, w_fq_side;         // double-word reflectors of the Q formation
+  vp::DevBuf w_sig;                   // kept centre singular values (modified compression)
   // Blocks handed back to the caller's allocator only once the work queued
   // before their release has finished (the allocator callbacks know no
   // streams, and this context's kernels run on several).
@@ -209,6 +211,10 @@ int launch_site_sum(vp_ctx* ctx, const SiteSum& s, double* out, int ol, int orr)
 int launch_phys_sum(vp_ctx* ctx, const double* core, int rl, int rr, double* T);
 int launch_copy(vp_ctx* ctx, const double* src, double* dst, size_t n);
 int launch_scale(vp_ctx* ctx, double* x, size_t n, double s);
+// Core (a, 2, b) -> (b, 2, a): the site read in the opposite chain direction.
+int launch_core_transpose(vp_ctx* ctx, const double* in, int a, int b, double* out);
+// Rows of a row-major (rows x cols) matrix scaled by sv (or 1/sv, 0 for 0).
+int launch_scale_rows(vp_ctx* ctx, double* x, int rows, int cols, const double* sv, int invert);
 // dense f[ix][iv] -> site-ordered vector (gather) and back.
 int launch_permute_to_sites(vp_ctx* ctx, const double* f, int nx, int nv, int mapping, double* out,
                             int inverse);

@@ -103,6 +103,42 @@ int launch_scale(vp_ctx* ctx, double* x, size_t n, double s) {
   return check_launch(ctx, "scale");
 }
 
+// A core (a, 2, b) read back to front: out (b, 2, a), out[j][s][i] = in[i][s][j]
+// (the same site in a chain taken in the opposite order).
+__global__ void k_core_transpose(const double* __restrict__ in, int a, int b, double* __restrict__ out) {
+  const size_t total = (size_t)a * 2 * b;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int j = (int)(e / (2 * (size_t)a)), sb = (int)((e / a) % 2), i = (int)(e % a);
+    out[e] = in[((size_t)i * 2 + sb) * b + j];
+  }
+}
+
+int launch_core_transpose(vp_ctx* ctx, const double* in, int a, int b, double* out) {
+  const size_t n = (size_t)a * 2 * b;
+  if (n == 0) return VP_OK;
+  ctx->launches++;
+  k_core_transpose<<<grid_for(ctx, n), 256, 0, ctx->stream>>>(in, a, b, out);
+  return check_launch(ctx, "core_transpose");
+}
+
+// Row i of a (rows x cols) row-major matrix times s[i] (invert: 1/s[i], and 0
+// where s[i] is 0).
+__global__ void k_scale_rows(double* x, int rows, int cols, const double* __restrict__ sv, int invert) {
+  const size_t total = (size_t)rows * cols;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const double v = sv[e / cols];
+    x[e] *= invert ? (v != 0.0 ? 1.0 / v : 0.0) : v;
+  }
+}
+
+int launch_scale_rows(vp_ctx* ctx, double* x, int rows, int cols, const double* sv, int invert) {
+  const size_t n = (size_t)rows * cols;
+  if (n == 0) return VP_OK;
+  ctx->launches++;
+  k_scale_rows<<<grid_for(ctx, n), 256, 0, ctx->stream>>>(x, rows, cols, sv, invert);
+  return check_launch(ctx, "scale_rows");
+}
+
 // Site-ordered index <-> (ix, iv).  Site order: SEQ = x bits then v bits;
 // INTERLEAVED = x0 v0 x1 v1 ... with leftover bits of the longer dimension.
 __device__ __forceinline__ size_t bitrev_n(size_t x, int n) { return n > 0 ? __brevll(x) >> (64 - n) : 0; }

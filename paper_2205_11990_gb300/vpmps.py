@@ -37,7 +37,7 @@ EXPORTS = [
     "mps_to_dense", "mps_to_grid", "mps_save", "mps_load",
     "mpo_create_vp", "mpo_create_vlasov", "mpo_create_cores", "mpo_destroy", "mpo_num_sites", "mpo_bonds",
     "mpo_to_dense",
-    "mps_apply_mpo", "mps_axpby", "mps_compress", "vp_density", "vp_poisson", "vp_poisson_noalloc", "vp_gemm",
+    "mps_apply_mpo", "mps_axpby", "mps_compress", "mps_compress_modified", "vp_density", "vp_poisson", "vp_poisson_noalloc", "vp_gemm",
     "vp_sim_create", "vp_sim_destroy", "vp_step", "vp_sim_state", "vp_sim_entropy", "vp_sim_flops", "vp_run",
     "vp_footprint_bytes", "vp_batch_create", "vp_batch_submit", "vp_batch_start", "vp_batch_wait", "vp_batch_poll",
     "vp_batch_records", "vp_batch_destroy",
@@ -61,7 +61,8 @@ class CLayout(C.Structure):
 
 class CConfig(C.Structure):
     _fields_ = [("dt", C.c_double), ("chi", C.c_int), ("tol", C.c_double), ("e_tol", C.c_double),
-                ("streams", C.c_int), ("level", C.c_int), ("e_chi", C.c_int), ("precision", C.c_int)]
+                ("streams", C.c_int), ("level", C.c_int), ("e_chi", C.c_int), ("precision", C.c_int),
+                ("compression", C.c_int)]
 
 
 class CResult(C.Structure):
@@ -130,6 +131,7 @@ def load():
         "mps_apply_mpo": (I, [P, P, P, P]),
         "mps_axpby": (I, [P, D, P, D, P, P]),
         "mps_compress": (I, [P, P, I, D, DP]),
+        "mps_compress_modified": (I, [P, P, I, I, D, DP]),
         "vp_density": (I, [P, C.POINTER(CLayout), P, P]),
         "vp_poisson": (I, [P, P, I, D, P, DP]),
         "vp_poisson_noalloc": (I, [P, P, I, D, P, DP, DP]),
@@ -310,6 +312,11 @@ class Context:
         self._check(self.lib.mps_compress(self.h, x.h, chi, tol, _dp(errs)))
         return errs[: x.n - 1]
 
+    def compress_modified(self, x: "MPS", split: int, chi: int, tol: float) -> np.ndarray:
+        errs = np.zeros(max(1, x.n - 1))
+        self._check(self.lib.mps_compress_modified(self.h, x.h, split, chi, tol, _dp(errs)))
+        return errs[: x.n - 1]
+
     def density(self, lay: Layout, f: "MPS"):
         rho = self.torch.empty(lay.Nx, dtype=self.torch.float64, device="cuda")
         self._check(self.lib.vp_density(self.h, C.byref(clayout(lay)), f.h, C.c_void_p(rho.data_ptr())))
@@ -347,9 +354,9 @@ class Context:
         return Cout
 
     def sim(self, lay: Layout, f0: "MPS", dt: float, chi: int, tol: float = 1e-10, e_tol: float = 1e-10,
-            streams: int = 2, level: int = 1, e_chi: int = 0, precision: int = 0) -> "Sim":
+            streams: int = 2, level: int = 1, e_chi: int = 0, precision: int = 0, compression: int = 0) -> "Sim":
         h = C.c_void_p()
-        cfg = CConfig(dt, chi, tol, e_tol, streams, level, e_chi, precision)
+        cfg = CConfig(dt, chi, tol, e_tol, streams, level, e_chi, precision, compression)
         self._check(self.lib.vp_sim_create(self.h, C.byref(clayout(lay)), C.byref(cfg), f0.h, C.byref(h)))
         return Sim(self, h, lay)
 

@@ -338,3 +338,42 @@ def test_profile_trace_records(ctx):
     assert qr and all(r["m"] >= 1 and r["n"] >= 1 for r in qr)
     jac = [r for r in tr if r["class"] == "jacobi"]
     assert jac and all(r["m"] == r["n"] and r["k"] >= 1 for r in jac)
+
+
+# ------------------------------------ modified compression (SI scheme, f1)
+@pytest.mark.parametrize("ranks,split,chi,tol", [
+    ([1, 2, 4, 8, 16, 32, 16, 8, 4, 2, 1], 5, 1 << 10, 0.0),
+    ([1, 2, 4, 8, 16, 32, 16, 8, 4, 2, 1], 5, 6, 1e-10),
+    ([1, 2, 4, 8, 16, 32, 70, 64, 31, 8, 2, 1], 6, 24, 1e-12),
+    ([1, 2, 3, 37, 90, 41, 7, 2, 1], 3, 1 << 10, 1e-3),
+])
+def test_compress_modified_random(ctx, ranks, split, chi, tol):
+    cores = I.random_cores(ranks, seed=len(ranks) + split)
+    ref, ref_errs, _ = OS.compress_modified(cores, chi, tol, split)
+    m = ctx.mps_from_cores(cores)
+    errs = ctx.compress_modified(m, split, chi, tol)
+    assert m.bonds() == OS.bonds(ref)
+    assert rel(m.to_dense(), OS.to_dense(ref)) < F_TOL
+    np.testing.assert_allclose(errs, ref_errs, rtol=1e-6, atol=1e-14)
+
+
+@pytest.mark.parametrize("mapping", [I.SEQ, I.SEQ_S2, I.SEQ_S3])
+def test_rk4_steps_modified_compression(ctx, mapping):
+    lay = I.Layout(5, 5, 0.0, 10 * math.pi, -8.0, 8.0, mapping)
+    f0 = I.saturated_two_stream(lay, modes=6)
+    dt, chi = 0.05, 12
+    m = ctx.mps_from_grid(lay, f0, chi, 1e-10)
+    sim = ctx.sim(lay, m, dt, chi, compression=1)
+    ref = OV.mps_from_f(f0, lay, chi, 1e-10)
+    for _ in range(2):
+        rec = sim.step(1)[0]
+        ref, d = OV.rk4_step(ref, lay, dt, chi, modified=True)
+        assert abs(rec["field_energy"] - d["field_energy"]) <= WE_TOL * d["field_energy"]
+        assert sim.state().bonds() == d["bonds"]
+        assert rel(sim.state().to_grid(lay), OV.mps_to_f(ref, lay)) < F_TOL
+        np.testing.assert_allclose(sim.entropy(), d["entropy"], rtol=1e-8, atol=1e-12)
+    sim.close()
+    from paper_2205_11990_gb300.vpmps import VpError
+    lay_i = I.Layout(4, 4, 0.0, 4 * math.pi, -6.0, 6.0, I.INTERLEAVED)
+    with pytest.raises(VpError):
+        ctx.sim(lay_i, ctx.mps_from_grid(lay_i, I.landau(lay_i), 8, 1e-10), 0.05, 8, compression=1)
