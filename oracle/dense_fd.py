@@ -11,7 +11,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from .vp import field, grid_steps
+from .vp import field, grid_steps, species_params
 
 
 def d_backward_x(f, dx):
@@ -26,6 +26,21 @@ def d_centered_v_zero_gradient(f, dv):
     g = np.zeros_like(f)
     g[:, 1:-1] = (f[:, 2:] - f[:, :-2]) / (2.0 * dv)
     return g  # ghost node equal to the node inside the boundary: derivative 0 at both ends
+
+
+def d_second_v_zero_gradient(f, dv):
+    g = np.empty_like(f)
+    g[:, 1:-1] = (f[:, 2:] - 2.0 * f[:, 1:-1] + f[:, :-2]) / (dv * dv)
+    g[:, 0] = 2.0 * (f[:, 1] - f[:, 0]) / (dv * dv)      # ghost f_{-1} = f_1
+    g[:, -1] = 2.0 * (f[:, -2] - f[:, -1]) / (dv * dv)   # ghost f_N = f_{N-2}
+    return g
+
+
+def dougherty(f, v, dv, nu, u, vth):
+    """nu d/dv [(v - u) f + vth^2 df/dv] (Methods, "Collision Operator") with
+    u, vth the species' drift and thermal speed: centred drag, three-point
+    diffusion, zero-gradient ghosts on both."""
+    return nu * (d_centered_v_zero_gradient((v - u)[None, :] * f, dv) + vth * vth * d_second_v_zero_gradient(f, dv))
 
 
 def rhs(f, layout):
@@ -85,3 +100,37 @@ def fit_rate(ts, wes, t0, t1):
         raise ValueError("not enough maxima to fit")
     p = np.polyfit(ts[idx], np.log(wes[idx]), 1)
     return 0.5 * p[0]
+
+
+def multi_rhs(fs, layouts, species):
+    """Several species sharing E (see oracle.vp.multi_rk4_step): the field
+    from -sum_s q_s rho_s, species s advanced with E scaled by -q_s / m_s."""
+    dx, _ = grid_steps(layouts[0])
+    rhos = []
+    for f, lay in zip(fs, layouts):
+        _, dv = grid_steps(lay)
+        rhos.append(f.sum(axis=1) * dv)
+    net = -sum(species_params(sp)[0] * r for sp, r in zip(species, rhos))
+    E, we = field(net, dx)
+    out = []
+    for f, lay, sp in zip(fs, layouts, species):
+        q, m, nu, u, vth = species_params(sp)
+        _, dv = grid_steps(lay)
+        v = lay.v()
+        vp = np.where(v > 0, v, 0.0)[None, :]
+        vm = np.where(v > 0, 0.0, v)[None, :]
+        d = (-vp * d_backward_x(f, dx) - vm * d_forward_x(f, dx)
+             + (-q / m) * E[:, None] * d_centered_v_zero_gradient(f, dv))
+        if nu:
+            d = d + dougherty(f, v, dv, nu, u, vth)
+        out.append(d)
+    return out, we, rhos
+
+
+def multi_rk4_step(fs, layouts, species, dt):
+    k1, we, rhos = multi_rhs(fs, layouts, species)
+    k2, _, _ = multi_rhs([f + 0.5 * dt * k for f, k in zip(fs, k1)], layouts, species)
+    k3, _, _ = multi_rhs([f + 0.5 * dt * k for f, k in zip(fs, k2)], layouts, species)
+    k4, _, _ = multi_rhs([f + dt * k for f, k in zip(fs, k3)], layouts, species)
+    new = [f + dt / 6.0 * (a + 2 * b + 2 * c + d) for f, a, b, c, d in zip(fs, k1, k2, k3, k4)]
+    return new, we, rhos

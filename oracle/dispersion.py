@@ -52,3 +52,11 @@ def landau_root(k, guess=None):
 
 def two_stream_root(k, u=3.0, vth=1.0, guess=0.3j):
     return root(k, [(0.5, u, vth), (0.5, -u, vth)], guess)
+
+
+def buneman_root(k, mass_ratio, v0, vth_i, vth_e=1.0, guess=None):
+    """Electrons drifting at v0 through ions of mass mass_ratio (charge 1):
+    each species enters eps with weight omega_ps^2 = n q^2 / m."""
+    g = guess if guess is not None else complex(0.5 * (1.0 / mass_ratio) ** (1.0 / 3.0),
+                                                0.8 * (0.5 / mass_ratio) ** (1.0 / 3.0))
+    return root(k, [(1.0, v0, vth_e), (1.0 / mass_ratio, 0.0, vth_i)], g)

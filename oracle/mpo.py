@@ -111,6 +111,38 @@ def second_periodic(L, dx):
     return _chain(L, row, mid, col, scale=1.0 / (dx * dx))
 
 
+def second_zero_gradient(L, dx):
+    """Second derivative with the zero-gradient ghosts of
+    :func:`centered_zero_gradient` (f_{-1} = f_1, f_N = f_{N-2}): the
+    non-periodic backbone of "Second Derivative, Centered" (the carry that
+    would wrap around is absorbed at the first site) plus row 0 += c1 f_1 and
+    row N-1 += c1 f_{N-2}.  Used by the Dougherty diffusion term (Methods,
+    "Collision Operator"); the SI prints no zero-gradient second derivative."""
+    c0, c1 = -2.0, 1.0
+    row = [I2, SP, SM]
+    mid = [[I2, SP, SM], [Z2, SM, Z2], [Z2, Z2, SP]]
+    col = [c0 * I2 + c1 * (SM + SP), c1 * SM, c1 * SP]
+    backbone = _chain(L, row, mid, col)
+    m_left = [P0[None, :, :, None].copy() for _ in range(L - 1)]
+    m_left.append(np.array([[0.0, c1], [0.0, 0.0]])[None, :, :, None])
+    m_right = [P1[None, :, :, None].copy() for _ in range(L - 1)]
+    m_right.append(np.array([[0.0, 0.0], [c1, 0.0]])[None, :, :, None])
+    op = mpo_sum(mpo_sum(backbone, m_left), m_right)
+    op[0] = op[0] / (dx * dx)
+    return op
+
+
+def mpo_product(a, b):
+    """The MPO of a @ b (b acts first): per site C[(l,m), o, i, (r,s)] =
+    sum_j a[l, o, j, r] b[m, j, i, s]."""
+    out = []
+    for A, B in zip(a, b):
+        c = np.einsum("lojr,mjis->lmoirs", A, B)
+        s = c.shape
+        out.append(c.reshape(s[0] * s[1], 2, 2, s[4] * s[5]))
+    return out
+
+
 def identity(L):
     return [I2[None, :, :, None].copy() for _ in range(L)]
 

@@ -335,3 +335,78 @@ def _rk4_step_levels(f, layout, dt, chi, tol, e_tol, level, e_chi, comp=S.compre
     diag["trunc_err"] = errs
     diag["bonds"] = S.bonds(out)
     return out, diag
+
+
+# ------------------------------------------- several species sharing E
+def species_params(sp):
+    """(q, m) or (q, m, nu, u, vth) -> (q, m, nu, u, vth): charge and mass in
+    electron units, Dougherty collision rate, drift and thermal speed."""
+    sp = tuple(sp)
+    return sp + (0.0, 0.0, 1.0)[len(sp) - 2:] if len(sp) < 5 else sp
+
+
+def collision_mpo(layout, nu, u, vth):
+    """nu d/dv [(v - u) f + vth^2 df/dv] (Methods, "Collision Operator",
+    the Dougherty operator) with u and vth the species' drift and thermal
+    speed: nu [D_c^v diag(v - u) + vth^2 D_vv] on the v bits, both
+    derivatives with zero-gradient ghosts, identity on the x bits."""
+    _, dv = grid_steps(layout)
+    drift = M.diag_from_mps(S.from_dense(layout.v() - u, layout.nv, 1 << layout.nv, 1e-14))
+    cv = M.mpo_sum(M.mpo_product(M.centered_zero_gradient(layout.nv, dv), drift),
+                   M.mpo_scale(M.second_zero_gradient(layout.nv, dv), vth * vth))
+    cv = M.mpo_scale(cv, nu)
+    return M.place([M.identity(layout.nx), orient(cv, layout, 1)], sitemap(layout))
+
+
+def multi_stage_field(fs, layouts, species):
+    """E from the net charge sum_s q_s n_s of all species (Problem
+    Statement, every species evolved: no fixed background).  The periodic
+    solve is the one of :func:`field`, fed with -sum_s q_s rho_s (for
+    electrons alone that is rho_e: the one-species equation).  Returns
+    (E, W_E, per-species densities)."""
+    dx, _ = grid_steps(layouts[0])
+    rhos = [density(c, lay) for c, lay in zip(fs, layouts)]
+    net = -sum(species_params(sp)[0] * r for sp, r in zip(species, rhos))
+    E, we = field(net, dx)
+    return E, we, rhos
+
+
+def multi_rk4_step(fs, layouts, species, dt, chi, tol=TOL, e_tol=TOL):
+    """One RK4-C1 step of several species sharing the field: species s obeys
+    df_s/dt = -v df_s/dx - (q_s / m_s) E df_s/dv + C[f_s], the one-species
+    operator with E scaled by -q_s / m_s (electrons: +1) plus the Dougherty
+    term when nu_s > 0.  The stage field is computed once from all species'
+    stage states; every species then follows the C1 schedule of
+    :func:`rk4_step`.  Returns (new states, diagnostics)."""
+    n = len(fs)
+    accs = list(fs)
+    fis = list(fs)
+    coll = []
+    for sp, lay in zip(species, layouts):
+        _, _, nu, u, vth = species_params(sp)
+        coll.append(collision_mpo(lay, nu, u, vth) if nu else None)
+    diag = {}
+    for i in range(4):
+        E, we, rhos = multi_stage_field(fis, layouts, species)
+        if i == 0:
+            dx, _ = grid_steps(layouts[0])
+            diag["field_energy"] = we
+            diag["mass"] = [float(np.sum(r)) * dx for r in rhos]
+        ks = []
+        for s in range(n):
+            q, m = species_params(species[s])[:2]
+            L = operator(field_mps(-q / m * E, layouts[s], e_tol), layouts[s])
+            if coll[s] is not None:
+                L = M.mpo_sum(L, coll[s])
+            ks.append(S.apply_mpo(L, fis[s]))
+        errs = []
+        for s in range(n):
+            if i < 3:
+                fis[s], _ = S.compress(S.add(fs[s], ks[s], 1.0, A_RK[i] * dt), 1 << 30, tol)
+                accs[s], _ = S.compress(S.add(accs[s], ks[s], 1.0, B_RK[i] * dt), 1 << 30, tol)
+            else:
+                accs[s], e = S.compress(S.add(accs[s], ks[s], 1.0, B_RK[3] * dt), chi, tol)
+                errs.append(e)
+    diag["trunc_err"] = errs
+    diag["bonds"] = [S.bonds(a) for a in accs]
+    return accs, diag

@@ -72,6 +72,25 @@ def nonlinear_landau(layout: Layout):
     return landau(layout, amp=0.5, k=0.5)
 
 
+def buneman_layouts(nx, nv_e, nv_i, k=0.1, mass_ratio=25.0, mapping=SEQ):
+    """Electron and ion grids of the Buneman problem (Methods, "Buneman
+    instability"): x in [-pi/k, pi/k); electron v in +-6 omega_pe / k; ion v in
+    +-50 v_th,i with v_th,i = sqrt(T_i / m_i) at T_i = T_e."""
+    vth_i = 1.0 / math.sqrt(mass_ratio)
+    lay_e = Layout(nx, nv_e, -math.pi / k, math.pi / k, -6.0 / k, 6.0 / k, mapping)
+    lay_i = Layout(nx, nv_i, -math.pi / k, math.pi / k, -50.0 * vth_i, 50.0 * vth_i, mapping)
+    return lay_e, lay_i
+
+
+def buneman(lay_e: Layout, lay_i: Layout, amp=1e-3, k=0.1, mass_ratio=25.0):
+    """(f_e, f_i): ions a Maxwellian at rest, uniform in x; electrons a
+    Maxwellian drifting at v0 = omega_pe / k, perturbed by (1 + A cos kx)."""
+    vth_i = 1.0 / math.sqrt(mass_ratio)
+    f_i = np.outer(np.ones(lay_i.Nx), maxwellian(lay_i.v(), vth_i))
+    f_e = np.outer(1.0 + amp * np.cos(k * lay_e.x()), maxwellian(lay_e.v(), 1.0, 1.0 / k))
+    return f_e, f_i
+
+
 def two_stream(layout: Layout, amp=1e-3, k=0.2, v0=3.0):
     """f0 = (1 + A cos kx) [e^{-(v-v0)^2/2} + e^{-(v+v0)^2/2}] / (2 sqrt(2 pi))."""
     x, v = layout.x(), layout.v()
