@@ -326,6 +326,45 @@ double vp_sim_flops(const vp_sim* sim);
 int vp_run(vp_ctx* ctx, const vp_layout* layout, const vp_config* cfg, const double* f0_host,
            int nsteps, double* fT_host, vp_record* records);
 
+/* ------------------------------------------------ several species (f_s) */
+
+/* Species s of a multi-species run (Problem Statement: the Vlasov equation of
+ * every species, Poisson's equation for the net charge; Methods, "Buneman
+ * instability", "Collision Operator").  Units: electron charge magnitude and
+ * mass; electrons are q = -1, m = 1. */
+typedef struct {
+  double q;    /* charge (ions +1, electrons -1) */
+  double m;    /* mass (> 0) */
+  double nu;   /* Dougherty collision rate (0: collisionless) */
+  double u;    /* drift of the Dougherty operator nu d/dv[(v - u) f + vth^2 df/dv] */
+  double vth;  /* thermal speed of the Dougherty operator (> 0 when nu > 0) */
+} vp_species;
+
+typedef struct vp_multi vp_multi;
+
+/* ns species (1..16) sharing one electric field.  layouts[s] gives species
+ * s its own v grid; every layout has the same nx, xmin and xmax (one x
+ * grid, one field).  f0[s] (ns device MPS, copied) is species s's initial
+ * state on layouts[s].  cfg is that of vp_sim_create, applied to every
+ * species; only compression level C1 (cfg->level 0 or 1).  Each RK4 stage
+ * computes every species' density rho_s, solves Poisson once for the net
+ * density -sum_s q_s rho_s (for electrons alone: rho_e, the one-species
+ * equation), and advances species s with the one-species operator whose
+ * field term is diag(-q_s/m_s E) (x) D_v, plus nu_s [D_c^v diag(v - u_s) +
+ * vth_s^2 D_vv] (zero-gradient v derivatives) when nu_s > 0.  Errors:
+ * VP_EINVAL (bad argument, x grids differ, level > 1), VP_ECFL (max |v| dt /
+ * dx above 0.6963 for some species), VP_ECUDA, VP_ENOMEM. */
+int vp_multi_create(vp_ctx* ctx, int ns, const vp_layout* layouts, const vp_species* species,
+                    const vp_config* cfg, const mps_t* const* f0, vp_multi** out);
+int vp_multi_destroy(vp_multi* m);
+/* Advance nsteps; records[nsteps * ns] (host, or NULL): record n*ns + s is
+ * step n of species s -- t, the shared field energy W_E, the species' mass
+ * sum f_s dx dv (both of the state at the start of the step), its max bond
+ * and truncation error after the step. */
+int vp_multi_step(vp_multi* m, int nsteps, vp_record* records);
+/* Current state of species s (owned by the run; valid until the next step). */
+const mps_t* vp_multi_state(const vp_multi* m, int s);
+
 /* ------------------------------------------------- batching and serving */
 
 /* Many independent runs on one GPU (no counterpart in the paper: the

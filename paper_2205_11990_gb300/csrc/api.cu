@@ -1174,6 +1174,7 @@ struct vp_sim {
   std::vector<double> entropy;  // per-bond EE of the last final compression
   vp_ctx* ctxB = nullptr;  // second stream: the f_{i+1} compressions run beside the acc ones
   cudaEvent_t evA = nullptr, evB = nullptr;
+  double ecoef = 1.0;      // -q/m of the species: the field term is diag(ecoef E) (x) D_v
 };
 
 namespace vp {
@@ -1225,6 +1226,22 @@ static int assemble_operator(vp_sim* s, bool with_upwind = true, mpo_t* dst = nu
   return VP_OK;
 }
 
+// E (device, Nx) as an MPS in the site order of the x bits (tolerance
+// e_tol, cap e_chi) -> L(E).
+static int field_operator(vp_sim* s, const double* E) {
+  vp_ctx* ctx = s->ctx;
+  const int Nx = 1 << s->lay.nx;
+  mps_free(&s->em);
+  const double* Ev = E;
+  if (xdesc(&s->lay)) {
+    VP_TRY(reserve(ctx, s->evec, (size_t)Nx));
+    VP_TRY(launch_permute_to_sites(ctx, E, s->lay.nx, 0, VP_SEQ_S2, s->evec.p, 0));
+    Ev = s->evec.p;
+  }
+  VP_TRY(from_vector(ctx, &s->em, s->lay.nx, Ev, s->cfg.e_chi > 0 ? s->cfg.e_chi : 1 << 30, s->cfg.e_tol));
+  return assemble_operator(s);
+}
+
 // Field of a stage: rho -> E -> E as an MPS (tolerance e_tol) -> L(E).
 static int stage_operator(vp_sim* s, const mps_t* f, double* we_mass) {
   vp_ctx* ctx = s->ctx;
@@ -1233,15 +1250,7 @@ static int stage_operator(vp_sim* s, const mps_t* f, double* we_mass) {
   VP_TRY(launch_poisson(ctx, s->rho.p, Nx, grid_dx(&s->lay), s->E.p, ctx->d_smalld + 8));
   if (we_mass)
     VP_CUDA(ctx, cudaMemcpyAsync(we_mass, ctx->d_smalld + 8, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
-  mps_free(&s->em);
-  const double* Ev = s->E.p;
-  if (xdesc(&s->lay)) {  // field MPS in the site order of the x bits
-    VP_TRY(reserve(ctx, s->evec, (size_t)Nx));
-    VP_TRY(launch_permute_to_sites(ctx, s->E.p, s->lay.nx, 0, VP_SEQ_S2, s->evec.p, 0));
-    Ev = s->evec.p;
-  }
-  VP_TRY(from_vector(ctx, &s->em, s->lay.nx, Ev, s->cfg.e_chi > 0 ? s->cfg.e_chi : 1 << 30, s->cfg.e_tol));
-  return assemble_operator(s);
+  return field_operator(s, s->E.p);
 }
 
 // Compression levels C2..C5 (and a capped field bond): one stream, the
@@ -1343,11 +1352,74 @@ static int sim_step(vp_sim* s, vp_record* rec) {
   return st;
 }
 
-static int sim_step_impl(vp_sim* s, vp_record* rec) {
+// Stage i of RK4-C1 once the stage operator L is assembled: for i < 3
+// acc <- C_tol(acc + B_i dt L f_i) and f_{i+1} <- C_tol(f + A_i dt L f_i)
+// (concurrently on the second stream when there is one); for i = 3
+// f <- C_chi(acc + B_3 dt L f_3), its per-bond errors in errs.
+static int c1_stage(vp_sim* s, int i, const mps_t*& fi, const mps_t*& acc, double* errs) {
   vp_ctx* ctx = s->ctx;
   static const double A[3] = {0.5, 0.5, 1.0};
   static const double B[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
   const double dt = s->cfg.dt;
+  if (i < 3 && s->ctxB) {
+    // The two tolerance compressions of a stage are independent: acc_i on
+    // this context's stream, f_{i+1} on the second stream from a second
+    // host thread.  Each MPS keeps its buffers on the context that
+    // compresses it (acc, wa, f: first; fi, wb: second).
+    vp_ctx* cb = s->ctxB;
+    VP_CUDA(ctx, cudaEventRecord(s->evA, ctx->stream));
+    VP_CUDA(ctx, cudaStreamWaitEvent(cb->stream, s->evA, 0));
+    VP_TRY(site_sum_mps(ctx, 1.0, acc, B[i] * dt, &s->L, fi, &s->wa));
+    VP_TRY(site_sum_mps(cb, 1.0, &s->f, A[i] * dt, &s->L, fi, &s->wb));
+    const int cap0 = ctx->coop_cap;
+    ctx->coop_cap = cb->coop_cap = ctx->num_sms / 2;
+    int stB = VP_OK;
+    Flops fB;
+    const bool prof = ctx->prof_on;
+    std::thread worker([&] {
+      cb->prof_on = prof;
+      g_flops = &fB;
+      stB = compress(cb, &s->wb, 1 << 30, s->cfg.tol, nullptr);
+      g_flops = nullptr;
+    });
+    const int stA = compress(ctx, &s->wa, 1 << 30, s->cfg.tol, nullptr);
+    worker.join();
+    ctx->coop_cap = cap0;
+    if (stA != VP_OK) return stA;
+    if (stB != VP_OK) return fail(ctx, stB, cb->err);
+    VP_CUDA(ctx, cudaEventRecord(s->evB, cb->stream));
+    VP_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, s->evB, 0));
+    s->flops.qr += fB.qr;
+    s->flops.formq += fB.formq;
+    s->flops.gemm += fB.gemm;
+    s->flops.jacobi += fB.jacobi;
+    std::swap(s->acc, s->wa);
+    std::swap(s->fi, s->wb);
+    acc = &s->acc;
+    fi = &s->fi;
+  } else if (i < 3) {
+    VP_TRY(site_sum_mps(ctx, 1.0, acc, B[i] * dt, &s->L, fi, &s->wa));
+    VP_TRY(site_sum_mps(ctx, 1.0, &s->f, A[i] * dt, &s->L, fi, &s->wb));
+    VP_TRY(compress(ctx, &s->wa, 1 << 30, s->cfg.tol, nullptr));
+    VP_TRY(compress(ctx, &s->wb, 1 << 30, s->cfg.tol, nullptr));
+    std::swap(s->acc, s->wa);
+    std::swap(s->fi, s->wb);
+    acc = &s->acc;
+    fi = &s->fi;
+  } else {
+    VP_TRY(site_sum_mps(ctx, 1.0, acc, B[3] * dt, &s->L, fi, &s->wa));
+    s->entropy.assign(std::max(1, s->f.n - 1), 0.0);
+    g_entropy = s->entropy.data();
+    const int stc = compress(ctx, &s->wa, s->cfg.chi, s->cfg.tol, errs);
+    g_entropy = nullptr;
+    VP_TRY(stc);
+    std::swap(s->f, s->wa);
+  }
+  return VP_OK;
+}
+
+static int sim_step_impl(vp_sim* s, vp_record* rec) {
+  vp_ctx* ctx = s->ctx;
   const mps_t* fi = &s->f;
   const mps_t* acc = &s->f;
   double wm[2] = {0, 0};
@@ -1355,60 +1427,7 @@ static int sim_step_impl(vp_sim* s, vp_record* rec) {
   g_flops = &s->flops;
   for (int i = 0; i < 4; ++i) {
     VP_TRY(stage_operator(s, fi, i == 0 ? s->ctx->h_smalld + 16 : nullptr));
-    if (i < 3 && s->ctxB) {
-      // The two tolerance compressions of a stage are independent: acc_i on
-      // this context's stream, f_{i+1} on the second stream from a second
-      // host thread.  Each MPS keeps its buffers on the context that
-      // compresses it (acc, wa, f: first; fi, wb: second).
-      vp_ctx* cb = s->ctxB;
-      VP_CUDA(ctx, cudaEventRecord(s->evA, ctx->stream));
-      VP_CUDA(ctx, cudaStreamWaitEvent(cb->stream, s->evA, 0));
-      VP_TRY(site_sum_mps(ctx, 1.0, acc, B[i] * dt, &s->L, fi, &s->wa));
-      VP_TRY(site_sum_mps(cb, 1.0, &s->f, A[i] * dt, &s->L, fi, &s->wb));
-      const int cap0 = ctx->coop_cap;
-      ctx->coop_cap = cb->coop_cap = ctx->num_sms / 2;
-      int stB = VP_OK;
-      Flops fB;
-      const bool prof = ctx->prof_on;
-      std::thread worker([&] {
-        cb->prof_on = prof;
-        g_flops = &fB;
-        stB = compress(cb, &s->wb, 1 << 30, s->cfg.tol, nullptr);
-        g_flops = nullptr;
-      });
-      const int stA = compress(ctx, &s->wa, 1 << 30, s->cfg.tol, nullptr);
-      worker.join();
-      ctx->coop_cap = cap0;
-      if (stA != VP_OK) return stA;
-      if (stB != VP_OK) return fail(ctx, stB, cb->err);
-      VP_CUDA(ctx, cudaEventRecord(s->evB, cb->stream));
-      VP_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, s->evB, 0));
-      s->flops.qr += fB.qr;
-      s->flops.formq += fB.formq;
-      s->flops.gemm += fB.gemm;
-      s->flops.jacobi += fB.jacobi;
-      std::swap(s->acc, s->wa);
-      std::swap(s->fi, s->wb);
-      acc = &s->acc;
-      fi = &s->fi;
-    } else if (i < 3) {
-      VP_TRY(site_sum_mps(ctx, 1.0, acc, B[i] * dt, &s->L, fi, &s->wa));
-      VP_TRY(site_sum_mps(ctx, 1.0, &s->f, A[i] * dt, &s->L, fi, &s->wb));
-      VP_TRY(compress(ctx, &s->wa, 1 << 30, s->cfg.tol, nullptr));
-      VP_TRY(compress(ctx, &s->wb, 1 << 30, s->cfg.tol, nullptr));
-      std::swap(s->acc, s->wa);
-      std::swap(s->fi, s->wb);
-      acc = &s->acc;
-      fi = &s->fi;
-    } else {
-      VP_TRY(site_sum_mps(ctx, 1.0, acc, B[3] * dt, &s->L, fi, &s->wa));
-      s->entropy.assign(std::max(1, s->f.n - 1), 0.0);
-      g_entropy = s->entropy.data();
-      const int stc = compress(ctx, &s->wa, s->cfg.chi, s->cfg.tol, errs.data());
-      g_entropy = nullptr;
-      VP_TRY(stc);
-      std::swap(s->f, s->wa);
-    }
+    VP_TRY(c1_stage(s, i, fi, acc, errs.data()));
   }
   g_flops = nullptr;
   VP_TRY(sync_status(ctx));
@@ -1422,7 +1441,7 @@ static int sim_step_impl(vp_sim* s, vp_record* rec) {
     rec->max_bond = *std::max_element(s->f.r.begin(), s->f.r.end());
     rec->trunc_err = errs.empty() ? 0.0 : *std::max_element(errs.begin(), errs.end());
   }
-  s->t += dt;
+  s->t += s->cfg.dt;
   return VP_OK;
 }
 
@@ -1463,16 +1482,17 @@ static void sim_free(vp_sim* s) {
   release(ctx, s->evec);
 }
 
-}  // namespace vp
-
-extern "C" {
-
-int vp_sim_create(vp_ctx* ctx, const vp_layout* L, const vp_config* cfg, const mps_t* f0, vp_sim** out) {
+// A sim of one species: sp == NULL is the electron species against a fixed
+// neutralising background; otherwise the field factor -q/m and, for nu > 0,
+// the Dougherty term joins the static part of the operator.
+static int sim_create(vp_ctx* ctx, const vp_layout* L, const vp_config* cfg, const mps_t* f0, const vp_species* sp,
+                      vp_sim** out) {
   if (!ctx || !cfg || !f0 || !out || !layout_ok(L) || L->nx + L->nv != f0->n || cfg->chi < 1 || cfg->tol < 0 ||
       cfg->e_tol < 0 || !(cfg->dt > 0))
     return fail(ctx, VP_EINVAL, "vp_sim_create: bad argument");
   const double dx = grid_dx(L);
-  if (L->vmax * cfg->dt / dx > 0.6963) return fail(ctx, VP_ECFL, "dt above the RK4 upwind stability limit");
+  if (std::max(std::fabs(L->vmin), std::fabs(L->vmax)) * cfg->dt / dx > 0.6963)
+    return fail(ctx, VP_ECFL, "dt above the RK4 upwind stability limit");
   vp_sim* s = new vp_sim();
   s->ctx = ctx;
   s->lay = *L;
@@ -1482,6 +1502,14 @@ int vp_sim_create(vp_ctx* ctx, const vp_layout* L, const vp_config* cfg, const m
   int st = mps_copy(ctx, f0, &s->f);
   if (st == VP_OK) {
     s->U = upwind_operator(L->nx, L->nv, s->dims, dx, L->vmin, grid_dv(L), xdesc(L), vdesc(L));
+    if (sp) {
+      s->ecoef = -sp->q / sp->m;
+      if (sp->nu > 0.0) {
+        Chain cv = collision_chain(L->nv, L->vmin, grid_dv(L), sp->nu, sp->u, sp->vth);
+        if (vdesc(L)) cv = reverse_chain(cv);
+        s->U = chain_sum(s->U, place2(identity_chain(L->nx), cv, s->dims));
+      }
+    }
     s->Dv = zero_gradient_chain(L->nv, grid_dv(L));
     if (vdesc(L)) s->Dv = reverse_chain(s->Dv);
     st = upload_chain(ctx, s->U, s->Ud);
@@ -1511,6 +1539,14 @@ int vp_sim_create(vp_ctx* ctx, const vp_layout* L, const vp_config* cfg, const m
   }
   *out = s;
   return VP_OK;
+}
+
+}  // namespace vp
+
+extern "C" {
+
+int vp_sim_create(vp_ctx* ctx, const vp_layout* L, const vp_config* cfg, const mps_t* f0, vp_sim** out) {
+  return sim_create(ctx, L, cfg, f0, nullptr, out);
 }
 
 int vp_sim_destroy(vp_sim* s) {
@@ -1551,6 +1587,167 @@ int vp_run(vp_ctx* ctx, const vp_layout* L, const vp_config* cfg, const double* 
   if (st == VP_OK && fT) st = mps_to_grid(ctx, &s->f, L, fT);
   vp_sim_destroy(s);
   return st;
+}
+
+}  // extern "C"
+
+// ================================================================ several species
+struct vp_multi {
+  vp_ctx* ctx = nullptr;
+  std::vector<vp_sim*> sp;
+  std::vector<vp_species> par;
+  vp_config cfg{};
+  DevBuf net, E, Es;
+  double t = 0.0;
+};
+
+namespace vp {
+
+// One RK4-C1 step of all species in lockstep: per stage every species'
+// density, one Poisson solve for the net density, then each species' field
+// operator (E scaled by -q/m) and its C1 stage update.
+static int multi_step_impl(vp_multi* M, vp_record* rec) {
+  vp_ctx* ctx = M->ctx;
+  const int ns = (int)M->sp.size();
+  const vp_layout& L0 = M->sp[0]->lay;
+  const int Nx = 1 << L0.nx;
+  const double dx = grid_dx(&L0);
+  std::vector<const mps_t*> fi(ns), acc(ns);
+  std::vector<std::vector<double>> errs(ns);
+  SpeciesRho sr{};
+  sr.ns = ns;
+  for (int s = 0; s < ns; ++s) {
+    fi[s] = acc[s] = &M->sp[s]->f;
+    errs[s].assign(M->sp[s]->f.n, 0.0);
+    sr.rho[s] = M->sp[s]->rho.p;
+    sr.w[s] = -M->par[s].q;
+  }
+  for (int i = 0; i < 4; ++i) {
+    for (int s = 0; s < ns; ++s) VP_TRY(density(ctx, &M->sp[s]->lay, fi[s], M->sp[s]->rho.p));
+    VP_TRY(launch_species_net(ctx, sr, Nx, dx, M->net.p, ctx->d_smalld + 32));
+    VP_TRY(launch_poisson(ctx, M->net.p, Nx, dx, M->E.p, ctx->d_smalld + 8));
+    if (i == 0) {
+      VP_CUDA(ctx, cudaMemcpyAsync(ctx->h_smalld + 24, ctx->d_smalld + 8, sizeof(double), cudaMemcpyDeviceToHost,
+                                   ctx->stream));
+      VP_CUDA(ctx, cudaMemcpyAsync(ctx->h_smalld + 32, ctx->d_smalld + 32, ns * sizeof(double),
+                                   cudaMemcpyDeviceToHost, ctx->stream));
+    }
+    for (int s = 0; s < ns; ++s) {
+      vp_sim* sp = M->sp[s];
+      const double* Ev = M->E.p;
+      if (sp->ecoef != 1.0) {
+        VP_TRY(launch_copy(ctx, M->E.p, M->Es.p, (size_t)Nx));
+        VP_TRY(launch_scale(ctx, M->Es.p, (size_t)Nx, sp->ecoef));
+        Ev = M->Es.p;
+      }
+      VP_TRY(field_operator(sp, Ev));
+      g_flops = &sp->flops;
+      const int st = c1_stage(sp, i, fi[s], acc[s], errs[s].data());
+      g_flops = nullptr;
+      VP_TRY(st);
+    }
+  }
+  VP_TRY(sync_status(ctx));
+  const double we = ctx->h_smalld[24];
+  if (!std::isfinite(we)) return fail(ctx, VP_ENUMERIC, "non-finite field energy");
+  for (int s = 0; s < ns; ++s) {
+    vp_sim* sp = M->sp[s];
+    if (rec) {
+      rec[s].t = M->t;
+      rec[s].field_energy = we;
+      rec[s].mass = ctx->h_smalld[32 + s];
+      rec[s].max_bond = *std::max_element(sp->f.r.begin(), sp->f.r.end());
+      rec[s].trunc_err = errs[s].empty() ? 0.0 : *std::max_element(errs[s].begin(), errs[s].end());
+    }
+    sp->t += M->cfg.dt;
+  }
+  M->t += M->cfg.dt;
+  return VP_OK;
+}
+
+static int multi_step(vp_multi* M, vp_record* rec) {
+  vp_ctx* ctx = M->ctx;
+  const int p0 = ctx->precision, m0 = ctx->modified_split;
+  const int split = M->cfg.compression == VP_COMPRESS_MODIFIED ? M->sp[0]->lay.nx : 0;
+  ctx->precision = M->cfg.precision;
+  ctx->modified_split = split;
+  for (vp_sim* sp : M->sp)
+    if (sp->ctxB) {
+      sp->ctxB->precision = M->cfg.precision;
+      sp->ctxB->modified_split = split;
+    }
+  const int st = multi_step_impl(M, rec);
+  ctx->precision = p0;
+  ctx->modified_split = m0;
+  return st;
+}
+
+static void multi_free(vp_multi* M) {
+  for (vp_sim* s : M->sp) {
+    sim_free(s);
+    delete s;
+  }
+  M->sp.clear();
+  release(M->ctx, M->net);
+  release(M->ctx, M->E);
+  release(M->ctx, M->Es);
+}
+
+}  // namespace vp
+
+extern "C" {
+
+int vp_multi_create(vp_ctx* ctx, int ns, const vp_layout* layouts, const vp_species* species, const vp_config* cfg,
+                    const mps_t* const* f0, vp_multi** out) {
+  if (!ctx || ns < 1 || ns > kMaxSpecies || !layouts || !species || !cfg || !f0 || !out || cfg->level > 1)
+    return fail(ctx, VP_EINVAL, "vp_multi_create: bad argument");
+  for (int s = 0; s < ns; ++s) {
+    const vp_layout& L = layouts[s];
+    const vp_species& p = species[s];
+    if (!layout_ok(&L) || L.nx != layouts[0].nx || L.xmin != layouts[0].xmin || L.xmax != layouts[0].xmax || !f0[s])
+      return fail(ctx, VP_EINVAL, "vp_multi_create: every species needs a valid layout on the same x grid");
+    if (!(p.m > 0.0) || !std::isfinite(p.q) || !(p.nu >= 0.0) || !std::isfinite(p.u) || (p.nu > 0.0 && !(p.vth > 0.0)))
+      return fail(ctx, VP_EINVAL, "vp_multi_create: bad species parameters");
+  }
+  vp_multi* M = new vp_multi();
+  M->ctx = ctx;
+  M->cfg = *cfg;
+  M->par.assign(species, species + ns);
+  int st = VP_OK;
+  for (int s = 0; s < ns && st == VP_OK; ++s) {
+    vp_sim* sim = nullptr;
+    st = sim_create(ctx, &layouts[s], cfg, f0[s], &species[s], &sim);
+    if (st == VP_OK) M->sp.push_back(sim);
+  }
+  const size_t Nx = (size_t)1 << layouts[0].nx;
+  if (st == VP_OK) st = reserve(ctx, M->net, Nx);
+  if (st == VP_OK) st = reserve(ctx, M->E, Nx);
+  if (st == VP_OK) st = reserve(ctx, M->Es, Nx);
+  if (st != VP_OK) {
+    multi_free(M);
+    delete M;
+    return st;
+  }
+  *out = M;
+  return VP_OK;
+}
+
+int vp_multi_destroy(vp_multi* M) {
+  if (!M) return VP_EINVAL;
+  multi_free(M);
+  delete M;
+  return VP_OK;
+}
+
+int vp_multi_step(vp_multi* M, int nsteps, vp_record* records) {
+  if (!M || nsteps < 0) return VP_EINVAL;
+  const int ns = (int)M->sp.size();
+  for (int n = 0; n < nsteps; ++n) VP_TRY(multi_step(M, records ? records + (size_t)n * ns : nullptr));
+  return VP_OK;
+}
+
+const mps_t* vp_multi_state(const vp_multi* M, int s) {
+  return (M && s >= 0 && s < (int)M->sp.size()) ? &M->sp[s]->f : nullptr;
 }
 
 }  // extern "C"

@@ -219,6 +219,14 @@ int launch_scale_rows(vp_ctx* ctx, double* x, int rows, int cols, const double* 
 int launch_permute_to_sites(vp_ctx* ctx, const double* f, int nx, int nv, int mapping, double* out,
                             int inverse);
 int launch_poisson(vp_ctx* ctx, const double* rho, int N, double dx, double* E, double* we_dev);
+// Several species: net density sum_s w[s] rho[s][i] and masses sum rho_s dx.
+constexpr int kMaxSpecies = 16;
+struct SpeciesRho {
+  const double* rho[kMaxSpecies];
+  double w[kMaxSpecies];
+  int ns;
+};
+int launch_species_net(vp_ctx* ctx, const SpeciesRho& sr, int N, double dx, double* net, double* mass);
 // MPO core on one site for the E-term diag(E) (x) D_v (placed product).
 struct ETermSite {
   int is_x;                 // site carries an x bit

@@ -55,14 +55,15 @@ Chain stencil_chain(int L, const std::vector<std::vector<double>>& coeffs, bool 
   return c;
 }
 
-Chain zero_gradient_chain(int L, double dv) {
-  const double c1 = 0.5 / dv;
-  std::vector<std::vector<double>> co = {{0.0, -c1, 0.0, c1, 0.0}};
-  Chain base = stencil_chain(L, co, false);
-  if (L == 1) {  // both nodes are boundary nodes
-    Chain z;
-    z.alloc({1, 1});
-    return z;
+// Non-periodic stencil sum_s c_s f_{n+s} plus ghost corrections on the end
+// rows: row 0 gains first * f_1, row N-1 gains last * f_{N-2} (the mirrored
+// ghosts f_{-1} = f_1 and f_N = f_{N-2} folded back onto the grid).
+static Chain ghost_chain(int L, const std::vector<double>& co, double first, double last) {
+  Chain base = stencil_chain(L, {co}, false);
+  if (L == 1) {
+    base.at(0, 0, 0, 1, 0) += first;
+    base.at(0, 0, 1, 0, 0) += last;
+    return base;
   }
   std::vector<int> w(L + 1, 5);
   w[0] = 1;
@@ -84,11 +85,54 @@ Chain zero_gradient_chain(int L, double dv) {
       c.at(k, 3, 0, 0, 3) = 1.0;
       c.at(k, 4, 1, 1, 4) = 1.0;
     } else {
-      c.at(k, 3, 0, 1, 0) = -c1;  // row 0 loses +c1 f_1: ghost f_{-1} = f_1
-      c.at(k, 4, 1, 0, 0) = c1;   // row N-1 loses -c1 f_{N-2}: ghost f_N = f_{N-2}
+      c.at(k, 3, 0, 1, 0) = first;
+      c.at(k, 4, 1, 0, 0) = last;
     }
   }
   return c;
+}
+
+Chain zero_gradient_chain(int L, double dv) {
+  const double c1 = 0.5 / dv;
+  // row 0 loses +c1 f_1 (ghost f_{-1} = f_1), row N-1 loses -c1 f_{N-2}
+  return ghost_chain(L, {0.0, -c1, 0.0, c1, 0.0}, -c1, c1);
+}
+
+Chain second_zero_gradient_chain(int L, double dv) {
+  const double s = 1.0 / (dv * dv);
+  // the ghosts add s f_1 to row 0 and s f_{N-2} to row N-1
+  return ghost_chain(L, {0.0, s, -2.0 * s, s, 0.0}, s, s);
+}
+
+Chain chain_product(const Chain& a, const Chain& b) {
+  const int L = (int)a.core.size();
+  std::vector<int> w(L + 1);
+  for (int k = 0; k <= L; ++k) w[k] = a.w[k] * b.w[k];
+  Chain c;
+  c.alloc(w);
+  for (int k = 0; k < L; ++k) {
+    const int al = a.w[k], ar = a.w[k + 1], bl = b.w[k], br = b.w[k + 1];
+    for (int la = 0; la < al; ++la)
+      for (int ra = 0; ra < ar; ++ra)
+        for (int o = 0; o < 2; ++o)
+          for (int j = 0; j < 2; ++j) {
+            const double x = a.core[k][((size_t)la * 4 + o * 2 + j) * ar + ra];
+            if (x == 0.0) continue;
+            for (int lb = 0; lb < bl; ++lb)
+              for (int rb = 0; rb < br; ++rb)
+                for (int i = 0; i < 2; ++i) {
+                  const double y = b.core[k][((size_t)lb * 4 + j * 2 + i) * br + rb];
+                  if (y != 0.0) c.at(k, la * bl + lb, o, i, ra * br + rb) += x * y;
+                }
+          }
+  }
+  return c;
+}
+
+Chain collision_chain(int L, double vmin, double dv, double nu, double u, double vth) {
+  Chain drag = chain_product(zero_gradient_chain(L, dv), velocity_chain(L, vmin - u, dv, 0));
+  Chain c = chain_sum(drag, scaled(second_zero_gradient_chain(L, dv), vth * vth));
+  return scaled(c, nu);
 }
 
 static double hsel(int which, int bit) {

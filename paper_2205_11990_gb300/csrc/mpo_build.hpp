@@ -26,6 +26,13 @@ Chain stencil_chain(int L, const std::vector<std::vector<double>>& coeffs, bool 
 // Centred first derivative with zero-gradient ends (ghost node equal to the
 // node inside the boundary): derivative zero on the first and last node.
 Chain zero_gradient_chain(int L, double dv);
+// Three-point second derivative with the same mirrored ghosts.
+Chain second_zero_gradient_chain(int L, double dv);
+// The operator a b (b applied first); bonds multiply.
+Chain chain_product(const Chain& a, const Chain& b);
+// Dougherty collision operator on the v bits (Methods, "Collision Operator"):
+// nu [D_c diag(v - u) + vth^2 D_vv], both derivatives zero-gradient.
+Chain collision_chain(int L, double vmin, double dv, double nu, double u, double vth);
 // diag(v * h(v_msb)) on L bits, v_j = vmin + j dv, h selects v > 0 (upper
 // half) when positive, else v < 0; as an affine chain of bond 2.  If
 // left_channels == 2 the first core takes a 2-channel left bond with

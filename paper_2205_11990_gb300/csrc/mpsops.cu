@@ -272,6 +272,38 @@ int launch_poisson(vp_ctx* ctx, const double* rho, int N, double dx, double* E, 
   return check_launch(ctx, "poisson");
 }
 
+// Net density of several species, net_i = sum_s w_s rho_s[i], and each
+// species' mass sum_i rho_s[i] dx (one block).
+__global__ void k_species_net(SpeciesRho sr, int N, double dx, double* __restrict__ net, double* __restrict__ mass) {
+  __shared__ double red[32];
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
+  for (int i = tid; i < N; i += nt) {
+    double a = 0.0;
+    for (int s = 0; s < sr.ns; ++s) a = fma(sr.w[s], sr.rho[s][i], a);
+    net[i] = a;
+  }
+  for (int s = 0; s < sr.ns; ++s) {
+    double loc = 0.0;
+    for (int i = tid; i < N; i += nt) loc += sr.rho[s][i];
+    for (int o = 16; o > 0; o >>= 1) loc += __shfl_xor_sync(0xffffffffu, loc, o);
+    if (lane == 0) red[warp] = loc;
+    __syncthreads();
+    if (tid == 0) {
+      double t = 0.0;
+      for (int w = 0; w < nt / 32; ++w) t += red[w];
+      mass[s] = t * dx;
+    }
+    __syncthreads();
+  }
+}
+
+int launch_species_net(vp_ctx* ctx, const SpeciesRho& sr, int N, double dx, double* net, double* mass) {
+  if (sr.ns < 1 || sr.ns > kMaxSpecies) return fail(ctx, VP_EINVAL, "species_net: bad species count");
+  ctx->launches++;
+  k_species_net<<<1, 256, 0, ctx->stream>>>(sr, N, dx, net, mass);
+  return check_launch(ctx, "species_net");
+}
+
 // L core = blockdiag(U, T) with T the placed field term diag(E) (x) D_v.
 // Bond indices of T flatten (E channel, D_v channel) in that order.
 __global__ void k_assemble(const double* __restrict__ U, int ul, int ur, ETermSite e, int first, int last,

@@ -41,6 +41,7 @@ EXPORTS = [
     "vp_sim_create", "vp_sim_destroy", "vp_step", "vp_sim_state", "vp_sim_entropy", "vp_sim_flops", "vp_run",
     "vp_footprint_bytes", "vp_batch_create", "vp_batch_submit", "vp_batch_start", "vp_batch_wait", "vp_batch_poll",
     "vp_batch_records", "vp_batch_destroy",
+    "vp_multi_create", "vp_multi_destroy", "vp_multi_step", "vp_multi_state",
 ]
 
 
@@ -63,6 +64,10 @@ class CConfig(C.Structure):
     _fields_ = [("dt", C.c_double), ("chi", C.c_int), ("tol", C.c_double), ("e_tol", C.c_double),
                 ("streams", C.c_int), ("level", C.c_int), ("e_chi", C.c_int), ("precision", C.c_int),
                 ("compression", C.c_int)]
+
+
+class CSpecies(C.Structure):
+    _fields_ = [("q", C.c_double), ("m", C.c_double), ("nu", C.c_double), ("u", C.c_double), ("vth", C.c_double)]
 
 
 class CResult(C.Structure):
@@ -151,6 +156,11 @@ def load():
         "vp_batch_poll": (I, [P, C.POINTER(CResult), I, C.POINTER(I)]),
         "vp_batch_records": (I, [P, C.c_uint64, C.POINTER(CRecord), DP, DP]),
         "vp_batch_destroy": (I, [P]),
+        "vp_multi_create": (I, [P, I, C.POINTER(CLayout), C.POINTER(CSpecies), C.POINTER(CConfig), C.POINTER(P),
+                                C.POINTER(P)]),
+        "vp_multi_destroy": (I, [P]),
+        "vp_multi_step": (I, [P, I, C.POINTER(CRecord)]),
+        "vp_multi_state": (P, [P, I]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -360,6 +370,25 @@ class Context:
         self._check(self.lib.vp_sim_create(self.h, C.byref(clayout(lay)), C.byref(cfg), f0.h, C.byref(h)))
         return Sim(self, h, lay)
 
+    def multi(self, lays, species, f0s, dt: float, chi: int, tol: float = 1e-10, e_tol: float = 1e-10,
+              streams: int = 2, e_chi: int = 0, precision: int = 0, compression: int = 0) -> "Multi":
+        """Several species sharing one field (vp_multi_*).  species: per
+        species (q, m) or (q, m, nu, u, vth); f0s: per species an MPS."""
+        ns = len(lays)
+        if not (len(species) == len(f0s) == ns):
+            raise ValueError("multi: one layout, species and initial state per species")
+        cl = (CLayout * ns)(*[clayout(l) for l in lays])
+        sp = []
+        for t in species:
+            t = tuple(t) + (0.0, 0.0, 1.0)[len(t) - 2:] if len(t) < 5 else tuple(t)
+            sp.append(CSpecies(*[float(x) for x in t]))
+        cs = (CSpecies * ns)(*sp)
+        fp = (C.c_void_p * ns)(*[f.h for f in f0s])
+        cfg = CConfig(dt, chi, tol, e_tol, streams, 1, e_chi, precision, compression)
+        h = C.c_void_p()
+        self._check(self.lib.vp_multi_create(self.h, ns, cl, cs, C.byref(cfg), fp, C.byref(h)))
+        return Multi(self, h, list(lays))
+
     def run(self, lay: Layout, f0: np.ndarray, dt: float, nsteps: int, chi: int, tol: float = 1e-10,
             e_tol: float = 1e-10, want_f: bool = True):
         f0 = np.ascontiguousarray(f0, dtype=np.float64)
@@ -540,6 +569,44 @@ class Sim:
     def close(self):
         if self.h and self.ctx.h:
             self.ctx.lib.vp_sim_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Multi:
+    """Several species advanced in lockstep on one field (vp_multi_*)."""
+
+    def __init__(self, ctx: Context, h, lays):
+        self.ctx, self.h, self.lays = ctx, h, lays
+        ctx._children.add(self)
+
+    def step(self, nsteps: int = 1):
+        """Per step: t, the shared field energy, and per species mass,
+        max bond and truncation error (lists)."""
+        ns = len(self.lays)
+        recs = (CRecord * max(1, nsteps * ns))()
+        self.ctx._check(self.ctx.lib.vp_multi_step(self.h, nsteps, recs))
+        out = []
+        for n in range(nsteps):
+            r = [recs[n * ns + s] for s in range(ns)]
+            out.append(dict(t=r[0].t, field_energy=r[0].field_energy, mass=[x.mass for x in r],
+                            max_bond=[x.max_bond for x in r], trunc_err=[x.trunc_err for x in r]))
+        return out
+
+    def state(self, s: int) -> MPS:
+        p = self.ctx.lib.vp_multi_state(self.h, s)
+        if not p:
+            raise IndexError(s)
+        return MPS(self.ctx, C.c_void_p(p), owned=False)
+
+    def close(self):
+        if self.h and self.ctx.h:
+            self.ctx.lib.vp_multi_destroy(self.h)
         self.h = None
 
     def __del__(self):
