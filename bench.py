@@ -39,8 +39,11 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline (profiling runs)")
-    p.add_argument("--mode", default="step", choices=["step", "batch", "serve", "precision"],
-                   help="step: the headline single-run steps/s; batch / serve: many runs on one GPU")
+    p.add_argument("--mode", default="step", choices=["step", "batch", "serve", "precision", "species"],
+                   help="step: the headline single-run steps/s; batch / serve: many runs on one GPU; "
+                        "species: electrons and ions on one field (Buneman, Dougherty collisions)")
+    p.add_argument("--species-workload", default="saturated_buneman_512x512_s3",
+                   help="named workload of paper_2205_11990_gb300.inputs.SPECIES_WORKLOADS (--mode species)")
     p.add_argument("--instances", type=int, default=32)
     p.add_argument("--concurrency", type=int, default=8)
     p.add_argument("--rate", type=float, default=20.0, help="serve: mean Poisson arrival rate (req/s)")
@@ -184,23 +187,7 @@ def run_ours(args, rank, world):
         ms = float(t.item())
     steps_per_s = world * args.steps / (ms / 1e3)
 
-    # dominant kernel class and its roofline
-    top = max(prof, key=lambda k: prof[k][0])
-    tms, tl, work = prof[top]
-    if top == "apply":
-        achieved = work / (tms / 1e3) / 1e9
-        roof = {"bound": "hbm", "achieved": achieved, "peak": 6783.1, "unit": "GB/s"}
-    else:
-        achieved = work / (tms / 1e3) / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS / 1e3, "unit": "TFLOP/s"}
-    roof["frac"] = roof["achieved"] / roof["peak"]
-    # DRAM bytes (read + write) per launch of the dominant kernel, from the ncu
-    # captures summarised under profiles/ (two launches each, this workload)
-    roof["traffic"] = NCU_TRAFFIC.get(top) if WORKLOAD == "saturated_two_stream_1024x1024_seq" else None
-    roof["kernel"] = {"qr_factor": "k_qr_factor_dw", "jacobi": "k_jacobi_dw", "gemm": "k_gemm",
-                      "qr_formq": "k_qr_formq_dw", "apply": "k_site_sum", "select": "k_select"}.get(top, top)
-    roof["launches"] = tl
-    roof["share_of_step"] = tms / ms * world if ms else None
+    roof = roofline(prof, ms, world, NCU_TRAFFIC if WORKLOAD == "saturated_two_stream_1024x1024_seq" else {})
 
     e2e = None
     if not args.no_e2e:
@@ -233,6 +220,116 @@ def run_ours(args, rank, world):
     }
     if rank == 0:
         out["cpu_baseline"] = None if args.no_cpu else cpu_baseline(lay, f0, budget_s=25.0)
+        print(json.dumps(out), flush=True)
+
+
+def roofline(prof, ms, world, traffic):
+    """Roofline entry of the dominant kernel class of the profiled window."""
+    top = max(prof, key=lambda k: prof[k][0])
+    tms, tl, work = prof[top]
+    if top == "apply":
+        achieved = work / (tms / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": 6783.1, "unit": "GB/s"}
+    else:
+        achieved = work / (tms / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS / 1e3, "unit": "TFLOP/s"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    # DRAM bytes (read + write) per launch of the dominant kernel, from the ncu
+    # captures summarised under profiles/ (two launches each, that workload)
+    roof["traffic"] = traffic.get(top)
+    roof["kernel"] = {"qr_factor": "k_qr_factor_dw", "jacobi": "k_jacobi_dw", "gemm": "k_gemm",
+                      "qr_formq": "k_qr_formq_dw", "apply": "k_site_sum", "select": "k_select"}.get(top, top)
+    roof["launches"] = tl
+    roof["share_of_step"] = tms / ms * world if ms else None
+    return roof
+
+
+def run_species(args, rank, world):
+    """Electrons and ions sharing one field: RK4-C1 steps of both species
+    (Buneman set-up with Dougherty collisions), timed like the headline."""
+    import torch
+
+    import __graft_entry__ as g
+    g.build()
+    from paper_2205_11990_gb300 import inputs as I
+    from paper_2205_11990_gb300 import vpmps
+
+    name = args.species_workload
+    lays, fs, species, chi, dt = I.species_workload(name)
+    ctx = vpmps.Context()
+    run = ctx.multi(lays, species, [ctx.mps_from_grid(l, f, chi, TOL) for l, f in zip(lays, fs)], dt, chi, TOL, TOL)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    for _ in range(args.warmup):
+        run.step(1)
+    torch.cuda.synchronize()
+    clocks = Clocks()
+    clocks.start()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = ctx.kernel_launches
+    ctx.profile(True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    recs = []
+    for i in range(args.steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        recs += run.step(1)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    launches = ctx.kernel_launches - launches0
+    clk = clocks.stop()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    e2e = None
+    if not args.no_e2e:
+        # public API end to end: host grids in (MPS creation), steps, host grids out
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r2 = ctx.multi(lays, species, [ctx.mps_from_grid(l, f, chi, TOL) for l, f in zip(lays, fs)], dt, chi,
+                       TOL, TOL)
+        r2.step(args.steps)
+        outs = [r2.state(s).to_grid(l) for s, l in enumerate(lays)]
+        t1 = time.perf_counter() - t0
+        r2.close()
+        nb = sum(f.size * 8 for f in fs)
+        e2e = {"value": world * args.steps / t1, "unit": "steps/s", "h2d_bytes_per_step": nb / args.steps,
+               "d2h_bytes_per_step": (sum(o.size * 8 for o in outs) + 40 * len(lays) * args.steps) / args.steps}
+    le = lays[0]
+    out = {
+        "metric": f"MPS VP two-species steps/s (RK4-C1, Buneman {le.Nx}x{le.Nv} electrons + {lays[1].Nx}x{lays[1].Nv} "
+                  f"ions, S3, chi={chi}, Dougherty collisions)",
+        "value": world * args.steps / (ms / 1e3), "unit": "steps/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": name, "species": species, "chi": chi, "tol": TOL, "dt": dt,
+                   "parallelism": f"replicas x{world}", "l2": "flushed between timed steps (256 MB write)"},
+        "roofline": roofline(prof, ms, world, {}),
+        "gpu_launches": launches, "clocks": clk, "e2e": e2e,
+        "diag": {"max_bond": [max(r["max_bond"][s] for r in recs) for s in range(len(lays))],
+                 "field_energy": recs[-1]["field_energy"], "kernel_ms": {k: round(v[0], 3) for k, v in prof.items()}},
+    }
+    if rank == 0:
+        if not args.no_cpu:
+            from oracle import vp as OV
+            cs = [OV.mps_from_f(f, l, chi, TOL) for f, l in zip(fs, lays)]
+            done, t = 0, 0.0
+            while t < 25.0:
+                t0 = time.perf_counter()
+                cs, _ = OV.multi_rk4_step(cs, lays, species, dt, chi, TOL, TOL)
+                t += time.perf_counter() - t0
+                done += 1
+            out["cpu_baseline"] = {"value": done / t, "unit": "steps/s", "cores": os.cpu_count(), "kind": "oracle",
+                                   "sample": f"{done} two-species RK4-C1 step(s) of the same workload "
+                                             f"(numpy/LAPACK, all host cores), {t:.1f} s"}
         print(json.dumps(out), flush=True)
 
 
@@ -435,6 +532,8 @@ def main():
     rank, world = dist_init(args.gpus)
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.mode == "species":
+        run_species(args, rank, world)
     else:
         run_ours(args, rank, world)
     if world > 1:

@@ -1507,7 +1507,9 @@ static int sim_create(vp_ctx* ctx, const vp_layout* L, const vp_config* cfg, con
       if (sp->nu > 0.0) {
         Chain cv = collision_chain(L->nv, L->vmin, grid_dv(L), sp->nu, sp->u, sp->vth);
         if (vdesc(L)) cv = reverse_chain(cv);
-        s->U = chain_sum(s->U, place2(identity_chain(L->nx), cv, s->dims));
+        // the summed chain carries redundant channels (bond 15 on the v
+        // sites for a numerical rank of 6): reduce it once, exactly
+        s->U = reduce_chain(chain_sum(s->U, place2(identity_chain(L->nx), cv, s->dims)), 1e-13);
       }
     }
     s->Dv = zero_gradient_chain(L->nv, grid_dv(L));

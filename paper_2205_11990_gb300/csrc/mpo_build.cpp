@@ -9,6 +9,7 @@
 // its carry (periodic) or requires it to vanish (non-periodic).
 #include "mpo_build.hpp"
 
+#include <algorithm>
 #include <cmath>
 #include <stdexcept>
 
@@ -125,6 +126,131 @@ Chain chain_product(const Chain& a, const Chain& b) {
                   if (y != 0.0) c.at(k, la * bl + lb, o, i, ra * br + rb) += x * y;
                 }
           }
+  }
+  return c;
+}
+
+// Thin SVD of a small row-major m x n matrix by one-sided (Hestenes)
+// Jacobi rotations on the columns of A (m >= n) or of A^T (m < n):
+// A = U diag(s) Vt, s descending, U m x k, Vt k x n, k = min(m, n).
+static void small_svd(int m, int n, const std::vector<double>& A, std::vector<double>& U, std::vector<double>& s,
+                      std::vector<double>& Vt) {
+  const bool tr = m < n;
+  const int R = tr ? n : m, C = tr ? m : n;  // work on W (R x C), R >= C
+  std::vector<double> W((size_t)R * C), V((size_t)C * C, 0.0);
+  for (int i = 0; i < R; ++i)
+    for (int j = 0; j < C; ++j) W[(size_t)i * C + j] = tr ? A[(size_t)j * n + i] : A[(size_t)i * n + j];
+  for (int j = 0; j < C; ++j) V[(size_t)j * C + j] = 1.0;
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    double off = 0.0;
+    for (int p = 0; p < C - 1; ++p)
+      for (int q = p + 1; q < C; ++q) {
+        double a = 0, b = 0, g = 0;
+        for (int i = 0; i < R; ++i) {
+          const double x = W[(size_t)i * C + p], y = W[(size_t)i * C + q];
+          a += x * x;
+          b += y * y;
+          g += x * y;
+        }
+        if (g == 0.0 || std::fabs(g) <= 1e-15 * std::sqrt(a * b)) continue;
+        off = std::max(off, std::fabs(g) / std::sqrt(a * b));
+        const double zeta = (b - a) / (2.0 * g);
+        const double t = (zeta >= 0 ? 1.0 : -1.0) / (std::fabs(zeta) + std::sqrt(1.0 + zeta * zeta));
+        const double c = 1.0 / std::sqrt(1.0 + t * t), sn = c * t;
+        for (int i = 0; i < R; ++i) {
+          const double x = W[(size_t)i * C + p], y = W[(size_t)i * C + q];
+          W[(size_t)i * C + p] = c * x - sn * y;
+          W[(size_t)i * C + q] = sn * x + c * y;
+        }
+        for (int i = 0; i < C; ++i) {
+          const double x = V[(size_t)i * C + p], y = V[(size_t)i * C + q];
+          V[(size_t)i * C + p] = c * x - sn * y;
+          V[(size_t)i * C + q] = sn * x + c * y;
+        }
+      }
+    if (off <= 1e-15) break;
+  }
+  std::vector<int> ord(C);
+  std::vector<double> nrm(C);
+  for (int j = 0; j < C; ++j) {
+    double a = 0;
+    for (int i = 0; i < R; ++i) a += W[(size_t)i * C + j] * W[(size_t)i * C + j];
+    nrm[j] = std::sqrt(a);
+    ord[j] = j;
+  }
+  std::sort(ord.begin(), ord.end(), [&](int x, int y) { return nrm[x] > nrm[y]; });
+  // W = Ul S with Ul = W / s column-wise; A = W V^T (or A^T = W V^T)
+  std::vector<double> Ul((size_t)R * C, 0.0);
+  s.assign(C, 0.0);
+  for (int jj = 0; jj < C; ++jj) {
+    const int j = ord[jj];
+    s[jj] = nrm[j];
+    if (nrm[j] > 0)
+      for (int i = 0; i < R; ++i) Ul[(size_t)i * C + jj] = W[(size_t)i * C + j] / nrm[j];
+  }
+  if (!tr) {  // A = Ul S V^T
+    U = Ul;
+    Vt.assign((size_t)C * n, 0.0);
+    for (int jj = 0; jj < C; ++jj)
+      for (int i = 0; i < n; ++i) Vt[(size_t)jj * n + i] = V[(size_t)i * C + ord[jj]];
+  } else {  // A^T = Ul S V^T  =>  A = V S Ul^T
+    U.assign((size_t)m * C, 0.0);
+    for (int i = 0; i < m; ++i)
+      for (int jj = 0; jj < C; ++jj) U[(size_t)i * C + jj] = V[(size_t)i * C + ord[jj]];
+    Vt.assign((size_t)C * n, 0.0);
+    for (int jj = 0; jj < C; ++jj)
+      for (int i = 0; i < n; ++i) Vt[(size_t)jj * n + i] = Ul[(size_t)i * C + jj];
+  }
+}
+
+Chain reduce_chain(const Chain& in, double rel) {
+  Chain c = in;
+  const int L = (int)c.core.size();
+  auto keep = [&](const std::vector<double>& s) {
+    int r = 0;
+    while (r < (int)s.size() && s[r] > rel * s[0]) ++r;
+    return std::max(r, 1);
+  };
+  std::vector<double> U, s, Vt;
+  // left to right: core k = U (S Vt), S Vt absorbed into core k+1
+  for (int k = 0; k + 1 < L; ++k) {
+    const int wl = c.w[k], wr = c.w[k + 1], m = wl * 4;
+    small_svd(m, wr, c.core[k], U, s, Vt);
+    const int kk = std::min(m, wr), r = keep(s);
+    std::vector<double> ck((size_t)m * r);
+    for (int i = 0; i < m; ++i)
+      for (int j = 0; j < r; ++j) ck[(size_t)i * r + j] = U[(size_t)i * kk + j];
+    const int wn = c.w[k + 2];
+    std::vector<double> nx((size_t)r * 4 * wn, 0.0);
+    for (int j = 0; j < r; ++j)
+      for (int t = 0; t < wr; ++t) {
+        const double f = s[j] * Vt[(size_t)j * wr + t];
+        if (f == 0.0) continue;
+        for (int e = 0; e < 4 * wn; ++e) nx[(size_t)j * 4 * wn + e] += f * c.core[k + 1][(size_t)t * 4 * wn + e];
+      }
+    c.core[k] = ck;
+    c.core[k + 1] = nx;
+    c.w[k + 1] = r;
+  }
+  // right to left: core k = (U S) Vt, U S absorbed into core k-1
+  for (int k = L - 1; k > 0; --k) {
+    const int wl = c.w[k], wr = c.w[k + 1], n = 4 * wr;
+    small_svd(wl, n, c.core[k], U, s, Vt);
+    const int kk = std::min(wl, n), r = keep(s);
+    std::vector<double> ck((size_t)r * n);
+    for (int j = 0; j < r; ++j)
+      for (int e = 0; e < n; ++e) ck[(size_t)j * n + e] = Vt[(size_t)j * n + e];
+    const int wp = c.w[k - 1];
+    std::vector<double> pv((size_t)wp * 4 * r, 0.0);
+    for (int a = 0; a < wp * 4; ++a)
+      for (int t = 0; t < wl; ++t) {
+        const double x = c.core[k - 1][(size_t)a * wl + t];
+        if (x == 0.0) continue;
+        for (int j = 0; j < r; ++j) pv[(size_t)a * r + j] += x * U[(size_t)t * kk + j] * s[j];
+      }
+    c.core[k] = ck;
+    c.core[k - 1] = pv;
+    c.w[k] = r;
   }
   return c;
 }

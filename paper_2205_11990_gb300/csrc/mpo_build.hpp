@@ -33,6 +33,10 @@ Chain chain_product(const Chain& a, const Chain& b);
 // Dougherty collision operator on the v bits (Methods, "Collision Operator"):
 // nu [D_c diag(v - u) + vth^2 D_vv], both derivatives zero-gradient.
 Chain collision_chain(int L, double vmin, double dv, double nu, double u, double vth);
+// The same operator with every bond reduced to its numerical rank: an SVD
+// sweep left to right, then right to left, dropping singular values at or
+// below rel times the largest of their bond (host, small cores only).
+Chain reduce_chain(const Chain& c, double rel);
 // diag(v * h(v_msb)) on L bits, v_j = vmin + j dv, h selects v > 0 (upper
 // half) when positive, else v < 0; as an affine chain of bond 2.  If
 // left_channels == 2 the first core takes a 2-channel left bond with

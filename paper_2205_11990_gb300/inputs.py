@@ -130,6 +130,33 @@ def saturated_two_stream(layout: Layout, modes=32, eps=0.05, k=0.2, v0=3.0, seed
     return h[None, :] * (1.0 + eps * pert)
 
 
+def saturated_buneman(lay_e: Layout, lay_i: Layout, modes=32, eps=0.05, k=0.1, mass_ratio=25.0, seed=0):
+    """Buneman background (drifting electrons, ions at rest) plus seeded
+    broadband perturbations of both species, built like
+    :func:`saturated_two_stream`: f_s = h_s(v) [1 + eps_s sum_m a_m cos(m k x +
+    phi_m) psi_m(v)], psi_m a Hermite-Gauss shape around the species' drift
+    (ions at a fifth of the electron amplitude).  On 512 x 512 grids with 32
+    modes both species' middle bonds reach 62-63 at tol = 1e-10: the cost
+    profile of the nonlinear phase of the instability at chi = 64."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    vth_i = 1.0 / math.sqrt(mass_ratio)
+    out = []
+    for lay, u, vth, amp in ((lay_e, 1.0 / k, 1.0, eps), (lay_i, 0.0, vth_i, 0.2 * eps)):
+        x, v = lay.x(), lay.v()
+        a = rng.uniform(0.3, 1.0, size=modes) / np.arange(1, modes + 1) ** 0.5
+        phi = rng.uniform(0, 2 * math.pi, size=modes)
+        order = rng.integers(0, 4, size=modes)
+        width = rng.uniform(0.6, 1.4, size=modes) * vth
+        pert = np.zeros((lay.Nx, lay.Nv))
+        for m in range(modes):
+            s = (v - u) / width[m]
+            psi = np.polynomial.hermite.hermval(s, [0] * order[m] + [1]) * np.exp(-s * s / 2)
+            psi = psi / np.max(np.abs(psi))
+            pert += a[m] * np.outer(np.cos((m + 1) * k * x + phi[m]), psi)
+        out.append(maxwellian(v, vth, u)[None, :] * (1.0 + amp * pert))
+    return out[0], out[1]
+
+
 def random_cores(ranks, seed=0, d=2):
     """Random MPS cores with the given bond list ``ranks`` (length n+1, ends 1)."""
     rng = np.random.Generator(np.random.PCG64(seed))
@@ -167,6 +194,28 @@ WORKLOADS = {
     "two_stream_4096x4096_seq": dict(layout=Layout(12, 12, 0.0, 10 * math.pi, -8.0, 8.0, SEQ),
                                      ic="two_stream", chi=128, dt=0.6 * (10 * math.pi / 4096) / 8.0),
 }
+
+
+# Several-species workloads (Methods, "Buneman instability": m_i/m_e = 25,
+# k = 0.10, electrons drifting at omega_pe/k, collision rate ~0.007 omega_ps
+# per species).  Species: (q, m, nu, u, vth); layouts from buneman_layouts.
+SPECIES_WORKLOADS = {
+    "saturated_buneman_512x512_s3": dict(bits=(9, 9, 9), mapping=SEQ_S3, ic="saturated_buneman", chi=64,
+                                         species=[(-1.0, 1.0, 0.007, 10.0, 1.0), (1.0, 25.0, 0.0014, 0.0, 0.2)]),
+    "saturated_buneman_64x64_s3": dict(bits=(6, 6, 6), mapping=SEQ_S3, ic="saturated_buneman", chi=24,
+                                       species=[(-1.0, 1.0, 0.007, 10.0, 1.0), (1.0, 25.0, 0.0014, 0.0, 0.2)]),
+}
+
+
+def species_workload(name: str):
+    """(layouts, initial grids, species, chi, dt) of a several-species
+    workload; dt = 0.6 dx / max|v| of the electrons."""
+    w = SPECIES_WORKLOADS[name]
+    nx, nve, nvi = w["bits"]
+    lay_e, lay_i = buneman_layouts(nx, nve, nvi, mapping=w["mapping"])
+    fe, fi = {"saturated_buneman": saturated_buneman, "buneman": buneman}[w["ic"]](lay_e, lay_i)
+    dt = 0.6 * ((lay_e.xmax - lay_e.xmin) / lay_e.Nx) / max(abs(lay_e.vmin), abs(lay_e.vmax))
+    return [lay_e, lay_i], [fe, fi], w["species"], w["chi"], dt
 
 
 def initial_condition(name: str, layout: Layout) -> np.ndarray:

@@ -61,3 +61,20 @@ def test_interleaved_mid_size_steps(ctx):
         ref, d = OV.rk4_step(ref, lay, dt, 32)
         assert abs(rec["field_energy"] - d["field_energy"]) <= 1e-9 * d["field_energy"]
     assert rel(sim.state().to_grid(lay), OV.mps_to_f(ref, lay)) < 1e-10
+
+
+def test_full_size_two_species_step(ctx):
+    # the two-species bench workload: Buneman electrons and ions, 512 x 512
+    # each (S3), chi = 64, Dougherty collisions; one step launched as the
+    # bench launches it (vp_multi, two streams)
+    lays, fs, species, chi, dt = I.species_workload("saturated_buneman_512x512_s3")
+    ms = [ctx.mps_from_grid(l, f, chi, 1e-10) for l, f in zip(lays, fs)]
+    refs = [OV.mps_from_f(f, l, chi, 1e-10) for l, f in zip(lays, fs)]
+    run = ctx.multi(lays, species, ms, dt, chi)
+    rec = run.step(1)[0]
+    refs, d = OV.multi_rk4_step(refs, lays, species, dt, chi)
+    assert abs(rec["field_energy"] - d["field_energy"]) <= 1e-9 * d["field_energy"]
+    for s, (l, r) in enumerate(zip(lays, refs)):
+        assert run.state(s).bonds() == d["bonds"][s]
+        assert rel(run.state(s).to_grid(l), OV.mps_to_f(r, l)) < 1e-10
+    run.close()
