@@ -26,6 +26,7 @@ SEQ = 0          # S1: x bits coarse->fine, then v bits coarse->fine
 INTERLEAVED = 1  # IF: x_1, v_1, x_2, v_2, ... (coarse first)
 SEQ_S2 = 2       # S2: x bits fine->coarse, then v bits coarse->fine
 SEQ_S3 = 3       # S3: x bits coarse->fine, then v bits fine->coarse
+GROUPED = 4      # IG: the IF site order with each (x_j, v_j) pair one d = 4 site (nx == nv)
 
 
 @dataclasses.dataclass(frozen=True)
