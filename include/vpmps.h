@@ -32,7 +32,14 @@
  *    v_0..v_{nv-1}; VP_SEQ_S2: x_{nx-1}..x_0 (fine to coarse), then
  *    v_0..v_{nv-1}; VP_SEQ_S3: x_0..x_{nx-1}, then v_{nv-1}..v_0;
  *    VP_INTERLEAVED (IF): x_0, v_0, x_1, v_1, ..., leftover bits of the longer
- *    dimension last.
+ *    dimension last.  VP_INTERLEAVED_GROUPED (IG, nx == nv): the grouped
+ *    interleaved ordering, each (x_j, v_j) pair one site of dimension 4.  It
+ *    is held in the IF site order with the bond inside every pair left
+ *    untruncated (kept to 1e-13, never capped at chi): the same state and the
+ *    same truncations at the pair bonds as d = 4 cores.  Bond lists and
+ *    entropies then have the pair bonds at the even positions of the IF
+ *    list (after sites 1, 3, 5, ...).  The IG rule applies to mps_create and
+ *    to every compression of a sim or multi-species run on an IG layout.
  *  - Grid: x_i = xmin + i dx, dx = (xmax - xmin)/2^nx (periodic, right end
  *    excluded); v_j = vmin + j dv, dv = (vmax - vmin)/(2^nv - 1) (both ends
  *    included, zero-gradient boundaries).  The v domain must be symmetric
@@ -62,7 +69,7 @@ enum {
   VP_EIO = 9         /* checkpoint file missing, unreadable or malformed */
 };
 
-enum { VP_SEQ = 0, VP_INTERLEAVED = 1, VP_SEQ_S2 = 2, VP_SEQ_S3 = 3 };
+enum { VP_SEQ = 0, VP_INTERLEAVED = 1, VP_SEQ_S2 = 2, VP_SEQ_S3 = 3, VP_INTERLEAVED_GROUPED = 4 };
 
 /* Opaque handles. */
 typedef struct vp_ctx vp_ctx;
@@ -77,7 +84,7 @@ typedef void (*vp_free_fn)(void* ptr, size_t bytes, void* user);
 
 typedef struct {
   int nx, nv;      /* bits per dimension, each in [2, 14] */
-  int mapping;     /* VP_SEQ, VP_INTERLEAVED, VP_SEQ_S2 or VP_SEQ_S3 */
+  int mapping;     /* VP_SEQ, VP_INTERLEAVED, VP_SEQ_S2, VP_SEQ_S3 or VP_INTERLEAVED_GROUPED */
   double xmin, xmax, vmin, vmax;
 } vp_layout;
 

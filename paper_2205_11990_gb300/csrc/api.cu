@@ -401,8 +401,19 @@ static int svd_site(vp_ctx* ctx, mps_t* s, int k, int chi, double tol, double* e
   return VP_OK;
 }
 
+// Tolerance of the bonds inside the (x_j, v_j) pairs of the IG ordering:
+// three orders below the step's 1e-10, so the pair cores are represented
+// exactly to FP64 working accuracy.
+constexpr double kPairTol = 1e-13;
+
 static int svd_sweep(vp_ctx* ctx, mps_t* s, int chi, double tol, double* errs) {
-  for (int k = s->n - 1; k >= 1; --k) VP_TRY(svd_site(ctx, s, k, chi, tol, errs ? errs + (k - 1) : nullptr));
+  for (int k = s->n - 1; k >= 1; --k) {
+    // site k splits the bond after site k-1; in the IG ordering the bonds
+    // after the even sites (2j: x_j | v_j) lie inside a pair
+    const bool inner = ctx->grouped && (k & 1);
+    VP_TRY(svd_site(ctx, s, k, inner ? 1 << 30 : chi, inner ? std::min(tol, kPairTol) : tol,
+                    errs ? errs + (k - 1) : nullptr));
+  }
   return VP_OK;
 }
 
@@ -565,10 +576,14 @@ static int to_dense_dev(vp_ctx* ctx, const mps_t* s, DevBuf& out) {
 // ------------------------------------------------------------ density
 static bool xdesc(const vp_layout* L) { return L->mapping == VP_SEQ_S2; }
 static bool vdesc(const vp_layout* L) { return L->mapping == VP_SEQ_S3; }
+static bool interleaved(const vp_layout* L) {
+  return L->mapping == VP_INTERLEAVED || L->mapping == VP_INTERLEAVED_GROUPED;
+}
+static bool grouped(const vp_layout* L) { return L->mapping == VP_INTERLEAVED_GROUPED; }
 
 static std::vector<int> site_dims(const vp_layout* L) {
   std::vector<int> d;
-  if (L->mapping != VP_INTERLEAVED) {
+  if (!interleaved(L)) {
     for (int b = 0; b < L->nx; ++b) d.push_back(0);
     for (int b = 0; b < L->nv; ++b) d.push_back(1);
   } else {
@@ -654,7 +669,8 @@ static int density(vp_ctx* ctx, const vp_layout* L, const mps_t* f, double* rho)
 
 static bool layout_ok(const vp_layout* L) {
   return L && L->nx >= 2 && L->nv >= 2 && L->nx <= 14 && L->nv <= 14 &&
-         L->mapping >= VP_SEQ && L->mapping <= VP_SEQ_S3 && L->xmax > L->xmin && L->vmax > L->vmin &&
+         L->mapping >= VP_SEQ && L->mapping <= VP_INTERLEAVED_GROUPED &&
+         (L->mapping != VP_INTERLEAVED_GROUPED || L->nx == L->nv) && L->xmax > L->xmin && L->vmax > L->vmin &&
          std::fabs(L->vmin + L->vmax) <= 1e-12 * std::fabs(L->vmax);
 }
 
@@ -839,7 +855,10 @@ int mps_create(vp_ctx* ctx, const vp_layout* L, const double* f, int f_on_device
                                f_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->stream));
   VP_TRY(launch_permute_to_sites(ctx, grid.p, L->nx, L->nv, L->mapping, sites.p, 0));
   mps_t* m = new mps_t();
+  const int g0 = ctx->grouped;
+  ctx->grouped = grouped(L) ? 1 : 0;
   int s = from_vector(ctx, m, n, sites.p, chi, tol);
+  ctx->grouped = g0;
   release(ctx, grid);
   release(ctx, sites);
   if (s == VP_OK) s = sync_status(ctx);
@@ -1238,7 +1257,11 @@ static int field_operator(vp_sim* s, const double* E) {
     VP_TRY(launch_permute_to_sites(ctx, E, s->lay.nx, 0, VP_SEQ_S2, s->evec.p, 0));
     Ev = s->evec.p;
   }
-  VP_TRY(from_vector(ctx, &s->em, s->lay.nx, Ev, s->cfg.e_chi > 0 ? s->cfg.e_chi : 1 << 30, s->cfg.e_tol));
+  const int g0 = ctx->grouped;  // the field MPS holds x bits only: no pairs
+  ctx->grouped = 0;
+  const int st = from_vector(ctx, &s->em, s->lay.nx, Ev, s->cfg.e_chi > 0 ? s->cfg.e_chi : 1 << 30, s->cfg.e_tol);
+  ctx->grouped = g0;
+  VP_TRY(st);
   return assemble_operator(s);
 }
 
@@ -1338,17 +1361,20 @@ static int sim_step_impl(vp_sim* s, vp_record* rec);
 // So does the compression scheme (the modified one cuts first at the x / v
 // bond, after the x sites).
 static int sim_step(vp_sim* s, vp_record* rec) {
-  const int p0 = s->ctx->precision, m0 = s->ctx->modified_split;
+  const int p0 = s->ctx->precision, m0 = s->ctx->modified_split, g0 = s->ctx->grouped;
   const int split = s->cfg.compression == VP_COMPRESS_MODIFIED ? s->lay.nx : 0;
   s->ctx->precision = s->cfg.precision;
   s->ctx->modified_split = split;
+  s->ctx->grouped = grouped(&s->lay) ? 1 : 0;
   if (s->ctxB) {
     s->ctxB->precision = s->cfg.precision;
     s->ctxB->modified_split = split;
+    s->ctxB->grouped = s->ctx->grouped;
   }
   const int st = s->cfg.level > 1 ? sim_step_levels(s, rec) : sim_step_impl(s, rec);
   s->ctx->precision = p0;
   s->ctx->modified_split = m0;
+  s->ctx->grouped = g0;
   return st;
 }
 
@@ -1522,7 +1548,7 @@ static int sim_create(vp_ctx* ctx, const vp_layout* L, const vp_config* cfg, con
   if (cfg->level < 0 || cfg->level > 5 || cfg->e_chi < 0 || cfg->precision < VP_PREC_FP64 || cfg->precision > VP_PREC_TF32X3)
     st = fail(ctx, VP_EINVAL, "vp_sim_create: bad level/e_chi/precision");
   if (st == VP_OK && (cfg->compression < VP_COMPRESS_SWEEPS || cfg->compression > VP_COMPRESS_MODIFIED ||
-                      (cfg->compression == VP_COMPRESS_MODIFIED && (L->mapping == VP_INTERLEAVED || L->nx < 1 || L->nv < 1))))
+                      (cfg->compression == VP_COMPRESS_MODIFIED && (interleaved(L) || L->nx < 1 || L->nv < 1))))
     st = fail(ctx, VP_EINVAL, "vp_sim_create: the modified compression needs a sequential ordering");
   if (st == VP_OK && cfg->streams != 1 && cfg->level <= 1) {
     s->ctxB = ctx_child(ctx);
@@ -1644,7 +1670,11 @@ static int multi_step_impl(vp_multi* M, vp_record* rec) {
       }
       VP_TRY(field_operator(sp, Ev));
       g_flops = &sp->flops;
+      const int g0 = ctx->grouped;
+      ctx->grouped = grouped(&sp->lay) ? 1 : 0;
+      if (sp->ctxB) sp->ctxB->grouped = ctx->grouped;
       const int st = c1_stage(sp, i, fi[s], acc[s], errs[s].data());
+      ctx->grouped = g0;
       g_flops = nullptr;
       VP_TRY(st);
     }

@@ -46,6 +46,7 @@ struct vp_ctx {
   int coop_cap = 0;      // max blocks of a cooperative grid launch (0: one per SM)
   int precision = 0;     // VP_PREC_* of the GEMM contractions (factorisations stay FP64)
   int modified_split = 0;  // > 0: compressions use the centre-bond-first scheme about this bond
+  int grouped = 0;         // 1: the bond inside every (x_j, v_j) site pair is not truncated (IG ordering)
   bool owns_stream = false;
   std::vector<vp_ctx*> children;  // contexts created for concurrent work
   cudaStream_t side = nullptr;     // side stream: Q formation beside the Jacobi SVD
