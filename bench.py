@@ -28,7 +28,7 @@ sys.path.insert(0, ROOT)
 WORKLOAD = "saturated_two_stream_1024x1024_seq"
 CHI, TOL, DT = 64, 1e-10, 0.002
 FP64_PEAK_GFLOPS = 2 * 2 * 152 * 2.070  # 2 DFMA/clk/SM x 2 flop x 152 SMs x 2070 MHz (nominal 1.25 TF/s)
-NCU_TRAFFIC = {"qr_factor": 208.0e3, "jacobi": 70.3e3}  # bytes per launch, profiles/k_*_dw_*.md
+NCU_TRAFFIC = {"jacobi": 70.3e3}  # DRAM bytes per launch from the ncu captures under profiles/
 
 
 def parse():
@@ -237,7 +237,7 @@ def roofline(prof, ms, world, traffic):
     # DRAM bytes (read + write) per launch of the dominant kernel, from the ncu
     # captures summarised under profiles/ (two launches each, that workload)
     roof["traffic"] = traffic.get(top)
-    roof["kernel"] = {"qr_factor": "k_qr_factor_dw", "jacobi": "k_jacobi_dw", "gemm": "k_gemm",
+    roof["kernel"] = {"qr_factor": "k_qr_factor_cl", "jacobi": "k_jacobi_dw", "gemm": "k_gemm",
                       "qr_formq": "k_qr_formq_dw", "apply": "k_site_sum", "select": "k_select"}.get(top, top)
     roof["launches"] = tl
     roof["share_of_step"] = tms / ms * world if ms else None

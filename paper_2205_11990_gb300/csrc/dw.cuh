@@ -115,6 +115,89 @@ __device__ __forceinline__ dw dw_warp_sum(dw v) {
   return fast_two_sum(s, c);
 }
 
+// x * 2^e for a DW value (exact unless the low part leaves the FP32 range).
+__device__ __forceinline__ dw dw_ldexp(dw x, int e) { return {ldexpf(x.hi, e), ldexpf(x.lo, e)}; }
+
+// Lane-strided loops over rows i = i0 + lane, i0 + lane + 32, ... < m, in
+// batches of four rows per lane: the four loads are issued before any
+// arithmetic and the four stores after it, so that the dependent chains of
+// four rows overlap (the compiler cannot reorder the loads of one row past
+// the store of another through shared-memory pointers).  The accumulation
+// order of each lane is unchanged (rows ascending), so results are identical
+// to the plain loop.
+__device__ __forceinline__ void dw_dot_rows(dw_acc& acc, const dw* __restrict__ a, const dw* __restrict__ b, int i0,
+                                            int m, int lane) {
+  int i = i0 + lane;
+  for (; i + 96 < m; i += 128) {
+    const dw a0 = a[i], a1 = a[i + 32], a2 = a[i + 64], a3 = a[i + 96];
+    const dw b0 = b[i], b1 = b[i + 32], b2 = b[i + 64], b3 = b[i + 96];
+    dw_dot_step(acc, a0, b0);
+    dw_dot_step(acc, a1, b1);
+    dw_dot_step(acc, a2, b2);
+    dw_dot_step(acc, a3, b3);
+  }
+  for (; i < m; i += 32) dw_dot_step(acc, a[i], b[i]);
+}
+
+// c[i] <- c[i] - w v[i] over the same rows.
+__device__ __forceinline__ void dw_axpy_rows(dw* c, const dw* v, dw w, int i0, int m, int lane) {
+  int i = i0 + lane;
+  for (; i + 96 < m; i += 128) {
+    const dw c0 = c[i], c1 = c[i + 32], c2 = c[i + 64], c3 = c[i + 96];
+    const dw v0 = v[i], v1 = v[i + 32], v2 = v[i + 64], v3 = v[i + 96];
+    const dw r0 = dw_add(c0, dw_neg(dw_mul(w, v0)));
+    const dw r1 = dw_add(c1, dw_neg(dw_mul(w, v1)));
+    const dw r2 = dw_add(c2, dw_neg(dw_mul(w, v2)));
+    const dw r3 = dw_add(c3, dw_neg(dw_mul(w, v3)));
+    c[i] = r0;
+    c[i + 32] = r1;
+    c[i + 64] = r2;
+    c[i + 96] = r3;
+  }
+  for (; i < m; i += 32) c[i] = dw_add(c[i], dw_neg(dw_mul(w, v[i])));
+}
+
+// Sum of squares of x[i] 2^-e over the rows (the same steps as a
+// dw_dot_step of each scaled value with itself).
+__device__ __forceinline__ void dw_sumsq_rows(dw_acc& acc, const dw* __restrict__ x, int e, int i0, int m, int lane) {
+  int i = i0 + lane;
+  for (; i + 96 < m; i += 128) {
+    const dw x0 = dw_ldexp(x[i], -e), x1 = dw_ldexp(x[i + 32], -e), x2 = dw_ldexp(x[i + 64], -e),
+             x3 = dw_ldexp(x[i + 96], -e);
+    dw_dot_step(acc, x0, x0);
+    dw_dot_step(acc, x1, x1);
+    dw_dot_step(acc, x2, x2);
+    dw_dot_step(acc, x3, x3);
+  }
+  for (; i < m; i += 32) {
+    const dw x0 = dw_ldexp(x[i], -e);
+    dw_dot_step(acc, x0, x0);
+  }
+}
+
+// x[i] <- (x[i] 2^-e) s over the rows.
+__device__ __forceinline__ void dw_scale_rows(dw* x, int e, dw s, int i0, int m, int lane) {
+  int i = i0 + lane;
+  for (; i + 96 < m; i += 128) {
+    const dw x0 = x[i], x1 = x[i + 32], x2 = x[i + 64], x3 = x[i + 96];
+    x[i] = dw_mul(dw_ldexp(x0, -e), s);
+    x[i + 32] = dw_mul(dw_ldexp(x1, -e), s);
+    x[i + 64] = dw_mul(dw_ldexp(x2, -e), s);
+    x[i + 96] = dw_mul(dw_ldexp(x3, -e), s);
+  }
+  for (; i < m; i += 32) x[i] = dw_mul(dw_ldexp(x[i], -e), s);
+}
+
+// max |x[i].hi| over the rows (one lane's part).
+__device__ __forceinline__ float dw_absmax_rows(const dw* x, int i0, int m, int lane) {
+  float mx = 0.f;
+  int i = i0 + lane;
+  for (; i + 96 < m; i += 128)
+    mx = fmaxf(fmaxf(fmaxf(mx, fabsf(x[i].hi)), fmaxf(fabsf(x[i + 32].hi), fabsf(x[i + 64].hi))), fabsf(x[i + 96].hi));
+  for (; i < m; i += 32) mx = fmaxf(mx, fabsf(x[i].hi));
+  return mx;
+}
+
 // 1 / sqrt(x) for x > 0 to DW accuracy: FP32 seed and one Newton step
 // y <- y + y (1 - x y^2) / 2 evaluated in DW (the correction is small, so
 // its own rounding is of order u^2).
@@ -144,7 +227,5 @@ __device__ __forceinline__ dw dw_div(dw a, dw b) {
   return fast_two_sum(q0, r.hi / b.hi);
 }
 
-// x * 2^e for a DW value (exact unless the low part leaves the FP32 range).
-__device__ __forceinline__ dw dw_ldexp(dw x, int e) { return {ldexpf(x.hi, e), ldexpf(x.lo, e)}; }
 
 }  // namespace vp

@@ -448,6 +448,157 @@ __global__ void __launch_bounds__(kThreads) k_qr_factor_cdw(double* A, int m, in
   }
 }
 
+// Cluster-resident double-word QR, pull model (factors up to a 16-CTA
+// cluster's shared memory).  Column k lives in CTA k % CS (slot k / CS) as
+// double words scaled by its own power of two, and each reflector stays where
+// it was formed: in its column, below the diagonal, with its tau in the
+// owner's tau slot.  Step j: one cluster barrier makes reflector j visible,
+// every CTA copies it (rows >= j, leading 1) from the owner's shared memory
+// into its own buffer through distributed shared memory, then in the owner
+// of column j+1 warp 0 applies H_j to that column and forms reflector j+1 in
+// place while every other warp applies H_j to the columns right of j+1.  A
+// reflector's column is never written after it is formed, so one barrier
+// per column orders everything.  The arithmetic per element is that of
+// k_qr_factor_dw (same double-word steps in the same order), so the output
+// is the same whichever kernel factors a matrix.
+template <int NT>
+__global__ void __launch_bounds__(NT) k_qr_factor_cl(double* A, int m, int n, double* tau) {
+  constexpr int NW = NT / 32;
+  cg::cluster_group cl = cg::this_cluster();
+  const int CS = (int)cl.num_blocks(), rank = (int)cl.block_rank();
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int p = min(m, n);
+  const int nmax = (n + CS - 1) / CS;
+  const int nown = rank < n ? (n - rank + CS - 1) / CS : 0;
+  extern __shared__ double qsm_raw[];
+  dw* cols = reinterpret_cast<dw*>(qsm_raw);  // nmax columns of m
+  dw* vin = cols + (size_t)nmax * m;          // reflector of the step (m)
+  dw* tsl = vin + m;                          // tau of each owned reflector (nmax)
+  dw* tin = tsl + nmax;                       // tau of the step
+  int* cexp = reinterpret_cast<int*>(tin + 1);
+
+  for (int lc = warp; lc < nown; lc += NW) {
+    const double* a = A + (size_t)(rank + lc * CS) * m;
+    float mx = 0.f;
+    for (int i = lane; i < m; i += 32) mx = fmaxf(mx, fabsf(__double2float_rn(a[i])));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    int e = 0;
+    if (mx > 0.f) frexpf(mx, &e);
+    if (lane == 0) cexp[lc] = e;
+    const double sc = ldexp(1.0, -e);
+    dw* c = cols + (size_t)lc * m;
+    for (int i = lane; i < m; i += 32) c[i] = dw_from(a[i] * sc);
+  }
+
+  auto apply = [&](int j, dw* c) {
+    const dw t = *tin;
+    if (t.hi == 0.f) return;
+    dw_acc acc;
+    dw_dot_rows(acc, vin, c, j, m, lane);
+    const dw w = dw_mul(dw_warp_sum(dw_acc_value(acc)), t);
+    if (w.hi == 0.f) return;
+    dw_axpy_rows(c, vin, w, j, m, lane);
+  };
+  // reflector j formed in place in local column c (slot lc), tau kept locally
+  auto reflect = [&](int j, dw* c, int lc) {
+    float mx = dw_absmax_rows(c, j, m, lane);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    int e = 0;
+    if (mx > 0.f) frexpf(mx, &e);
+    dw_acc acc;
+    dw_sumsq_rows(acc, c, e, j + 1, m, lane);
+    const dw s = dw_warp_sum(dw_acc_value(acc));
+    const dw x0 = dw_ldexp(c[j], -e);
+    dw t = {0.f, 0.f}, beta = x0, scale = {0.f, 0.f};
+    if (s.hi > 0.f) {
+      const dw nrm = dw_sqrt(dw_add(dw_mul(x0, x0), s));
+      beta = x0.hi >= 0.f ? dw_neg(nrm) : nrm;
+      t = dw_div(dw_add(beta, dw_neg(x0)), beta);
+      scale = dw_div({1.0f, 0.0f}, dw_add(x0, dw_neg(beta)));
+    }
+    dw_scale_rows(c, e, scale, j + 1, m, lane);
+    __syncwarp();
+    if (lane == 0) {
+      c[j] = dw_ldexp(beta, e);
+      tsl[lc] = t;
+      tau[j] = dw_to(t);
+    }
+  };
+
+  __syncthreads();
+  if (rank == 0 && warp == 0 && p > 0) reflect(0, cols, 0);
+  for (int j = 0; j < p; ++j) {
+    cl.sync();  // reflector j formed; every CTA done with the previous step
+    {
+      const int oj = j % CS, sj = j / CS;
+      const dw* src = cl.map_shared_rank(cols + (size_t)sj * m, oj);
+      for (int i = j + tid; i < m; i += NT) vin[i] = (i == j) ? dw{1.0f, 0.0f} : src[i];
+      if (tid == 0) *tin = *cl.map_shared_rank(tsl + sj, oj);
+    }
+    __syncthreads();
+    const bool owner = j + 1 < p && rank == (j + 1) % CS;
+    if (owner && warp == 0) {
+      const int lc = (j + 1) / CS;
+      dw* c = cols + (size_t)lc * m;
+      apply(j, c);
+      __syncwarp();
+      reflect(j + 1, c, lc);
+    } else {
+      const int wk = owner ? warp - 1 : warp, nwk = owner ? NW - 1 : NW;
+      const int lc0 = (j + 2 - rank + CS - 1) / CS > 0 ? (j + 2 - rank + CS - 1) / CS : 0;
+      for (int lc = lc0 + wk; lc < nown; lc += nwk) apply(j, cols + (size_t)lc * m);
+    }
+  }
+  cl.sync();  // no CTA leaves while another may still read its reflectors
+  for (int lc = warp; lc < nown; lc += NW) {
+    const int k = rank + lc * CS;
+    const double sc = ldexp(1.0, cexp[lc]);
+    const dw* c = cols + (size_t)lc * m;
+    double* a = A + (size_t)k * m;
+    for (int i = lane; i < m; i += 32) a[i] = (k < p && i > k) ? dw_to(c[i]) : dw_to(c[i]) * sc;
+  }
+}
+
+static size_t qr_cl_smem(int m, int n, int CS) {
+  const size_t nmax = (size_t)(n + CS - 1) / CS;
+  return (nmax * m + (size_t)m + nmax + 1) * sizeof(dw) + nmax * sizeof(int);
+}
+
+template <int NT>
+static int launch_cl(vp_ctx* ctx, double* A, int m, int n, double* tau, int cs, size_t need) {
+  static bool cattr = false;
+  if (!cattr) {
+    VP_CUDA(ctx, cudaFuncSetAttribute(k_qr_factor_cl<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    VP_CUDA(ctx, cudaFuncSetAttribute(k_qr_factor_cl<NT>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    cattr = true;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute at[1];
+  cfg.gridDim = dim3(cs);
+  cfg.blockDim = dim3(NT);
+  cfg.dynamicSmemBytes = std::max<size_t>(need, 116 * 1024);  // one CTA of the cluster per SM
+  cfg.stream = ctx->stream;
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = cs;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  ctx->launches++;
+  VP_CUDA(ctx, cudaLaunchKernelEx(&cfg, k_qr_factor_cl<NT>, A, m, n, tau));
+  return VP_OK;
+}
+
+int launch_qr_factor_cl(vp_ctx* ctx, double* A, int m, int n, double* tau, int cs, int threads) {
+  const size_t need = qr_cl_smem(m, n, cs);
+  if (need > 200 * 1024) return fail(ctx, VP_ECAPACITY, "qr_factor_cl: factor too large for the cluster");
+  if (threads >= 1024) return launch_cl<1024>(ctx, A, m, n, tau, cs, need);
+  if (threads >= 512) return launch_cl<512>(ctx, A, m, n, tau, cs, need);
+  return launch_cl<256>(ctx, A, m, n, tau, cs, need);
+}
+
 static size_t qr_cdw_smem(int m, int n, int CS) {
   const size_t nmax = (size_t)(n + CS - 1) / CS;
   return (nmax * m + 2 * (size_t)m + 2) * sizeof(dw) + nmax * sizeof(int);
@@ -487,6 +638,19 @@ int launch_qr_factor(vp_ctx* ctx, double* A, int m, int n, double* tau, double* 
       VP_CUDA(ctx, cudaLaunchKernelEx(&cfg, k_qr_factor_cdw, A, m, n, tau));
       return VP_OK;
     }
+  }
+  // Larger factors that fit a cluster: the pull-model kernel (measured per
+  // column on GB300: 128x128 3.1 us against 3.7, 368x128 4.9 against 7.2,
+  // 512x341 6.3 against 7.7, 1088x64 8.5 against 17.7).  4 CTAs for narrow
+  // factors (the reflector pulls dominate), 16 for wide ones (the column
+  // updates dominate), 8 otherwise.  The dispatch depends on the shape only,
+  // and every QR kernel computes the same double-word steps, so results do
+  // not depend on the context.
+  if (ctx->cluster_size >= 8) {
+    int cs = n <= 64 ? 4 : (n >= 200 ? 16 : 8);
+    while (cs < ctx->cluster_size && qr_cl_smem(m, n, cs) > 200 * 1024) cs *= 2;
+    if (cs <= ctx->cluster_size && qr_cl_smem(m, n, cs) <= 200 * 1024)
+      return launch_qr_factor_cl(ctx, A, m, n, tau, cs, cs == 8 && n >= 300 ? 512 : 256);
   }
   // enough blocks that each owns a few columns, but never more than one per SM
   const int cap = ctx->coop_cap > 0 ? std::min(ctx->coop_cap, ctx->num_sms) : ctx->num_sms;
