@@ -28,7 +28,7 @@ sys.path.insert(0, ROOT)
 WORKLOAD = "saturated_two_stream_1024x1024_seq"
 CHI, TOL, DT = 64, 1e-10, 0.002
 FP64_PEAK_GFLOPS = 2 * 2 * 152 * 2.070  # 2 DFMA/clk/SM x 2 flop x 152 SMs x 2070 MHz (nominal 1.25 TF/s)
-NCU_TRAFFIC = {"jacobi": 70.3e3}  # DRAM bytes per launch from the ncu captures under profiles/
+NCU_TRAFFIC = {"qr_factor": 637.6e3, "jacobi": 70.3e3}  # DRAM bytes per launch from the ncu captures under profiles/
 
 
 def parse():

@@ -454,16 +454,18 @@ __global__ void __launch_bounds__(kThreads) k_qr_factor_cdw(double* A, int m, in
 // it was formed: in its column, below the diagonal, with its tau in the
 // owner's tau slot.  Step j: one cluster barrier makes reflector j visible,
 // every CTA copies it (rows >= j, leading 1) from the owner's shared memory
-// into its own buffer through distributed shared memory, then in the owner
-// of column j+1 warp 0 applies H_j to that column and forms reflector j+1 in
-// place while every other warp applies H_j to the columns right of j+1.  A
-// reflector's column is never written after it is formed, so one barrier
-// per column orders everything.  The arithmetic per element is that of
-// k_qr_factor_dw (same double-word steps in the same order), so the output
-// is the same whichever kernel factors a matrix.
-template <int NT>
+// into its own buffer through distributed shared memory; then in the owner
+// of column j+1 the first CW warps apply H_j to that column and form
+// reflector j+1 in place (rows split over the CW warps, partial sums
+// combined in a fixed order behind a named barrier), while every other warp
+// applies H_j to the columns right of j+1.  A reflector's column is never
+// written after it is formed, so one cluster barrier per column orders
+// everything.  The per-row arithmetic is that of k_qr_factor_dw; only the
+// order in which the critical column's partial sums are added differs.
+template <int NT, int CW>
 __global__ void __launch_bounds__(NT) k_qr_factor_cl(double* A, int m, int n, double* tau) {
   constexpr int NW = NT / 32;
+  static_assert(CW >= 1 && CW < NW, "critical warps must leave bulk warps");
   cg::cluster_group cl = cg::this_cluster();
   const int CS = (int)cl.num_blocks(), rank = (int)cl.block_rank();
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -476,6 +478,8 @@ __global__ void __launch_bounds__(NT) k_qr_factor_cl(double* A, int m, int n, do
   dw* tsl = vin + m;                          // tau of each owned reflector (nmax)
   dw* tin = tsl + nmax;                       // tau of the step
   int* cexp = reinterpret_cast<int*>(tin + 1);
+  __shared__ dw red[3][CW];                   // partial sums of the critical warps
+  __shared__ float redm[CW];
 
   for (int lc = warp; lc < nown; lc += NW) {
     const double* a = A + (size_t)(rank + lc * CS) * m;
@@ -491,6 +495,7 @@ __global__ void __launch_bounds__(NT) k_qr_factor_cl(double* A, int m, int n, do
     for (int i = lane; i < m; i += 32) c[i] = dw_from(a[i] * sc);
   }
 
+  // H_j applied to a bulk column by one warp
   auto apply = [&](int j, dw* c) {
     const dw t = *tin;
     if (t.hi == 0.f) return;
@@ -500,27 +505,57 @@ __global__ void __launch_bounds__(NT) k_qr_factor_cl(double* A, int m, int n, do
     if (w.hi == 0.f) return;
     dw_axpy_rows(c, vin, w, j, m, lane);
   };
-  // reflector j formed in place in local column c (slot lc), tau kept locally
-  auto reflect = [&](int j, dw* c, int lc) {
-    float mx = dw_absmax_rows(c, j, m, lane);
+  auto cbar = [] { asm volatile("bar.sync 1, %0;" ::"r"(CW * 32) : "memory"); };
+  // Critical warps (warp < CW): H_{j-1} applied to column j (when j > 0),
+  // then reflector j formed in place; warp w handles rows i with
+  // (i - j) / 32 = w mod CW.
+  auto critical = [&](int j, dw* c, int lc) {
+    const int r0 = j + 32 * warp + lane, rs = 32 * CW;
+    if (j > 0) {  // H_{j-1} acts on rows >= j - 1 (its leading 1 sits in row j - 1)
+      const int a0 = r0 - 1;
+      const dw t = *tin;
+      dw_acc acc;
+      for (int i = a0; i < m; i += rs) dw_dot_step(acc, vin[i], c[i]);
+      const dw part = dw_warp_sum(dw_acc_value(acc));
+      if (lane == 0) red[0][warp] = part;
+      cbar();
+      dw dot = red[0][0];
+      for (int w = 1; w < CW; ++w) dot = dw_add(dot, red[0][w]);
+      const dw wv = dw_mul(dot, t);
+      if (t.hi != 0.f && wv.hi != 0.f)
+        for (int i = a0; i < m; i += rs) c[i] = dw_add(c[i], dw_neg(dw_mul(wv, vin[i])));
+    }
+    float mx = 0.f;
+    for (int i = r0; i < m; i += rs) mx = fmaxf(mx, fabsf(c[i].hi));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) redm[warp] = mx;
+    cbar();
+    for (int w = 0; w < CW; ++w) mx = fmaxf(mx, redm[w]);
     int e = 0;
     if (mx > 0.f) frexpf(mx, &e);
-    dw_acc acc;
-    dw_sumsq_rows(acc, c, e, j + 1, m, lane);
-    const dw s = dw_warp_sum(dw_acc_value(acc));
     const dw x0 = dw_ldexp(c[j], -e);
+    dw_acc acc;
+    for (int i = r0; i < m; i += rs)
+      if (i > j) {
+        const dw x = dw_ldexp(c[i], -e);
+        dw_dot_step(acc, x, x);
+      }
+    const dw part = dw_warp_sum(dw_acc_value(acc));
+    if (lane == 0) red[1][warp] = part;
+    cbar();  // every critical warp has read x0 and its partial sum is in
+    dw sq = red[1][0];
+    for (int w = 1; w < CW; ++w) sq = dw_add(sq, red[1][w]);
     dw t = {0.f, 0.f}, beta = x0, scale = {0.f, 0.f};
-    if (s.hi > 0.f) {
-      const dw nrm = dw_sqrt(dw_add(dw_mul(x0, x0), s));
+    if (sq.hi > 0.f) {
+      const dw nrm = dw_sqrt(dw_add(dw_mul(x0, x0), sq));
       beta = x0.hi >= 0.f ? dw_neg(nrm) : nrm;
       t = dw_div(dw_add(beta, dw_neg(x0)), beta);
       scale = dw_div({1.0f, 0.0f}, dw_add(x0, dw_neg(beta)));
     }
-    dw_scale_rows(c, e, scale, j + 1, m, lane);
-    __syncwarp();
-    if (lane == 0) {
+    for (int i = r0; i < m; i += rs)
+      if (i > j) c[i] = dw_mul(dw_ldexp(c[i], -e), scale);
+    if (warp == 0 && lane == 0) {
       c[j] = dw_ldexp(beta, e);
       tsl[lc] = t;
       tau[j] = dw_to(t);
@@ -528,25 +563,37 @@ __global__ void __launch_bounds__(NT) k_qr_factor_cl(double* A, int m, int n, do
   };
 
   __syncthreads();
-  if (rank == 0 && warp == 0 && p > 0) reflect(0, cols, 0);
+  if (rank == 0 && warp < CW && p > 0) critical(0, cols, 0);
   for (int j = 0; j < p; ++j) {
     cl.sync();  // reflector j formed; every CTA done with the previous step
     {
+      // every remote load of the batch issued before any local store
+      constexpr int PB = 8;
       const int oj = j % CS, sj = j / CS;
       const dw* src = cl.map_shared_rank(cols + (size_t)sj * m, oj);
-      for (int i = j + tid; i < m; i += NT) vin[i] = (i == j) ? dw{1.0f, 0.0f} : src[i];
-      if (tid == 0) *tin = *cl.map_shared_rank(tsl + sj, oj);
+      const dw tj = tid == 0 ? *cl.map_shared_rank(tsl + sj, oj) : dw{0.f, 0.f};
+      for (int i0 = j + tid; i0 < m; i0 += NT * PB) {
+        dw tmp[PB];
+#pragma unroll
+        for (int u = 0; u < PB; ++u) {
+          const int i = i0 + u * NT;
+          if (i < m) tmp[u] = src[i];
+        }
+#pragma unroll
+        for (int u = 0; u < PB; ++u) {
+          const int i = i0 + u * NT;
+          if (i < m) vin[i] = (i == j) ? dw{1.0f, 0.0f} : tmp[u];
+        }
+      }
+      if (tid == 0) *tin = tj;
     }
     __syncthreads();
     const bool owner = j + 1 < p && rank == (j + 1) % CS;
-    if (owner && warp == 0) {
+    if (owner && warp < CW) {
       const int lc = (j + 1) / CS;
-      dw* c = cols + (size_t)lc * m;
-      apply(j, c);
-      __syncwarp();
-      reflect(j + 1, c, lc);
+      critical(j + 1, cols + (size_t)lc * m, lc);
     } else {
-      const int wk = owner ? warp - 1 : warp, nwk = owner ? NW - 1 : NW;
+      const int wk = owner ? warp - CW : warp, nwk = owner ? NW - CW : NW;
       const int lc0 = (j + 2 - rank + CS - 1) / CS > 0 ? (j + 2 - rank + CS - 1) / CS : 0;
       for (int lc = lc0 + wk; lc < nown; lc += nwk) apply(j, cols + (size_t)lc * m);
     }
@@ -566,12 +613,12 @@ static size_t qr_cl_smem(int m, int n, int CS) {
   return (nmax * m + (size_t)m + nmax + 1) * sizeof(dw) + nmax * sizeof(int);
 }
 
-template <int NT>
+template <int NT, int CW>
 static int launch_cl(vp_ctx* ctx, double* A, int m, int n, double* tau, int cs, size_t need) {
   static bool cattr = false;
   if (!cattr) {
-    VP_CUDA(ctx, cudaFuncSetAttribute(k_qr_factor_cl<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    VP_CUDA(ctx, cudaFuncSetAttribute(k_qr_factor_cl<NT>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    VP_CUDA(ctx, cudaFuncSetAttribute(k_qr_factor_cl<NT, CW>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    VP_CUDA(ctx, cudaFuncSetAttribute(k_qr_factor_cl<NT, CW>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
     cattr = true;
   }
   cudaLaunchConfig_t cfg = {};
@@ -587,16 +634,14 @@ static int launch_cl(vp_ctx* ctx, double* A, int m, int n, double* tau, int cs, 
   cfg.attrs = at;
   cfg.numAttrs = 1;
   ctx->launches++;
-  VP_CUDA(ctx, cudaLaunchKernelEx(&cfg, k_qr_factor_cl<NT>, A, m, n, tau));
+  VP_CUDA(ctx, cudaLaunchKernelEx(&cfg, k_qr_factor_cl<NT, CW>, A, m, n, tau));
   return VP_OK;
 }
 
-int launch_qr_factor_cl(vp_ctx* ctx, double* A, int m, int n, double* tau, int cs, int threads) {
+int launch_qr_factor_cl(vp_ctx* ctx, double* A, int m, int n, double* tau, int cs) {
   const size_t need = qr_cl_smem(m, n, cs);
   if (need > 200 * 1024) return fail(ctx, VP_ECAPACITY, "qr_factor_cl: factor too large for the cluster");
-  if (threads >= 1024) return launch_cl<1024>(ctx, A, m, n, tau, cs, need);
-  if (threads >= 512) return launch_cl<512>(ctx, A, m, n, tau, cs, need);
-  return launch_cl<256>(ctx, A, m, n, tau, cs, need);
+  return launch_cl<512, 4>(ctx, A, m, n, tau, cs, need);
 }
 
 static size_t qr_cdw_smem(int m, int n, int CS) {
@@ -607,11 +652,16 @@ static size_t qr_cdw_smem(int m, int n, int CS) {
 int launch_qr_factor(vp_ctx* ctx, double* A, int m, int n, double* tau, double* vbuf) {
   const int p = std::min(m, n);
   if (p <= 0) return VP_OK;
-  // Measured per column on GB300 (headline workload): the cluster kernel is
-  // faster up to ~1e4 elements (2.5-4 us against 5-13 us), the grid kernel
-  // above (its reflector pushes to every CTA would cost more than the L2
-  // flags of the grid kernel).
-  if (ctx->cluster_size > 1 && (long long)m * n <= 10000) {
+  // Measured per column on GB300 (the step's shapes): up to ~4e3 elements
+  // the push-model cluster kernel (2.5 us); above, the pull-model kernel with
+  // four critical warps (128x128 2.9 us, 368x128 4.2, 464x184 4.8, 512x341
+  // 5.9, 682x132 6.1, 1088x64 7.3, against 3.7-17.7 for the grid kernel):
+  // 8 CTAs, 16 for many columns (the column updates dominate), 4 for tall
+  // narrow ones (the reflector copies dominate); factors more than twice as
+  // wide as tall stay on the grid kernel (64x1024: 3.5 us against 4.8).  The
+  // dispatch depends on the shape only, so results do not depend on the
+  // context.
+  if (ctx->cluster_size > 1 && (long long)m * n <= 4096) {
     int cs = 2;
     while (cs < std::min(ctx->cluster_size, 4) && cs * 8 < n) cs *= 2;
     const size_t need = qr_cdw_smem(m, n, cs);
@@ -639,18 +689,11 @@ int launch_qr_factor(vp_ctx* ctx, double* A, int m, int n, double* tau, double* 
       return VP_OK;
     }
   }
-  // Larger factors that fit a cluster: the pull-model kernel (measured per
-  // column on GB300: 128x128 3.1 us against 3.7, 368x128 4.9 against 7.2,
-  // 512x341 6.3 against 7.7, 1088x64 8.5 against 17.7).  4 CTAs for narrow
-  // factors (the reflector pulls dominate), 16 for wide ones (the column
-  // updates dominate), 8 otherwise.  The dispatch depends on the shape only,
-  // and every QR kernel computes the same double-word steps, so results do
-  // not depend on the context.
-  if (ctx->cluster_size >= 8) {
-    int cs = n <= 64 ? 4 : (n >= 200 ? 16 : 8);
+  if (ctx->cluster_size >= 8 && 2 * m >= n) {  // very wide factors: the grid kernel is as fast
+    int cs = n >= 300 ? 16 : (n <= 64 && m >= 512 ? 4 : 8);
     while (cs < ctx->cluster_size && qr_cl_smem(m, n, cs) > 200 * 1024) cs *= 2;
     if (cs <= ctx->cluster_size && qr_cl_smem(m, n, cs) <= 200 * 1024)
-      return launch_qr_factor_cl(ctx, A, m, n, tau, cs, cs == 8 && n >= 300 ? 512 : 256);
+      return launch_qr_factor_cl(ctx, A, m, n, tau, cs);
   }
   // enough blocks that each owns a few columns, but never more than one per SM
   const int cap = ctx->coop_cap > 0 ? std::min(ctx->coop_cap, ctx->num_sms) : ctx->num_sms;
