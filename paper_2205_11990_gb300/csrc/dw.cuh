@@ -198,6 +198,29 @@ __device__ __forceinline__ float dw_absmax_rows(const dw* x, int i0, int m, int 
   return mx;
 }
 
+// Plane rotation of two rows over q < m: (u, v) <- (c u - s v, s u + c v),
+// four columns per lane per batch (loads first, stores last).
+__device__ __forceinline__ void dw_rot_rows(dw* ri, dw* rj, dw cs, dw sn, int m, int lane) {
+  int q = lane;
+  for (; q + 96 < m; q += 128) {
+    const dw u0 = ri[q], u1 = ri[q + 32], u2 = ri[q + 64], u3 = ri[q + 96];
+    const dw v0 = rj[q], v1 = rj[q + 32], v2 = rj[q + 64], v3 = rj[q + 96];
+    ri[q] = dw_add(dw_mul(cs, u0), dw_neg(dw_mul(sn, v0)));
+    rj[q] = dw_add(dw_mul(sn, u0), dw_mul(cs, v0));
+    ri[q + 32] = dw_add(dw_mul(cs, u1), dw_neg(dw_mul(sn, v1)));
+    rj[q + 32] = dw_add(dw_mul(sn, u1), dw_mul(cs, v1));
+    ri[q + 64] = dw_add(dw_mul(cs, u2), dw_neg(dw_mul(sn, v2)));
+    rj[q + 64] = dw_add(dw_mul(sn, u2), dw_mul(cs, v2));
+    ri[q + 96] = dw_add(dw_mul(cs, u3), dw_neg(dw_mul(sn, v3)));
+    rj[q + 96] = dw_add(dw_mul(sn, u3), dw_mul(cs, v3));
+  }
+  for (; q < m; q += 32) {
+    const dw u = ri[q], v = rj[q];
+    ri[q] = dw_add(dw_mul(cs, u), dw_neg(dw_mul(sn, v)));
+    rj[q] = dw_add(dw_mul(sn, u), dw_mul(cs, v));
+  }
+}
+
 // 1 / sqrt(x) for x > 0 to DW accuracy: FP32 seed and one Newton step
 // y <- y + y (1 - x y^2) / 2 evaluated in DW (the correction is small, so
 // its own rounding is of order u^2).
