@@ -78,3 +78,29 @@ def test_full_size_two_species_step(ctx):
         assert run.state(s).bonds() == d["bonds"][s]
         assert rel(run.state(s).to_grid(l), OV.mps_to_f(r, l)) < 1e-10
     run.close()
+
+
+def test_full_size_4096_step_against_stored_oracle(ctx):
+    # 4096 x 4096 (12 + 12 sites), chi = 128: the oracle's step takes minutes,
+    # so its result is stored (tests/golden/make_fullsize_4096.py) and the
+    # GPU step, launched as the sims run it, is compared on 4096 seeded grid
+    # points, its field energy, mass and bonds
+    import json
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "fullsize_4096_step.json")
+    g = json.load(open(path))
+    w = I.WORKLOADS[g["workload"]]
+    lay = w["layout"]
+    f0 = I.initial_condition(w["ic"], lay)
+    m = ctx.mps_from_grid(lay, f0, g["chi"], g["tol"])
+    assert m.bonds() == g["start_bonds"]
+    sim = ctx.sim(lay, m, g["dt"], g["chi"])
+    rec = sim.step(1)[0]
+    assert abs(rec["field_energy"] - g["field_energy"]) <= 1e-9 * g["field_energy"]
+    assert abs(rec["mass"] - g["mass"]) <= 1e-10 * abs(g["mass"])
+    assert sim.state().bonds() == g["bonds"]
+    f1 = sim.state().to_grid(lay)
+    ref = np.array(g["f"])
+    got = f1[np.array(g["ix"]), np.array(g["iv"])]
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-10
+    sim.close()
