@@ -837,7 +837,7 @@ int vp_profile_trace(vp_ctx* c, vp_trace_rec* out, int cap, int* n_out) {
 int64_t vp_kernel_launches(const vp_ctx* c) {
   if (!c) return 0;
   int64_t n = c->launches;
-  for (const vp_ctx* ch : c->children) n += ch->launches;
+  for (const vp_ctx* ch : c->children) n += vp_kernel_launches(ch);
   return n;
 }
 
@@ -1194,6 +1194,7 @@ struct vp_sim {
   vp_ctx* ctxB = nullptr;  // second stream: the f_{i+1} compressions run beside the acc ones
   cudaEvent_t evA = nullptr, evB = nullptr;
   double ecoef = 1.0;      // -q/m of the species: the field term is diag(ecoef E) (x) D_v
+  int coop_div = 1;        // runs sharing the GPU at once: grid-cooperative QRs get num_sms / (2 coop_div)
 };
 
 namespace vp {
@@ -1398,7 +1399,7 @@ static int c1_stage(vp_sim* s, int i, const mps_t*& fi, const mps_t*& acc, doubl
     VP_TRY(site_sum_mps(ctx, 1.0, acc, B[i] * dt, &s->L, fi, &s->wa));
     VP_TRY(site_sum_mps(cb, 1.0, &s->f, A[i] * dt, &s->L, fi, &s->wb));
     const int cap0 = ctx->coop_cap;
-    ctx->coop_cap = cb->coop_cap = ctx->num_sms / 2;
+    ctx->coop_cap = cb->coop_cap = std::max(2, ctx->num_sms / (2 * s->coop_div));
     int stB = VP_OK;
     Flops fB;
     const bool prof = ctx->prof_on;
@@ -1624,6 +1625,9 @@ struct vp_multi {
   vp_ctx* ctx = nullptr;
   std::vector<vp_sim*> sp;
   std::vector<vp_species> par;
+  std::vector<vp_ctx*> sctx;       // context of each species' sim (children of ctx when ns > 1)
+  std::vector<cudaEvent_t> sev;    // per species: its stream has finished a stage
+  cudaEvent_t mev = nullptr;       // the main stream has the stage field
   vp_config cfg{};
   DevBuf net, E, Es;
   double t = 0.0;
@@ -1650,7 +1654,13 @@ static int multi_step_impl(vp_multi* M, vp_record* rec) {
     sr.rho[s] = M->sp[s]->rho.p;
     sr.w[s] = -M->par[s].q;
   }
+  const bool par = ns > 1 && M->sctx[0] != ctx;  // species on their own streams, one host thread each
   for (int i = 0; i < 4; ++i) {
+    if (par)  // the stage states were written on the species' streams
+      for (int s = 0; s < ns; ++s) {
+        VP_CUDA(ctx, cudaEventRecord(M->sev[s], M->sctx[s]->stream));
+        VP_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, M->sev[s], 0));
+      }
     for (int s = 0; s < ns; ++s) VP_TRY(density(ctx, &M->sp[s]->lay, fi[s], M->sp[s]->rho.p));
     VP_TRY(launch_species_net(ctx, sr, Nx, dx, M->net.p, ctx->d_smalld + 32));
     VP_TRY(launch_poisson(ctx, M->net.p, Nx, dx, M->E.p, ctx->d_smalld + 8));
@@ -1660,25 +1670,49 @@ static int multi_step_impl(vp_multi* M, vp_record* rec) {
       VP_CUDA(ctx, cudaMemcpyAsync(ctx->h_smalld + 32, ctx->d_smalld + 32, ns * sizeof(double),
                                    cudaMemcpyDeviceToHost, ctx->stream));
     }
-    for (int s = 0; s < ns; ++s) {
+    if (par) VP_CUDA(ctx, cudaEventRecord(M->mev, ctx->stream));
+    // one species' stage: its field operator (E scaled by -q/m) and C1 update
+    auto species_stage = [&](int s) -> int {
       vp_sim* sp = M->sp[s];
+      vp_ctx* cs = sp->ctx;
       const double* Ev = M->E.p;
-      if (sp->ecoef != 1.0) {
-        VP_TRY(launch_copy(ctx, M->E.p, M->Es.p, (size_t)Nx));
-        VP_TRY(launch_scale(ctx, M->Es.p, (size_t)Nx, sp->ecoef));
+      if (par) {
+        VP_CUDA(cs, cudaStreamWaitEvent(cs->stream, M->mev, 0));
+        VP_TRY(launch_copy(cs, M->E.p, sp->E.p, (size_t)Nx));
+        if (sp->ecoef != 1.0) VP_TRY(launch_scale(cs, sp->E.p, (size_t)Nx, sp->ecoef));
+        Ev = sp->E.p;
+      } else if (sp->ecoef != 1.0) {
+        VP_TRY(launch_copy(cs, M->E.p, M->Es.p, (size_t)Nx));
+        VP_TRY(launch_scale(cs, M->Es.p, (size_t)Nx, sp->ecoef));
         Ev = M->Es.p;
       }
       VP_TRY(field_operator(sp, Ev));
       g_flops = &sp->flops;
-      const int g0 = ctx->grouped;
-      ctx->grouped = grouped(&sp->lay) ? 1 : 0;
-      if (sp->ctxB) sp->ctxB->grouped = ctx->grouped;
+      const int g0 = cs->grouped;
+      cs->grouped = grouped(&sp->lay) ? 1 : 0;
+      if (sp->ctxB) sp->ctxB->grouped = cs->grouped;
       const int st = c1_stage(sp, i, fi[s], acc[s], errs[s].data());
-      ctx->grouped = g0;
+      cs->grouped = g0;
       g_flops = nullptr;
-      VP_TRY(st);
+      return st;
+    };
+    if (par) {
+      std::vector<int> st(ns, VP_OK);
+      std::vector<std::thread> th;
+      for (int s = 1; s < ns; ++s) th.emplace_back([&, s] { st[s] = species_stage(s); });
+      st[0] = species_stage(0);
+      for (auto& t : th) t.join();
+      for (int s = 0; s < ns; ++s)
+        if (st[s] != VP_OK) return fail(ctx, st[s], M->sctx[s]->err);
+    } else {
+      for (int s = 0; s < ns; ++s) VP_TRY(species_stage(s));
     }
   }
+  if (par)
+    for (int s = 0; s < ns; ++s) {
+      const int st = sync_status(M->sctx[s]);
+      if (st != VP_OK) return fail(ctx, st, M->sctx[s]->err);
+    }
   VP_TRY(sync_status(ctx));
   const double we = ctx->h_smalld[24];
   if (!std::isfinite(we)) return fail(ctx, VP_ENUMERIC, "non-finite field energy");
@@ -1704,10 +1738,11 @@ static int multi_step(vp_multi* M, vp_record* rec) {
   ctx->precision = M->cfg.precision;
   ctx->modified_split = split;
   for (vp_sim* sp : M->sp)
-    if (sp->ctxB) {
-      sp->ctxB->precision = M->cfg.precision;
-      sp->ctxB->modified_split = split;
-    }
+    for (vp_ctx* c : {sp->ctx, sp->ctxB})
+      if (c) {
+        c->precision = M->cfg.precision;
+        c->modified_split = split;
+      }
   const int st = multi_step_impl(M, rec);
   ctx->precision = p0;
   ctx->modified_split = m0;
@@ -1715,11 +1750,24 @@ static int multi_step(vp_multi* M, vp_record* rec) {
 }
 
 static void multi_free(vp_multi* M) {
+  cudaStreamSynchronize(M->ctx->stream);
   for (vp_sim* s : M->sp) {
     sim_free(s);
     delete s;
   }
   M->sp.clear();
+  auto& ch = M->ctx->children;
+  for (vp_ctx* c : M->sctx)
+    if (c && c != M->ctx) {
+      ch.erase(std::remove(ch.begin(), ch.end(), c), ch.end());
+      vp_ctx_destroy(c);
+    }
+  M->sctx.clear();
+  for (cudaEvent_t e : M->sev)
+    if (e) cudaEventDestroy(e);
+  M->sev.clear();
+  if (M->mev) cudaEventDestroy(M->mev);
+  M->mev = nullptr;
   release(M->ctx, M->net);
   release(M->ctx, M->E);
   release(M->ctx, M->Es);
@@ -1746,11 +1794,32 @@ int vp_multi_create(vp_ctx* ctx, int ns, const vp_layout* layouts, const vp_spec
   M->cfg = *cfg;
   M->par.assign(species, species + ns);
   int st = VP_OK;
+  // with several species, each runs on a child context (own stream) so that
+  // their stage updates proceed concurrently; f0 is read on those streams
+  VP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   for (int s = 0; s < ns && st == VP_OK; ++s) {
+    vp_ctx* cs = ns > 1 ? ctx_child(ctx) : ctx;
+    if (!cs) {
+      st = fail(ctx, VP_ENOMEM, "vp_multi_create: no context for a species");
+      break;
+    }
+    M->sctx.push_back(cs);
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+      st = fail(ctx, VP_ECUDA, "vp_multi_create: event creation failed");
+      break;
+    }
+    M->sev.push_back(e);
     vp_sim* sim = nullptr;
-    st = sim_create(ctx, &layouts[s], cfg, f0[s], &species[s], &sim);
-    if (st == VP_OK) M->sp.push_back(sim);
+    st = sim_create(cs, &layouts[s], cfg, f0[s], &species[s], &sim);
+    if (st != VP_OK && cs != ctx) st = fail(ctx, st, cs->err);
+    if (st == VP_OK) {
+      sim->coop_div = ns;
+      M->sp.push_back(sim);
+    }
   }
+  if (st == VP_OK && cudaEventCreateWithFlags(&M->mev, cudaEventDisableTiming) != cudaSuccess)
+    st = fail(ctx, VP_ECUDA, "vp_multi_create: event creation failed");
   const size_t Nx = (size_t)1 << layouts[0].nx;
   if (st == VP_OK) st = reserve(ctx, M->net, Nx);
   if (st == VP_OK) st = reserve(ctx, M->E, Nx);
