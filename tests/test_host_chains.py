@@ -24,9 +24,9 @@ def driver(tmp_path_factory):
     return exe
 
 
-def dense(driver, kind, L, vmin, dv, nu=0.0, u=0.0, vth=1.0):
-    out = subprocess.run([driver, kind, str(L), repr(vmin), repr(dv), repr(nu), repr(u), repr(vth)],
-                         check=True, capture_output=True, text=True).stdout.splitlines()
+def dense(driver, kind, L, vmin, dv, nu=0.0, u=0.0, vth=1.0, extra=()):
+    out = subprocess.run([driver, kind, str(L), repr(vmin), repr(dv), repr(nu), repr(u), repr(vth)]
+                         + [str(x) for x in extra], check=True, capture_output=True, text=True).stdout.splitlines()
     bonds = [int(x) for x in out[0].split()[1:]]
     return bonds, np.array([[float(x) for x in line.split()] for line in out[1:]])
 
@@ -57,3 +57,22 @@ def test_collision_chain_and_its_reduction(driver, L):
     np.testing.assert_allclose(R, ref, atol=1e-13 * scale)
     # the reduction keeps the numerical rank (at most 6 here) and never grows a bond
     assert all(r <= s for r, s in zip(b1, b0)) and max(b1) <= 6
+
+
+@pytest.mark.parametrize("mapping", [0, 1, 2, 3])
+def test_collisional_static_operator_equals_oracle(driver, mapping):
+    # the static part of a collisional species' operator as the sim builds it
+    # (upwind + placed Dougherty chain, reduced to its numerical rank) against
+    # the oracle's printed-MPO upwind operator plus its collision MPO
+    import math
+
+    from oracle import mpo as M
+    from oracle import vp as V
+    from paper_2205_11990_gb300 import inputs as I
+    lay = I.Layout(3, 4, 0.0, 2 * math.pi, -7.0, 7.0, mapping)
+    dx, dv = V.grid_steps(lay)
+    nu, u, vth = 0.3, 1.5, 0.8
+    bonds, got = dense(driver, "static", lay.nv, lay.vmin, dv, nu, u, vth, (lay.nx, repr(dx), mapping))
+    up, _ = V._static_parts(lay)
+    ref = M.to_dense(M.mpo_sum(up, V.collision_mpo(lay, nu, u, vth)))
+    np.testing.assert_allclose(got, ref, atol=1e-12 * np.abs(ref).max())
