@@ -72,6 +72,29 @@ def dist_init(n):
     return rank, world
 
 
+def barrier(world):
+    """Barrier across the replicas (no-op for one process)."""
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(ms, world, device="cuda"):
+    """The slowest replica's timed duration (ms): the job's duration."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world, steps, ms):
+    """Whole-job throughput: the steps of every replica over the job's duration."""
+    return world * steps / (ms / 1e3)
+
+
 def metric_name(lay):
     from paper_2205_11990_gb300 import inputs as I
     mp = "seq" if lay.mapping == 0 else "interleaved"
@@ -153,14 +176,9 @@ def run_ours(args, rank, world):
         sim.step(1)
     torch.cuda.synchronize()
 
-    def barrier():
-        if world > 1:
-            import torch.distributed as dist
-            dist.barrier()
-
     clocks = Clocks()
     clocks.start()
-    barrier()
+    barrier(world)
     torch.cuda.synchronize()
     launches0 = ctx.kernel_launches
     ctx.profile(True)
@@ -173,19 +191,14 @@ def run_ours(args, rank, world):
         recs += sim.step(1)
         ev[i][1].record(stream)
     torch.cuda.synchronize()
-    barrier()
+    barrier(world)
     t_wall = time.perf_counter() - t_wall
     prof = ctx.profile_read()
     ctx.profile(False)
     launches = ctx.kernel_launches - launches0
     clk = clocks.stop()
-    ms = sum(a.elapsed_time(b) for a, b in ev)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    steps_per_s = world * args.steps / (ms / 1e3)
+    ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev), world)
+    steps_per_s = job_rate(world, args.steps, ms)
 
     roof = roofline(prof, ms, world, NCU_TRAFFIC if WORKLOAD == "saturated_two_stream_1024x1024_seq" else {})
 
@@ -265,9 +278,7 @@ def run_species(args, rank, world):
     torch.cuda.synchronize()
     clocks = Clocks()
     clocks.start()
-    if world > 1:
-        import torch.distributed as dist
-        dist.barrier()
+    barrier(world)
     torch.cuda.synchronize()
     launches0 = ctx.kernel_launches
     ctx.profile(True)
@@ -283,12 +294,9 @@ def run_species(args, rank, world):
     ctx.profile(False)
     launches = ctx.kernel_launches - launches0
     clk = clocks.stop()
-    ms = sum(a.elapsed_time(b) for a, b in ev)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    torch.cuda.synchronize()
+    barrier(world)
+    ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev), world)
     e2e = None
     if not args.no_e2e:
         # public API end to end: host grids in (MPS creation), steps, host grids out
@@ -307,7 +315,7 @@ def run_species(args, rank, world):
     out = {
         "metric": f"MPS VP two-species steps/s (RK4-C1, Buneman {le.Nx}x{le.Nv} electrons + {lays[1].Nx}x{lays[1].Nv} "
                   f"ions, S3, chi={chi}, Dougherty collisions)",
-        "value": world * args.steps / (ms / 1e3), "unit": "steps/s", "n_gpus": world, "steps": args.steps,
+        "value": job_rate(world, args.steps, ms), "unit": "steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": name, "species": species, "chi": chi, "tol": TOL, "dt": dt,
