@@ -1551,11 +1551,16 @@ __global__ void __launch_bounds__(kThreads) k_jacobi_dw(double* X, int b, int c,
       }
     }
     __syncthreads();
-    for (int pi = warp; pi < nb; pi += kWarps) {
-      if (par[3 * pi].hi == 0.f) continue;
+    // the columns of a pair split over wpp warps when there are fewer pairs
+    // than warps (each column is rotated by the same steps either way)
+    const int wpp = nb >= kWarps ? 1 : (nb * 2 >= kWarps ? 2 : 4);
+    const int span = (w + wpp - 1) / wpp;
+    for (int pw = warp; pw < nb * wpp; pw += kWarps) {
+      const int pi = pw / wpp, q0 = (pw % wpp) * span;
+      if (par[3 * pi].hi == 0.f || q0 >= w) continue;
       dw *ri, *rj;
       pair_rows(pi, ri, rj);
-      dw_rot_rows(ri, rj, par[3 * pi + 1], par[3 * pi + 2], w, lane);
+      dw_rot_rows(ri + q0, rj + q0, par[3 * pi + 1], par[3 * pi + 2], min(span, w - q0), lane);
     }
     __syncthreads();
   };
