@@ -29,6 +29,7 @@ WORKLOAD = "saturated_two_stream_1024x1024_seq"
 CHI, TOL, DT = 64, 1e-10, 0.002
 FP64_PEAK_GFLOPS = 2 * 2 * 152 * 2.070  # 2 DFMA/clk/SM x 2 flop x 152 SMs x 2070 MHz (nominal 1.25 TF/s)
 NCU_TRAFFIC = {"qr_factor": 637.6e3, "jacobi": 70.3e3}  # DRAM bytes per launch from the ncu captures under profiles/
+NCU_TRAFFIC_SPECIES = {"qr_factor": 466.0e3}  # two-species workload, same source
 
 
 def parse():
@@ -320,7 +321,7 @@ def run_species(args, rank, world):
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": name, "species": species, "chi": chi, "tol": TOL, "dt": dt,
                    "parallelism": f"replicas x{world}", "l2": "flushed between timed steps (256 MB write)"},
-        "roofline": roofline(prof, ms, world, {}),
+        "roofline": roofline(prof, ms, world, NCU_TRAFFIC_SPECIES if name == "saturated_buneman_512x512_s3" else {}),
         "gpu_launches": launches, "clocks": clk, "e2e": e2e,
         "diag": {"max_bond": [max(r["max_bond"][s] for r in recs) for s in range(len(lays))],
                  "field_energy": recs[-1]["field_energy"], "kernel_ms": {k: round(v[0], 3) for k, v in prof.items()}},
