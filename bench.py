@@ -120,7 +120,10 @@ class Clocks:
 
     def __init__(self):
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        # raw samples: $VP_CLOCKS_DIR when set (kept with the run's other output), else the temp dir
+        import tempfile
+        d = os.environ.get("VP_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(d, f"clocks_{os.getpid()}.csv")
 
     def start(self):
         try:

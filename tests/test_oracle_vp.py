@@ -62,7 +62,7 @@ def test_vlasov_operator_equals_dense_rhs(lay):
 
 @pytest.mark.parametrize("lay", LAYOUTS[:2])
 def test_untruncated_mps_step_matches_dense_grid(lay):
-    # spec pin: chi = 2^(n/2), tol = 0  ->  same as the dense FD solver
+    # untruncated MPS (chi = 2^(n/2), tol = 0): the same step as the dense FD solver
     f = I.landau(lay, 0.3, 0.5)
     cores = V.mps_from_f(f, lay, 1 << 10, 0.0)
     fd = f.copy()
