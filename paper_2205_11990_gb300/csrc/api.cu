@@ -217,39 +217,15 @@ static double qr_flops(double m, double n) {
 
 // ------------------------------------------------------------ compression
 // QR step at site k: core_k (2 r_k x r_{k+1}) = Q R; core_k <- Q, core_{k+1} <- R core_{k+1}.
-static int qr_site(vp_ctx* ctx, mps_t* s, int k) {
-  const int m = 2 * s->r[k], n = s->r[k + 1], p = std::min(m, n);
-  const int nn = 2 * s->r[k + 2];
-  VP_TRY(reserve(ctx, ctx->w_fac, (size_t)m * n));
-  VP_TRY(reserve(ctx, ctx->w_p, (size_t)2 * m + p + 8));
-  double* tau = ctx->w_p.p;
-  double* vbuf = ctx->w_p.p + p + 8;
-  VP_TRY(launch_to_colmajor(ctx, s->core[k].p, m, n, ctx->w_fac.p));
-  prof_begin(ctx, VP_K_QR);
-  VP_TRY(launch_qr_factor(ctx, ctx->w_fac.p, m, n, tau, vbuf));
-  prof_end(ctx, VP_K_QR, qr_flops(m, n), m, n);
-  prof_begin(ctx, VP_K_FORMQ);
-  VP_TRY(launch_qr_formq(ctx, ctx->w_fac.p, m, n, tau, s->core[k].p));
-  prof_end(ctx, VP_K_FORMQ, 4.0 * m * p * p - 4.0 / 3.0 * p * p * p, m, p);
-  VP_TRY(reserve(ctx, ctx->w_gemm, (size_t)p * nn));
-  prof_begin(ctx, VP_K_GEMM);
-  VP_TRY(launch_gemm_r(ctx, p, nn, n, ctx->w_fac.p, m, s->core[k + 1].p, nn, ctx->w_gemm.p, nn));
-  prof_end(ctx, VP_K_GEMM, 2.0 * p * n * nn, p, nn, n);
-  std::swap(s->core[k + 1], ctx->w_gemm);
-  s->r[k + 1] = p;
-  if (g_flops) {
-    g_flops->qr += qr_flops(m, n);
-    g_flops->formq += 4.0 * m * p * p - 4.0 / 3.0 * p * p * p;
-    g_flops->gemm += 2.0 * p * n * nn;
-  }
-  return VP_OK;
-}
-
 static int ensure_side(vp_ctx* ctx) {
   if (ctx->side) return VP_OK;
   VP_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking));
   VP_CUDA(ctx, cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
   VP_CUDA(ctx, cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming));
+  for (int b = 0; b < 2; ++b) {
+    VP_CUDA(ctx, cudaEventCreateWithFlags(&ctx->ev_qf[b], cudaEventDisableTiming));
+    VP_CUDA(ctx, cudaEventCreateWithFlags(&ctx->ev_qd[b], cudaEventDisableTiming));
+  }
   return VP_OK;
 }
 
@@ -267,6 +243,60 @@ struct SideScope {
     std::swap(c->w_fq, c->w_fq_side);
   }
 };
+
+// QR sweep over sites 0..kend-1 (left-canonical form up to site kend): at
+// site k the Householder QR of the (2 r_{k-1} x r_k) reshape, R multiplied
+// into core k+1 on the context's stream, while Q (the new core k) is formed
+// on the side stream; the factor of site k lives in one of two buffers, so
+// the Q of site k is formed while site k+1 is factored.  Returns with every Q
+// formed (the context's stream waits for the side stream).
+static int qr_sweep(vp_ctx* ctx, mps_t* s, int kend) {
+  VP_TRY(ensure_side(ctx));
+  bool busy[2] = {false, false};
+  for (int k = 0; k < kend; ++k) {
+    const int b = k & 1;
+    DevBuf& F = b ? ctx->w_fac_b : ctx->w_fac;
+    DevBuf& P = b ? ctx->w_p_b : ctx->w_p;
+    if (busy[b]) {  // the Q formation two sites back still reads this buffer
+      VP_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, ctx->ev_qd[b], 0));
+      busy[b] = false;
+    }
+    const int m = 2 * s->r[k], n = s->r[k + 1], p = std::min(m, n);
+    const int nn = 2 * s->r[k + 2];
+    VP_TRY(reserve(ctx, F, (size_t)m * n));
+    VP_TRY(reserve(ctx, P, (size_t)2 * m + p + 8));
+    double* tau = P.p;
+    double* vbuf = P.p + p + 8;
+    VP_TRY(launch_to_colmajor(ctx, s->core[k].p, m, n, F.p));
+    prof_begin(ctx, VP_K_QR);
+    VP_TRY(launch_qr_factor(ctx, F.p, m, n, tau, vbuf));
+    prof_end(ctx, VP_K_QR, qr_flops(m, n), m, n);
+    VP_CUDA(ctx, cudaEventRecord(ctx->ev_qf[b], ctx->stream));
+    {
+      SideScope side(ctx);
+      VP_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, ctx->ev_qf[b], 0));
+      prof_begin(ctx, VP_K_FORMQ);
+      VP_TRY(launch_qr_formq(ctx, F.p, m, n, tau, s->core[k].p));
+      prof_end(ctx, VP_K_FORMQ, 4.0 * m * p * p - 4.0 / 3.0 * p * p * p, m, p);
+      VP_CUDA(ctx, cudaEventRecord(ctx->ev_qd[b], ctx->stream));
+    }
+    busy[b] = true;
+    VP_TRY(reserve(ctx, ctx->w_gemm, (size_t)p * nn));
+    prof_begin(ctx, VP_K_GEMM);
+    VP_TRY(launch_gemm_r(ctx, p, nn, n, F.p, m, s->core[k + 1].p, nn, ctx->w_gemm.p, nn));
+    prof_end(ctx, VP_K_GEMM, 2.0 * p * n * nn, p, nn, n);
+    std::swap(s->core[k + 1], ctx->w_gemm);
+    s->r[k + 1] = p;
+    if (g_flops) {
+      g_flops->qr += qr_flops(m, n);
+      g_flops->formq += 4.0 * m * p * p - 4.0 / 3.0 * p * p * p;
+      g_flops->gemm += 2.0 * p * n * nn;
+    }
+  }
+  for (int b = 0; b < 2; ++b)
+    if (busy[b]) VP_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, ctx->ev_qd[b], 0));
+  return VP_OK;
+}
 
 // SVD step at site k >= 1 of a left-canonical MPS whose right part is
 // already right-canonical: M = core_k (r_k x 2 r_{k+1}); keep r singular
@@ -466,7 +496,7 @@ static int compress_modified(vp_ctx* ctx, mps_t* s, int split, int chi, double t
   const int n = s->n;
   if (split < 1 || split >= n) return fail(ctx, VP_EINVAL, "modified compression: bad split");
   for (int k = n - 1; k > split; --k) VP_TRY(lq_site(ctx, s, k));
-  for (int k = 0; k < split; ++k) VP_TRY(qr_site(ctx, s, k));
+  VP_TRY(qr_sweep(ctx, s, split));
   VP_TRY(reserve(ctx, ctx->w_sig, (size_t)s->r[split] + 8));
   VP_TRY(svd_site(ctx, s, split, chi, tol, errs ? errs + split - 1 : nullptr, ctx->w_sig.p));
   const int rc = s->r[split];
@@ -517,7 +547,7 @@ static int compress_modified(vp_ctx* ctx, mps_t* s, int split, int chi, double t
 int compress(vp_ctx* ctx, mps_t* s, int chi, double tol, double* errs) {
   if (ctx->modified_split > 0 && ctx->modified_split < s->n)
     return compress_modified(ctx, s, ctx->modified_split, chi, tol, errs);
-  for (int k = 0; k + 1 < s->n; ++k) VP_TRY(qr_site(ctx, s, k));
+  VP_TRY(qr_sweep(ctx, s, s->n - 1));
   return svd_sweep(ctx, s, chi, tol, errs);
 }
 
@@ -749,7 +779,7 @@ int vp_ctx_destroy(vp_ctx* c) {
   for (DevBuf* b : {&c->w_fac, &c->w_q, &c->w_gemm, &c->w_j, &c->w_p, &c->w_tmp, &c->w_tmp2, &c->w_vec, &c->w_split,
                     &c->w_piv, &c->w_q1, &c->w_q2, &c->w_r, &c->w_p2, &c->w_a, &c->w_b, &c->w_c, &c->w_l,
                     &c->w_q_side, &c->w_split_side, &c->w_tca, &c->w_tcb, &c->w_tca_side, &c->w_tcb_side,
-                    &c->w_qrv, &c->w_qrc, &c->w_fq, &c->w_fq_side})
+                    &c->w_qrv, &c->w_qrc, &c->w_fq, &c->w_fq_side, &c->w_fac_b, &c->w_p_b})
     release(c, *b);
   for (auto& b : c->w_chain) release(c, b);
   dev_free(c, c->status, sizeof(DevStatus));
@@ -765,6 +795,8 @@ int vp_ctx_destroy(vp_ctx* c) {
   if (c->side) cudaStreamDestroy(c->side);
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   if (c->ev_join) cudaEventDestroy(c->ev_join);
+  for (cudaEvent_t e : {c->ev_qf[0], c->ev_qf[1], c->ev_qd[0], c->ev_qd[1]})
+    if (e) cudaEventDestroy(e);
   if (c->owns_stream) cudaStreamDestroy(c->stream);
   delete c;
   return VP_OK;

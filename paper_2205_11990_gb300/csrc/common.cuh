@@ -51,6 +51,11 @@ struct vp_ctx {
   std::vector<vp_ctx*> children;  // contexts created for concurrent work
   cudaStream_t side = nullptr;     // side stream: Q formation beside the Jacobi SVD
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  // QR sweep: site k factors into w_fac / w_p (k even) or w_fac_b / w_p_b (k
+  // odd) and forms its Q on the side stream; ev_qf[b] = buffer b factored,
+  // ev_qd[b] = its Q formed (buffer free again)
+  vp::DevBuf w_fac_b, w_p_b;
+  cudaEvent_t ev_qf[2] = {nullptr, nullptr}, ev_qd[2] = {nullptr, nullptr};
   cudaStream_t stream = nullptr;
   vp_alloc_fn alloc = nullptr;
   vp_free_fn freef = nullptr;
