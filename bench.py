@@ -28,6 +28,9 @@ sys.path.insert(0, ROOT)
 WORKLOAD = "saturated_two_stream_1024x1024_seq"
 CHI, TOL, DT = 64, 1e-10, 0.002
 FP64_PEAK_GFLOPS = 2 * 2 * 152 * 2.070  # 2 DFMA/clk/SM x 2 flop x 152 SMs x 2070 MHz (nominal 1.25 TF/s)
+# What the path computes in: FP64 storage, contractions, Poisson and truncation
+# rule; the QR, Q formation and Jacobi SVD in double-word FP32 (~2^-48).
+DTYPE = "f64 storage/contractions, df32 (~2^-48) factorisations"
 NCU_TRAFFIC = {"qr_factor": 637.6e3, "jacobi": 70.3e3}  # DRAM bytes per launch from the ncu captures under profiles/
 NCU_TRAFFIC_SPECIES = {"qr_factor": 466.0e3}  # two-species workload, same source
 
@@ -222,7 +225,7 @@ def run_ours(args, rank, world):
         "metric": metric_name(lay),
         "value": steps_per_s, "unit": "steps/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64", "data": "synthetic",
+        "dtype": DTYPE, "data": "synthetic",
         "config": {"workload": WORKLOAD, "grid": f"{lay.Nx}x{lay.Nv}", "sites": f"{lay.nx}+{lay.nv}",
                    "mapping": "seq" if lay.mapping == 0 else "interleaved", "chi": CHI,
                    "tol": TOL, "dt": DT, "parallelism": f"replicas x{world}",
@@ -321,7 +324,7 @@ def run_species(args, rank, world):
                   f"ions, S3, chi={chi}, Dougherty collisions)",
         "value": job_rate(world, args.steps, ms), "unit": "steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "vs_baseline": None, "dtype": DTYPE, "data": "synthetic",
         "config": {"workload": name, "species": species, "chi": chi, "tol": TOL, "dt": dt,
                    "parallelism": f"replicas x{world}", "l2": "flushed between timed steps (256 MB write)"},
         "roofline": roofline(prof, ms, world, NCU_TRAFFIC_SPECIES if name == "saturated_buneman_512x512_s3" else {}),
@@ -361,10 +364,16 @@ def oracle_steps(lay, f0, nsteps, budget_s):
 
 
 def cpu_baseline(lay, f0, budget_s):
+    from oracle import mps as OM
+    OM.TIE_STATS.update(cuts=0, fired=0, min_gap=float("inf"))
     done, t = oracle_steps(lay, f0, 1000, budget_s)
+    ts = dict(OM.TIE_STATS)
     return {"value": done / t, "unit": "steps/s", "cores": os.cpu_count(), "kind": "oracle",
             "sample": f"{done} RK4-C1 step(s) of the same workload from the same initial MPS "
-                      f"(numpy/LAPACK, all host cores), {t:.1f} s"}
+                      f"(numpy/LAPACK, all host cores), {t:.1f} s",
+            # how often the truncation tie rule moved a cut in those steps, and
+            # the smallest relative gap at a cut it left alone
+            "tie_rule": {"cuts": ts["cuts"], "fired": ts["fired"], "min_gap_at_cut": ts["min_gap"]}}
 
 
 def run_reference(args, rank, world):
@@ -379,7 +388,7 @@ def run_reference(args, rank, world):
         "impl": "reference", "metric": metric_name(lay),
         "value": v, "unit": "steps/s", "n_gpus": world, "steps": done, "warmup": min(args.warmup, 1),
         "ms_per_step": 1e3 * t / done, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64", "data": "synthetic",
+        "dtype": "f64 (numpy/LAPACK oracle)", "data": "synthetic",
         "config": {"workload": WORKLOAD, "grid": f"{lay.Nx}x{lay.Nv}", "sites": f"{lay.nx}+{lay.nv}",
                    "mapping": "seq" if lay.mapping == 0 else "interleaved", "chi": CHI, "tol": TOL, "dt": DT,
                    "parallelism": "cpu"},
@@ -437,7 +446,7 @@ def run_batch(args):
         b.close()
     print(json.dumps({
         "metric": "batched sims/s (RK4-C1 runs, mixed sizes/chi/mappings)", "value": out["batched"]["sims_per_s"],
-        "unit": "sims/s", "n_gpus": 1, "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+        "unit": "sims/s", "n_gpus": 1, "higher_is_better": True, "dtype": DTYPE, "data": "synthetic",
         "config": {"workload": "mixed Landau/bump-on-tail, grid bits 6..9 per dim, chi 16/32/64, seq/interleaved",
                    "instances": args.instances, "steps_per_run": steps, "concurrency": args.concurrency,
                    "seed": 0},
@@ -481,7 +490,7 @@ def run_serve(args):
     b.close()
     print(json.dumps({
         "metric": "served sims/s with p50/p99 step and run latency (continuous batching)",
-        "value": len(done) / wall, "unit": "sims/s", "n_gpus": 1, "higher_is_better": True, "dtype": "f64",
+        "value": len(done) / wall, "unit": "sims/s", "n_gpus": 1, "higher_is_better": True, "dtype": DTYPE,
         "data": "synthetic",
         "config": {"arrivals": "Poisson", "rate_per_s": args.rate, "window_s": args.window, "requests": len(done),
                    "steps_per_run": f"U[{max(2, args.steps // 4)}, {args.steps}]", "concurrency": args.concurrency,
@@ -492,8 +501,8 @@ def run_serve(args):
 
 
 def run_precision(args):
-    """FP64 path vs the reduced-precision contraction modes (factorisations
-    FP64) on the same state: steps/s of each and the field-energy and f errors
+    """FP64-contraction path vs the reduced-precision contraction modes
+    (factorisations double-word FP32 in every mode) on the same state: steps/s of each and the field-energy and f errors
     against the FP64 run."""
     import numpy as np
     import torch
@@ -527,7 +536,7 @@ def run_precision(args):
     print(json.dumps({
         "metric": metric_name(lay) + " - contraction precision modes", "value": best, "unit": "steps/s",
         "n_gpus": 1, "steps": args.steps, "higher_is_better": True,
-        "dtype": "tf32x3 contractions (tcgen05), f64 factorisations", "data": "synthetic",
+        "dtype": "tf32x3 contractions (tcgen05), df32 (~2^-48) factorisations", "data": "synthetic",
         "config": {"workload": WORKLOAD, "chi": CHI, "tol": TOL, "dt": DT,
                    "errors": "after 1 + steps steps, against the FP64 run from the same state"},
         "modes": modes}), flush=True)

@@ -15,8 +15,20 @@
  * Conventions
  *  - Every function returns an int status (VP_OK = 0); vp_last_error() gives
  *    a one-line description of the last failure on a context.
- *  - All arithmetic is IEEE FP64 on the GPU.  No function falls back to the
- *    CPU: without a usable CUDA device vp_ctx_create fails with VP_ECUDA.
+ *  - Precision.  Every array in memory (MPS and MPO cores, densities,
+ *    fields) is IEEE FP64, and so are the contractions (MPO x MPS, the GEMMs
+ *    of the sweeps in the default VP_PREC_FP64 mode), the Poisson solve and
+ *    the truncation rule.  The latency-bound factorisations of the
+ *    compression sweeps -- Householder QR, the formation of Q and the
+ *    truncating one-sided Jacobi SVD -- compute in double-word FP32
+ *    arithmetic (each value the unevaluated sum of two floats, about 48
+ *    significant bits, unit roundoff ~2^-48 instead of FP64's 2^-53) behind
+ *    exact power-of-two prescaling; they read and write FP64.  Against an
+ *    FP64 LAPACK implementation of the same method this leaves f within
+ *    ~1e-12 relative (L2) and the field energy within ~1e-12 relative per
+ *    step.  Compressions with tol = 0 (exact mode) use an FP64 Jacobi SVD.
+ *    No function falls back to the CPU: without a usable CUDA device
+ *    vp_ctx_create fails with VP_ECUDA.
  *  - Handles (vp_ctx, mps_t, mpo_t, vp_sim) are opaque and owned by the
  *    caller: each *_create has a matching *_destroy.  MPS/MPO/sim objects
  *    must be destroyed before their context.
@@ -98,6 +110,16 @@ int vp_ctx_create(void* cuda_stream, vp_alloc_fn alloc, vp_free_fn free_fn, void
                   vp_ctx** out);
 int vp_ctx_destroy(vp_ctx* ctx);
 const char* vp_last_error(const vp_ctx* ctx);
+/* Failure detection (no counterpart in the paper).  The device-side waits of
+ * the cooperative kernels (the grid barrier, the published-reflector counter
+ * of the grid QR) spin at most `clocks` SM clocks (default 2e9, ~1 s; 0
+ * restores it) before they give up: the kernel records the timeout and
+ * returns, and the call that launched it fails with VP_ETIMEOUT while the
+ * context stays usable (its status words are reset).  A small limit is a
+ * way to exercise that path without a real fault; it also applies to the
+ * contexts this one creates for concurrent work.  Synchronises the stream.
+ * Errors: VP_EINVAL (clocks < 0). */
+int vp_ctx_set_wait_limit(vp_ctx* ctx, long long clocks);
 /* Number of kernels this context has launched so far (diagnostics). */
 int64_t vp_kernel_launches(const vp_ctx* ctx);
 
@@ -151,10 +173,17 @@ int mps_get_cores(vp_ctx* ctx, const mps_t* mps, double* host_out, size_t capaci
  * "VPMPS01\0", int32 n, int32 0, int32 ranks[n+1], zero padding to 8 bytes,
  * then the cores packed as in mps_get_cores (FP64), little-endian.  mps_save
  * writes `path`.tmp and renames it over `path`; mps_load rejects a file whose
- * size disagrees with its bond ranks.  Errors: VP_EIO (open/read/write or
+ * size disagrees with its bond ranks before it allocates anything.  Errors: VP_EIO (open/read/write or
  * format), VP_EINVAL, VP_ENOMEM. */
 int mps_save(vp_ctx* ctx, const mps_t* mps, const char* path);
 int mps_load(vp_ctx* ctx, const char* path, mps_t** out);
+/* Validate a checkpoint file without loading it (host only, no context, no
+ * GPU): magic, header, bond ranks (1 <= r <= 2^20, boundary ranks 1) and a
+ * file size equal to header + 8 * payload elements; the header is checked
+ * before anything is allocated.  n_out (may be NULL): number of sites;
+ * ranks_out (may be NULL): n+1 ints (at most 65); elems_out (may be NULL):
+ * FP64 payload elements.  Errors: VP_EINVAL (NULL path), VP_EIO. */
+int mps_file_info(const char* path, int* n_out, int* ranks_out, size_t* elems_out);
 /* Contract to the dense 2^n vector indexed by site bits (site 0 = MSB), host
  * output.  n <= 24. */
 int mps_to_dense(vp_ctx* ctx, const mps_t* mps, double* host_out);
@@ -239,11 +268,16 @@ int vp_poisson(vp_ctx* ctx, const double* rho_dev, int nx, double dx, double* E_
  * process exits; nothing in it needs clearing between calls (each call writes
  * every element it reads).  All calls on a device share that array, so calls
  * that overlap on the GPU race: serialise them (one stream, or events).  The
- * first call on a device looks up the array's device address
- * (cudaGetSymbolAddress with that device current); make that first call
- * before any stream capture.  Errors: VP_EINVAL, VP_ECAPACITY (nx > 14: 2^nx
- * beyond the static scratch), VP_ECUDA.  Synchronises `cuda_stream` when a
- * host output is requested.  Calls no allocator. */
+ * first call on a device is its set-up: it looks up the array's device
+ * address (cudaGetSymbolAddress with that device current), and under CUDA's
+ * lazy module loading that lookup can load the library's device code, which
+ * may itself allocate device memory for the module.  So make one call (any
+ * valid size) during the caller's own set-up, before its no-allocation phase
+ * and before any stream capture; every later call on that device allocates
+ * nothing.  `cuda_stream` must belong to the current device (VP_EINVAL
+ * otherwise).  Errors: VP_EINVAL, VP_ECAPACITY (nx > 14: 2^nx beyond the
+ * static scratch), VP_ECUDA.  Synchronises `cuda_stream` when a host output
+ * is requested. */
 int vp_poisson_noalloc(void* cuda_stream, const double* rho_dev, int nx, double dx, double* E_dev,
                        double* field_energy_host, double* mass_host);
 
@@ -275,9 +309,12 @@ typedef struct {
   int e_chi;        /* bond cap D_F of the field MPS (main text, "Approximation
                        of the nonlinear term"); 0: no cap */
   int precision;    /* VP_PREC_*: arithmetic of the dense contractions of the
-                       sweeps (R x next core, the Q and U S products).  QR,
-                       Jacobi SVD, truncation, the MPO application and the
-                       Poisson solve stay FP64 in every mode.
+                       sweeps (R x next core, the Q and U S products).  The
+                       other steps do not change with the mode: the MPO
+                       application, the truncation rule and the Poisson
+                       solve stay FP64, and the QR, Q formation and Jacobi
+                       SVD stay in double-word FP32 (~2^-48, see the
+                       precision convention at the top of this file).
                          FP64          FP64 FMA;
                          FP32_CONTRACT FP32 FMA, FP32 accumulation (CUDA cores);
                          TF32          tensor cores, operands rounded to TF32,

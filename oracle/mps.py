@@ -27,8 +27,21 @@ import scipy.linalg as sla
 
 # Two singular values closer than this fraction of the smaller kept one are
 # treated as one degenerate cluster that is kept or dropped as a whole, so the
-# kept subspace (and hence f) is unique up to rounding.
+# kept subspace (and hence f) is unique up to rounding.  The width follows
+# from Wedin's sin-theta bound: if two computations of the same bond matrix
+# differ in their singular values by delta ~ c u sigma_1 (u the unit roundoff
+# of the arithmetic), a cut inside a relative gap g = (s_r - s_{r+1}) / s_r
+# mixes the kept and discarded vectors by an angle up to delta / (g s_r), so
+# f moves by up to ~2 delta / g relative to sigma_1.  With the double-word
+# factorisations of the GPU path (u ~ 2^-48 ~ 3.6e-15, c of order 1-10) and
+# the 1e-10 parity contract on f, gaps below ~1e-5 .. 1e-4 are not resolved
+# identically by two correct implementations.
 TIE_REL = 1e-5
+
+# Counters of the rank choices (instrumentation for reports; no effect on
+# the result): cuts made, cuts moved down by the tie rule, and the smallest
+# relative gap s_{r-1} - s_r seen at a cut that the rule did not move.
+TIE_STATS = {"cuts": 0, "fired": 0, "min_gap": float("inf")}
 
 
 def to_dense(cores):
@@ -74,9 +87,16 @@ def choose_rank(s, chi, tol):
     else:
         r_tol = m
     r = min(chi, r_tol, m)
+    r0 = r
     while 1 < r < m and (s[r - 1] - s[r]) <= TIE_REL * s[r - 1]:
         r -= 1
     r = max(r, 1)
+    if 1 <= r0 < m:
+        TIE_STATS["cuts"] += 1
+        if r != r0:
+            TIE_STATS["fired"] += 1
+        elif s[r - 1] > 0.0:
+            TIE_STATS["min_gap"] = min(TIE_STATS["min_gap"], float((s[r - 1] - s[r]) / s[r - 1]))
     return r, math.sqrt(tail2[r] / nrm2)
 
 

@@ -7,6 +7,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <thread>
 #include <string>
@@ -152,6 +153,26 @@ void prof_end(vp_ctx* ctx, int cls, double work, int m, int n, int k) {
   ctx->prof_launches[cls] += 1;
 }
 
+int AttrOnce::ensure(vp_ctx* ctx, const void* fn, int smem_bytes, bool cluster) {
+  static std::mutex mu;
+  const int dev = ctx->device;
+  const unsigned long long bit = dev >= 0 && dev < 64 ? 1ull << dev : 0ull;
+  if (bit && (done.load(std::memory_order_acquire) & bit)) return VP_OK;
+  std::lock_guard<std::mutex> lk(mu);
+  if (bit && (done.load(std::memory_order_relaxed) & bit)) return VP_OK;
+  if (smem_bytes > 0) VP_CUDA(ctx, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes));
+  if (cluster) VP_CUDA(ctx, cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+  done.fetch_or(bit, std::memory_order_release);
+  return VP_OK;
+}
+
+int write_wait_limit(vp_ctx* ctx) {
+  VP_CUDA(ctx, cudaMemcpyAsync(&ctx->status->wait_clocks, &ctx->wait_clocks, sizeof(long long),
+                               cudaMemcpyHostToDevice, ctx->stream));
+  // the source is pageable host memory: the copy has read it on return
+  return VP_OK;
+}
+
 int sync_status(vp_ctx* ctx) {
   VP_CUDA(ctx, cudaMemcpyAsync(ctx->h_small + 60, &ctx->status->err, sizeof(int), cudaMemcpyDeviceToHost,
                                ctx->stream));
@@ -159,6 +180,7 @@ int sync_status(vp_ctx* ctx) {
   const int err = ctx->h_small[60];
   if (err == 0) return VP_OK;
   VP_CUDA(ctx, cudaMemsetAsync(ctx->status, 0, sizeof(DevStatus), ctx->stream));
+  VP_TRY(write_wait_limit(ctx));
   if (err == 1) return fail(ctx, VP_ETIMEOUT, "a device-side grid barrier gave up waiting");
   if (err == 2) return fail(ctx, VP_ENUMERIC, "NaN or Inf in singular values");
   return fail(ctx, VP_ENUMERIC, "Jacobi SVD did not converge");
@@ -252,7 +274,18 @@ struct SideScope {
 // formed (the context's stream waits for the side stream).
 static int qr_sweep(vp_ctx* ctx, mps_t* s, int kend) {
   VP_TRY(ensure_side(ctx));
-  bool busy[2] = {false, false};
+  // On every exit (error paths included) the context's stream waits for the
+  // Q formations still in flight: later frees of the factor buffers and
+  // writes of the cores are ordered after them.
+  struct JoinGuard {
+    vp_ctx* c;
+    bool busy[2] = {false, false};
+    ~JoinGuard() {
+      for (int b = 0; b < 2; ++b)
+        if (busy[b]) cudaStreamWaitEvent(c->stream, c->ev_qd[b], 0);
+    }
+  } guard{ctx};
+  bool* busy = guard.busy;
   for (int k = 0; k < kend; ++k) {
     const int b = k & 1;
     DevBuf& F = b ? ctx->w_fac_b : ctx->w_fac;
@@ -294,7 +327,10 @@ static int qr_sweep(vp_ctx* ctx, mps_t* s, int kend) {
     }
   }
   for (int b = 0; b < 2; ++b)
-    if (busy[b]) VP_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, ctx->ev_qd[b], 0));
+    if (busy[b]) {
+      busy[b] = false;
+      VP_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, ctx->ev_qd[b], 0));
+    }
   return VP_OK;
 }
 
@@ -357,6 +393,12 @@ static int svd_site(vp_ctx* ctx, mps_t* s, int k, int chi, double tol, double* e
     if (tall) VP_TRY(launch_gemm(ctx, pl, q, m, 1.0, s->core[k - 1].p, m, ctx->w_q1.p, q, ctx->w_tmp2.p, q));
   }
   VP_CUDA(ctx, cudaEventRecord(ctx->ev_join, ctx->side));
+  // every exit from here on makes the context's stream wait for the side
+  // stream's products (the normal path joins before the outputs, again below)
+  struct SideJoin {
+    vp_ctx* c;
+    ~SideJoin() { cudaStreamWaitEvent(c->stream, c->ev_join, 0); }
+  } side_join{ctx};
   VP_TRY(reserve(ctx, ctx->w_tmp, (size_t)q * q));
   double* X = ctx->w_tmp.p;
   VP_TRY(launch_lower_from_upper(ctx, ctx->w_r.p, q, X));
@@ -720,6 +762,11 @@ static vp_ctx* ctx_child(vp_ctx* parent) {
     return nullptr;
   }
   c->owns_stream = true;
+  c->wait_clocks = parent->wait_clocks;
+  if (write_wait_limit(c) != VP_OK) {
+    vp_ctx_destroy(c);
+    return nullptr;
+  }
   parent->children.push_back(c);
   return c;
 }
@@ -765,7 +812,7 @@ int vp_ctx_create(void* cuda_stream, vp_alloc_fn alloc, vp_free_fn free_fn, void
     return VP_ENOMEM;
   }
   cudaMemsetAsync(c->status, 0, sizeof(DevStatus), c->stream);
-  if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
+  if (write_wait_limit(c) != VP_OK || cudaStreamSynchronize(c->stream) != cudaSuccess) {
     delete c;
     return VP_ECUDA;
   }
@@ -779,7 +826,8 @@ int vp_ctx_destroy(vp_ctx* c) {
   for (DevBuf* b : {&c->w_fac, &c->w_q, &c->w_gemm, &c->w_j, &c->w_p, &c->w_tmp, &c->w_tmp2, &c->w_vec, &c->w_split,
                     &c->w_piv, &c->w_q1, &c->w_q2, &c->w_r, &c->w_p2, &c->w_a, &c->w_b, &c->w_c, &c->w_l,
                     &c->w_q_side, &c->w_split_side, &c->w_tca, &c->w_tcb, &c->w_tca_side, &c->w_tcb_side,
-                    &c->w_qrv, &c->w_qrc, &c->w_fq, &c->w_fq_side, &c->w_fac_b, &c->w_p_b})
+                    &c->w_qrv, &c->w_qrc, &c->w_fq, &c->w_fq_side, &c->w_fac_b, &c->w_p_b,
+                    &c->w_sig, &c->w_wq, &c->w_wr})
     release(c, *b);
   for (auto& b : c->w_chain) release(c, b);
   dev_free(c, c->status, sizeof(DevStatus));
@@ -803,6 +851,15 @@ int vp_ctx_destroy(vp_ctx* c) {
 }
 
 const char* vp_last_error(const vp_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+int vp_ctx_set_wait_limit(vp_ctx* c, long long clocks) {
+  if (!c || clocks < 0) return VP_EINVAL;
+  c->wait_clocks = clocks > 0 ? clocks : kDefaultWaitClocks;
+  VP_TRY(write_wait_limit(c));
+  for (vp_ctx* ch : c->children) VP_TRY(vp_ctx_set_wait_limit(ch, clocks));
+  VP_CUDA(c, cudaStreamSynchronize(c->stream));
+  return VP_OK;
+}
 
 int vp_profile_enable(vp_ctx* c, int on) {
   if (!c) return VP_EINVAL;

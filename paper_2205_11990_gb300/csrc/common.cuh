@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
 #include <cstdio>
 #include <string>
@@ -29,7 +30,10 @@ struct DevStatus {
   unsigned long long pub_base;   // pub_count when the next QR launch starts
   unsigned int pub_done;         // blocks of the current QR launch that have finished
   int pad3;
+  long long wait_clocks;         // SM clocks a device-side wait spins before giving up (err = 1)
 };
+
+constexpr long long kDefaultWaitClocks = 2000000000ll;  // ~1 s at 2 GHz
 
 // Grow-only device buffer owned by a context.
 struct DevBuf {
@@ -47,6 +51,7 @@ struct vp_ctx {
   int precision = 0;     // VP_PREC_* of the GEMM contractions (factorisations stay FP64)
   int modified_split = 0;  // > 0: compressions use the centre-bond-first scheme about this bond
   int grouped = 0;         // 1: the bond inside every (x_j, v_j) site pair is not truncated (IG ordering)
+  long long wait_clocks = vp::kDefaultWaitClocks;  // limit of the device-side waits (DevStatus::wait_clocks)
   bool owns_stream = false;
   std::vector<vp_ctx*> children;  // contexts created for concurrent work
   cudaStream_t side = nullptr;     // side stream: Q formation beside the Jacobi SVD
@@ -90,6 +95,7 @@ struct vp_ctx {
   vp::DevBuf w_qrc;                   // its columns when they exceed shared memory
   vp::DevBuf w_fq, w_fq_side;         // double-word reflectors of the Q formation
   vp::DevBuf w_sig;                   // kept centre singular values (modified compression)
+  vp::DevBuf w_wq, w_wr;              // wide QR: Q of the leading square block, R2^T
   // Blocks handed back to the caller's allocator only once the work queued
   // before their release has finished (the allocator callbacks know no
   // streams, and this context's kernels run on several).
@@ -147,6 +153,18 @@ void prof_begin(vp_ctx* ctx, int cls);
 void prof_end(vp_ctx* ctx, int cls, double work, int m = 0, int n = 0, int k = 0);
 // Synchronise and read the device status word; maps errors to VP codes.
 int sync_status(vp_ctx* ctx);
+// Write ctx->wait_clocks into the device status words (stream-ordered).
+int write_wait_limit(vp_ctx* ctx);
+
+// Kernel attributes (dynamic shared memory limit, non-portable cluster size)
+// set once per device for one kernel.  cudaFuncSetAttribute applies to the
+// current device only, and the library's host threads (the second stream of
+// a sim, species threads, batch workers) may launch the same kernel at once:
+// a bit per device in an atomic mask, set under a mutex on first use.
+struct AttrOnce {
+  std::atomic<unsigned long long> done{0};
+  int ensure(vp_ctx* ctx, const void* fn, int smem_bytes, bool cluster);
+};
 
 // ------------------------------------------------------------ kernels (linalg.cu)
 // Row-major (m x n) -> column-major copy.

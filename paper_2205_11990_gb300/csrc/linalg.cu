@@ -47,9 +47,10 @@ __device__ __forceinline__ int ld_volatile(const int* p) { return *(const volati
 // Grid-wide barrier for cooperative launches: one monotonic 64-bit arrival
 // counter, a release add per block and acquire polling (no reset, no
 // generation word).  Every block starts from the counter value the previous
-// cooperative kernel left in bar_base.  Waits have a clock limit (~1 s): on
-// expiry the block records err = 1 and the barrier reports failure, so the
-// kernel returns instead of hanging.
+// cooperative kernel left in bar_base.  Waits have a clock limit
+// (DevStatus::wait_clocks, ~1 s by default): on expiry the block records
+// err = 1 and the barrier reports failure, so the kernel returns instead of
+// hanging.
 struct GridSync {
   DevStatus* st;
   unsigned nb;
@@ -64,10 +65,10 @@ struct GridSync {
       if (threadIdx.x == 0) {
         cuda::atomic_ref<unsigned long long, cuda::thread_scope_device> cnt(st->bar_count);
         cnt.fetch_add(1ull, cuda::memory_order_release);
-        const long long t0 = clock64();
+        const long long t0 = clock64(), limit = *(volatile long long*)&st->wait_clocks;
         while (cnt.load(cuda::memory_order_acquire) < target) {
           if (ld_volatile(&st->err) != 0) break;
-          if (clock64() - t0 > 2000000000ll) {
+          if (clock64() - t0 > limit) {
             atomicExch(&st->err, 1);
             break;
           }
@@ -285,13 +286,13 @@ __global__ void __launch_bounds__(kThreads) k_qr_factor_dw(double* A, int m, int
   auto wait = [&](int j) -> bool {
     if (tid == 0) {
       int ok = 1;
-      const long long t0 = clock64();
+      const long long t0 = clock64(), limit = *(volatile long long*)&st->wait_clocks;
       while (pub.load(cuda::memory_order_acquire) < base + j + 1) {
         if (ld_volatile(&st->err) != 0) {
           ok = 0;
           break;
         }
-        if (clock64() - t0 > 2000000000ll) {
+        if (clock64() - t0 > limit) {
           atomicExch(&st->err, 1);
           ok = 0;
           break;
@@ -615,12 +616,8 @@ static size_t qr_cl_smem(int m, int n, int CS) {
 
 template <int NT, int CW>
 static int launch_cl(vp_ctx* ctx, double* A, int m, int n, double* tau, int cs, size_t need) {
-  static bool cattr = false;
-  if (!cattr) {
-    VP_CUDA(ctx, cudaFuncSetAttribute(k_qr_factor_cl<NT, CW>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    VP_CUDA(ctx, cudaFuncSetAttribute(k_qr_factor_cl<NT, CW>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
-    cattr = true;
-  }
+  static AttrOnce cattr;
+  VP_TRY(cattr.ensure(ctx, (const void*)k_qr_factor_cl<NT, CW>, 200 * 1024, true));
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute at[1];
   cfg.gridDim = dim3(cs);
@@ -652,6 +649,26 @@ static size_t qr_cdw_smem(int m, int n, int CS) {
 int launch_qr_factor(vp_ctx* ctx, double* A, int m, int n, double* tau, double* vbuf) {
   const int p = std::min(m, n);
   if (p <= 0) return VP_OK;
+  // Factors more than twice as wide as tall: the m reflectors depend on the
+  // leading m columns alone, so that square block (contiguous in the
+  // column-major layout) is factored in place by the square-factor kernels,
+  // Q is formed from its reflectors, and the rest of R is one FP64 GEMM,
+  // R2 = Q^T A2 (stored as R2^T = A2^T Q, which is A2's column-major layout),
+  // instead of a cooperative grid that applies every reflector to all n
+  // columns one column step at a time.  Same LAPACK layout on output.
+  if (n > 2 * m && m >= 2) {
+    VP_TRY(launch_qr_factor(ctx, A, m, m, tau, vbuf));
+    VP_TRY(reserve(ctx, ctx->w_wq, (size_t)m * m));
+    VP_TRY(launch_qr_formq(ctx, A, m, m, tau, ctx->w_wq.p));
+    const size_t rest = (size_t)(n - m) * m;
+    VP_TRY(reserve(ctx, ctx->w_wr, rest));
+    const int prec = ctx->precision;  // R is part of the factorisation: FP64 in every mode
+    ctx->precision = VP_PREC_FP64;
+    const int st = launch_gemm(ctx, n - m, m, m, 1.0, A + (size_t)m * m, m, ctx->w_wq.p, m, ctx->w_wr.p, m);
+    ctx->precision = prec;
+    VP_TRY(st);
+    return launch_copy(ctx, ctx->w_wr.p, A + (size_t)m * m, rest);
+  }
   // Measured per column on GB300 (the step's shapes): up to ~4e3 elements
   // the push-model cluster kernel (2.5 us); above, the pull-model kernel with
   // four critical warps (128x128 2.9 us, 368x128 4.2, 464x184 4.8, 512x341
@@ -666,12 +683,8 @@ int launch_qr_factor(vp_ctx* ctx, double* A, int m, int n, double* tau, double* 
     while (cs < std::min(ctx->cluster_size, 4) && cs * 8 < n) cs *= 2;
     const size_t need = qr_cdw_smem(m, n, cs);
     if (need <= 200 * 1024) {
-      static bool cattr = false;
-      if (!cattr) {
-        VP_CUDA(ctx, cudaFuncSetAttribute(k_qr_factor_cdw, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-        VP_CUDA(ctx, cudaFuncSetAttribute(k_qr_factor_cdw, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
-        cattr = true;
-      }
+      static AttrOnce cattr;
+      VP_TRY(cattr.ensure(ctx, (const void*)k_qr_factor_cdw, 200 * 1024, true));
       cudaLaunchConfig_t cfg = {};
       cudaLaunchAttribute at[1];
       cfg.gridDim = dim3(cs);
@@ -704,11 +717,8 @@ int launch_qr_factor(vp_ctx* ctx, double* A, int m, int n, double* tau, double* 
     // result does not depend on the context's block cap
     const int nmax = (n + blocks - 1) / blocks;
     const size_t smem = (size_t)nmax * m * sizeof(dw) + (size_t)nmax * sizeof(int);
-    static bool qattr = false;
-    if (!qattr) {
-      VP_CUDA(ctx, cudaFuncSetAttribute(k_qr_factor_dw, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-      qattr = true;
-    }
+    static AttrOnce qattr;
+    VP_TRY(qattr.ensure(ctx, (const void*)k_qr_factor_dw, 200 * 1024, false));
     VP_TRY(reserve(ctx, ctx->w_qrv, (size_t)m * p + p + 8));
     dw* V = reinterpret_cast<dw*>(ctx->w_qrv.p);
     dw* T = V + (size_t)m * p;
@@ -1666,12 +1676,8 @@ int launch_jacobi_rows(vp_ctx* ctx, double* X, int b, int c, double* J, bool flo
   const int CS = ctx->cluster_size;
   const JacBlockCfg bc = jac_block_cfg(b, c, J != nullptr, std::max(1, CS));
   if (floor_ok && b > 1 && jac_dw_smem(bc) <= 200 * 1024) {
-    static bool dattr_done = false;
-    if (!dattr_done) {
-      VP_CUDA(ctx, cudaFuncSetAttribute(k_jacobi_dw, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-      VP_CUDA(ctx, cudaFuncSetAttribute(k_jacobi_dw, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
-      dattr_done = true;
-    }
+    static AttrOnce dattr_done;
+    VP_TRY(dattr_done.ensure(ctx, (const void*)k_jacobi_dw, 200 * 1024, true));
     const size_t smem = std::max<size_t>(jac_dw_smem(bc), 120 * 1024);
     // rotate while |gamma| > eps sqrt(alpha beta); eps above the double-word
     // dot-product noise, which grows like sqrt(c) u^2
@@ -1695,12 +1701,8 @@ int launch_jacobi_rows(vp_ctx* ctx, double* X, int b, int c, double* J, bool flo
     return VP_OK;
   }
   if (b > 1 && jac_block_smem(bc) <= 200 * 1024) {
-    static bool battr_done = false;
-    if (!battr_done) {
-      VP_CUDA(ctx, cudaFuncSetAttribute(k_jacobi_block, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-      VP_CUDA(ctx, cudaFuncSetAttribute(k_jacobi_block, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
-      battr_done = true;
-    }
+    static AttrOnce battr_done;
+    VP_TRY(battr_done.ensure(ctx, (const void*)k_jacobi_block, 200 * 1024, true));
     // one CTA per SM: the FP64 pipe of each SM is the limit
     const size_t smem = std::max<size_t>(jac_block_smem(bc), 120 * 1024);
     double eps = 1e-15 * std::sqrt((double)c);
@@ -1723,14 +1725,10 @@ int launch_jacobi_rows(vp_ctx* ctx, double* X, int b, int c, double* J, bool flo
     return VP_OK;
   }
   if (CS > 0 && b > 1 && cluster_jacobi_smem(b, c, CS, J != nullptr) <= 200 * 1024) {
-    static bool attr_done = false;
+    static AttrOnce attr_done;
     // at least 120 KB per CTA, so no two CTAs of the cluster share an SM
     const size_t smem = std::max<size_t>(cluster_jacobi_smem(b, c, CS, J != nullptr), 120 * 1024);
-    if (!attr_done) {
-      VP_CUDA(ctx, cudaFuncSetAttribute(k_jacobi_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-      VP_CUDA(ctx, cudaFuncSetAttribute(k_jacobi_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
-      attr_done = true;
-    }
+    VP_TRY(attr_done.ensure(ctx, (const void*)k_jacobi_cluster, 200 * 1024, true));
     double eps = 1e-15 * std::sqrt((double)c);
     int max_sweeps = 60;
     cudaLaunchConfig_t cfg = {};
@@ -1767,6 +1765,15 @@ int launch_jacobi_rows(vp_ctx* ctx, double* X, int b, int c, double* J, bool flo
 }
 
 // ------------------------------------------------------------ truncation
+// Descending order with ties broken by index, as a strict total order even
+// when values are NaN (NaNs first, by index): the rank of each element is
+// then a permutation, so the indices written from it always stay in range.
+__device__ __forceinline__ bool sorts_before(double a, int ia, double b, int ib) {
+  const bool na = isnan(a), nb = isnan(b);
+  if (na || nb) return na && (!nb || ia < ib);
+  return a > b || (a == b && ia < ib);
+}
+
 // Single block: row norms, descending order (ties by index), kept rank by the
 // rule r = min(chi, r_tol), r_tol the smallest r with sqrt(sum_{i>=r} s_i^2)
 // <= tol ||s|| (tail summed smallest first, tol = 0: keep all), moved down
@@ -1791,10 +1798,7 @@ __global__ void k_select(const double* __restrict__ X, int b, int c, int chi, do
     const double si = s[i];
     if (!isfinite(si)) atomicCAS(&st->err, 0, 2);
     int pos = 0;
-    for (int j = 0; j < b; ++j) {
-      const double sj = s[j];
-      pos += (sj > si) || (sj == si && j < i);
-    }
+    for (int j = 0; j < b; ++j) pos += sorts_before(s[j], j, si, i);
     perm[pos] = i;
     sigma[pos] = si;
   }
@@ -1843,8 +1847,10 @@ int launch_select(vp_ctx* ctx, const double* X, int b, int c, int chi, double to
                   int* d_rank, double* d_err) {
   const size_t smem = (size_t)(2 * b + 1) * sizeof(double);
   if (smem > 200 * 1024) return fail(ctx, VP_ECAPACITY, "select: bond too large");
-  if (smem > 48 * 1024)
-    VP_CUDA(ctx, cudaFuncSetAttribute(k_select, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  if (smem > 48 * 1024) {
+    static AttrOnce sattr;  // the largest size once, never lowered under another thread's launch
+    VP_TRY(sattr.ensure(ctx, (const void*)k_select, 200 * 1024, false));
+  }
   ctx->launches++;
   k_select<<<1, 512, smem, ctx->stream>>>(X, b, c, chi, tol, perm, sigma, d_rank, d_err, ctx->status);
   return check_launch(ctx, "select");
@@ -1897,7 +1903,7 @@ __global__ void k_norm_order(const double* __restrict__ M, int m, int c, int by_
   for (int j = threadIdx.x; j < q; j += blockDim.x) {
     const double v = nrm[j];
     int pos = 0;
-    for (int k = 0; k < q; ++k) pos += (nrm[k] > v) || (nrm[k] == v && k < j);
+    for (int k = 0; k < q; ++k) pos += sorts_before(nrm[k], k, v, j);
     piv[pos] = j;
   }
 }
@@ -1906,8 +1912,10 @@ int launch_norm_order(vp_ctx* ctx, const double* M, int m, int c, int by_cols, i
   const int q = by_cols ? c : m;
   const size_t smem = (size_t)q * sizeof(double);
   if (smem > 200 * 1024) return fail(ctx, VP_ECAPACITY, "norm_order: too many columns");
-  if (smem > 48 * 1024)
-    VP_CUDA(ctx, cudaFuncSetAttribute(k_norm_order, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  if (smem > 48 * 1024) {
+    static AttrOnce nattr;  // the largest size once, never lowered under another thread's launch
+    VP_TRY(nattr.ensure(ctx, (const void*)k_norm_order, 200 * 1024, false));
+  }
   ctx->launches++;
   k_norm_order<<<1, 512, smem, ctx->stream>>>(M, m, c, by_cols, piv);
   return check_launch(ctx, "norm_order");

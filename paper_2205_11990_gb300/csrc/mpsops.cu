@@ -265,8 +265,10 @@ int launch_poisson(vp_ctx* ctx, const double* rho, int N, double dx, double* E, 
   const int nt = 256;
   const size_t smem = (size_t)(N + 33 + nt) * sizeof(double);
   if (smem > 200 * 1024) return fail(ctx, VP_ECAPACITY, "poisson: 2^nx too large");
-  if (smem > 48 * 1024)
-    VP_CUDA(ctx, cudaFuncSetAttribute(k_poisson, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  if (smem > 48 * 1024) {
+    static AttrOnce pattr;  // the largest size once, never lowered under another thread's launch
+    VP_TRY(pattr.ensure(ctx, (const void*)k_poisson, 200 * 1024, false));
+  }
   ctx->launches++;
   k_poisson<<<1, nt, smem, ctx->stream>>>(rho, N, dx, E, we_dev);
   return check_launch(ctx, "poisson");

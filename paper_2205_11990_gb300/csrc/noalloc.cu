@@ -115,10 +115,14 @@ extern "C" int vp_poisson_noalloc(void* cuda_stream, const double* rho_dev, int 
                                   double* field_energy_host, double* mass_host) {
   if (!rho_dev || !E_dev || nx < 1 || !(dx > 0)) return VP_EINVAL;
   if (nx > 14) return VP_ECAPACITY;  // 2^nx beyond the static scratch (16384 points)
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  // the scratch address is the current device's: the stream must be on it
+  int cur = 0, sdev = 0;
+  if (cudaGetDevice(&cur) != cudaSuccess || cudaStreamGetDevice(st, &sdev) != cudaSuccess) return VP_ECUDA;
+  if (sdev != cur) return VP_EINVAL;
   double* scratch = nullptr;
   const int s = scratch_for_current_device(&scratch);
   if (s != VP_OK) return s;
-  cudaStream_t st = (cudaStream_t)cuda_stream;
   k_poisson_noalloc<<<1, 256, 0, st>>>(rho_dev, 1 << nx, dx, E_dev, scratch, scratch + kMaxN);
   if (cudaGetLastError() != cudaSuccess) return VP_ECUDA;
   if (field_energy_host || mass_host) {

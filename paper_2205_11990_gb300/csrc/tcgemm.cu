@@ -316,13 +316,8 @@ size_t tc_smem_bytes(int bn) {
 template <bool BF16, int BN>
 int launch_tc(vp_ctx* ctx, const CUtensorMap& ta, const CUtensorMap& tb, int M, int N, int kblocks, double alpha,
               double* C, int ldc) {
-  static std::once_flag once;
-  static cudaError_t attr_err = cudaSuccess;
-  std::call_once(once, [] {
-    attr_err = cudaFuncSetAttribute(k_tc_gemm<BF16, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)tc_smem_bytes(BN));
-  });
-  VP_CUDA(ctx, attr_err);
+  static AttrOnce attr;  // per device
+  VP_TRY(attr.ensure(ctx, (const void*)k_tc_gemm<BF16, BN>, (int)tc_smem_bytes(BN), false));
   dim3 grid((N + BN - 1) / BN, (M + 127) / 128);
   ctx->launches++;
   k_tc_gemm<BF16, BN><<<grid, 128, tc_smem_bytes(BN), ctx->stream>>>(ta, tb, M, N, kblocks, alpha, C, ldc,

@@ -31,10 +31,10 @@ ERRORS = {1: "VP_EINVAL", 2: "VP_ENOMEM", 3: "VP_ECAPACITY", 4: "VP_ECUDA", 5: "
           6: "VP_ENUMERIC", 7: "VP_ECFL", 8: "VP_EBUSY", 9: "VP_EIO"}
 
 EXPORTS = [
-    "vp_ctx_create", "vp_ctx_destroy", "vp_last_error", "vp_kernel_launches", "vp_profile_enable",
+    "vp_ctx_create", "vp_ctx_destroy", "vp_last_error", "vp_ctx_set_wait_limit", "vp_kernel_launches", "vp_profile_enable",
     "vp_profile_read", "vp_profile_trace",
     "mps_create", "mps_create_cores", "mps_destroy", "mps_num_sites", "mps_bonds", "mps_get_cores",
-    "mps_to_dense", "mps_to_grid", "mps_save", "mps_load",
+    "mps_to_dense", "mps_to_grid", "mps_save", "mps_load", "mps_file_info",
     "mpo_create_vp", "mpo_create_vlasov", "mpo_create_cores", "mpo_destroy", "mpo_num_sites", "mpo_bonds",
     "mpo_to_dense",
     "mps_apply_mpo", "mps_axpby", "mps_compress", "mps_compress_modified", "vp_density", "vp_poisson", "vp_poisson_noalloc", "vp_gemm",
@@ -112,6 +112,7 @@ def load():
         "vp_ctx_create": (I, [P, ALLOC_FN, FREE_FN, P, C.POINTER(P)]),
         "vp_ctx_destroy": (I, [P]),
         "vp_last_error": (C.c_char_p, [P]),
+        "vp_ctx_set_wait_limit": (I, [P, C.c_longlong]),
         "vp_kernel_launches": (C.c_int64, [P]),
         "vp_profile_enable": (I, [P, I]),
         "vp_profile_read": (I, [P, I, DP, C.POINTER(C.c_int64), DP]),
@@ -126,6 +127,7 @@ def load():
         "mps_to_grid": (I, [P, P, C.POINTER(CLayout), DP]),
         "mps_save": (I, [P, P, C.c_char_p]),
         "mps_load": (I, [P, C.c_char_p, C.POINTER(P)]),
+        "mps_file_info": (I, [C.c_char_p, IP, IP, C.POINTER(S)]),
         "mpo_create_vp": (I, [P, C.POINTER(CLayout), I, C.POINTER(P)]),
         "mpo_create_vlasov": (I, [P, C.POINTER(CLayout), DP, D, C.POINTER(P)]),
         "mpo_create_cores": (I, [P, I, IP, DP, C.POINTER(P)]),
@@ -169,6 +171,19 @@ def load():
     return lib
 
 
+def mps_file_info(path: str):
+    """Validate a checkpoint file (host only, no device): (n, bond ranks,
+    payload elements); raises VpError(VP_EIO) on a malformed file."""
+    lib = load()
+    n = C.c_int(0)
+    ranks = np.zeros(65, dtype=np.int32)
+    elems = C.c_size_t(0)
+    st = lib.mps_file_info(os.fsencode(path), C.byref(n), _ip(ranks), C.byref(elems))
+    if st != 0:
+        raise VpError(st, f"mps_file_info: {path}")
+    return n.value, [int(r) for r in ranks[: n.value + 1]], elems.value
+
+
 def _dp(a: np.ndarray):
     return a.ctypes.data_as(C.POINTER(C.c_double))
 
@@ -192,10 +207,17 @@ class Context:
         self.torch = torch
         self.device = torch.cuda.current_device()
         self.stream = torch.cuda.current_stream()
+        # allocation budget for failure-injection tests: None = unlimited,
+        # else the number of further device allocations that may succeed
+        self._budget = budget = [None]
         if use_torch_allocator:
             dev, stream = self.device, self.stream
 
             def _alloc(nbytes, _user):
+                if budget[0] is not None:
+                    if budget[0] <= 0:
+                        return None
+                    budget[0] -= 1
                 try:
                     return torch.cuda.caching_allocator_alloc(int(nbytes), dev, stream)
                 except RuntimeError:
@@ -219,6 +241,15 @@ class Context:
             h = self.h if ctx == "self" else None
             msg = self.lib.vp_last_error(h).decode() if h is not None else "context creation failed"
             raise VpError(code, msg)
+
+    def set_alloc_budget(self, n):
+        """Let only the next n device allocations succeed (None: no limit).
+        Failure injection on the host: the allocator hook returns NULL."""
+        self._budget[0] = n
+
+    def set_wait_limit(self, clocks: int):
+        """SM clocks a device-side wait spins before giving up (0: default)."""
+        self._check(self.lib.vp_ctx_set_wait_limit(self.h, int(clocks)))
 
     @property
     def kernel_launches(self) -> int:

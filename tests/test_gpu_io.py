@@ -96,6 +96,7 @@ def test_malformed_files_rejected(ctx, tmp_path):
         "truncated": raw[:-8],
         "trailing": raw + b"\0" * 8,
         "rank": raw[:16] + np.array([2], dtype="<i4").tobytes() + raw[20:],
+        "inflated": raw[:20] + np.array([1 << 20], dtype="<i4").tobytes() + raw[24:],
     }
     for name, data in cases.items():
         p = str(tmp_path / f"{name}.mps")

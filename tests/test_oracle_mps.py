@@ -92,6 +92,38 @@ def test_choose_rank_rules():
     assert r == 1 and abs(e - 1e-3 / np.hypot(3.0, 1e-3)) < 1e-15
 
 
+def test_tie_window_edges():
+    # the tie window is a relative gap of TIE_REL between the last kept and
+    # the first dropped value: just outside it the chi cut stands, just
+    # inside it the pair is dropped as one cluster
+    w = S.TIE_REL
+    for chi in (2, 3):
+        top = [1.0, 0.7, 0.5][:chi - 1]
+        outside = np.array(top + [0.25, 0.25 * (1 - 2 * w), 0.01])
+        inside = np.array(top + [0.25, 0.25 * (1 - 0.5 * w), 0.01])
+        assert S.choose_rank(outside, chi, 0.0)[0] == chi
+        assert S.choose_rank(inside, chi, 0.0)[0] == chi - 1
+    # a cluster of three within the window moves the cut to its start
+    s = np.array([1.0, 0.5, 0.5 * (1 - 0.3 * w), 0.5 * (1 - 0.6 * w), 0.1])
+    assert S.choose_rank(s, 3, 0.0)[0] == 1
+    # the tolerance cut obeys the same rule: tol lands between a near-equal
+    # pair (tail of the pair above tol, the last value alone below it)
+    s = np.array([1.0, 1e-3, 1e-3 * (1 - 0.5 * w), 1e-12])
+    assert S.choose_rank(s, 10, 1e-9)[0] == 3
+    s2 = np.array([1.0, 1e-3, 1e-3 * (1 - 0.5 * w)])
+    assert S.choose_rank(s2, 2, 0.0)[0] == 1
+    assert S.choose_rank(s2, 2, 0.0)[1] > 1e-3
+
+
+def test_tie_stats_count_the_rule():
+    S.TIE_STATS.update(cuts=0, fired=0, min_gap=float("inf"))
+    S.choose_rank(np.array([1.0, 0.3, 0.3, 0.1]), 2, 0.0)       # fires
+    S.choose_rank(np.array([1.0, 0.5, 0.25, 0.1]), 2, 0.0)      # cut with gap 0.5
+    S.choose_rank(np.array([1.0, 0.5]), 5, 0.0)                # keeps all: no cut
+    assert S.TIE_STATS["cuts"] == 2 and S.TIE_STATS["fired"] == 1
+    assert S.TIE_STATS["min_gap"] == 0.5
+
+
 def test_entanglement_entropy_closed_forms():
     # maximally entangled: r equal values -> log2 r; product state -> 0
     assert abs(S.entanglement_entropy(np.ones(8), 8) - 3.0) < 1e-14
