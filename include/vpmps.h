@@ -370,6 +370,49 @@ double vp_sim_flops(const vp_sim* sim);
 int vp_run(vp_ctx* ctx, const vp_layout* layout, const vp_config* cfg, const double* f0_host,
            int nsteps, double* fT_host, vp_record* records);
 
+/* -------------------------------------------- lockstep groups of sims */
+
+/* One RK4-C1 step of many independent simulations at once (no counterpart in
+ * the paper: the batching layer around its time stepper).  Every kernel
+ * launch of a group step serves all members at the same position of the
+ * step -- the MPO x MPS contractions and sums of every site (SI
+ * "Matrix-vector multiplication", "Addition"), the Householder QR and the
+ * preconditioned Jacobi SVD of the same sweep site of every member's
+ * compressions (SI "Canonicalization and Compression"), the densities,
+ * Poisson solves and field MPS (SI "Integration", "Dot Product") -- and the
+ * host waits once per SVD site for the kept ranks of all members instead of
+ * once per member.  Members may differ in grid bits, mapping, chi, tol and
+ * dt; members with fewer sites simply sit out the sweep positions they do not
+ * have.  Each member runs the kernel variants and launch geometries of its
+ * own vp_step, so its result does not depend on the group.
+ *
+ * Members are sims created with vp_sim_create on the group's context with
+ * cfg.streams = 1, compression level C1 (cfg.level 0 or 1), the plain sweeps
+ * (VP_COMPRESS_SWEEPS), precision VP_PREC_FP64 or VP_PREC_FP32_CONTRACT and
+ * tol, e_tol >= 1e-13.  A group holds no reference to a member's memory
+ * beyond its workspaces: remove a sim before destroying it. */
+typedef struct vp_group vp_group;
+/* Errors: VP_EINVAL (max_members outside 1..4096), VP_ENOMEM, VP_ECUDA. */
+int vp_group_create(vp_ctx* ctx, int max_members, vp_group** out);
+/* Append a member (member index = number of members before the call).
+ * Errors: VP_EINVAL (sim not eligible, see above, or already a member),
+ * VP_ECAPACITY (group full). */
+int vp_group_add(vp_group* g, vp_sim* sim);
+/* Remove a member; the members after it move down one index. */
+int vp_group_remove(vp_group* g, vp_sim* sim);
+int vp_group_size(const vp_group* g);
+/* Advance every running member by one step.  records[i] (host, size() or
+ * NULL) receives member i's a11 diagnostics as vp_step would; status[i]
+ * (host, size() or NULL) its state: VP_OK, or the error that stopped it --
+ * VP_ENUMERIC (NaN/Inf or a Jacobi that did not converge in its own
+ * arithmetic) or VP_ETIMEOUT (a device wait of its own gave up).  A member
+ * that failed stops there, the others go on, and it stays stopped (its state
+ * undefined) until removed.  The return value is VP_OK unless the group's
+ * own launches failed (VP_ENOMEM, VP_ECUDA, ...), which stops every member.
+ * Synchronises the context's stream. */
+int vp_group_step(vp_group* g, vp_record* records, int* status);
+int vp_group_destroy(vp_group* g);
+
 /* ------------------------------------------------ several species (f_s) */
 
 /* Species s of a multi-species run (Problem Statement: the Vlasov equation of

@@ -15,6 +15,7 @@
 
 #include "common.cuh"
 #include "mpo_build.hpp"
+#include "sim.hpp"
 
 using vp::DevBuf;
 
@@ -187,9 +188,9 @@ int sync_status(vp_ctx* ctx) {
 }
 
 // ------------------------------------------------------------ MPS helpers
-static size_t core_elems(const mps_t* m, int k) { return (size_t)m->r[k] * 2 * m->r[k + 1]; }
+size_t core_elems(const mps_t* m, int k) { return (size_t)m->r[k] * 2 * m->r[k + 1]; }
 
-static int mps_init(vp_ctx* ctx, mps_t* m, int n) {
+int mps_init(vp_ctx* ctx, mps_t* m, int n) {
   m->ctx = ctx;
   m->n = n;
   m->r.assign(n + 1, 1);
@@ -197,7 +198,7 @@ static int mps_init(vp_ctx* ctx, mps_t* m, int n) {
   return VP_OK;
 }
 
-static void mps_free(mps_t* m) {
+void mps_free(mps_t* m) {
   for (auto& b : m->core) release(m->ctx, b);
   m->core.clear();
 }
@@ -226,10 +227,6 @@ static int read_rank(vp_ctx* ctx, int* r, double* err) {
   return VP_OK;
 }
 
-// Flop counters of the factorisations (algorithmic counts).
-struct Flops {
-  double qr = 0, formq = 0, gemm = 0, jacobi = 0;
-};
 static thread_local Flops* g_flops = nullptr;
 static thread_local double* g_entropy = nullptr;  // per-bond entanglement entropy of the compression running
 
@@ -646,14 +643,14 @@ static int to_dense_dev(vp_ctx* ctx, const mps_t* s, DevBuf& out) {
 }
 
 // ------------------------------------------------------------ density
-static bool xdesc(const vp_layout* L) { return L->mapping == VP_SEQ_S2; }
-static bool vdesc(const vp_layout* L) { return L->mapping == VP_SEQ_S3; }
-static bool interleaved(const vp_layout* L) {
+bool xdesc(const vp_layout* L) { return L->mapping == VP_SEQ_S2; }
+bool vdesc(const vp_layout* L) { return L->mapping == VP_SEQ_S3; }
+bool interleaved(const vp_layout* L) {
   return L->mapping == VP_INTERLEAVED || L->mapping == VP_INTERLEAVED_GROUPED;
 }
-static bool grouped(const vp_layout* L) { return L->mapping == VP_INTERLEAVED_GROUPED; }
+bool grouped(const vp_layout* L) { return L->mapping == VP_INTERLEAVED_GROUPED; }
 
-static std::vector<int> site_dims(const vp_layout* L) {
+std::vector<int> site_dims(const vp_layout* L) {
   std::vector<int> d;
   if (!interleaved(L)) {
     for (int b = 0; b < L->nx; ++b) d.push_back(0);
@@ -739,7 +736,7 @@ static int density(vp_ctx* ctx, const vp_layout* L, const mps_t* f, double* rho)
   return VP_OK;
 }
 
-static bool layout_ok(const vp_layout* L) {
+bool layout_ok(const vp_layout* L) {
   return L && L->nx >= 2 && L->nv >= 2 && L->nx <= 14 && L->nv <= 14 &&
          L->mapping >= VP_SEQ && L->mapping <= VP_INTERLEAVED_GROUPED &&
          (L->mapping != VP_INTERLEAVED_GROUPED || L->nx == L->nv) && L->xmax > L->xmin && L->vmax > L->vmin &&
@@ -1070,8 +1067,12 @@ static int mpo_from_chain(vp_ctx* ctx, const Chain& c, mpo_t** out) {
   return VP_OK;
 }
 
-static double grid_dx(const vp_layout* L) { return (L->xmax - L->xmin) / (double)(1 << L->nx); }
-static double grid_dv(const vp_layout* L) { return (L->vmax - L->vmin) / (double)((1 << L->nv) - 1); }
+}  // extern "C"
+namespace vp {
+double grid_dx(const vp_layout* L) { return (L->xmax - L->xmin) / (double)(1 << L->nx); }
+double grid_dv(const vp_layout* L) { return (L->vmax - L->vmin) / (double)((1 << L->nv) - 1); }
+}  // namespace vp
+extern "C" {
 
 int mpo_create_vp(vp_ctx* ctx, const vp_layout* L, int kind, mpo_t** out) {
   if (!ctx || !out || !layout_ok(L)) return fail(ctx, VP_EINVAL, "mpo_create_vp: bad argument");
@@ -1263,28 +1264,6 @@ int vp_poisson(vp_ctx* ctx, const double* rho, int nx, double dx, double* E, dou
 }  // extern "C"
 
 // ====================================================================== stepper
-struct vp_sim {
-  vp_ctx* ctx = nullptr;
-  vp_layout lay{};
-  vp_config cfg{};
-  std::vector<int> dims;
-  mps_t f, fi, acc, wa, wb, em;
-  mps_t kd, ku, kt;              // derivative and its two terms (levels C4, C5)
-  mpo_t LT;                      // field term alone (level C5)
-  Chain U;                       // static upwind part (host copy, for bonds)
-  std::vector<DevBuf> Ud;        // device cores of U
-  Chain Dv;                      // zero-gradient v derivative chain
-  std::vector<DevBuf> Dvd;
-  mpo_t L;                       // operator of the current stage
-  DevBuf rho, E, evec;
-  double t = 0.0;
-  Flops flops;
-  std::vector<double> entropy;  // per-bond EE of the last final compression
-  vp_ctx* ctxB = nullptr;  // second stream: the f_{i+1} compressions run beside the acc ones
-  cudaEvent_t evA = nullptr, evB = nullptr;
-  double ecoef = 1.0;      // -q/m of the species: the field term is diag(ecoef E) (x) D_v
-  int coop_div = 1;        // runs sharing the GPU at once: grid-cooperative QRs get num_sms / (2 coop_div)
-};
 
 namespace vp {
 

@@ -172,6 +172,13 @@ int launch_to_colmajor(vp_ctx* ctx, const double* A, int m, int n, double* out);
 // In-place Householder QR of the column-major m x n matrix A (lda = m):
 // R in the upper triangle, reflectors below, tau[min(m,n)].
 int launch_qr_factor(vp_ctx* ctx, double* A, int m, int n, double* tau, double* vbuf);
+// Kernel that factors an m x n matrix (shape and device only).
+enum { QR_NONE = 0, QR_WIDE, QR_CDW, QR_CL, QR_GRID };
+struct QRPlan {
+  int kind;
+  int cs;  // CTAs per cluster (QR_CDW, QR_CL)
+};
+QRPlan qr_plan(const vp_ctx* ctx, int m, int n);
 // Q (m x p, p = min(m,n)) written row-major from the factored A.
 int launch_qr_formq(vp_ctx* ctx, const double* A, int m, int n, const double* tau, double* Q);
 // Upper-trapezoidal R (p x n) of the factored A, written row-major.
@@ -209,6 +216,9 @@ int launch_gemm_r(vp_ctx* ctx, int M, int N, int K, const double* Acm, int lda, 
 // largest (tol >= 1e-13), so the double-word kernel, which leaves rows under
 // 1e-15 of the largest unrotated, may be used.
 int launch_jacobi_rows(vp_ctx* ctx, double* X, int b, int c, double* J, bool floor_ok);
+// The same on a given stream with given status words.
+int jacobi_rows_on(vp_ctx* ctx, cudaStream_t stream, DevStatus* status, double* X, int b, int c, double* J,
+                   bool floor_ok);
 // Largest cluster (16 or 8 CTAs, one per SM) the cluster-resident kernels
 // can use on this device; 0 if none.
 int probe_cluster_size();
@@ -263,6 +273,93 @@ struct ETermSite {
 // Fill L core = blockdiag(U core, E-term core) (first/last concatenation).
 int launch_assemble_site(vp_ctx* ctx, const double* U, int ul, int ur, const ETermSite& e, int first,
                          int last, double* out, int ol, int orr);
+// ------------------------------------------------------------ batched launches
+// One launch serves up to kMaxBatch independent problems of one kind: the
+// same sweep position of several compressions, or the same step of several
+// simulations.  The per-problem arguments travel in the kernel's parameter
+// block (Pack), the problem index is a grid coordinate, and every problem
+// runs the kernel variant and launch geometry its own single launch would
+// use, so its arithmetic does not depend on the batch.  Launchers take the
+// problems as a vector, split it into packs and, where the single path picks
+// a kernel variant by shape, into one launch per variant; problems that no
+// batched kernel serves (factors beyond a cluster's shared memory) run one
+// by one.  Per-problem scratch comes from a BScratch owned by the caller.
+constexpr int kMaxBatch = 32;
+template <class A>
+struct Pack {
+  A a[kMaxBatch];
+};
+
+// Several jobs of one launcher call may name the same BScratch (the two Q
+// formations of an SVD site, its output GEMMs): each takes its own slot.
+constexpr int kScratchSlots = 4;
+struct BScratch {
+  DevBuf wq, wr;                  // wide QR: Q of the square block, R2^T
+  DevBuf qrv, qrc;                // grid QR: published reflectors, columns beyond shared memory
+  DevBuf fq[kScratchSlots];       // Q formation: double-word reflectors
+  DevBuf qscr[kScratchSlots];     // Q formation: column scratch (m > 512)
+  DevBuf split[kScratchSlots];    // GEMM split-K partial products
+  DevStatus* st = nullptr;        // status words of the problem (device)
+};
+void release_scratch(vp_ctx* ctx, BScratch& s);
+
+struct BColMajor { const double* A; int m, n; double* out; };
+struct BQR { double* A; int m, n; double* tau; double* vbuf; BScratch* s; };
+struct BFormQ { const double* A; int m, n; const double* tau; double* Q; BScratch* s; };
+struct BGetR { const double* A; int m, n; double* R; };
+enum { BG_AB = 0, BG_ABT = 1, BG_RB = 2 };  // A row-major x B row-major / B^T given / triu(A col-major) x B
+struct BGemm {
+  int kind;  // BG_*
+  int fp32;  // FP32 contraction mode
+  int M, N, K;
+  double alpha;
+  const double* A; int lda;
+  const double* B; int ldb;
+  double* C; int ldc;
+  BScratch* s;
+};
+struct BNormOrder { const double* M; int m, c, by_cols; int* piv; };
+struct BGather { const double* M; int m, c; const int* piv; int tall; double* out; };
+struct BLowerUpper { const double* R; int q; double* L; };
+struct BCopy { const double* src; double* dst; size_t n; };
+struct BJacobi { double* X; int b, c; double* J; DevStatus* st; };
+struct BSelect {
+  const double* X; int b, c, chi; double tol; int* perm; double* sigma; int* d_rank; double* d_err; DevStatus* st;
+};
+struct BSvdOut { const double* X; const double* J; int b, c, r; const int* perm; const double* sigma; double* Vt; double* W; };
+struct BSvdOutWide { const double* X; const double* J; int b, r; const int* perm; double* U; double* Wv; };
+struct BScatter { const double* Y; int rows, cols_n; const int* piv; int cols; double* out; };
+
+int blaunch_to_colmajor(vp_ctx* ctx, cudaStream_t st, const std::vector<BColMajor>& v);
+int blaunch_qr_factor(vp_ctx* ctx, cudaStream_t st, const std::vector<BQR>& v);
+int blaunch_qr_formq(vp_ctx* ctx, cudaStream_t st, const std::vector<BFormQ>& v);
+int blaunch_qr_getr(vp_ctx* ctx, cudaStream_t st, const std::vector<BGetR>& v);
+int blaunch_gemm(vp_ctx* ctx, cudaStream_t st, const std::vector<BGemm>& v);
+int blaunch_norm_order(vp_ctx* ctx, cudaStream_t st, const std::vector<BNormOrder>& v);
+int blaunch_gather_cm(vp_ctx* ctx, cudaStream_t st, const std::vector<BGather>& v);
+int blaunch_lower_from_upper(vp_ctx* ctx, cudaStream_t st, const std::vector<BLowerUpper>& v);
+// Jacobi of truncating compressions (tol >= 1e-13: the double-word kernel).
+int blaunch_jacobi(vp_ctx* ctx, cudaStream_t st, const std::vector<BJacobi>& v);
+int blaunch_select(vp_ctx* ctx, cudaStream_t st, const std::vector<BSelect>& v);
+int blaunch_svd_outputs(vp_ctx* ctx, cudaStream_t st, const std::vector<BSvdOut>& v);
+int blaunch_svd_outputs_wide(vp_ctx* ctx, cudaStream_t st, const std::vector<BSvdOutWide>& v);
+int blaunch_scatter(vp_ctx* ctx, cudaStream_t st, const std::vector<BScatter>& v);
+
+// mpsops.cu
+struct BSiteSum { SiteSum s; double* out; int ol, orr; };
+struct BPhysSum { const double* core; int rl, rr; double* T; };
+struct BScale { double* x; size_t n; double s; };
+struct BPoisson { const double* rho; int N; double dx; double* E; double* we; };
+struct BAssemble { const double* U; int ul, ur; ETermSite e; int first, last; double* out; int ol, orr; };
+struct BPermute { const double* f; int nx, nv, mapping; double* out; int inverse; };
+int blaunch_copy(vp_ctx* ctx, cudaStream_t st, const std::vector<BCopy>& v);
+int blaunch_site_sum(vp_ctx* ctx, cudaStream_t st, const std::vector<BSiteSum>& v);
+int blaunch_phys_sum(vp_ctx* ctx, cudaStream_t st, const std::vector<BPhysSum>& v);
+int blaunch_scale(vp_ctx* ctx, cudaStream_t st, const std::vector<BScale>& v);
+int blaunch_poisson(vp_ctx* ctx, cudaStream_t st, const std::vector<BPoisson>& v);
+int blaunch_assemble(vp_ctx* ctx, cudaStream_t st, const std::vector<BAssemble>& v);
+int blaunch_permute(vp_ctx* ctx, cudaStream_t st, const std::vector<BPermute>& v);
+
 // MPO -> dense (small n), and MPS eval helpers
 int launch_mpo_dense_step(vp_ctx* ctx, const double* T, int rows, int cols, int w, const double* core,
                           int wr, double* out);

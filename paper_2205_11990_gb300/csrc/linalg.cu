@@ -84,10 +84,10 @@ struct GridSync {
   }
 };
 
-static int coop_launch(vp_ctx* ctx, const void* fn, int blocks, int threads, void** args, size_t smem,
-                       const char* what) {
+static int coop_launch(vp_ctx* ctx, cudaStream_t stream, const void* fn, int blocks, int threads, void** args,
+                       size_t smem, const char* what) {
   ctx->launches++;
-  cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(threads), args, smem, ctx->stream);
+  cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(threads), args, smem, stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, what);
   return VP_OK;
 }
@@ -350,7 +350,7 @@ __global__ void __launch_bounds__(kThreads) k_qr_factor_dw(double* A, int m, int
 // distributed shared memory; the other warps, and every other CTA, apply H_j
 // (read from the local incoming buffer j % 2) to their columns right of j+1.
 // One hardware cluster barrier per step orders the pushes.
-__global__ void __launch_bounds__(kThreads) k_qr_factor_cdw(double* A, int m, int n, double* tau) {
+__device__ __forceinline__ void k_qr_factor_cdw_body(double* A, int m, int n, double* tau) {
   cg::cluster_group cl = cg::this_cluster();
   const int CS = (int)cl.num_blocks(), rank = (int)cl.block_rank();
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -448,6 +448,7 @@ __global__ void __launch_bounds__(kThreads) k_qr_factor_cdw(double* A, int m, in
     for (int i = lane; i < m; i += 32) a[i] = (k < p && i > k) ? dw_to(c[i]) : dw_to(c[i]) * sc;
   }
 }
+__global__ void __launch_bounds__(kThreads) k_qr_factor_cdw(double* A, int m, int n, double* tau) { k_qr_factor_cdw_body(A, m, n, tau); }
 
 // Cluster-resident double-word QR, pull model (factors up to a 16-CTA
 // cluster's shared memory).  Column k lives in CTA k % CS (slot k / CS) as
@@ -464,7 +465,7 @@ __global__ void __launch_bounds__(kThreads) k_qr_factor_cdw(double* A, int m, in
 // everything.  The per-row arithmetic is that of k_qr_factor_dw; only the
 // order in which the critical column's partial sums are added differs.
 template <int NT, int CW>
-__global__ void __launch_bounds__(NT) k_qr_factor_cl(double* A, int m, int n, double* tau) {
+__device__ __forceinline__ void k_qr_factor_cl_body(double* A, int m, int n, double* tau) {
   constexpr int NW = NT / 32;
   static_assert(CW >= 1 && CW < NW, "critical warps must leave bulk warps");
   cg::cluster_group cl = cg::this_cluster();
@@ -608,6 +609,8 @@ __global__ void __launch_bounds__(NT) k_qr_factor_cl(double* A, int m, int n, do
     for (int i = lane; i < m; i += 32) a[i] = (k < p && i > k) ? dw_to(c[i]) : dw_to(c[i]) * sc;
   }
 }
+template <int NT, int CW>
+__global__ void __launch_bounds__(NT) k_qr_factor_cl(double* A, int m, int n, double* tau) { k_qr_factor_cl_body<NT, CW>(A, m, n, tau); }
 
 static size_t qr_cl_smem(int m, int n, int CS) {
   const size_t nmax = (size_t)(n + CS - 1) / CS;
@@ -646,53 +649,100 @@ static size_t qr_cdw_smem(int m, int n, int CS) {
   return (nmax * m + 2 * (size_t)m + 2) * sizeof(dw) + nmax * sizeof(int);
 }
 
-int launch_qr_factor(vp_ctx* ctx, double* A, int m, int n, double* tau, double* vbuf) {
-  const int p = std::min(m, n);
-  if (p <= 0) return VP_OK;
-  // Factors more than twice as wide as tall: the m reflectors depend on the
-  // leading m columns alone, so that square block (contiguous in the
-  // column-major layout) is factored in place by the square-factor kernels,
-  // Q is formed from its reflectors, and the rest of R is one FP64 GEMM,
-  // R2 = Q^T A2 (stored as R2^T = A2^T Q, which is A2's column-major layout),
-  // instead of a cooperative grid that applies every reflector to all n
-  // columns one column step at a time.  Same LAPACK layout on output.
-  if (n > 2 * m && m >= 2) {
-    VP_TRY(launch_qr_factor(ctx, A, m, m, tau, vbuf));
-    VP_TRY(reserve(ctx, ctx->w_wq, (size_t)m * m));
-    VP_TRY(launch_qr_formq(ctx, A, m, m, tau, ctx->w_wq.p));
-    const size_t rest = (size_t)(n - m) * m;
-    VP_TRY(reserve(ctx, ctx->w_wr, rest));
-    const int prec = ctx->precision;  // R is part of the factorisation: FP64 in every mode
-    ctx->precision = VP_PREC_FP64;
-    const int st = launch_gemm(ctx, n - m, m, m, 1.0, A + (size_t)m * m, m, ctx->w_wq.p, m, ctx->w_wr.p, m);
-    ctx->precision = prec;
-    VP_TRY(st);
-    return launch_copy(ctx, ctx->w_wr.p, A + (size_t)m * m, rest);
-  }
-  // Measured per column on GB300 (the step's shapes): up to ~4e3 elements
-  // the push-model cluster kernel (2.5 us); above, the pull-model kernel with
-  // four critical warps (128x128 2.9 us, 368x128 4.2, 464x184 4.8, 512x341
-  // 5.9, 682x132 6.1, 1088x64 7.3, against 3.7-17.7 for the grid kernel):
-  // 8 CTAs, 16 for many columns (the column updates dominate), 4 for tall
-  // narrow ones (the reflector copies dominate); factors more than twice as
-  // wide as tall stay on the grid kernel (64x1024: 3.5 us against 4.8).  The
-  // dispatch depends on the shape only, so results do not depend on the
-  // context.
+// Which kernel factors an m x n matrix.  Measured per column on GB300 (the
+// step's shapes): up to ~4e3 elements the push-model cluster kernel (2.5 us);
+// above, the pull-model kernel with four critical warps (128x128 2.9 us,
+// 368x128 4.2, 464x184 4.8, 512x341 5.9, 682x132 6.1, 1088x64 7.3, against
+// 3.7-17.7 for the grid kernel): 8 CTAs, 16 for many columns (the column
+// updates dominate), 4 for tall narrow ones (the reflector copies dominate);
+// the grid kernel takes what no cluster's shared memory holds.  Factors more
+// than twice as wide as tall: the m reflectors depend on the leading m
+// columns alone, so that square block (contiguous in the column-major layout)
+// is factored in place, Q is formed from its reflectors, and the rest of R is
+// one FP64 GEMM, R2 = Q^T A2 (stored as R2^T = A2^T Q, which is A2's
+// column-major layout), instead of applying every reflector to all n columns
+// one column step at a time.  The choice depends on the shape and the device
+// only, so that results do not depend on the context or on the batch.
+QRPlan qr_plan(const vp_ctx* ctx, int m, int n) {
+  if (std::min(m, n) <= 0) return {QR_NONE, 0};
+  if (n > 2 * m && m >= 2) return {QR_WIDE, 0};
   if (ctx->cluster_size > 1 && (long long)m * n <= 4096) {
     int cs = 2;
     while (cs < std::min(ctx->cluster_size, 4) && cs * 8 < n) cs *= 2;
-    const size_t need = qr_cdw_smem(m, n, cs);
-    if (need <= 200 * 1024) {
+    if (qr_cdw_smem(m, n, cs) <= 200 * 1024) return {QR_CDW, cs};
+  }
+  if (ctx->cluster_size >= 8 && 2 * m >= n) {
+    int cs = n >= 300 ? 16 : (n <= 64 && m >= 512 ? 4 : 8);
+    while (cs < ctx->cluster_size && qr_cl_smem(m, n, cs) > 200 * 1024) cs *= 2;
+    if (cs <= ctx->cluster_size && qr_cl_smem(m, n, cs) <= 200 * 1024) return {QR_CL, cs};
+  }
+  return {QR_GRID, 0};
+}
+
+// The cooperative grid kernels, for factors beyond a cluster's shared memory:
+// enough blocks that each owns a few columns, never more than one per SM.
+// st, qrv, qrc: the status words and scratch of the caller (context or batch
+// problem).
+int qr_factor_grid(vp_ctx* ctx, cudaStream_t stream, DevStatus* st, DevBuf& qrv, DevBuf& qrc, double* A, int m,
+                   int n, double* tau, double* vbuf) {
+  const int p = std::min(m, n);
+  const int cap = ctx->coop_cap > 0 ? std::min(ctx->coop_cap, ctx->num_sms) : ctx->num_sms;
+  const int blocks = std::min(cap, std::max(1, n / 2));
+  if (blocks > 1) {
+    // the same double-word arithmetic whichever the storage, so that the
+    // result does not depend on the context's block cap
+    const int nmax = (n + blocks - 1) / blocks;
+    const size_t smem = (size_t)nmax * m * sizeof(dw) + (size_t)nmax * sizeof(int);
+    static AttrOnce qattr;
+    VP_TRY(qattr.ensure(ctx, (const void*)k_qr_factor_dw, 200 * 1024, false));
+    VP_TRY(reserve(ctx, qrv, (size_t)m * p + p + 8));
+    dw* V = reinterpret_cast<dw*>(qrv.p);
+    dw* T = V + (size_t)m * p;
+    dw* gcols = nullptr;
+    int* gexp = nullptr;
+    size_t dyn = smem;
+    if (smem > 200 * 1024) {
+      VP_TRY(reserve(ctx, qrc, (size_t)m * n + n / 2 + 8));
+      gcols = reinterpret_cast<dw*>(qrc.p);
+      gexp = reinterpret_cast<int*>(gcols + (size_t)m * n);
+      dyn = 0;
+    }
+    void* args[] = {&A, &m, &n, &tau, &V, &T, &gcols, &gexp, &st};
+    return coop_launch(ctx, stream, (const void*)k_qr_factor_dw, blocks, kThreads, args, dyn, "qr_factor_dw");
+  }
+  void* args[] = {&A, &m, &n, &tau, &vbuf, &st};
+  return coop_launch(ctx, stream, (const void*)k_qr_factor<GridSync>, blocks, kThreads, args, 0, "qr_factor");
+}
+
+int launch_qr_factor(vp_ctx* ctx, double* A, int m, int n, double* tau, double* vbuf) {
+  const QRPlan pl = qr_plan(ctx, m, n);
+  switch (pl.kind) {
+    case QR_NONE:
+      return VP_OK;
+    case QR_WIDE: {
+      VP_TRY(launch_qr_factor(ctx, A, m, m, tau, vbuf));
+      VP_TRY(reserve(ctx, ctx->w_wq, (size_t)m * m));
+      VP_TRY(launch_qr_formq(ctx, A, m, m, tau, ctx->w_wq.p));
+      const size_t rest = (size_t)(n - m) * m;
+      VP_TRY(reserve(ctx, ctx->w_wr, rest));
+      const int prec = ctx->precision;  // R is part of the factorisation: FP64 in every mode
+      ctx->precision = VP_PREC_FP64;
+      const int st = launch_gemm(ctx, n - m, m, m, 1.0, A + (size_t)m * m, m, ctx->w_wq.p, m, ctx->w_wr.p, m);
+      ctx->precision = prec;
+      VP_TRY(st);
+      return launch_copy(ctx, ctx->w_wr.p, A + (size_t)m * m, rest);
+    }
+    case QR_CDW: {
       static AttrOnce cattr;
       VP_TRY(cattr.ensure(ctx, (const void*)k_qr_factor_cdw, 200 * 1024, true));
       cudaLaunchConfig_t cfg = {};
       cudaLaunchAttribute at[1];
-      cfg.gridDim = dim3(cs);
+      cfg.gridDim = dim3(pl.cs);
       cfg.blockDim = dim3(kThreads);
-      cfg.dynamicSmemBytes = std::max<size_t>(need, 116 * 1024);  // one CTA of the cluster per SM
+      cfg.dynamicSmemBytes = std::max<size_t>(qr_cdw_smem(m, n, pl.cs), 116 * 1024);  // one CTA of the cluster per SM
       cfg.stream = ctx->stream;
       at[0].id = cudaLaunchAttributeClusterDimension;
-      at[0].val.clusterDim.x = cs;
+      at[0].val.clusterDim.x = pl.cs;
       at[0].val.clusterDim.y = 1;
       at[0].val.clusterDim.z = 1;
       cfg.attrs = at;
@@ -701,41 +751,11 @@ int launch_qr_factor(vp_ctx* ctx, double* A, int m, int n, double* tau, double* 
       VP_CUDA(ctx, cudaLaunchKernelEx(&cfg, k_qr_factor_cdw, A, m, n, tau));
       return VP_OK;
     }
+    case QR_CL:
+      return launch_qr_factor_cl(ctx, A, m, n, tau, pl.cs);
+    default:
+      return qr_factor_grid(ctx, ctx->stream, ctx->status, ctx->w_qrv, ctx->w_qrc, A, m, n, tau, vbuf);
   }
-  if (ctx->cluster_size >= 8 && 2 * m >= n) {  // very wide factors: the grid kernel is as fast
-    int cs = n >= 300 ? 16 : (n <= 64 && m >= 512 ? 4 : 8);
-    while (cs < ctx->cluster_size && qr_cl_smem(m, n, cs) > 200 * 1024) cs *= 2;
-    if (cs <= ctx->cluster_size && qr_cl_smem(m, n, cs) <= 200 * 1024)
-      return launch_qr_factor_cl(ctx, A, m, n, tau, cs);
-  }
-  // enough blocks that each owns a few columns, but never more than one per SM
-  const int cap = ctx->coop_cap > 0 ? std::min(ctx->coop_cap, ctx->num_sms) : ctx->num_sms;
-  const int blocks = std::min(cap, std::max(1, n / 2));
-  DevStatus* st = ctx->status;
-  if (blocks > 1) {
-    // the same double-word arithmetic whichever the storage, so that the
-    // result does not depend on the context's block cap
-    const int nmax = (n + blocks - 1) / blocks;
-    const size_t smem = (size_t)nmax * m * sizeof(dw) + (size_t)nmax * sizeof(int);
-    static AttrOnce qattr;
-    VP_TRY(qattr.ensure(ctx, (const void*)k_qr_factor_dw, 200 * 1024, false));
-    VP_TRY(reserve(ctx, ctx->w_qrv, (size_t)m * p + p + 8));
-    dw* V = reinterpret_cast<dw*>(ctx->w_qrv.p);
-    dw* T = V + (size_t)m * p;
-    dw* gcols = nullptr;
-    int* gexp = nullptr;
-    size_t dyn = smem;
-    if (smem > 200 * 1024) {
-      VP_TRY(reserve(ctx, ctx->w_qrc, (size_t)m * n + n / 2 + 8));
-      gcols = reinterpret_cast<dw*>(ctx->w_qrc.p);
-      gexp = reinterpret_cast<int*>(gcols + (size_t)m * n);
-      dyn = 0;
-    }
-    void* args[] = {&A, &m, &n, &tau, &V, &T, &gcols, &gexp, &st};
-    return coop_launch(ctx, (const void*)k_qr_factor_dw, blocks, kThreads, args, dyn, "qr_factor_dw");
-  }
-  void* args[] = {&A, &m, &n, &tau, &vbuf, &st};
-  return coop_launch(ctx, (const void*)k_qr_factor<GridSync>, blocks, kThreads, args, 0, "qr_factor");
 }
 
 // Q = H_0 ... H_{p-1} [I_p; 0] in double words: the reflectors (below the
@@ -743,7 +763,7 @@ int launch_qr_factor(vp_ctx* ctx, double* A, int m, int n, double* tau, double* 
 // once, then one warp per column k of Q applies H_k, ..., H_0 to e_k with
 // double-word dot products and updates (each step would otherwise be a chain
 // of FP64 FMAs at ~400 cycles apiece); Q is stored row-major (m x p).
-__global__ void k_reflectors_to_dw(const double* __restrict__ A, int m, int p, const double* __restrict__ tau,
+__device__ __forceinline__ void k_reflectors_to_dw_body(const double* __restrict__ A, int m, int p, const double* __restrict__ tau,
                                    dw* __restrict__ V, dw* __restrict__ T) {
   const size_t total = (size_t)m * p;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
@@ -752,8 +772,10 @@ __global__ void k_reflectors_to_dw(const double* __restrict__ A, int m, int p, c
     if (e < (size_t)p) T[e] = dw_from(tau[e]);
   }
 }
+__global__ void k_reflectors_to_dw(const double* __restrict__ A, int m, int p, const double* __restrict__ tau,
+                                   dw* __restrict__ V, dw* __restrict__ T) { k_reflectors_to_dw_body(A, m, p, tau, V, T); }
 
-__global__ void k_qr_formq_dw(const dw* __restrict__ V, int m, int p, const dw* __restrict__ T, dw* __restrict__ scratch,
+__device__ __forceinline__ void k_qr_formq_dw_body(const dw* __restrict__ V, int m, int p, const dw* __restrict__ T, dw* __restrict__ scratch,
                               double* __restrict__ Q) {
   const int lane = threadIdx.x & 31;
   const int k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -773,6 +795,8 @@ __global__ void k_qr_formq_dw(const dw* __restrict__ V, int m, int p, const dw* 
   }
   for (int i = lane; i < m; i += 32) Q[(size_t)i * p + k] = dw_to(q[i]);
 }
+__global__ void k_qr_formq_dw(const dw* __restrict__ V, int m, int p, const dw* __restrict__ T, dw* __restrict__ scratch,
+                              double* __restrict__ Q) { k_qr_formq_dw_body(V, m, p, T, scratch, Q); }
 
 // The same product with column k of Q held in registers (rows lane + 32 u,
 // u < R, for m <= 32 R): per reflector the R reflector entries of a lane are
@@ -781,7 +805,7 @@ __global__ void k_qr_formq_dw(const dw* __restrict__ V, int m, int p, const dw* 
 // Rows above the reflector's start hold zeros in V, which leave the sums and
 // the column unchanged.
 template <int R>
-__global__ void k_qr_formq_reg(const dw* __restrict__ V, int m, int p, const dw* __restrict__ T,
+__device__ __forceinline__ void k_qr_formq_reg_body(const dw* __restrict__ V, int m, int p, const dw* __restrict__ T,
                                double* __restrict__ Q) {
   const int lane = threadIdx.x & 31;
   const int k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -818,6 +842,9 @@ __global__ void k_qr_formq_reg(const dw* __restrict__ V, int m, int p, const dw*
     if (i < m) Q[(size_t)i * p + k] = dw_to(q[u]);
   }
 }
+template <int R>
+__global__ void k_qr_formq_reg(const dw* __restrict__ V, int m, int p, const dw* __restrict__ T,
+                               double* __restrict__ Q) { k_qr_formq_reg_body<R>(V, m, p, T, Q); }
 
 int launch_qr_formq(vp_ctx* ctx, const double* A, int m, int n, const double* tau, double* Q) {
   const int p = std::min(m, n);
@@ -844,13 +871,14 @@ int launch_qr_formq(vp_ctx* ctx, const double* A, int m, int n, const double* ta
   return check_launch(ctx, "qr_formq");
 }
 
-__global__ void k_qr_getr(const double* __restrict__ A, int m, int n, int p, double* __restrict__ R) {
+__device__ __forceinline__ void k_qr_getr_body(const double* __restrict__ A, int m, int n, int p, double* __restrict__ R) {
   const size_t total = (size_t)p * n;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
     const int j = (int)(e / n), k = (int)(e % n);
     R[e] = (j <= k) ? A[(size_t)k * m + j] : 0.0;
   }
 }
+__global__ void k_qr_getr(const double* __restrict__ A, int m, int n, int p, double* __restrict__ R) { k_qr_getr_body(A, m, n, p, R); }
 
 int launch_qr_getr(vp_ctx* ctx, const double* A, int m, int n, double* R) {
   const int p = std::min(m, n);
@@ -891,15 +919,15 @@ struct BTransposed {
   __device__ double operator()(int k, int n) const { return B[(size_t)n * ldb + k]; }
 };
 
-template <class ALoad, class BLoad, class T = double>
-__global__ void __launch_bounds__(256) k_gemm(int M, int N, int K, double alpha, ALoad a, BLoad bl,
-                                              double* __restrict__ C, int ldc, int kslice, size_t slice_stride) {
+template <class ALoad, class BLoad, class T>
+__device__ __forceinline__ void gemm_body(int M, int N, int K, double alpha, ALoad a, BLoad bl, double* __restrict__ C,
+                                          int ldc, int kslice, size_t slice_stride, int bx, int by, int bz) {
   __shared__ T As[16][64 + 1];
   __shared__ T Bs[16][64];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  const int row0 = blockIdx.x * 64, col0 = blockIdx.y * 64;
-  const int kbeg = blockIdx.z * kslice, kend = min(K, kbeg + kslice);
-  C += blockIdx.z * slice_stride;
+  const int row0 = bx * 64, col0 = by * 64;
+  const int kbeg = bz * kslice, kend = min(K, kbeg + kslice);
+  C += bz * slice_stride;
   T acc[4][4] = {};
   for (int k0 = kbeg; k0 < kend; k0 += 16) {
     for (int e = threadIdx.x; e < 64 * 16; e += 256) {
@@ -939,8 +967,14 @@ __global__ void __launch_bounds__(256) k_gemm(int M, int N, int K, double alpha,
   }
 }
 
+template <class ALoad, class BLoad, class T = double>
+__global__ void __launch_bounds__(256) k_gemm(int M, int N, int K, double alpha, ALoad a, BLoad bl,
+                                              double* __restrict__ C, int ldc, int kslice, size_t slice_stride) {
+  gemm_body<ALoad, BLoad, T>(M, N, K, alpha, a, bl, C, ldc, kslice, slice_stride, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
 // Sum of `slices` partial products (fixed order: deterministic).
-__global__ void k_sum_slices(const double* __restrict__ P, int M, int N, int slices, size_t stride, double* C,
+__device__ __forceinline__ void k_sum_slices_body(const double* __restrict__ P, int M, int N, int slices, size_t stride, double* C,
                              int ldc) {
   const size_t total = (size_t)M * N;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
@@ -949,6 +983,8 @@ __global__ void k_sum_slices(const double* __restrict__ P, int M, int N, int sli
     C[(e / N) * ldc + e % N] = acc;
   }
 }
+__global__ void k_sum_slices(const double* __restrict__ P, int M, int N, int slices, size_t stride, double* C,
+                             int ldc) { k_sum_slices_body(P, M, N, slices, stride, C, ldc); }
 
 // The same operands as (row, k) maps for the tensor-core path.
 static TcOperand tc_a(const ARowMajor& a) { return {a.A, a.lda, 0}; }
@@ -1457,7 +1493,7 @@ __global__ void __launch_bounds__(kThreads) k_jacobi_block(double* X, int b, int
 // either way.  Pairs rotate while |gamma| > eps sqrt(alpha beta) with eps
 // above the ~1e-14 noise of a double-word dot product.  Row layout (stride
 // w + 1, w = c + jb, in double-word units): x (c), rotation row (jb), alpha.
-__global__ void __launch_bounds__(kThreads) k_jacobi_dw(double* X, int b, int c, double* J, float eps,
+__device__ __forceinline__ void k_jacobi_dw_body(double* X, int b, int c, double* J, float eps,
                                                         int max_sweeps, int nb, DevStatus* st) {
   cg::cluster_group cl = cg::this_cluster();
   extern __shared__ double smd[];
@@ -1647,6 +1683,8 @@ __global__ void __launch_bounds__(kThreads) k_jacobi_dw(double* X, int b, int c,
   }
   cl.sync();  // keep every CTA's shared memory alive until all remote accesses are done
 }
+__global__ void __launch_bounds__(kThreads) k_jacobi_dw(double* X, int b, int c, double* J, float eps,
+                                                        int max_sweeps, int nb, DevStatus* st) { k_jacobi_dw_body(X, b, c, J, eps, max_sweeps, nb, st); }
 
 static JacBlockCfg jac_block_cfg(int b, int c, bool withJ, int cs_max) {
   JacBlockCfg g{1, 2, 0};
@@ -1671,7 +1709,8 @@ static size_t jac_block_smem(const JacBlockCfg& g) {
   return (4 * (size_t)g.nb * g.stride + 4 * (size_t)g.nb) * sizeof(double) + 4 * sizeof(unsigned);
 }
 
-int launch_jacobi_rows(vp_ctx* ctx, double* X, int b, int c, double* J, bool floor_ok) {
+int jacobi_rows_on(vp_ctx* ctx, cudaStream_t stream, DevStatus* status, double* X, int b, int c, double* J,
+                   bool floor_ok) {
   if (b <= 0) return VP_OK;
   const int CS = ctx->cluster_size;
   const JacBlockCfg bc = jac_block_cfg(b, c, J != nullptr, std::max(1, CS));
@@ -1689,7 +1728,7 @@ int launch_jacobi_rows(vp_ctx* ctx, double* X, int b, int c, double* J, bool flo
     cfg.gridDim = dim3(bc.CS);
     cfg.blockDim = dim3(kThreads);
     cfg.dynamicSmemBytes = smem;
-    cfg.stream = ctx->stream;
+    cfg.stream = stream;
     at[0].id = cudaLaunchAttributeClusterDimension;
     at[0].val.clusterDim.x = bc.CS;
     at[0].val.clusterDim.y = 1;
@@ -1697,7 +1736,7 @@ int launch_jacobi_rows(vp_ctx* ctx, double* X, int b, int c, double* J, bool flo
     cfg.attrs = at;
     cfg.numAttrs = 1;
     ctx->launches++;
-    VP_CUDA(ctx, cudaLaunchKernelEx(&cfg, k_jacobi_dw, X, b, c, J, eps, max_sweeps, nb, ctx->status));
+    VP_CUDA(ctx, cudaLaunchKernelEx(&cfg, k_jacobi_dw, X, b, c, J, eps, max_sweeps, nb, status));
     return VP_OK;
   }
   if (b > 1 && jac_block_smem(bc) <= 200 * 1024) {
@@ -1713,7 +1752,7 @@ int launch_jacobi_rows(vp_ctx* ctx, double* X, int b, int c, double* J, bool flo
     cfg.gridDim = dim3(bc.CS);
     cfg.blockDim = dim3(kThreads);
     cfg.dynamicSmemBytes = smem;
-    cfg.stream = ctx->stream;
+    cfg.stream = stream;
     at[0].id = cudaLaunchAttributeClusterDimension;
     at[0].val.clusterDim.x = bc.CS;
     at[0].val.clusterDim.y = 1;
@@ -1721,7 +1760,7 @@ int launch_jacobi_rows(vp_ctx* ctx, double* X, int b, int c, double* J, bool flo
     cfg.attrs = at;
     cfg.numAttrs = 1;
     ctx->launches++;
-    VP_CUDA(ctx, cudaLaunchKernelEx(&cfg, k_jacobi_block, X, b, c, J, eps, max_sweeps, nb, ctx->status));
+    VP_CUDA(ctx, cudaLaunchKernelEx(&cfg, k_jacobi_block, X, b, c, J, eps, max_sweeps, nb, status));
     return VP_OK;
   }
   if (CS > 0 && b > 1 && cluster_jacobi_smem(b, c, CS, J != nullptr) <= 200 * 1024) {
@@ -1736,7 +1775,7 @@ int launch_jacobi_rows(vp_ctx* ctx, double* X, int b, int c, double* J, bool flo
     cfg.gridDim = dim3(CS);
     cfg.blockDim = dim3(kThreads);
     cfg.dynamicSmemBytes = smem;
-    cfg.stream = ctx->stream;
+    cfg.stream = stream;
     at[0].id = cudaLaunchAttributeClusterDimension;
     at[0].val.clusterDim.x = CS;
     at[0].val.clusterDim.y = 1;
@@ -1744,12 +1783,12 @@ int launch_jacobi_rows(vp_ctx* ctx, double* X, int b, int c, double* J, bool flo
     cfg.attrs = at;
     cfg.numAttrs = 1;
     ctx->launches++;
-    VP_CUDA(ctx, cudaLaunchKernelEx(&cfg, k_jacobi_cluster, X, b, c, J, eps, max_sweeps, ctx->status));
+    VP_CUDA(ctx, cudaLaunchKernelEx(&cfg, k_jacobi_cluster, X, b, c, J, eps, max_sweeps, status));
     return VP_OK;
   }
   if (J) {
     ctx->launches++;
-    k_identity<<<std::min(1024, (b * b + 255) / 256 + 1), 256, 0, ctx->stream>>>(J, b);
+    k_identity<<<std::min(1024, (b * b + 255) / 256 + 1), 256, 0, stream>>>(J, b);
     VP_TRY(check_launch(ctx, "identity"));
   }
   if (b == 1) return VP_OK;
@@ -1759,9 +1798,13 @@ int launch_jacobi_rows(vp_ctx* ctx, double* X, int b, int c, double* J, bool flo
   // rotate while |<x_i,x_j>| > eps |x_i||x_j|; eps grows with the dot length
   double eps = 1e-15 * std::sqrt((double)c);
   int max_sweeps = 60;
-  DevStatus* st = ctx->status;
+  DevStatus* st = status;
   void* args[] = {&X, &b, &c, &J, &eps, &max_sweeps, &st};
-  return coop_launch(ctx, (const void*)k_jacobi_rows, blocks, kThreads, args, 0, "jacobi_rows");
+  return coop_launch(ctx, stream, (const void*)k_jacobi_rows, blocks, kThreads, args, 0, "jacobi_rows");
+}
+
+int launch_jacobi_rows(vp_ctx* ctx, double* X, int b, int c, double* J, bool floor_ok) {
+  return jacobi_rows_on(ctx, ctx->stream, ctx->status, X, b, c, J, floor_ok);
 }
 
 // ------------------------------------------------------------ truncation
@@ -1778,7 +1821,7 @@ __device__ __forceinline__ bool sorts_before(double a, int ia, double b, int ib)
 // rule r = min(chi, r_tol), r_tol the smallest r with sqrt(sum_{i>=r} s_i^2)
 // <= tol ||s|| (tail summed smallest first, tol = 0: keep all), moved down
 // to the start of a cluster of values within a relative 1e-5.
-__global__ void k_select(const double* __restrict__ X, int b, int c, int chi, double tol, int* perm,
+__device__ __forceinline__ void k_select_body(const double* __restrict__ X, int b, int c, int chi, double tol, int* perm,
                          double* sigma, int* d_rank, double* d_err, DevStatus* st) {
   extern __shared__ double sm[];
   double* s = sm;          // b
@@ -1842,6 +1885,8 @@ __global__ void k_select(const double* __restrict__ X, int b, int c, int chi, do
     d_err[1] = ee;
   }
 }
+__global__ void k_select(const double* __restrict__ X, int b, int c, int chi, double tol, int* perm,
+                         double* sigma, int* d_rank, double* d_err, DevStatus* st) { k_select_body(X, b, c, chi, tol, perm, sigma, d_rank, d_err, st); }
 
 int launch_select(vp_ctx* ctx, const double* X, int b, int c, int chi, double tol, int* perm, double* sigma,
                   int* d_rank, double* d_err) {
@@ -1856,7 +1901,7 @@ int launch_select(vp_ctx* ctx, const double* X, int b, int c, int chi, double to
   return check_launch(ctx, "select");
 }
 
-__global__ void k_svd_outputs(const double* __restrict__ X, const double* __restrict__ J, int b, int c, int r,
+__device__ __forceinline__ void k_svd_outputs_body(const double* __restrict__ X, const double* __restrict__ J, int b, int c, int r,
                               const int* __restrict__ perm, const double* __restrict__ sigma, double* Vt,
                               double* W) {
   const size_t nv = (size_t)r * c, nw = J ? (size_t)b * r : 0;
@@ -1872,6 +1917,9 @@ __global__ void k_svd_outputs(const double* __restrict__ X, const double* __rest
     }
   }
 }
+__global__ void k_svd_outputs(const double* __restrict__ X, const double* __restrict__ J, int b, int c, int r,
+                              const int* __restrict__ perm, const double* __restrict__ sigma, double* Vt,
+                              double* W) { k_svd_outputs_body(X, J, b, c, r, perm, sigma, Vt, W); }
 
 int launch_svd_outputs(vp_ctx* ctx, const double* X, const double* J, int b, int c, int r, const int* perm,
                        const double* sigma, double* Vt, double* W) {
@@ -1886,7 +1934,7 @@ int launch_svd_outputs(vp_ctx* ctx, const double* X, const double* J, int b, int
 // Static pivoting for the Jacobi SVD: order the columns (tall) or rows (wide)
 // of M by decreasing norm, so that the triangular factor of the reordered
 // matrix is graded and one-sided Jacobi on it converges in fewer sweeps.
-__global__ void k_norm_order(const double* __restrict__ M, int m, int c, int by_cols, int* __restrict__ piv) {
+__device__ __forceinline__ void k_norm_order_body(const double* __restrict__ M, int m, int c, int by_cols, int* __restrict__ piv) {
   extern __shared__ double nrm[];
   const int q = by_cols ? c : m, len = by_cols ? m : c;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -1907,6 +1955,7 @@ __global__ void k_norm_order(const double* __restrict__ M, int m, int c, int by_
     piv[pos] = j;
   }
 }
+__global__ void k_norm_order(const double* __restrict__ M, int m, int c, int by_cols, int* __restrict__ piv) { k_norm_order_body(M, m, c, by_cols, piv); }
 
 int launch_norm_order(vp_ctx* ctx, const double* M, int m, int c, int by_cols, int* piv) {
   const int q = by_cols ? c : m;
@@ -1923,7 +1972,7 @@ int launch_norm_order(vp_ctx* ctx, const double* M, int m, int c, int by_cols, i
 
 // Column-major copy of the reordered matrix: tall, A = M[:, piv] (m x c);
 // wide, A = (M[piv, :])^T (c x m).
-__global__ void k_gather_cm(const double* __restrict__ M, int m, int c, const int* __restrict__ piv, int tall,
+__device__ __forceinline__ void k_gather_cm_body(const double* __restrict__ M, int m, int c, const int* __restrict__ piv, int tall,
                             double* __restrict__ out) {
   const size_t total = (size_t)m * c;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
@@ -1936,6 +1985,8 @@ __global__ void k_gather_cm(const double* __restrict__ M, int m, int c, const in
     }
   }
 }
+__global__ void k_gather_cm(const double* __restrict__ M, int m, int c, const int* __restrict__ piv, int tall,
+                            double* __restrict__ out) { k_gather_cm_body(M, m, c, piv, tall, out); }
 
 int launch_gather_cm(vp_ctx* ctx, const double* M, int m, int c, const int* piv, int tall, double* out) {
   const size_t total = (size_t)m * c;
@@ -1947,13 +1998,14 @@ int launch_gather_cm(vp_ctx* ctx, const double* M, int m, int c, const int* piv,
 
 // L = R^T, row-major, from a factored column-major q x q matrix whose upper
 // triangle holds R (the reflectors below are dropped).
-__global__ void k_lower_from_upper(const double* __restrict__ Rcm, int q, double* __restrict__ L) {
+__device__ __forceinline__ void k_lower_from_upper_body(const double* __restrict__ Rcm, int q, double* __restrict__ L) {
   const size_t total = (size_t)q * q;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
     const size_t i = e / q, j = e % q;
     L[e] = (j <= i) ? Rcm[e] : 0.0;
   }
 }
+__global__ void k_lower_from_upper(const double* __restrict__ Rcm, int q, double* __restrict__ L) { k_lower_from_upper_body(Rcm, q, L); }
 
 int launch_lower_from_upper(vp_ctx* ctx, const double* Rcm, int q, double* L) {
   const size_t total = (size_t)q * q;
@@ -1965,7 +2017,7 @@ int launch_lower_from_upper(vp_ctx* ctx, const double* Rcm, int q, double* L) {
 
 // Undo the static pivoting: cols = 1: out[t][piv[j]] = Y[t][j] (rows x q);
 // cols = 0: out[piv[j]][t] = Y[j][t] (q x rows_len).
-__global__ void k_scatter(const double* __restrict__ Y, int rows, int cols_n, const int* __restrict__ piv, int cols,
+__device__ __forceinline__ void k_scatter_body(const double* __restrict__ Y, int rows, int cols_n, const int* __restrict__ piv, int cols,
                           double* __restrict__ out) {
   const size_t total = (size_t)rows * cols_n;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
@@ -1976,6 +2028,8 @@ __global__ void k_scatter(const double* __restrict__ Y, int rows, int cols_n, co
       out[(size_t)piv[a] * cols_n + b] = Y[e];
   }
 }
+__global__ void k_scatter(const double* __restrict__ Y, int rows, int cols_n, const int* __restrict__ piv, int cols,
+                          double* __restrict__ out) { k_scatter_body(Y, rows, cols_n, piv, cols, out); }
 
 int launch_scatter(vp_ctx* ctx, const double* Y, int rows, int cols_n, const int* piv, int cols, double* out) {
   const size_t total = (size_t)rows * cols_n;
@@ -1987,7 +2041,7 @@ int launch_scatter(vp_ctx* ctx, const double* Y, int rows, int cols_n, const int
 
 // Wide-case outputs: Urows (r x b) = J[perm[t]] (rows of the accumulated
 // rotation), Wv (b x r) = X[perm[t]][i] (= V diag(s) of the factor).
-__global__ void k_svd_outputs_wide(const double* __restrict__ X, const double* __restrict__ J, int b, int r,
+__device__ __forceinline__ void k_svd_outputs_wide_body(const double* __restrict__ X, const double* __restrict__ J, int b, int r,
                                    const int* __restrict__ perm, double* Urows, double* Wv) {
   const size_t nu = (size_t)r * b;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < 2 * nu; e += (size_t)gridDim.x * blockDim.x) {
@@ -2001,6 +2055,8 @@ __global__ void k_svd_outputs_wide(const double* __restrict__ X, const double* _
     }
   }
 }
+__global__ void k_svd_outputs_wide(const double* __restrict__ X, const double* __restrict__ J, int b, int r,
+                                   const int* __restrict__ perm, double* Urows, double* Wv) { k_svd_outputs_wide_body(X, J, b, r, perm, Urows, Wv); }
 
 int launch_svd_outputs_wide(vp_ctx* ctx, const double* X, const double* J, int b, int r, const int* perm,
                             double* Urows, double* Wv) {
@@ -2009,6 +2065,508 @@ int launch_svd_outputs_wide(vp_ctx* ctx, const double* X, const double* J, int b
   ctx->launches++;
   k_svd_outputs_wide<<<blocks, 256, 0, ctx->stream>>>(X, J, b, r, perm, Urows, Wv);
   return check_launch(ctx, "svd_outputs_wide");
+}
+
+// ====================================================== batched launches
+// Each kernel below runs the body of its single-problem counterpart for the
+// problem the grid's batch coordinate selects (y for one-dimensional grids,
+// z for tiled ones), with that problem's own launch geometry.
+
+void release_scratch(vp_ctx* ctx, BScratch& s) {
+  for (DevBuf* b : {&s.wq, &s.wr, &s.qrv, &s.qrc}) release(ctx, *b);
+  for (int i = 0; i < kScratchSlots; ++i) {
+    release(ctx, s.fq[i]);
+    release(ctx, s.qscr[i]);
+    release(ctx, s.split[i]);
+  }
+}
+
+namespace {
+// Slot of a job's scratch within one launcher call: the n-th job naming the
+// same BScratch takes slot n.
+struct SlotCounter {
+  std::vector<std::pair<const BScratch*, int>> seen;
+  int next(vp_ctx* ctx, const BScratch* s, int* slot) {
+    for (auto& e : seen)
+      if (e.first == s) {
+        if (e.second >= kScratchSlots) return fail(ctx, VP_ECAPACITY, "batched launch: too many jobs on one scratch");
+        *slot = e.second++;
+        return VP_OK;
+      }
+    seen.push_back({s, 1});
+    *slot = 0;
+    return VP_OK;
+  }
+};
+}  // namespace
+
+namespace {
+
+size_t grid_stride_blocks(const vp_ctx* ctx, size_t total, size_t cap_per_sm) {
+  return std::max<size_t>(1, std::min<size_t>((total + 255) / 256, (size_t)ctx->num_sms * cap_per_sm));
+}
+
+// kern<<<(gx, nb), threads, smem>>>(pack) for every pack of the problems;
+// gx(problem) gives the x extent a problem's own launch would use.
+template <class A, class GX>
+int run_packs(vp_ctx* ctx, cudaStream_t st, const std::vector<A>& v, void (*kern)(const Pack<A>), int threads,
+              size_t smem, GX gx, const char* what) {
+  for (size_t i0 = 0; i0 < v.size(); i0 += kMaxBatch) {
+    const int nb = (int)std::min<size_t>(kMaxBatch, v.size() - i0);
+    Pack<A> pk{};
+    int gxm = 1;
+    for (int i = 0; i < nb; ++i) {
+      pk.a[i] = v[i0 + i];
+      gxm = std::max(gxm, (int)gx(v[i0 + i]));
+    }
+    ctx->launches++;
+    kern<<<dim3(gxm, nb), threads, smem, st>>>(pk);
+    VP_TRY(check_launch(ctx, what));
+  }
+  return VP_OK;
+}
+
+// The same for cluster kernels: grid (cs, nb), clusters of cs CTAs along x.
+template <class A>
+int run_cluster_packs(vp_ctx* ctx, cudaStream_t st, const std::vector<A>& v, void (*kern)(const Pack<A>), int cs,
+                      int threads, size_t smem) {
+  for (size_t i0 = 0; i0 < v.size(); i0 += kMaxBatch) {
+    const int nb = (int)std::min<size_t>(kMaxBatch, v.size() - i0);
+    Pack<A> pk{};
+    for (int i = 0; i < nb; ++i) pk.a[i] = v[i0 + i];
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    cfg.gridDim = dim3(cs, nb);
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = cs;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    ctx->launches++;
+    VP_CUDA(ctx, cudaLaunchKernelEx(&cfg, kern, pk));
+  }
+  return VP_OK;
+}
+
+}  // namespace
+
+__global__ void kb_to_colmajor(const __grid_constant__ Pack<BColMajor> pk) {
+  const BColMajor& a = pk.a[blockIdx.z];
+  __shared__ double tile[32][33];
+  const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+  if (bx >= a.n || by >= a.m) return;  // the whole block is outside this problem
+  for (int y = threadIdx.y; y < 32; y += 8) {
+    const int r = by + y, c = bx + threadIdx.x;
+    if (r < a.m && c < a.n) tile[y][threadIdx.x] = a.A[(size_t)r * a.n + c];
+  }
+  __syncthreads();
+  for (int y = threadIdx.y; y < 32; y += 8) {
+    const int c = bx + y, r = by + threadIdx.x;
+    if (r < a.m && c < a.n) a.out[(size_t)c * a.m + r] = tile[threadIdx.x][y];
+  }
+}
+
+int blaunch_to_colmajor(vp_ctx* ctx, cudaStream_t st, const std::vector<BColMajor>& v) {
+  for (size_t i0 = 0; i0 < v.size(); i0 += kMaxBatch) {
+    const int nb = (int)std::min<size_t>(kMaxBatch, v.size() - i0);
+    Pack<BColMajor> pk{};
+    int gx = 1, gy = 1;
+    for (int i = 0; i < nb; ++i) {
+      pk.a[i] = v[i0 + i];
+      gx = std::max(gx, (v[i0 + i].n + 31) / 32);
+      gy = std::max(gy, (v[i0 + i].m + 31) / 32);
+    }
+    ctx->launches++;
+    kb_to_colmajor<<<dim3(gx, gy, nb), dim3(32, 8), 0, st>>>(pk);
+    VP_TRY(check_launch(ctx, "b_to_colmajor"));
+  }
+  return VP_OK;
+}
+
+// --------------------------------------------------------------- QR
+struct QRArgs {
+  double* A;
+  int m, n;
+  double* tau;
+};
+__global__ void __launch_bounds__(kThreads) kb_qr_factor_cdw(const __grid_constant__ Pack<QRArgs> pk) {
+  const QRArgs& a = pk.a[blockIdx.y];
+  k_qr_factor_cdw_body(a.A, a.m, a.n, a.tau);
+}
+template <int NT, int CW>
+__global__ void __launch_bounds__(NT) kb_qr_factor_cl(const __grid_constant__ Pack<QRArgs> pk) {
+  const QRArgs& a = pk.a[blockIdx.y];
+  k_qr_factor_cl_body<NT, CW>(a.A, a.m, a.n, a.tau);
+}
+
+int blaunch_qr_factor(vp_ctx* ctx, cudaStream_t st, const std::vector<BQR>& v) {
+  std::vector<BQR> wide;
+  std::vector<QRArgs> cdw[17], cl[17];
+  size_t cdw_smem[17] = {}, cl_smem[17] = {};
+  for (const BQR& q : v) {
+    const QRPlan pl = qr_plan(ctx, q.m, q.n);
+    switch (pl.kind) {
+      case QR_NONE:
+        break;
+      case QR_WIDE:
+        wide.push_back(q);
+        break;
+      case QR_CDW:
+        cdw[pl.cs].push_back({q.A, q.m, q.n, q.tau});
+        cdw_smem[pl.cs] = std::max(cdw_smem[pl.cs], qr_cdw_smem(q.m, q.n, pl.cs));
+        break;
+      case QR_CL:
+        cl[pl.cs].push_back({q.A, q.m, q.n, q.tau});
+        cl_smem[pl.cs] = std::max(cl_smem[pl.cs], qr_cl_smem(q.m, q.n, pl.cs));
+        break;
+      default:
+        if (!q.s || !q.s->st) return fail(ctx, VP_EINVAL, "batched QR: no status words for a grid factor");
+        VP_TRY(qr_factor_grid(ctx, st, q.s->st, q.s->qrv, q.s->qrc, q.A, q.m, q.n, q.tau, q.vbuf));
+    }
+  }
+  for (int cs = 2; cs <= 16; ++cs) {
+    if (!cdw[cs].empty()) {
+      static AttrOnce a;
+      VP_TRY(a.ensure(ctx, (const void*)kb_qr_factor_cdw, 200 * 1024, true));
+      VP_TRY(run_cluster_packs(ctx, st, cdw[cs], kb_qr_factor_cdw, cs, kThreads,
+                               std::max<size_t>(cdw_smem[cs], 116 * 1024)));
+    }
+    if (!cl[cs].empty()) {
+      static AttrOnce a;
+      VP_TRY(a.ensure(ctx, (const void*)kb_qr_factor_cl<512, 4>, 200 * 1024, true));
+      VP_TRY(run_cluster_packs(ctx, st, cl[cs], kb_qr_factor_cl<512, 4>, cs, 512,
+                               std::max<size_t>(cl_smem[cs], 116 * 1024)));
+    }
+  }
+  if (!wide.empty()) {  // the square block, its Q, R2^T = A2^T Q in FP64, copied back (see qr_plan)
+    std::vector<BQR> sq;
+    std::vector<BFormQ> fq;
+    std::vector<BGemm> gm;
+    std::vector<BCopy> cp;
+    for (const BQR& q : wide) {
+      const int m = q.m;
+      const size_t rest = (size_t)(q.n - m) * m;
+      VP_TRY(reserve(ctx, q.s->wq, (size_t)m * m));
+      VP_TRY(reserve(ctx, q.s->wr, rest));
+      sq.push_back({q.A, m, m, q.tau, q.vbuf, q.s});
+      fq.push_back({q.A, m, m, q.tau, q.s->wq.p, q.s});
+      gm.push_back({BG_AB, 0, q.n - m, m, m, 1.0, q.A + (size_t)m * m, m, q.s->wq.p, m, q.s->wr.p, m, q.s});
+      cp.push_back({q.s->wr.p, q.A + (size_t)m * m, rest});
+    }
+    VP_TRY(blaunch_qr_factor(ctx, st, sq));
+    VP_TRY(blaunch_qr_formq(ctx, st, fq));
+    VP_TRY(blaunch_gemm(ctx, st, gm));
+    VP_TRY(blaunch_copy(ctx, st, cp));
+  }
+  return VP_OK;
+}
+
+struct R2DwArgs {
+  const double* A;
+  int m, p;
+  const double* tau;
+  dw* V;
+  dw* T;
+};
+__global__ void kb_reflectors_to_dw(const __grid_constant__ Pack<R2DwArgs> pk) {
+  const R2DwArgs& a = pk.a[blockIdx.y];
+  k_reflectors_to_dw_body(a.A, a.m, a.p, a.tau, a.V, a.T);
+}
+struct FormQArgs {
+  const dw* V;
+  int m, p;
+  const dw* T;
+  dw* scratch;
+  double* Q;
+};
+template <int R>
+__global__ void kb_qr_formq_reg(const __grid_constant__ Pack<FormQArgs> pk) {
+  const FormQArgs& a = pk.a[blockIdx.y];
+  k_qr_formq_reg_body<R>(a.V, a.m, a.p, a.T, a.Q);
+}
+__global__ void kb_qr_formq_dw(const __grid_constant__ Pack<FormQArgs> pk) {
+  const FormQArgs& a = pk.a[blockIdx.y];
+  k_qr_formq_dw_body(a.V, a.m, a.p, a.T, a.scratch, a.Q);
+}
+
+int blaunch_qr_formq(vp_ctx* ctx, cudaStream_t st, const std::vector<BFormQ>& v) {
+  std::vector<R2DwArgs> conv;
+  std::vector<FormQArgs> reg[5], gl;
+  SlotCounter slots;
+  for (const BFormQ& f : v) {
+    const int p = std::min(f.m, f.n);
+    if (p <= 0) continue;
+    int sl = 0;
+    VP_TRY(slots.next(ctx, f.s, &sl));
+    VP_TRY(reserve(ctx, f.s->fq[sl], (size_t)f.m * p + p + 8));
+    dw* V = reinterpret_cast<dw*>(f.s->fq[sl].p);
+    dw* T = V + (size_t)f.m * p;
+    conv.push_back({f.A, f.m, p, f.tau, V, T});
+    FormQArgs a{V, f.m, p, T, nullptr, f.Q};
+    if (f.m <= 64) reg[1].push_back(a);
+    else if (f.m <= 128) reg[2].push_back(a);
+    else if (f.m <= 256) reg[3].push_back(a);
+    else if (f.m <= 512) reg[4].push_back(a);
+    else {
+      VP_TRY(reserve(ctx, f.s->qscr[sl], (size_t)f.m * p));
+      a.scratch = reinterpret_cast<dw*>(f.s->qscr[sl].p);
+      gl.push_back(a);
+    }
+  }
+  VP_TRY(run_packs(ctx, st, conv, kb_reflectors_to_dw, 256, 0,
+                   [&](const R2DwArgs& a) { return grid_stride_blocks(ctx, (size_t)a.m * a.p, 8); }, "b_refl_to_dw"));
+  auto blocks4 = [](const FormQArgs& a) { return (a.p + 3) / 4; };
+  VP_TRY(run_packs(ctx, st, reg[1], kb_qr_formq_reg<2>, 128, 0, blocks4, "b_formq"));
+  VP_TRY(run_packs(ctx, st, reg[2], kb_qr_formq_reg<4>, 128, 0, blocks4, "b_formq"));
+  VP_TRY(run_packs(ctx, st, reg[3], kb_qr_formq_reg<8>, 128, 0, blocks4, "b_formq"));
+  VP_TRY(run_packs(ctx, st, reg[4], kb_qr_formq_reg<16>, 128, 0, blocks4, "b_formq"));
+  return run_packs(ctx, st, gl, kb_qr_formq_dw, 256, 0, [](const FormQArgs& a) { return (a.p + 7) / 8; },
+                   "b_formq_dw");
+}
+
+struct GetRArgs {
+  const double* A;
+  int m, n, p;
+  double* R;
+};
+__global__ void kb_qr_getr(const __grid_constant__ Pack<GetRArgs> pk) {
+  const GetRArgs& a = pk.a[blockIdx.y];
+  k_qr_getr_body(a.A, a.m, a.n, a.p, a.R);
+}
+int blaunch_qr_getr(vp_ctx* ctx, cudaStream_t st, const std::vector<BGetR>& v) {
+  std::vector<GetRArgs> g;
+  for (const BGetR& r : v) {
+    const int p = std::min(r.m, r.n);
+    if ((size_t)p * r.n > 0) g.push_back({r.A, r.m, r.n, p, r.R});
+  }
+  return run_packs(ctx, st, g, kb_qr_getr, 256, 0,
+                   [&](const GetRArgs& a) { return grid_stride_blocks(ctx, (size_t)a.p * a.n, 16); }, "b_getr");
+}
+
+// --------------------------------------------------------------- GEMM
+template <class ALoad, class BLoad>
+struct GemmJob {
+  int M, N, K, kslice, slices;
+  double alpha;
+  ALoad a;
+  BLoad b;
+  double* C;
+  int ldc;
+  size_t stride;
+};
+template <class ALoad, class BLoad, class T>
+__global__ void __launch_bounds__(256) kb_gemm(const __grid_constant__ Pack<GemmJob<ALoad, BLoad>> pk, int zs) {
+  const GemmJob<ALoad, BLoad>& j = pk.a[blockIdx.z / zs];
+  const int slice = blockIdx.z % zs;
+  if (slice >= j.slices || (int)blockIdx.x * 64 >= j.M || (int)blockIdx.y * 64 >= j.N) return;
+  gemm_body<ALoad, BLoad, T>(j.M, j.N, j.K, j.alpha, j.a, j.b, j.C, j.ldc, j.kslice, j.stride, blockIdx.x, blockIdx.y,
+                             slice);
+}
+struct SumArgs {
+  const double* P;
+  int M, N, slices;
+  size_t stride;
+  double* C;
+  int ldc;
+};
+__global__ void kb_sum_slices(const __grid_constant__ Pack<SumArgs> pk) {
+  const SumArgs& a = pk.a[blockIdx.y];
+  k_sum_slices_body(a.P, a.M, a.N, a.slices, a.stride, a.C, a.ldc);
+}
+
+namespace {
+// Split-K choice of gemm_dispatch for one problem.
+void gemm_split(const vp_ctx* ctx, int M, int N, int K, int* slices, int* kslice) {
+  const int tiles = ((M + 63) / 64) * ((N + 63) / 64);
+  int sl = 1;
+  if (tiles < ctx->num_sms && K >= 128) sl = std::min(std::min(2 * ctx->num_sms / tiles, K / 64), 32);
+  if (sl <= 1) {
+    *slices = 1;
+    *kslice = K;
+    return;
+  }
+  const int ks = ((K + sl - 1) / sl + 15) / 16 * 16;
+  *kslice = ks;
+  *slices = (K + ks - 1) / ks;
+}
+
+template <class ALoad, class BLoad, class T>
+int gemm_group(vp_ctx* ctx, cudaStream_t st, const std::vector<GemmJob<ALoad, BLoad>>& jobs) {
+  for (size_t i0 = 0; i0 < jobs.size(); i0 += kMaxBatch) {
+    const int nb = (int)std::min<size_t>(kMaxBatch, jobs.size() - i0);
+    Pack<GemmJob<ALoad, BLoad>> pk{};
+    int gx = 1, gy = 1, zs = 1;
+    for (int i = 0; i < nb; ++i) {
+      const auto& j = jobs[i0 + i];
+      pk.a[i] = j;
+      gx = std::max(gx, (j.M + 63) / 64);
+      gy = std::max(gy, (j.N + 63) / 64);
+      zs = std::max(zs, j.slices);
+    }
+    if (gy > 65535) return fail(ctx, VP_ECAPACITY, "gemm: N too large");
+    ctx->launches++;
+    kb_gemm<ALoad, BLoad, T><<<dim3(gx, gy, nb * zs), 256, 0, st>>>(pk, zs);
+    VP_TRY(check_launch(ctx, "b_gemm"));
+  }
+  return VP_OK;
+}
+}  // namespace
+
+int blaunch_gemm(vp_ctx* ctx, cudaStream_t st, const std::vector<BGemm>& v) {
+  std::vector<GemmJob<ARowMajor, BRowMajor>> ab[2];
+  std::vector<GemmJob<ARowMajor, BTransposed>> abt[2];
+  std::vector<GemmJob<AUpperColMajor, BRowMajor>> rb[2];
+  std::vector<SumArgs> sums;
+  SlotCounter slots;
+  for (const BGemm& g : v) {
+    if (g.M <= 0 || g.N <= 0) continue;
+    int slices = 1, kslice = g.K;
+    gemm_split(ctx, g.M, g.N, g.K, &slices, &kslice);
+    double* C = g.C;
+    int ldc = g.ldc;
+    size_t stride = 0;
+    if (slices > 1) {
+      int sl = 0;
+      VP_TRY(slots.next(ctx, g.s, &sl));
+      stride = (size_t)g.M * g.N;
+      VP_TRY(reserve(ctx, g.s->split[sl], stride * slices));
+      C = g.s->split[sl].p;
+      ldc = g.N;
+      sums.push_back({g.s->split[sl].p, g.M, g.N, slices, stride, g.C, g.ldc});
+    }
+    const int t = g.fp32 ? 1 : 0;
+    if (g.kind == BG_AB)
+      ab[t].push_back({g.M, g.N, g.K, kslice, slices, g.alpha, ARowMajor{g.A, g.lda}, BRowMajor{g.B, g.ldb}, C, ldc,
+                       stride});
+    else if (g.kind == BG_ABT)
+      abt[t].push_back({g.M, g.N, g.K, kslice, slices, g.alpha, ARowMajor{g.A, g.lda}, BTransposed{g.B, g.ldb}, C,
+                        ldc, stride});
+    else
+      rb[t].push_back({g.M, g.N, g.K, kslice, slices, g.alpha, AUpperColMajor{g.A, g.lda}, BRowMajor{g.B, g.ldb}, C,
+                       ldc, stride});
+  }
+  VP_TRY((gemm_group<ARowMajor, BRowMajor, double>(ctx, st, ab[0])));
+  VP_TRY((gemm_group<ARowMajor, BRowMajor, float>(ctx, st, ab[1])));
+  VP_TRY((gemm_group<ARowMajor, BTransposed, double>(ctx, st, abt[0])));
+  VP_TRY((gemm_group<ARowMajor, BTransposed, float>(ctx, st, abt[1])));
+  VP_TRY((gemm_group<AUpperColMajor, BRowMajor, double>(ctx, st, rb[0])));
+  VP_TRY((gemm_group<AUpperColMajor, BRowMajor, float>(ctx, st, rb[1])));
+  return run_packs(ctx, st, sums, kb_sum_slices, 256, 0,
+                   [&](const SumArgs& a) { return grid_stride_blocks(ctx, a.stride, 8); }, "b_sum_slices");
+}
+
+// --------------------------------------------------------------- SVD site helpers
+__global__ void kb_norm_order(const __grid_constant__ Pack<BNormOrder> pk) {
+  const BNormOrder& a = pk.a[blockIdx.y];
+  k_norm_order_body(a.M, a.m, a.c, a.by_cols, a.piv);
+}
+int blaunch_norm_order(vp_ctx* ctx, cudaStream_t st, const std::vector<BNormOrder>& v) {
+  size_t smem = 0;
+  for (const BNormOrder& a : v) smem = std::max(smem, (size_t)(a.by_cols ? a.c : a.m) * sizeof(double));
+  if (smem > 200 * 1024) return fail(ctx, VP_ECAPACITY, "norm_order: too many columns");
+  static AttrOnce at;
+  VP_TRY(at.ensure(ctx, (const void*)kb_norm_order, 200 * 1024, false));
+  return run_packs(ctx, st, v, kb_norm_order, 512, smem, [](const BNormOrder&) { return 1; }, "b_norm_order");
+}
+__global__ void kb_gather_cm(const __grid_constant__ Pack<BGather> pk) {
+  const BGather& a = pk.a[blockIdx.y];
+  k_gather_cm_body(a.M, a.m, a.c, a.piv, a.tall, a.out);
+}
+int blaunch_gather_cm(vp_ctx* ctx, cudaStream_t st, const std::vector<BGather>& v) {
+  return run_packs(ctx, st, v, kb_gather_cm, 256, 0,
+                   [&](const BGather& a) { return grid_stride_blocks(ctx, (size_t)a.m * a.c, 16); }, "b_gather_cm");
+}
+__global__ void kb_lower_from_upper(const __grid_constant__ Pack<BLowerUpper> pk) {
+  const BLowerUpper& a = pk.a[blockIdx.y];
+  k_lower_from_upper_body(a.R, a.q, a.L);
+}
+int blaunch_lower_from_upper(vp_ctx* ctx, cudaStream_t st, const std::vector<BLowerUpper>& v) {
+  return run_packs(ctx, st, v, kb_lower_from_upper, 256, 0,
+                   [&](const BLowerUpper& a) { return grid_stride_blocks(ctx, (size_t)a.q * a.q, 8); },
+                   "b_lower_from_upper");
+}
+
+struct JacArgs {
+  double* X;
+  int b, c;
+  double* J;
+  float eps;
+  int max_sweeps, nb;
+  DevStatus* st;
+};
+__global__ void __launch_bounds__(kThreads) kb_jacobi_dw(const __grid_constant__ Pack<JacArgs> pk) {
+  const JacArgs& a = pk.a[blockIdx.y];
+  k_jacobi_dw_body(a.X, a.b, a.c, a.J, a.eps, a.max_sweeps, a.nb, a.st);
+}
+int blaunch_jacobi(vp_ctx* ctx, cudaStream_t st, const std::vector<BJacobi>& v) {
+  const int CS = ctx->cluster_size;
+  std::vector<JacArgs> grp[17];
+  size_t smem[17] = {};
+  for (const BJacobi& j : v) {
+    if (j.b <= 1) continue;  // nothing to rotate (as in the single launch)
+    const JacBlockCfg bc = jac_block_cfg(j.b, j.c, j.J != nullptr, std::max(1, CS));
+    if (jac_dw_smem(bc) <= 200 * 1024) {
+      // the thresholds of launch_jacobi_rows
+      grp[bc.CS].push_back({j.X, j.b, j.c, j.J, (float)(4e-13 * std::sqrt((double)j.c)), 60, bc.nb, j.st});
+      smem[bc.CS] = std::max(smem[bc.CS], jac_dw_smem(bc));
+    } else {
+      VP_CUDA(ctx, cudaMemsetAsync(j.st->rot, 0, sizeof(j.st->rot), st));
+      VP_TRY(jacobi_rows_on(ctx, st, j.st, j.X, j.b, j.c, j.J, true));
+    }
+  }
+  for (int cs = 1; cs <= 16; ++cs)
+    if (!grp[cs].empty()) {
+      static AttrOnce a;
+      VP_TRY(a.ensure(ctx, (const void*)kb_jacobi_dw, 200 * 1024, true));
+      VP_TRY(run_cluster_packs(ctx, st, grp[cs], kb_jacobi_dw, cs, kThreads, std::max<size_t>(smem[cs], 120 * 1024)));
+    }
+  return VP_OK;
+}
+
+__global__ void kb_select(const __grid_constant__ Pack<BSelect> pk) {
+  const BSelect& a = pk.a[blockIdx.y];
+  k_select_body(a.X, a.b, a.c, a.chi, a.tol, a.perm, a.sigma, a.d_rank, a.d_err, a.st);
+}
+int blaunch_select(vp_ctx* ctx, cudaStream_t st, const std::vector<BSelect>& v) {
+  size_t smem = 0;
+  for (const BSelect& a : v) smem = std::max(smem, (size_t)(2 * a.b + 1) * sizeof(double));
+  if (smem > 200 * 1024) return fail(ctx, VP_ECAPACITY, "select: bond too large");
+  static AttrOnce at;
+  VP_TRY(at.ensure(ctx, (const void*)kb_select, 200 * 1024, false));
+  return run_packs(ctx, st, v, kb_select, 512, smem, [](const BSelect&) { return 1; }, "b_select");
+}
+__global__ void kb_svd_outputs(const __grid_constant__ Pack<BSvdOut> pk) {
+  const BSvdOut& a = pk.a[blockIdx.y];
+  k_svd_outputs_body(a.X, a.J, a.b, a.c, a.r, a.perm, a.sigma, a.Vt, a.W);
+}
+int blaunch_svd_outputs(vp_ctx* ctx, cudaStream_t st, const std::vector<BSvdOut>& v) {
+  return run_packs(ctx, st, v, kb_svd_outputs, 256, 0,
+                   [&](const BSvdOut& a) {
+                     return grid_stride_blocks(ctx, (size_t)a.r * a.c + (size_t)a.b * a.r, 8);
+                   },
+                   "b_svd_outputs");
+}
+__global__ void kb_svd_outputs_wide(const __grid_constant__ Pack<BSvdOutWide> pk) {
+  const BSvdOutWide& a = pk.a[blockIdx.y];
+  k_svd_outputs_wide_body(a.X, a.J, a.b, a.r, a.perm, a.U, a.Wv);
+}
+int blaunch_svd_outputs_wide(vp_ctx* ctx, cudaStream_t st, const std::vector<BSvdOutWide>& v) {
+  return run_packs(ctx, st, v, kb_svd_outputs_wide, 256, 0,
+                   [&](const BSvdOutWide& a) { return grid_stride_blocks(ctx, 2 * (size_t)a.r * a.b, 8); },
+                   "b_svd_outputs_wide");
+}
+__global__ void kb_scatter(const __grid_constant__ Pack<BScatter> pk) {
+  const BScatter& a = pk.a[blockIdx.y];
+  k_scatter_body(a.Y, a.rows, a.cols_n, a.piv, a.cols, a.out);
+}
+int blaunch_scatter(vp_ctx* ctx, cudaStream_t st, const std::vector<BScatter>& v) {
+  return run_packs(ctx, st, v, kb_scatter, 256, 0,
+                   [&](const BScatter& a) { return grid_stride_blocks(ctx, (size_t)a.rows * a.cols_n, 8); },
+                   "b_scatter");
 }
 
 }  // namespace vp

@@ -19,7 +19,7 @@ static int grid_for(vp_ctx* ctx, size_t total, int per = 256) {
 // MPS sum: a occupies the leading block of each bond, (B b) the trailing one
 // with bond index (alpha, beta) = a_b * w + b_w; the first site concatenates
 // along the right bond only and the last site along the left bond only.
-__global__ void k_site_sum(SiteSum s, double* __restrict__ out, int ol, int orr) {
+__device__ __forceinline__ void k_site_sum_body(SiteSum s, double* __restrict__ out, int ol, int orr) {
   const size_t total = (size_t)ol * 2 * orr;
   const int offl = (s.a && !s.first) ? s.al : 0;  // start of the (B b) block on the left bond
   const int offr = (s.a && !s.last) ? s.ar : 0;
@@ -57,6 +57,7 @@ __global__ void k_site_sum(SiteSum s, double* __restrict__ out, int ol, int orr)
     out[e] = v;
   }
 }
+__global__ void k_site_sum(SiteSum s, double* __restrict__ out, int ol, int orr) { k_site_sum_body(s, out, ol, orr); }
 
 int launch_site_sum(vp_ctx* ctx, const SiteSum& s, double* out, int ol, int orr) {
   const size_t total = (size_t)ol * 2 * orr;
@@ -65,13 +66,14 @@ int launch_site_sum(vp_ctx* ctx, const SiteSum& s, double* out, int ol, int orr)
   return check_launch(ctx, "site_sum");
 }
 
-__global__ void k_phys_sum(const double* __restrict__ core, int rl, int rr, double* __restrict__ T) {
+__device__ __forceinline__ void k_phys_sum_body(const double* __restrict__ core, int rl, int rr, double* __restrict__ T) {
   const size_t total = (size_t)rl * rr;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
     const size_t l = e / rr, r = e % rr;
     T[e] = core[(l * 2) * rr + r] + core[(l * 2 + 1) * rr + r];
   }
 }
+__global__ void k_phys_sum(const double* __restrict__ core, int rl, int rr, double* __restrict__ T) { k_phys_sum_body(core, rl, rr, T); }
 
 int launch_phys_sum(vp_ctx* ctx, const double* core, int rl, int rr, double* T) {
   ctx->launches++;
@@ -79,10 +81,11 @@ int launch_phys_sum(vp_ctx* ctx, const double* core, int rl, int rr, double* T) 
   return check_launch(ctx, "phys_sum");
 }
 
-__global__ void k_copy(const double* __restrict__ src, double* __restrict__ dst, size_t n) {
+__device__ __forceinline__ void k_copy_body(const double* __restrict__ src, double* __restrict__ dst, size_t n) {
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
     dst[e] = src[e];
 }
+__global__ void k_copy(const double* __restrict__ src, double* __restrict__ dst, size_t n) { k_copy_body(src, dst, n); }
 
 int launch_copy(vp_ctx* ctx, const double* src, double* dst, size_t n) {
   if (n == 0) return VP_OK;
@@ -91,10 +94,11 @@ int launch_copy(vp_ctx* ctx, const double* src, double* dst, size_t n) {
   return check_launch(ctx, "copy");
 }
 
-__global__ void k_scale(double* x, size_t n, double s) {
+__device__ __forceinline__ void k_scale_body(double* x, size_t n, double s) {
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
     x[e] *= s;
 }
+__global__ void k_scale(double* x, size_t n, double s) { k_scale_body(x, n, s); }
 
 int launch_scale(vp_ctx* ctx, double* x, size_t n, double s) {
   if (n == 0) return VP_OK;
@@ -168,7 +172,7 @@ __device__ __forceinline__ size_t site_to_grid(size_t s, int nx, int nv, int map
   return (ix << nv) | iv;
 }
 
-__global__ void k_permute(const double* __restrict__ f, int nx, int nv, int mapping, double* __restrict__ out,
+__device__ __forceinline__ void k_permute_body(const double* __restrict__ f, int nx, int nv, int mapping, double* __restrict__ out,
                           int inverse) {
   const size_t total = (size_t)1 << (nx + nv);
   for (size_t s = blockIdx.x * (size_t)blockDim.x + threadIdx.x; s < total; s += (size_t)gridDim.x * blockDim.x) {
@@ -179,6 +183,8 @@ __global__ void k_permute(const double* __restrict__ f, int nx, int nv, int mapp
       out[s] = f[g];
   }
 }
+__global__ void k_permute(const double* __restrict__ f, int nx, int nv, int mapping, double* __restrict__ out,
+                          int inverse) { k_permute_body(f, nx, nv, mapping, out, inverse); }
 
 int launch_permute_to_sites(vp_ctx* ctx, const double* f, int nx, int nv, int mapping, double* out,
                             int inverse) {
@@ -193,7 +199,7 @@ int launch_permute_to_sites(vp_ctx* ctx, const double* f, int nx, int nv, int ma
 // d_{i-1} = s_i, so d is a prefix sum fixed by sum_i d_i = 0 (periodicity),
 // and E_i = -(phi_{i+1} - phi_{i-1}) / (2 dx) = -(d_i + d_{i-1}) / (2 dx).
 // we[0] = 1/2 sum E^2 dx, we[1] = sum rho dx.
-__global__ void k_poisson(const double* __restrict__ rho, int N, double dx, double* __restrict__ E,
+__device__ __forceinline__ void k_poisson_body(const double* __restrict__ rho, int N, double dx, double* __restrict__ E,
                           double* __restrict__ we) {
   extern __shared__ double sm[];
   double* d = sm;           // N
@@ -260,6 +266,8 @@ __global__ void k_poisson(const double* __restrict__ rho, int N, double dx, doub
     we[1] = total * dx;
   }
 }
+__global__ void k_poisson(const double* __restrict__ rho, int N, double dx, double* __restrict__ E,
+                          double* __restrict__ we) { k_poisson_body(rho, N, dx, E, we); }
 
 int launch_poisson(vp_ctx* ctx, const double* rho, int N, double dx, double* E, double* we_dev) {
   const int nt = 256;
@@ -308,7 +316,7 @@ int launch_species_net(vp_ctx* ctx, const SpeciesRho& sr, int N, double dx, doub
 
 // L core = blockdiag(U, T) with T the placed field term diag(E) (x) D_v.
 // Bond indices of T flatten (E channel, D_v channel) in that order.
-__global__ void k_assemble(const double* __restrict__ U, int ul, int ur, ETermSite e, int first, int last,
+__device__ __forceinline__ void k_assemble_body(const double* __restrict__ U, int ul, int ur, ETermSite e, int first, int last,
                            double* __restrict__ out, int ol, int orr) {
   const size_t total = (size_t)ol * 4 * orr;
   const int tl = first ? 1 : ol - ul;  // T block sizes
@@ -344,6 +352,8 @@ __global__ void k_assemble(const double* __restrict__ U, int ul, int ur, ETermSi
     out[q] = v;
   }
 }
+__global__ void k_assemble(const double* __restrict__ U, int ul, int ur, ETermSite e, int first, int last,
+                           double* __restrict__ out, int ol, int orr) { k_assemble_body(U, ul, ur, e, first, last, out, ol, orr); }
 
 int launch_assemble_site(vp_ctx* ctx, const double* U, int ul, int ur, const ETermSite& e, int first, int last,
                          double* out, int ol, int orr) {
@@ -380,6 +390,95 @@ int launch_mpo_dense_step(vp_ctx* ctx, const double* T, int rows, int cols, int 
   ctx->launches++;
   k_mpo_dense_step<<<grid_for(ctx, no * no * wr), 256, 0, ctx->stream>>>(T, rows, w, core, wr, out);
   return check_launch(ctx, "mpo_dense");
+}
+
+// ====================================================== batched launches
+// (see common.cuh): the body of each single-problem kernel for the problem the
+// grid's y coordinate selects, with that problem's own x extent.
+namespace {
+template <class A, class GX>
+int run_packs(vp_ctx* ctx, cudaStream_t st, const std::vector<A>& v, void (*kern)(const Pack<A>), int threads,
+              size_t smem, GX gx, const char* what) {
+  for (size_t i0 = 0; i0 < v.size(); i0 += kMaxBatch) {
+    const int nb = (int)std::min<size_t>(kMaxBatch, v.size() - i0);
+    Pack<A> pk{};
+    int gxm = 1;
+    for (int i = 0; i < nb; ++i) {
+      pk.a[i] = v[i0 + i];
+      gxm = std::max(gxm, (int)gx(v[i0 + i]));
+    }
+    ctx->launches++;
+    kern<<<dim3(gxm, nb), threads, smem, st>>>(pk);
+    VP_TRY(check_launch(ctx, what));
+  }
+  return VP_OK;
+}
+}  // namespace
+
+__global__ void kb_copy(const __grid_constant__ Pack<BCopy> pk) {
+  const BCopy& a = pk.a[blockIdx.y];
+  k_copy_body(a.src, a.dst, a.n);
+}
+int blaunch_copy(vp_ctx* ctx, cudaStream_t st, const std::vector<BCopy>& v) {
+  std::vector<BCopy> nz;
+  for (const BCopy& c : v)
+    if (c.n) nz.push_back(c);
+  return run_packs(ctx, st, nz, kb_copy, 256, 0, [&](const BCopy& a) { return grid_for(ctx, a.n); }, "b_copy");
+}
+__global__ void kb_site_sum(const __grid_constant__ Pack<BSiteSum> pk) {
+  const BSiteSum& a = pk.a[blockIdx.y];
+  k_site_sum_body(a.s, a.out, a.ol, a.orr);
+}
+int blaunch_site_sum(vp_ctx* ctx, cudaStream_t st, const std::vector<BSiteSum>& v) {
+  return run_packs(ctx, st, v, kb_site_sum, 256, 0,
+                   [&](const BSiteSum& a) { return grid_for(ctx, (size_t)a.ol * 2 * a.orr); }, "b_site_sum");
+}
+__global__ void kb_phys_sum(const __grid_constant__ Pack<BPhysSum> pk) {
+  const BPhysSum& a = pk.a[blockIdx.y];
+  k_phys_sum_body(a.core, a.rl, a.rr, a.T);
+}
+int blaunch_phys_sum(vp_ctx* ctx, cudaStream_t st, const std::vector<BPhysSum>& v) {
+  return run_packs(ctx, st, v, kb_phys_sum, 256, 0,
+                   [&](const BPhysSum& a) { return grid_for(ctx, (size_t)a.rl * a.rr); }, "b_phys_sum");
+}
+__global__ void kb_scale(const __grid_constant__ Pack<BScale> pk) {
+  const BScale& a = pk.a[blockIdx.y];
+  k_scale_body(a.x, a.n, a.s);
+}
+int blaunch_scale(vp_ctx* ctx, cudaStream_t st, const std::vector<BScale>& v) {
+  std::vector<BScale> nz;
+  for (const BScale& c : v)
+    if (c.n) nz.push_back(c);
+  return run_packs(ctx, st, nz, kb_scale, 256, 0, [&](const BScale& a) { return grid_for(ctx, a.n); }, "b_scale");
+}
+__global__ void kb_poisson(const __grid_constant__ Pack<BPoisson> pk) {
+  const BPoisson& a = pk.a[blockIdx.y];
+  k_poisson_body(a.rho, a.N, a.dx, a.E, a.we);
+}
+int blaunch_poisson(vp_ctx* ctx, cudaStream_t st, const std::vector<BPoisson>& v) {
+  const int nt = 256;
+  size_t smem = 0;
+  for (const BPoisson& a : v) smem = std::max(smem, (size_t)(a.N + 33 + nt) * sizeof(double));
+  if (smem > 200 * 1024) return fail(ctx, VP_ECAPACITY, "poisson: 2^nx too large");
+  static AttrOnce at;
+  VP_TRY(at.ensure(ctx, (const void*)kb_poisson, 200 * 1024, false));
+  return run_packs(ctx, st, v, kb_poisson, nt, smem, [](const BPoisson&) { return 1; }, "b_poisson");
+}
+__global__ void kb_assemble(const __grid_constant__ Pack<BAssemble> pk) {
+  const BAssemble& a = pk.a[blockIdx.y];
+  k_assemble_body(a.U, a.ul, a.ur, a.e, a.first, a.last, a.out, a.ol, a.orr);
+}
+int blaunch_assemble(vp_ctx* ctx, cudaStream_t st, const std::vector<BAssemble>& v) {
+  return run_packs(ctx, st, v, kb_assemble, 256, 0,
+                   [&](const BAssemble& a) { return grid_for(ctx, (size_t)a.ol * 4 * a.orr); }, "b_assemble");
+}
+__global__ void kb_permute(const __grid_constant__ Pack<BPermute> pk) {
+  const BPermute& a = pk.a[blockIdx.y];
+  k_permute_body(a.f, a.nx, a.nv, a.mapping, a.out, a.inverse);
+}
+int blaunch_permute(vp_ctx* ctx, cudaStream_t st, const std::vector<BPermute>& v) {
+  return run_packs(ctx, st, v, kb_permute, 256, 0,
+                   [&](const BPermute& a) { return grid_for(ctx, (size_t)1 << (a.nx + a.nv)); }, "b_permute");
 }
 
 }  // namespace vp

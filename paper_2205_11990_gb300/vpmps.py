@@ -42,6 +42,7 @@ EXPORTS = [
     "vp_footprint_bytes", "vp_batch_create", "vp_batch_submit", "vp_batch_start", "vp_batch_wait", "vp_batch_poll",
     "vp_batch_records", "vp_batch_destroy",
     "vp_multi_create", "vp_multi_destroy", "vp_multi_step", "vp_multi_state",
+    "vp_group_create", "vp_group_add", "vp_group_remove", "vp_group_size", "vp_group_step", "vp_group_destroy",
 ]
 
 
@@ -163,6 +164,12 @@ def load():
         "vp_multi_destroy": (I, [P]),
         "vp_multi_step": (I, [P, I, C.POINTER(CRecord)]),
         "vp_multi_state": (P, [P, I]),
+        "vp_group_create": (I, [P, I, C.POINTER(P)]),
+        "vp_group_add": (I, [P, P]),
+        "vp_group_remove": (I, [P, P]),
+        "vp_group_size": (I, [P]),
+        "vp_group_step": (I, [P, C.POINTER(CRecord), IP]),
+        "vp_group_destroy": (I, [P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -401,6 +408,9 @@ class Context:
         self._check(self.lib.vp_sim_create(self.h, C.byref(clayout(lay)), C.byref(cfg), f0.h, C.byref(h)))
         return Sim(self, h, lay)
 
+    def group(self, max_members: int) -> "Group":
+        return Group(self, max_members)
+
     def multi(self, lays, species, f0s, dt: float, chi: int, tol: float = 1e-10, e_tol: float = 1e-10,
               streams: int = 2, e_chi: int = 0, precision: int = 0, compression: int = 0) -> "Multi":
         """Several species sharing one field (vp_multi_*).  species: per
@@ -600,6 +610,49 @@ class Sim:
     def close(self):
         if self.h and self.ctx.h:
             self.ctx.lib.vp_sim_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Group:
+    """Simulations stepped in lockstep, every launch serving all members
+    (vp_group_*).  Members: sims of this context created with streams=1."""
+
+    def __init__(self, ctx: Context, max_members: int):
+        self.ctx = ctx
+        h = C.c_void_p()
+        ctx._check(ctx.lib.vp_group_create(ctx.h, max_members, C.byref(h)))
+        self.h = h
+        self.members = []
+        ctx._children.add(self)
+
+    def add(self, sim: "Sim"):
+        self.ctx._check(self.ctx.lib.vp_group_add(self.h, sim.h))
+        self.members.append(sim)
+
+    def remove(self, sim: "Sim"):
+        self.ctx._check(self.ctx.lib.vp_group_remove(self.h, sim.h))
+        self.members.remove(sim)
+
+    def __len__(self):
+        return int(self.ctx.lib.vp_group_size(self.h))
+
+    def step(self):
+        """One step of every running member: (records, status) per member."""
+        n = len(self.members)
+        recs = (CRecord * max(1, n))()
+        st = np.zeros(max(1, n), dtype=np.int32)
+        self.ctx._check(self.ctx.lib.vp_group_step(self.h, recs, _ip(st)))
+        return _records(recs, n), [int(x) for x in st[:n]]
+
+    def close(self):
+        if self.h and self.ctx.h:
+            self.ctx.lib.vp_group_destroy(self.h)
         self.h = None
 
     def __del__(self):
