@@ -50,6 +50,9 @@ def parse():
                    help="named workload of paper_2205_11990_gb300.inputs.SPECIES_WORKLOADS (--mode species)")
     p.add_argument("--instances", type=int, default=32)
     p.add_argument("--concurrency", type=int, default=8)
+    p.add_argument("--groups", type=int, default=4, help="batch / serve: lockstep groups (bucketed by site count)")
+    p.add_argument("--bits", default="8,12", help="batch / serve: grid bits per dimension, min,max")
+    p.add_argument("--chis", default="16,32,64,128", help="batch / serve: bond caps drawn uniformly")
     p.add_argument("--rate", type=float, default=20.0, help="serve: mean Poisson arrival rate (req/s)")
     p.add_argument("--window", type=float, default=20.0, help="serve: arrival window (s)")
     p.add_argument("--workload", default=WORKLOAD,
@@ -398,61 +401,82 @@ def run_reference(args, rank, world):
     }), flush=True)
 
 
-def mixed_request(rng):
-    """One seeded request of the batching/serving mix: Landau or bump-on-tail,
-    sequential or interleaved, grid bits per dimension 6..9, chi in {16, 32, 64}."""
+def mixed_request(rng, bits=(6, 9), chis=(16, 32, 64), amp_range=(1e-3, 0.5)):
+    """One seeded request of the batching / serving mix (the batching
+    configuration's distribution): grid bits per dimension uniform in
+    bits[0]..bits[1] (square grids), chi uniform in chis, sequential or
+    interleaved 50/50, Landau (k ~ U[0.3, 0.6], amplitude log-uniform in
+    amp_range, v in [-6, 6]) or bump-on-tail (n_b = 0.1, v_b = 4.5,
+    sigma_b = 0.5, k ~ U[0.3, 0.6], v in [-8, 8]) 50/50, dt = 0.6 dx / vmax."""
     import math
     from paper_2205_11990_gb300 import inputs as I
-    nb = int(rng.integers(6, 10))
+    nb = int(rng.integers(bits[0], bits[1] + 1))
     mapping = I.SEQ if rng.random() < 0.5 else I.INTERLEAVED
+    k = float(rng.uniform(0.3, 0.6))
     if rng.random() < 0.5:
-        k = float(rng.uniform(0.3, 0.6))
-        amp = float(math.exp(rng.uniform(math.log(1e-3), math.log(0.5))))
+        amp = float(math.exp(rng.uniform(math.log(amp_range[0]), math.log(amp_range[1]))))
         lay = I.Layout(nb, nb, 0.0, 2 * math.pi / k, -6.0, 6.0, mapping)
         f0 = I.landau(lay, amp, k)
     else:
-        k = float(rng.uniform(0.3, 0.6))
         lay = I.Layout(nb, nb, 0.0, 2 * math.pi / k, -8.0, 8.0, mapping)
         f0 = I.bump_on_tail(lay, 1e-3, k)
     dx = (lay.xmax - lay.xmin) / lay.Nx
     dt = 0.6 * dx / lay.vmax
-    chi = int(rng.choice([16, 32, 64]))
+    chi = int(rng.choice(list(chis)))
     return lay, f0, dt, chi
 
 
+def _parse_range(s):
+    a, b = (int(x) for x in s.split(","))
+    return a, b
+
+
 def run_batch(args):
+    """Many independent runs on one GPU: the same seeded request set through
+    the plain per-instance path (one run at a time, vp_step) and through the
+    lockstep engine (bucketed groups, continuous batching); sims/s of each."""
     import numpy as np
     import __graft_entry__ as g
     g.build()
     from paper_2205_11990_gb300 import vpmps
     ctx = vpmps.Context()
     rng = np.random.Generator(np.random.PCG64(0))
-    reqs = [mixed_request(rng) for _ in range(args.instances)]
+    bits = _parse_range(args.bits)
+    chis = tuple(int(c) for c in args.chis.split(","))
+    reqs = [mixed_request(rng, bits, chis) for _ in range(args.instances)]
     steps = max(1, args.steps)
     out = {}
-    for label, conc in (("batched", args.concurrency), ("sequential", 1)):
-        b = vpmps.Batch(ctx, conc, 200 << 30)
-        for lay, f0, dt, chi in reqs:
-            b.submit(lay, f0, dt, steps, chi)
+    arms = [("lockstep", dict(max_concurrent=args.instances, lockstep=args.groups)),
+            ("sequential", dict(max_concurrent=1, lockstep=0))]
+    results = {}
+    for label, kw in arms:
+        b = vpmps.Batch(ctx, kw["max_concurrent"], 200 << 30, lockstep=kw["lockstep"])
+        ids = [b.submit(lay, f0, dt, steps, chi, keep_f=True) for lay, f0, dt, chi in reqs]
         t0 = time.perf_counter()
         b.start()
         b.wait()
         t = time.perf_counter() - t0
-        res = b.poll(4 * len(reqs))
-        assert all(r["status"] == 0 for r in res), res
-        out[label] = {"sims_per_s": len(reqs) / t, "wall_s": t,
-                      "step_ms_p50": float(np.median([r["step_ms_p50"] for r in res])),
-                      "step_ms_p99": float(np.max([r["step_ms_p99"] for r in res]))}
+        res = {r["id"]: r for r in b.poll(4 * len(reqs))}
+        assert all(r["status"] == 0 for r in res.values()), [r["status"] for r in res.values()]
+        step_ms = np.concatenate([b.records(i)[1] for i in ids])
+        results[label] = [b.records(i, want_f=True) for i in ids]
+        out[label] = {"sims_per_s": len(reqs) / t, "instance_steps_per_s": len(reqs) * steps / t, "wall_s": t,
+                      "step_ms_p50": float(np.percentile(step_ms, 50)),
+                      "step_ms_p99": float(np.percentile(step_ms, 99)),
+                      "run_ms_p50": float(np.median([r["queue_ms"] + r["run_ms"] for r in res.values()])),
+                      "run_ms_p99": float(np.percentile([r["queue_ms"] + r["run_ms"] for r in res.values()], 99))}
         b.close()
+    # the two arms compute the same runs: every final state and record equal
+    same = all(np.array_equal(a[2], c[2]) and a[0] == c[0] for a, c in zip(results["lockstep"], results["sequential"]))
     print(json.dumps({
-        "metric": "batched sims/s (RK4-C1 runs, mixed sizes/chi/mappings)", "value": out["batched"]["sims_per_s"],
+        "metric": "batched sims/s (RK4-C1 runs, mixed sizes/chi/mappings)", "value": out["lockstep"]["sims_per_s"],
         "unit": "sims/s", "n_gpus": 1, "higher_is_better": True, "dtype": DTYPE, "data": "synthetic",
-        "config": {"workload": "mixed Landau/bump-on-tail, grid bits 6..9 per dim, chi 16/32/64, seq/interleaved",
-                   "instances": args.instances, "steps_per_run": steps, "concurrency": args.concurrency,
-                   "seed": 0},
-        "batched": out["batched"], "sequential_fp64_per_instance": out["sequential"],
-        "speedup_vs_sequential": out["batched"]["sims_per_s"] / out["sequential"]["sims_per_s"],
-        "gpu_launches": ctx.kernel_launches}), flush=True)
+        "config": {"workload": f"mixed Landau/bump-on-tail, grid bits {bits[0]}..{bits[1]} per dim, chi {chis}, "
+                               f"seq/interleaved", "instances": args.instances, "steps_per_run": steps,
+                   "lockstep_groups": args.groups, "seed": 0},
+        "lockstep": out["lockstep"], "sequential_fp64_per_instance": out["sequential"],
+        "speedup_vs_sequential": out["lockstep"]["sims_per_s"] / out["sequential"]["sims_per_s"],
+        "results_identical": bool(same), "gpu_launches": ctx.kernel_launches}), flush=True)
 
 
 def run_serve(args):
@@ -467,9 +491,9 @@ def run_serve(args):
         t += float(rng.exponential(1.0 / args.rate))
         if t > args.window:
             break
-        lay, f0, dt, chi = mixed_request(rng)
+        lay, f0, dt, chi = mixed_request(rng, _parse_range(args.bits), tuple(int(c) for c in args.chis.split(",")))
         arrivals.append((t, lay, f0, dt, chi, int(rng.integers(max(2, args.steps // 4), args.steps + 1))))
-    b = vpmps.Batch(ctx, args.concurrency, 200 << 30)
+    b = vpmps.Batch(ctx, args.concurrency, 200 << 30, lockstep=args.groups)
     b.start()
     t0 = time.perf_counter()
     done, i = [], 0
@@ -493,7 +517,8 @@ def run_serve(args):
         "value": len(done) / wall, "unit": "sims/s", "n_gpus": 1, "higher_is_better": True, "dtype": DTYPE,
         "data": "synthetic",
         "config": {"arrivals": "Poisson", "rate_per_s": args.rate, "window_s": args.window, "requests": len(done),
-                   "steps_per_run": f"U[{max(2, args.steps // 4)}, {args.steps}]", "concurrency": args.concurrency,
+                   "steps_per_run": f"U[{max(2, args.steps // 4)}, {args.steps}]", "grid_bits": args.bits,
+                   "chis": args.chis, "lockstep_groups": args.groups, "resident_per_group": args.concurrency,
                    "seed": 1},
         "step_ms_p50": float(np.percentile(steps_ms, 50)), "step_ms_p99": float(np.percentile(steps_ms, 99)),
         "run_ms_p50": float(np.percentile(run_lat, 50)), "run_ms_p99": float(np.percentile(run_lat, 99)),

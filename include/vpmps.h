@@ -154,7 +154,8 @@ int vp_profile_trace(vp_ctx* ctx, vp_trace_rec* out, int cap, int* n_out);
  * Householder QR factorisations (iterated decomposition of reshapes, Sec.
  * "MPS Representation", Fig. 1a), then the truncated-SVD sweep with bond cap
  * chi and tolerance tol (truncation-error equation, Sec. "MPS
- * Representation").  Errors: VP_EINVAL (layout), VP_ENOMEM. */
+ * Representation").  Errors: VP_EINVAL (layout), VP_ENOMEM, VP_ENUMERIC (a
+ * NaN or Inf in f). */
 int mps_create(vp_ctx* ctx, const vp_layout* layout, const double* f, int f_on_device, int chi,
                double tol, mps_t** out);
 
@@ -411,6 +412,23 @@ int vp_group_size(const vp_group* g);
  * own launches failed (VP_ENOMEM, VP_ECUDA, ...), which stops every member.
  * Synchronises the context's stream. */
 int vp_group_step(vp_group* g, vp_record* records, int* status);
+/* Batched a1: `count` MPS at once (count <= 2 max_members), each exactly as
+ * mps_create would make it from the host grid f_host[i] on layouts[i] (site
+ * permutation, decomposition by a chain of Householder QR factorisations,
+ * truncated-SVD sweep with chi[i], tol[i]; the IG pair rule on IG layouts),
+ * with every factorisation of the same site of all grids in one batched
+ * launch.  out[i] receives the new MPS (owned by the caller, on the group's
+ * context) or NULL; status[i] VP_OK or the error of grid i alone (VP_EINVAL:
+ * bad layout, chi < 1 or tol < 1e-13; VP_ENUMERIC: NaN/Inf in the grid).
+ * The return value is VP_OK unless the batched launches themselves failed.
+ * Call between steps (it uses the group's rank records).  Synchronises the
+ * context's stream. */
+int vp_group_mps_create(vp_group* g, int count, const vp_layout* layouts, const double* const* f_host,
+                        const int* chi, const double* tol, mps_t** out, int* status);
+/* Diagnostics of the last vp_group_step: its host wall time (ms), the part
+ * spent waiting for the device at the rank reads (ms), the number of those
+ * waits and the number of kernels launched (each pointer may be NULL). */
+int vp_group_stats(const vp_group* g, double* step_ms, double* wait_ms, int64_t* waits, int64_t* launches);
 int vp_group_destroy(vp_group* g);
 
 /* ------------------------------------------------ several species (f_s) */
@@ -478,7 +496,24 @@ typedef struct {
 /* Device bytes a run needs (states, pre-compression sums, factorisation
  * workspaces), used for admission. */
 size_t vp_footprint_bytes(const vp_layout* layout, const vp_config* cfg);
+/* max_concurrent: resident runs at a time (1..64 worker threads; 1..4096 in
+ * lockstep mode).  Errors: VP_EINVAL. */
 int vp_batch_create(vp_ctx* ctx, int max_concurrent, size_t mem_budget_bytes, vp_batch** out);
+/* Lockstep mode (before vp_batch_start; groups = 0 turns it off): instead of
+ * one worker thread per run, `groups` workers (1..16), each with its own
+ * context and stream, keep their resident runs in a lockstep group
+ * (vp_group_*) and advance them all with one group step.  A worker holds runs
+ * of one site count at a time (the count of the first run it admits while
+ * empty), so runs of one size step together and the groups of different
+ * sizes overlap on the device.  Between steps, runs that have finished or
+ * failed leave and pending requests join -- first in, first out among those
+ * that match the worker's site count -- while at most max_concurrent runs
+ * are resident per worker and all footprints fit the budget (continuous
+ * batching).  A run's per-step latency is its group's step.  Requests must be
+ * eligible for a group (level C1, plain sweeps, FP64 or FP32 contractions,
+ * tol >= 1e-13); others end with VP_EINVAL.  Errors: VP_EINVAL, VP_EBUSY
+ * (already started). */
+int vp_batch_set_lockstep(vp_batch* b, int groups);
 /* Copies f0 (host, dense 2^(nx+nv)); keep_f != 0 keeps f(T) for
  * vp_batch_records.  Errors: VP_ECAPACITY (footprint above the budget). */
 int vp_batch_submit(vp_batch* b, const vp_layout* layout, const vp_config* cfg, const double* f0_host,

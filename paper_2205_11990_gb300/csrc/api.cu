@@ -61,7 +61,12 @@ void* dev_alloc(vp_ctx* ctx, size_t bytes) {
     return ctx->alloc(bytes, ctx->user);
   }
   void* p = nullptr;
-  if (cudaMallocAsync(&p, bytes, ctx->stream) != cudaSuccess) return nullptr;
+  const cudaError_t e = ctx->pool ? cudaMallocFromPoolAsync(&p, bytes, ctx->pool, ctx->stream)
+                                  : cudaMallocAsync(&p, bytes, ctx->stream);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    return nullptr;
+  }
   return p;
 }
 
@@ -183,7 +188,7 @@ int sync_status(vp_ctx* ctx) {
   VP_CUDA(ctx, cudaMemsetAsync(ctx->status, 0, sizeof(DevStatus), ctx->stream));
   VP_TRY(write_wait_limit(ctx));
   if (err == 1) return fail(ctx, VP_ETIMEOUT, "a device-side grid barrier gave up waiting");
-  if (err == 2) return fail(ctx, VP_ENUMERIC, "NaN or Inf in singular values");
+  if (err == 2) return fail(ctx, VP_ENUMERIC, "NaN or Inf in the input or the singular values");
   return fail(ctx, VP_ENUMERIC, "Jacobi SVD did not converge");
 }
 
@@ -793,6 +798,22 @@ int vp_ctx_create(void* cuda_stream, vp_alloc_fn alloc, vp_free_fn free_fn, void
     return VP_ECUDA;
   }
   c->num_sms = prop.multiProcessorCount;
+  if (!alloc) {
+    // a pool of this context's own that keeps freed memory for reuse (the
+    // device's default pool returns it to the system at every synchronise,
+    // and the sweeps synchronise once per SVD site)
+    cudaMemPoolProps pp = {};
+    pp.allocType = cudaMemAllocationTypePinned;
+    pp.handleTypes = cudaMemHandleTypeNone;
+    pp.location.type = cudaMemLocationTypeDevice;
+    pp.location.id = dev;
+    if (cudaMemPoolCreate(&c->pool, &pp) != cudaSuccess) {
+      delete c;
+      return VP_ECUDA;
+    }
+    uint64_t keep = ~0ull;
+    cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  }
   c->cluster_size = vp::probe_cluster_size();
   int coop = 0;
   cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
@@ -843,6 +864,8 @@ int vp_ctx_destroy(vp_ctx* c) {
   for (cudaEvent_t e : {c->ev_qf[0], c->ev_qf[1], c->ev_qd[0], c->ev_qd[1]})
     if (e) cudaEventDestroy(e);
   if (c->owns_stream) cudaStreamDestroy(c->stream);
+  // memory still outstanding (frees not yet completed) returns when they are
+  if (c->pool) cudaMemPoolDestroy(c->pool);
   delete c;
   return VP_OK;
 }
@@ -939,6 +962,7 @@ int mps_create(vp_ctx* ctx, const vp_layout* L, const double* f, int f_on_device
   VP_TRY(reserve(ctx, sites, N));
   VP_CUDA(ctx, cudaMemcpyAsync(grid.p, f, N * sizeof(double),
                                f_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->stream));
+  VP_TRY(launch_check_finite(ctx, grid.p, N));
   VP_TRY(launch_permute_to_sites(ctx, grid.p, L->nx, L->nv, L->mapping, sites.p, 0));
   mps_t* m = new mps_t();
   const int g0 = ctx->grouped;

@@ -58,6 +58,7 @@ double quantile(std::vector<double> v, double q) {
 struct vp_batch {
   vp_ctx* parent = nullptr;
   int max_conc = 1;
+  int lockstep = 0;  // > 0: that many workers, each stepping its resident runs as one lockstep group
   size_t budget = 0;
   std::mutex mu;
   std::condition_variable cv;
@@ -74,6 +75,13 @@ struct vp_batch {
 };
 
 extern "C" int vp_ctx_create(void* cuda_stream, vp_alloc_fn alloc, vp_free_fn free_fn, void* user, vp_ctx** out);
+
+// A request resident in the lockstep group.
+struct Resident {
+  Req* r = nullptr;
+  vp_sim* sim = nullptr;
+  int done = 0;
+};
 
 namespace {
 
@@ -98,6 +106,142 @@ void run_request(vp_ctx* ctx, Req* r) {
   r->f0.clear();
   r->f0.shrink_to_fit();
   r->status = st;
+}
+
+// Retire a resident run: its final state (keep_f) and its record.
+void retire(vp_batch* b, vp_ctx* ctx, vp_group* g, Resident& rs, int status) {
+  Req* r = rs.r;
+  if (status == VP_OK && r->keep_f) {
+    r->fT.resize((size_t)1 << (r->lay.nx + r->lay.nv));
+    status = mps_to_grid(ctx, vp_sim_state(rs.sim), &r->lay, r->fT.data());
+  }
+  if (rs.sim) {
+    if (g) vp_group_remove(g, rs.sim);
+    vp_sim_destroy(rs.sim);
+  }
+  r->recs.resize(rs.done);
+  r->step_ms.resize(rs.done);
+  r->status = status;
+  r->t_end = now_ms();
+  {
+    std::lock_guard<std::mutex> lk(b->mu);
+    b->in_use -= r->footprint;
+    b->active--;
+    b->unfinished--;
+    r->done = true;
+  }
+  b->cv.notify_all();
+}
+
+// Continuous batching in lockstep: between group steps, runs that finished
+// or failed leave the group and pending requests join it while slots and
+// memory allow; every group step advances all resident runs with batched
+// launches (vp_group_step).  A run's per-step latency is the group step's.
+// With several lockstep workers, each keeps a group of runs with the same
+// number of sites (its key, taken from the first run it admits while empty):
+// runs of one size step together, and the groups of different sizes overlap
+// on the device.  Requests are taken first-in first-out among those that
+// match the worker's key and fit the budget.
+int site_count(const Req* r) { return r->lay.nx + r->lay.nv; }
+
+void lockstep_loop(vp_batch* b, int w) {
+  vp_ctx* ctx = b->wctx[w];
+  cudaSetDevice(ctx->device);
+  vp_group* g = nullptr;
+  if (vp_group_create(ctx, b->max_conc, &g) != VP_OK) g = nullptr;
+  std::vector<Resident> res;
+  int key = -1;  // site count of this worker's runs (-1: none resident)
+  auto admissible = [&](std::deque<Req*>& q) {
+    for (auto it = q.begin(); it != q.end(); ++it)
+      if ((key < 0 || site_count(*it) == key) && b->in_use + (*it)->footprint <= b->budget) return it;
+    return q.end();
+  };
+  for (;;) {
+    std::vector<Req*> admit;
+    {
+      std::unique_lock<std::mutex> lk(b->mu);
+      b->cv.wait(lk, [&] { return b->stop || !res.empty() || admissible(b->pending) != b->pending.end(); });
+      if (b->stop) break;
+      for (;;) {
+        if ((int)(res.size() + admit.size()) >= b->max_conc) break;
+        auto it = admissible(b->pending);
+        if (it == b->pending.end()) break;
+        Req* r = *it;
+        b->pending.erase(it);
+        b->in_use += r->footprint;
+        b->active++;
+        key = site_count(r);
+        admit.push_back(r);
+      }
+    }
+    // the admitted runs' initial MPS in one batched decomposition
+    const int na = (int)admit.size();
+    std::vector<vp_layout> lays(na);
+    std::vector<const double*> fs(na);
+    std::vector<int> chis(na), cst(na, VP_OK);
+    std::vector<double> tols(na);
+    std::vector<mps_t*> ms(na, nullptr);
+    for (int a = 0; a < na; ++a) {
+      admit[a]->t_start = now_ms();
+      lays[a] = admit[a]->lay;
+      fs[a] = admit[a]->f0.data();
+      chis[a] = admit[a]->cfg.chi;
+      tols[a] = admit[a]->cfg.tol;
+    }
+    int gst = g ? VP_OK : VP_ENOMEM;
+    if (gst == VP_OK && na > 0)
+      gst = vp_group_mps_create(g, na, lays.data(), fs.data(), chis.data(), tols.data(), ms.data(), cst.data());
+    for (int a = 0; a < na; ++a) {
+      Req* r = admit[a];
+      Resident rs;
+      rs.r = r;
+      r->recs.resize(r->nsteps);
+      r->step_ms.resize(r->nsteps);
+      mps_t* m = ms[a];
+      int st = gst != VP_OK ? gst : cst[a];
+      if (st == VP_OK) st = vp_sim_create(ctx, &r->lay, &r->cfg, m, &rs.sim);
+      if (m) mps_destroy(m);
+      if (st == VP_OK && r->nsteps > 0) st = vp_group_add(g, rs.sim);
+      r->f0.clear();
+      r->f0.shrink_to_fit();
+      if (st != VP_OK || r->nsteps == 0) {
+        if (st != VP_OK && rs.sim) {
+          vp_sim_destroy(rs.sim);
+          rs.sim = nullptr;
+        }
+        retire(b, ctx, nullptr, rs, st);
+        continue;
+      }
+      res.push_back(rs);
+    }
+    if (res.empty()) {
+      key = -1;
+      continue;
+    }
+    std::vector<vp_record> recs(res.size());
+    std::vector<int> status(res.size(), VP_OK);
+    const double t0 = now_ms();
+    const int st = vp_group_step(g, recs.data(), status.data());
+    const double dt_ms = now_ms() - t0;
+    std::vector<Resident> keep;
+    for (size_t i = 0; i < res.size(); ++i) {
+      Resident& rs = res[i];
+      int si = st != VP_OK ? st : status[i];
+      if (si == VP_OK) {
+        rs.r->recs[rs.done] = recs[i];
+        rs.r->step_ms[rs.done] = dt_ms;
+        rs.done++;
+      }
+      if (si != VP_OK || rs.done >= rs.r->nsteps)
+        retire(b, ctx, g, rs, si);
+      else
+        keep.push_back(rs);
+    }
+    res.swap(keep);
+    if (res.empty()) key = -1;
+  }
+  for (Resident& rs : res) retire(b, ctx, g, rs, VP_EBUSY);
+  if (g) vp_group_destroy(g);
 }
 
 void worker_loop(vp_batch* b, int w) {
@@ -151,26 +295,50 @@ size_t vp_footprint_bytes(const vp_layout* L, const vp_config* cfg) {
 }
 
 int vp_batch_create(vp_ctx* parent, int max_concurrent, size_t mem_budget_bytes, vp_batch** out) {
-  if (!parent || !out || max_concurrent < 1 || max_concurrent > 64 || mem_budget_bytes == 0) return VP_EINVAL;
+  if (!parent || !out || max_concurrent < 1 || max_concurrent > 4096 || mem_budget_bytes == 0) return VP_EINVAL;
   vp_batch* b = new vp_batch();
   b->parent = parent;
   b->max_conc = max_concurrent;
   b->budget = mem_budget_bytes;
-  for (int w = 0; w < max_concurrent; ++w) {
+  *out = b;
+  return VP_OK;
+}
+
+// Worker contexts, each with its own stream: one per worker thread, or one
+// for the lockstep worker (whose grid-cooperative kernels may use every SM).
+static int make_workers(vp_batch* b) {
+  vp_ctx* parent = b->parent;
+  const int nw = b->lockstep ? b->lockstep : b->max_conc;
+  if (!b->lockstep && nw > 64) return vp::fail(parent, VP_EINVAL, "vp_batch: at most 64 worker threads");
+  for (int w = 0; w < nw; ++w) {
     cudaStream_t st = nullptr;
     vp_ctx* c = nullptr;
     if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||
         vp_ctx_create(st, nullptr, nullptr, nullptr, &c) != VP_OK) {
       if (st) cudaStreamDestroy(st);
       for (vp_ctx* x : b->wctx) vp_ctx_destroy(x);
-      delete b;
-      return vp::fail(parent, VP_ECUDA, "vp_batch_create: worker context failed");
+      b->wctx.clear();
+      return vp::fail(parent, VP_ECUDA, "vp_batch_start: worker context failed");
     }
     c->owns_stream = true;
-    c->coop_cap = std::max(16, parent->num_sms / max_concurrent);
+    c->coop_cap = std::max(16, parent->num_sms / nw);
+    c->wait_clocks = parent->wait_clocks;
+    if (vp::write_wait_limit(c) != VP_OK) {
+      vp_ctx_destroy(c);
+      for (vp_ctx* x : b->wctx) vp_ctx_destroy(x);
+      b->wctx.clear();
+      return vp::fail(parent, VP_ECUDA, "vp_batch_start: worker context failed");
+    }
     b->wctx.push_back(c);
   }
-  *out = b;
+  return VP_OK;
+}
+
+int vp_batch_set_lockstep(vp_batch* b, int groups) {
+  if (!b || groups < 0 || groups > 16) return VP_EINVAL;
+  std::lock_guard<std::mutex> lk(b->mu);
+  if (b->started) return vp::fail(b->parent, VP_EBUSY, "vp_batch_set_lockstep: workers already started");
+  b->lockstep = groups;
   return VP_OK;
 }
 
@@ -204,8 +372,12 @@ int vp_batch_start(vp_batch* b) {
   if (!b) return VP_EINVAL;
   std::lock_guard<std::mutex> lk(b->mu);
   if (b->started) return VP_OK;
+  VP_TRY(make_workers(b));
   b->started = true;
-  for (int w = 0; w < b->max_conc; ++w) b->workers.emplace_back(worker_loop, b, w);
+  if (b->lockstep)
+    for (int w = 0; w < b->lockstep; ++w) b->workers.emplace_back(lockstep_loop, b, w);
+  else
+    for (int w = 0; w < b->max_conc; ++w) b->workers.emplace_back(worker_loop, b, w);
   return VP_OK;
 }
 

@@ -64,6 +64,7 @@ struct vp_ctx {
   cudaStream_t stream = nullptr;
   vp_alloc_fn alloc = nullptr;
   vp_free_fn freef = nullptr;
+  cudaMemPool_t pool = nullptr;  // without caller allocator hooks: this context's pool (memory kept until destroy)
   void* user = nullptr;
   std::string err;
   int64_t launches = 0;
@@ -244,6 +245,8 @@ int launch_site_sum(vp_ctx* ctx, const SiteSum& s, double* out, int ol, int orr)
 // T (rl x rr) = core[:,0,:] + core[:,1,:]
 int launch_phys_sum(vp_ctx* ctx, const double* core, int rl, int rr, double* T);
 int launch_copy(vp_ctx* ctx, const double* src, double* dst, size_t n);
+// Status error 2 (VP_ENUMERIC at the next status read) if x holds a NaN or Inf.
+int launch_check_finite(vp_ctx* ctx, const double* x, size_t n);
 int launch_scale(vp_ctx* ctx, double* x, size_t n, double s);
 // Core (a, 2, b) -> (b, 2, a): the site read in the opposite chain direction.
 int launch_core_transpose(vp_ctx* ctx, const double* in, int a, int b, double* out);
@@ -352,6 +355,8 @@ struct BScale { double* x; size_t n; double s; };
 struct BPoisson { const double* rho; int N; double dx; double* E; double* we; };
 struct BAssemble { const double* U; int ul, ur; ETermSite e; int first, last; double* out; int ol, orr; };
 struct BPermute { const double* f; int nx, nv, mapping; double* out; int inverse; };
+struct BCheck { const double* x; size_t n; DevStatus* st; };
+int blaunch_check_finite(vp_ctx* ctx, cudaStream_t st, const std::vector<BCheck>& v);
 int blaunch_copy(vp_ctx* ctx, cudaStream_t st, const std::vector<BCopy>& v);
 int blaunch_site_sum(vp_ctx* ctx, cudaStream_t st, const std::vector<BSiteSum>& v);
 int blaunch_phys_sum(vp_ctx* ctx, cudaStream_t st, const std::vector<BPhysSum>& v);

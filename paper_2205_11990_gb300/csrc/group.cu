@@ -19,6 +19,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -84,6 +85,7 @@ struct Task {
   Work* w = nullptr;
   int slot = 0;    // TaskDev record
   int member = 0;
+  int* status = nullptr;  // the owner's status (a member's, or a creation job's)
   // the SVD site in flight
   int k = 0, m = 0, c = 0, pl = 0, q = 0, p = 0, r = 1;
   bool tall = false;
@@ -104,6 +106,13 @@ struct vp_group {
   cudaStream_t side = nullptr;
   cudaEvent_t ev_qf[2] = {nullptr, nullptr}, ev_qd[2] = {nullptr, nullptr};
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  // diagnostics of the last step: host wall time, time spent waiting for the
+  // device, host waits, kernel launches
+  double stat_step_ms = 0, stat_wait_ms = 0;
+  int64_t stat_waits = 0, stat_launches = 0;
+  // batched MPS creation: workspaces and buffers of each job (grow-only)
+  std::vector<vp::Work> cwork;
+  std::vector<vp::DevBuf> cgrid, csites, crem;
 };
 
 namespace vp {
@@ -120,23 +129,29 @@ struct OnSide {
   ~OnSide() { std::swap(c->stream, *side); }
 };
 
-bool alive(const vp_group* g, const Task* t) { return g->mem[t->member]->status == VP_OK; }
+bool alive(const vp_group*, const Task* t) { return *t->status == VP_OK; }
 
 // Wait for the group's stream, read every problem's record, and stop the
 // members whose kernels reported an error (each member fails alone).
+double wall_ms() {
+  return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
 int sync_records(vp_group* g, int ntask_slots) {
   vp_ctx* ctx = g->ctx;
   VP_CUDA(ctx, cudaMemcpyAsync(g->h_task, g->d_task, sizeof(TaskDev) * ntask_slots, cudaMemcpyDeviceToHost,
                                ctx->stream));
+  const double t0 = wall_ms();
   VP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  g->stat_wait_ms += wall_ms() - t0;
+  g->stat_waits++;
   return VP_OK;
 }
 
 void mark_failures(vp_group* g, const Tasks& ts) {
   for (Task* t : ts) {
     const int e = g->h_task[t->slot].st.err;
-    Member* mb = g->mem[t->member];
-    if (e != 0 && mb->status == VP_OK) mb->status = e == 1 ? VP_ETIMEOUT : VP_ENUMERIC;
+    if (e != 0 && *t->status == VP_OK) *t->status = e == 1 ? VP_ETIMEOUT : VP_ENUMERIC;
   }
 }
 
@@ -152,6 +167,19 @@ std::vector<int> live_ids(const vp_group* g, const std::vector<int>& ids) {
   for (int i : ids)
     if (g->mem[i]->status == VP_OK) o.push_back(i);
   return o;
+}
+
+// The contraction mode of a member's GEMMs (its whole step, as in vp_step).
+int fp32_of(const Member* mb) { return mb->sim->cfg.precision == VP_PREC_FP32_CONTRACT ? 1 : 0; }
+
+// Status words and rank records of every problem back to their initial
+// state (counters zero, the context's wait limit), in stream order.
+int reset_records(vp_group* g) {
+  vp_ctx* ctx = g->ctx;
+  for (int r = 0; r < 2 * g->cap; ++r) g->h_init[r].st.wait_clocks = ctx->wait_clocks;
+  VP_CUDA(ctx, cudaMemcpyAsync(g->d_task, g->h_init, sizeof(TaskDev) * 2 * g->cap, cudaMemcpyHostToDevice,
+                               ctx->stream));
+  return VP_OK;
 }
 
 // ------------------------------------------------------------ QR sweep
@@ -386,59 +414,67 @@ int compress(vp_group* g, const Tasks& ts) {
   return svd_sweep(g, ts);
 }
 
-// ------------------------------------------------------------ field
-// E (device, 2^nx) of every member as an MPS in the site order of the x bits
-// (api.cu's from_vector: a chain of QR factorisations of reshapes, then the
-// truncated-SVD sweep at e_tol, capped at e_chi).
-int field_mps(vp_group* g, const std::vector<int>& ids) {
+// ------------------------------------------------------------ decomposition
+// A site-ordered device vector (2^n) as an MPS, for several problems at once:
+// api.cu's from_vector -- a chain of Householder QR factorisations of the
+// reshapes (MPS decomposition, "MPS Representation"), then the truncated-SVD
+// sweep -- in lockstep over the sites.
+struct VecJob {
+  mps_t* out;
+  const double* vec;  // device, 2^n, read before anything is written
+  int n;
+  int chi;
+  double tol;
+  bool pairs;  // IG pair rule in the SVD sweep
+  int fp32;
+  Work* w;
+  DevBuf* rem;  // the remaining reshaped vector (2^n)
+  int slot;
+  int* status;
+};
+
+int from_vectors(vp_group* g, const std::vector<VecJob>& jobs) {
   vp_ctx* ctx = g->ctx;
   std::vector<BCopy> cp;
-  std::vector<BPermute> pm;
   int nmax = 0;
-  for (int i : ids) {
-    Member* mb = g->mem[i];
-    vp_sim* s = mb->sim;
-    const int nx = s->lay.nx;
-    const size_t N = (size_t)1 << nx;
-    mps_free(&s->em);
-    mps_init(ctx, &s->em, nx);
-    mb->wa.main.st = mb->wa.side.st = &g->d_task[2 * i].st;
-    VP_TRY(reserve(ctx, mb->rem, N));
-    if (xdesc(&s->lay)) {
-      VP_TRY(reserve(ctx, s->evec, N));
-      pm.push_back({s->E.p, nx, 0, VP_SEQ_S2, s->evec.p, 0});
-      cp.push_back({s->evec.p, mb->rem.p, N});
+  for (const VecJob& jb : jobs) {
+    const size_t N = (size_t)1 << jb.n;
+    if (jb.out->n != jb.n || jb.out->ctx != ctx) {
+      mps_free(jb.out);
+      mps_init(ctx, jb.out, jb.n);
     } else {
-      cp.push_back({s->E.p, mb->rem.p, N});
+      jb.out->r.assign(jb.n + 1, 1);  // the cores' buffers are kept and overwritten
     }
-    nmax = std::max(nmax, nx);
+    jb.w->main.st = jb.w->side.st = &g->d_task[jb.slot].st;
+    VP_TRY(reserve(ctx, *jb.rem, N));
+    cp.push_back({jb.vec, jb.rem->p, N});
+    nmax = std::max(nmax, jb.n);
   }
-  VP_TRY(blaunch_permute(ctx, ctx->stream, pm));
   VP_TRY(blaunch_copy(ctx, ctx->stream, cp));
-  std::vector<int> rr(g->mem.size(), 1);
+  std::vector<int> rr(jobs.size(), 1);
   for (int k = 0; k + 1 < nmax; ++k) {
     std::vector<BColMajor> cm;
     std::vector<BQR> qr;
     std::vector<BFormQ> fq;
     std::vector<BGetR> gr;
-    for (int i : ids) {
-      Member* mb = g->mem[i];
-      vp_sim* s = mb->sim;
-      const int n = s->lay.nx;
-      if (k + 1 >= n) continue;
-      Work& w = mb->wa;
-      const size_t N = (size_t)1 << n;
-      const int m = 2 * rr[i];
-      const int nc = (int)(N >> (k + 1)), p = std::min(m, nc);
+    for (size_t a = 0; a < jobs.size(); ++a) {
+      const VecJob& jb = jobs[a];
+      if (k + 1 >= jb.n) continue;
+      Work& w = *jb.w;
+      const size_t N = (size_t)1 << jb.n;
+      const int m = 2 * rr[a];
+      const size_t cols = N >> (k + 1);
+      if (cols > (size_t)1 << 30) return fail(ctx, VP_ECAPACITY, "vector too long");
+      const int nc = (int)cols, p = std::min(m, nc);
       VP_TRY(reserve(ctx, w.fac, (size_t)m * nc));
       VP_TRY(reserve(ctx, w.p, (size_t)2 * m + p + 8));
-      VP_TRY(reserve(ctx, s->em.core[k], (size_t)m * p));
-      cm.push_back({mb->rem.p, m, nc, w.fac.p});
+      VP_TRY(reserve(ctx, jb.out->core[k], (size_t)m * p));
+      cm.push_back({jb.rem->p, m, nc, w.fac.p});
       qr.push_back({w.fac.p, m, nc, w.p.p, w.p.p + p + 8, &w.main});
-      fq.push_back({w.fac.p, m, nc, w.p.p, s->em.core[k].p, &w.main});
-      gr.push_back({w.fac.p, m, nc, mb->rem.p});
-      s->em.r[k + 1] = p;
-      rr[i] = p;
+      fq.push_back({w.fac.p, m, nc, w.p.p, jb.out->core[k].p, &w.main});
+      gr.push_back({w.fac.p, m, nc, jb.rem->p});
+      jb.out->r[k + 1] = p;
+      rr[a] = p;
     }
     VP_TRY(blaunch_to_colmajor(ctx, ctx->stream, cm));
     VP_TRY(blaunch_qr_factor(ctx, ctx->stream, qr));
@@ -446,27 +482,49 @@ int field_mps(vp_group* g, const std::vector<int>& ids) {
     VP_TRY(blaunch_qr_getr(ctx, ctx->stream, gr));
   }
   cp.clear();
-  std::vector<Task> tasks(ids.size());
+  std::vector<Task> tasks(jobs.size());
   Tasks ts;
-  for (size_t a = 0; a < ids.size(); ++a) {
-    const int i = ids[a];
-    vp_sim* s = g->mem[i]->sim;
-    const int n = s->lay.nx;
-    VP_TRY(reserve(ctx, s->em.core[n - 1], (size_t)2 * rr[i]));
-    cp.push_back({g->mem[i]->rem.p, s->em.core[n - 1].p, (size_t)2 * rr[i]});
+  for (size_t a = 0; a < jobs.size(); ++a) {
+    const VecJob& jb = jobs[a];
+    VP_TRY(reserve(ctx, jb.out->core[jb.n - 1], (size_t)2 * rr[a]));
+    cp.push_back({jb.rem->p, jb.out->core[jb.n - 1].p, (size_t)2 * rr[a]});
     Task& t = tasks[a];
-    t.s = &s->em;
-    t.chi = s->cfg.e_chi > 0 ? s->cfg.e_chi : 1 << 30;
-    t.tol = s->cfg.e_tol;
-    t.pairs = false;  // the field MPS holds x bits only
-    t.fp32 = s->cfg.precision == VP_PREC_FP32_CONTRACT;
-    t.w = &g->mem[i]->wa;
-    t.slot = 2 * i;
-    t.member = i;
-    if (n > 1) ts.push_back(&t);
+    t.s = jb.out;
+    t.chi = jb.chi;
+    t.tol = jb.tol;
+    t.pairs = jb.pairs;
+    t.fp32 = jb.fp32;
+    t.w = jb.w;
+    t.slot = jb.slot;
+    t.status = jb.status;
+    if (jb.n > 1) ts.push_back(&t);
   }
   VP_TRY(blaunch_copy(ctx, ctx->stream, cp));
   return svd_sweep(g, ts);
+}
+
+// E (device, 2^nx) of every member as an MPS in the site order of the x
+// bits, truncated at e_tol and capped at e_chi (the field MPS holds x bits
+// only: no pair rule).
+int field_mps(vp_group* g, const std::vector<int>& ids) {
+  vp_ctx* ctx = g->ctx;
+  std::vector<BPermute> pm;
+  std::vector<VecJob> jobs;
+  for (int i : ids) {
+    Member* mb = g->mem[i];
+    vp_sim* s = mb->sim;
+    const int nx = s->lay.nx;
+    const double* ev = s->E.p;
+    if (xdesc(&s->lay)) {
+      VP_TRY(reserve(ctx, s->evec, (size_t)1 << nx));
+      pm.push_back({s->E.p, nx, 0, VP_SEQ_S2, s->evec.p, 0});
+      ev = s->evec.p;
+    }
+    jobs.push_back({&s->em, ev, nx, s->cfg.e_chi > 0 ? s->cfg.e_chi : 1 << 30, s->cfg.e_tol, false, fp32_of(mb),
+                    &mb->wa, &mb->rem, 2 * i, &mb->status});
+  }
+  VP_TRY(blaunch_permute(ctx, ctx->stream, pm));
+  return from_vectors(g, jobs);
 }
 
 // L(E) = U + diag(E) (x) D_v of every member (api.cu's assemble_operator):
@@ -516,9 +574,6 @@ int assemble(vp_group* g, const std::vector<int>& ids) {
   }
   return blaunch_assemble(ctx, ctx->stream, as);
 }
-
-// The contraction mode of a member's GEMMs (its whole step, as in vp_step).
-int fp32_of(const Member* mb) { return mb->sim->cfg.precision == VP_PREC_FP32_CONTRACT ? 1 : 0; }
 
 // rho = dv * (every v site contracted with [1, 1], the x chain expanded) for
 // every member (api.cu's density), lockstep over the site index.
@@ -730,9 +785,7 @@ int group_step(vp_group* g, vp_record* recs) {
   for (int i = 0; i < nm; ++i)
     if (g->mem[i]->status == VP_OK) ids.push_back(i);
   if (ids.empty()) return VP_OK;
-  for (int r = 0; r < 2 * g->cap; ++r) g->h_init[r].st.wait_clocks = ctx->wait_clocks;
-  VP_CUDA(ctx, cudaMemcpyAsync(g->d_task, g->h_init, sizeof(TaskDev) * 2 * g->cap, cudaMemcpyHostToDevice,
-                               ctx->stream));
+  VP_TRY(reset_records(g));
   for (int i : ids) {
     Member* mb = g->mem[i];
     mb->fi = mb->acc = &mb->sim->f;
@@ -755,6 +808,7 @@ int group_step(vp_group* g, vp_record* recs) {
       const double dt = s->cfg.dt;
       Task& ta = tasks[2 * a];
       ta.member = i;
+      ta.status = &mb->status;
       ta.slot = 2 * i;
       ta.tol = s->cfg.tol;
       ta.pairs = grouped(&s->lay);
@@ -805,6 +859,7 @@ int group_step(vp_group* g, vp_record* recs) {
   for (int i : live_ids(g, ids))
     for (int h = 0; h < 2; ++h) {
       chk[2 * i + h].member = i;
+      chk[2 * i + h].status = &g->mem[i]->status;
       chk[2 * i + h].slot = 2 * i + h;
       all.push_back(&chk[2 * i + h]);
     }
@@ -916,7 +971,13 @@ int vp_group_size(const vp_group* g) { return g ? (int)g->mem.size() : -1; }
 
 int vp_group_step(vp_group* g, vp_record* records, int* status) {
   if (!g) return VP_EINVAL;
+  g->stat_wait_ms = 0;
+  g->stat_waits = 0;
+  const int64_t l0 = g->ctx->launches;
+  const double t0 = wall_ms();
   const int st = group_step(g, records);
+  g->stat_step_ms = wall_ms() - t0;
+  g->stat_launches = g->ctx->launches - l0;
   if (st != VP_OK) {
     // an error of the group's own launches (not of one member's arithmetic):
     // every member that was still running is stopped with it
@@ -930,6 +991,85 @@ int vp_group_step(vp_group* g, vp_record* records, int* status) {
   return st;
 }
 
+int vp_group_mps_create(vp_group* g, int count, const vp_layout* layouts, const double* const* f_host,
+                        const int* chi, const double* tol, mps_t** out, int* status) {
+  if (!g || count < 0 || (count > 0 && (!layouts || !f_host || !chi || !tol || !out || !status)))
+    return VP_EINVAL;
+  vp_ctx* ctx = g->ctx;
+  if (count > 2 * g->cap) return fail(ctx, VP_ECAPACITY, "vp_group_mps_create: more than 2 max_members grids");
+  if ((int)g->cwork.size() < count) {
+    g->cwork.resize(count);
+    g->cgrid.resize(count);
+    g->csites.resize(count);
+    g->crem.resize(count);
+  }
+  VP_TRY(reset_records(g));
+  std::vector<BPermute> pm;
+  std::vector<VecJob> jobs;
+  for (int i = 0; i < count; ++i) {
+    out[i] = nullptr;
+    status[i] = VP_OK;
+    const vp_layout* L = &layouts[i];
+    if (!layout_ok(L) || !f_host[i] || chi[i] < 1 || !(tol[i] >= 1e-13)) {
+      status[i] = VP_EINVAL;
+      continue;
+    }
+    const int n = L->nx + L->nv;
+    const size_t N = (size_t)1 << n;
+    mps_t* m = new (std::nothrow) mps_t();
+    if (!m) {
+      status[i] = VP_ENOMEM;
+      continue;
+    }
+    int st = reserve(ctx, g->cgrid[i], N);
+    if (st == VP_OK) st = reserve(ctx, g->csites[i], N);
+    if (st == VP_OK && cudaMemcpyAsync(g->cgrid[i].p, f_host[i], N * sizeof(double), cudaMemcpyHostToDevice,
+                                       ctx->stream) != cudaSuccess)
+      st = fail(ctx, VP_ECUDA, "vp_group_mps_create: copy failed");
+    if (st != VP_OK) {
+      delete m;
+      status[i] = st;
+      continue;
+    }
+    out[i] = m;
+    pm.push_back({g->cgrid[i].p, L->nx, L->nv, L->mapping, g->csites[i].p, 0});
+    jobs.push_back({m, g->csites[i].p, n, chi[i], tol[i], grouped(L), 0, &g->cwork[i], &g->crem[i], i, &status[i]});
+  }
+  std::vector<BCheck> ck;
+  for (const VecJob& jb : jobs) ck.push_back({g->cgrid[jb.slot].p, (size_t)1 << jb.n, &g->d_task[jb.slot].st});
+  int st = blaunch_check_finite(ctx, ctx->stream, ck);
+  if (st == VP_OK) st = blaunch_permute(ctx, ctx->stream, pm);
+  if (st == VP_OK) st = from_vectors(g, jobs);
+  if (st == VP_OK) st = sync_records(g, count);
+  if (st == VP_OK) {
+    Tasks all;
+    std::vector<Task> chk(jobs.size());
+    for (size_t a = 0; a < jobs.size(); ++a) {
+      chk[a].slot = jobs[a].slot;
+      chk[a].status = jobs[a].status;
+      all.push_back(&chk[a]);
+    }
+    mark_failures(g, all);
+  }
+  for (int i = 0; i < count; ++i)
+    if (out[i] && (st != VP_OK || status[i] != VP_OK)) {
+      if (st != VP_OK && status[i] == VP_OK) status[i] = st;
+      mps_free(out[i]);
+      delete out[i];
+      out[i] = nullptr;
+    }
+  return st;
+}
+
+int vp_group_stats(const vp_group* g, double* step_ms, double* wait_ms, int64_t* waits, int64_t* launches) {
+  if (!g) return VP_EINVAL;
+  if (step_ms) *step_ms = g->stat_step_ms;
+  if (wait_ms) *wait_ms = g->stat_wait_ms;
+  if (waits) *waits = g->stat_waits;
+  if (launches) *launches = g->stat_launches;
+  return VP_OK;
+}
+
 int vp_group_destroy(vp_group* g) {
   if (!g) return VP_EINVAL;
   vp_ctx* ctx = g->ctx;
@@ -937,6 +1077,9 @@ int vp_group_destroy(vp_group* g) {
   cudaStreamSynchronize(ctx->stream);
   for (Member* m : g->mem) free_member(ctx, m);
   g->mem.clear();
+  for (Work& w : g->cwork) release_work(ctx, w);
+  for (auto* v : {&g->cgrid, &g->csites, &g->crem})
+    for (DevBuf& b : *v) release(ctx, b);
   dev_free(ctx, g->d_task, sizeof(TaskDev) * 2 * (size_t)g->cap);
   dev_free(ctx, g->d_we, sizeof(double) * 4 * (size_t)g->cap);
   if (g->h_task) cudaFreeHost(g->h_task);

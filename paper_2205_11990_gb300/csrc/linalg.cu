@@ -189,11 +189,12 @@ __global__ void __launch_bounds__(kThreads) k_qr_factor(double* A, int m, int n,
 // a further power of two (v and tau do not depend on the scale), so no
 // square leaves the FP32 range.  The output A, tau is the FP64 LAPACK layout
 // of k_qr_factor.
-__global__ void __launch_bounds__(kThreads) k_qr_factor_dw(double* A, int m, int n, double* tau, dw* V, dw* T,
-                                                          dw* gcols, int* gexp, DevStatus* st) {
+// nb blocks factor the matrix, this block is number bid of them.
+__device__ __forceinline__ void qr_factor_dw_body(double* A, int m, int n, double* tau, dw* V, dw* T, dw* gcols,
+                                                  int* gexp, DevStatus* st, const int nb, const int bid) {
   extern __shared__ dw cols_sm[];
   __shared__ int s_ok;
-  const int nb = gridDim.x, bid = blockIdx.x, tid = threadIdx.x;
+  const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
   const int p = min(m, n);
   const int nown = bid < n ? (n - bid + nb - 1) / nb : 0;
@@ -340,6 +341,11 @@ __global__ void __launch_bounds__(kThreads) k_qr_factor_dw(double* A, int m, int
       __threadfence();
     }
   }
+}
+
+__global__ void __launch_bounds__(kThreads) k_qr_factor_dw(double* A, int m, int n, double* tau, dw* V, dw* T,
+                                                          dw* gcols, int* gexp, DevStatus* st) {
+  qr_factor_dw_body(A, m, n, tau, V, T, gcols, gexp, st, gridDim.x, blockIdx.x);
 }
 
 // Cluster-resident double-word QR (small factors).  Column k lives in CTA
@@ -2203,8 +2209,68 @@ __global__ void __launch_bounds__(NT) kb_qr_factor_cl(const __grid_constant__ Pa
   k_qr_factor_cl_body<NT, CW>(a.A, a.m, a.n, a.tau);
 }
 
+// Several grid factors in one cooperative launch: problem i owns blocks
+// first .. first + nblocks - 1 and runs k_qr_factor_dw's body on them as if
+// they were its whole grid (the result does not depend on the block count).
+struct QRGridArgs {
+  double* A;
+  int m, n;
+  double* tau;
+  dw* V;
+  dw* T;
+  dw* gcols;
+  int* gexp;
+  DevStatus* st;
+  int first, nblocks;
+};
+__global__ void __launch_bounds__(kThreads) kb_qr_factor_dw(const __grid_constant__ Pack<QRGridArgs> pk, int count) {
+  int i = 0;
+  while (i + 1 < count && (int)blockIdx.x >= pk.a[i + 1].first) ++i;
+  const QRGridArgs& a = pk.a[i];
+  qr_factor_dw_body(a.A, a.m, a.n, a.tau, a.V, a.T, a.gcols, a.gexp, a.st, a.nblocks, blockIdx.x - a.first);
+}
+
+// The grid factors of a batch: each launch takes up to kMaxBatch problems
+// that each get at least two blocks, one block per SM in all.
+static int grid_qr_batch(vp_ctx* ctx, cudaStream_t st, const std::vector<const BQR*>& v) {
+  static AttrOnce qattr;
+  VP_TRY(qattr.ensure(ctx, (const void*)kb_qr_factor_dw, 200 * 1024, false));
+  const int per_launch = std::min(kMaxBatch, std::max(1, ctx->num_sms / 2));
+  for (size_t i0 = 0; i0 < v.size(); i0 += per_launch) {
+    const int cnt = (int)std::min<size_t>(per_launch, v.size() - i0);
+    const int share = std::max(2, ctx->num_sms / cnt);
+    Pack<QRGridArgs> pk{};
+    int total = 0;
+    size_t smem = 0;
+    for (int c = 0; c < cnt; ++c) {
+      const BQR& q = *v[i0 + c];
+      const int p = std::min(q.m, q.n);
+      const int blocks = std::max(2, std::min(share, q.n / 2));
+      const int nmax = (q.n + blocks - 1) / blocks;
+      const size_t need = (size_t)nmax * q.m * sizeof(dw) + (size_t)nmax * sizeof(int);
+      VP_TRY(reserve(ctx, q.s->qrv, (size_t)q.m * p + p + 8));
+      QRGridArgs& a = pk.a[c];
+      a = {q.A, q.m, q.n, q.tau, reinterpret_cast<dw*>(q.s->qrv.p), nullptr, nullptr, nullptr, q.s->st, total, blocks};
+      a.T = a.V + (size_t)q.m * p;
+      if (need > 200 * 1024) {  // columns in global scratch
+        VP_TRY(reserve(ctx, q.s->qrc, (size_t)q.m * q.n + q.n / 2 + 8));
+        a.gcols = reinterpret_cast<dw*>(q.s->qrc.p);
+        a.gexp = reinterpret_cast<int*>(a.gcols + (size_t)q.m * q.n);
+      } else {
+        smem = std::max(smem, need);
+      }
+      total += blocks;
+    }
+    int count = cnt;
+    void* args[] = {&pk, &count};
+    VP_TRY(coop_launch(ctx, st, (const void*)kb_qr_factor_dw, total, kThreads, args, smem, "b_qr_factor_dw"));
+  }
+  return VP_OK;
+}
+
 int blaunch_qr_factor(vp_ctx* ctx, cudaStream_t st, const std::vector<BQR>& v) {
   std::vector<BQR> wide;
+  std::vector<const BQR*> grid;
   std::vector<QRArgs> cdw[17], cl[17];
   size_t cdw_smem[17] = {}, cl_smem[17] = {};
   for (const BQR& q : v) {
@@ -2225,7 +2291,10 @@ int blaunch_qr_factor(vp_ctx* ctx, cudaStream_t st, const std::vector<BQR>& v) {
         break;
       default:
         if (!q.s || !q.s->st) return fail(ctx, VP_EINVAL, "batched QR: no status words for a grid factor");
-        VP_TRY(qr_factor_grid(ctx, st, q.s->st, q.s->qrv, q.s->qrc, q.A, q.m, q.n, q.tau, q.vbuf));
+        if (q.n / 2 >= 2)
+          grid.push_back(&q);
+        else  // a single block: the barrier kernel of the single path
+          VP_TRY(qr_factor_grid(ctx, st, q.s->st, q.s->qrv, q.s->qrc, q.A, q.m, q.n, q.tau, q.vbuf));
     }
   }
   for (int cs = 2; cs <= 16; ++cs) {
@@ -2242,6 +2311,7 @@ int blaunch_qr_factor(vp_ctx* ctx, cudaStream_t st, const std::vector<BQR>& v) {
                                std::max<size_t>(cl_smem[cs], 116 * 1024)));
     }
   }
+  if (!grid.empty()) VP_TRY(grid_qr_batch(ctx, st, grid));
   if (!wide.empty()) {  // the square block, its Q, R2^T = A2^T Q in FP64, copied back (see qr_plan)
     std::vector<BQR> sq;
     std::vector<BFormQ> fq;

@@ -392,6 +392,24 @@ int launch_mpo_dense_step(vp_ctx* ctx, const double* T, int rows, int cols, int 
   return check_launch(ctx, "mpo_dense");
 }
 
+// Input check: any NaN or Inf among n values sets the status error 2 (the
+// factorisations do not propagate every NaN: a column whose norm is NaN forms
+// no reflector, so a corrupt input must be caught before them).
+__device__ __forceinline__ void k_check_finite_body(const double* __restrict__ x, size_t n, DevStatus* st) {
+  bool bad = false;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+    bad |= !isfinite(x[e]);
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicCAS(&st->err, 0, 2);
+}
+__global__ void k_check_finite(const double* __restrict__ x, size_t n, DevStatus* st) { k_check_finite_body(x, n, st); }
+
+int launch_check_finite(vp_ctx* ctx, const double* x, size_t n) {
+  if (n == 0) return VP_OK;
+  ctx->launches++;
+  k_check_finite<<<grid_for(ctx, n), 256, 0, ctx->stream>>>(x, n, ctx->status);
+  return check_launch(ctx, "check_finite");
+}
+
 // ====================================================== batched launches
 // (see common.cuh): the body of each single-problem kernel for the problem the
 // grid's y coordinate selects, with that problem's own x extent.
@@ -415,6 +433,14 @@ int run_packs(vp_ctx* ctx, cudaStream_t st, const std::vector<A>& v, void (*kern
 }
 }  // namespace
 
+__global__ void kb_check_finite(const __grid_constant__ Pack<BCheck> pk) {
+  const BCheck& a = pk.a[blockIdx.y];
+  k_check_finite_body(a.x, a.n, a.st);
+}
+int blaunch_check_finite(vp_ctx* ctx, cudaStream_t st, const std::vector<BCheck>& v) {
+  return run_packs(ctx, st, v, kb_check_finite, 256, 0, [&](const BCheck& a) { return grid_for(ctx, a.n); },
+                   "b_check_finite");
+}
 __global__ void kb_copy(const __grid_constant__ Pack<BCopy> pk) {
   const BCopy& a = pk.a[blockIdx.y];
   k_copy_body(a.src, a.dst, a.n);

@@ -40,9 +40,9 @@ EXPORTS = [
     "mps_apply_mpo", "mps_axpby", "mps_compress", "mps_compress_modified", "vp_density", "vp_poisson", "vp_poisson_noalloc", "vp_gemm",
     "vp_sim_create", "vp_sim_destroy", "vp_step", "vp_sim_state", "vp_sim_entropy", "vp_sim_flops", "vp_run",
     "vp_footprint_bytes", "vp_batch_create", "vp_batch_submit", "vp_batch_start", "vp_batch_wait", "vp_batch_poll",
-    "vp_batch_records", "vp_batch_destroy",
+    "vp_batch_records", "vp_batch_destroy", "vp_batch_set_lockstep",
     "vp_multi_create", "vp_multi_destroy", "vp_multi_step", "vp_multi_state",
-    "vp_group_create", "vp_group_add", "vp_group_remove", "vp_group_size", "vp_group_step", "vp_group_destroy",
+    "vp_group_create", "vp_group_add", "vp_group_remove", "vp_group_size", "vp_group_step", "vp_group_stats", "vp_group_mps_create", "vp_group_destroy",
 ]
 
 
@@ -159,6 +159,7 @@ def load():
         "vp_batch_poll": (I, [P, C.POINTER(CResult), I, C.POINTER(I)]),
         "vp_batch_records": (I, [P, C.c_uint64, C.POINTER(CRecord), DP, DP]),
         "vp_batch_destroy": (I, [P]),
+        "vp_batch_set_lockstep": (I, [P, I]),
         "vp_multi_create": (I, [P, I, C.POINTER(CLayout), C.POINTER(CSpecies), C.POINTER(CConfig), C.POINTER(P),
                                 C.POINTER(P)]),
         "vp_multi_destroy": (I, [P]),
@@ -170,6 +171,8 @@ def load():
         "vp_group_size": (I, [P]),
         "vp_group_step": (I, [P, C.POINTER(CRecord), IP]),
         "vp_group_destroy": (I, [P]),
+        "vp_group_stats": (I, [P, DP, DP, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+        "vp_group_mps_create": (I, [P, I, C.POINTER(CLayout), C.POINTER(DP), IP, DP, C.POINTER(P), IP]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -442,13 +445,18 @@ class Context:
 
 
 class Batch:
-    """Concurrent independent runs (vp_batch_*): submit, start, wait/poll."""
+    """Concurrent independent runs (vp_batch_*): submit, start, wait/poll.
+    lockstep=G > 0: G workers, each stepping its resident runs (one site
+    count per worker) as one lockstep group (continuous batching); else one
+    worker thread per run."""
 
-    def __init__(self, ctx: Context, max_concurrent: int, mem_budget_bytes: int):
+    def __init__(self, ctx: Context, max_concurrent: int, mem_budget_bytes: int, lockstep: int = 0):
         self.ctx = ctx
         h = C.c_void_p()
         ctx._check(ctx.lib.vp_batch_create(ctx.h, max_concurrent, mem_budget_bytes, C.byref(h)))
         self.h = h
+        if lockstep:
+            ctx._check(ctx.lib.vp_batch_set_lockstep(h, int(lockstep)))
         self.nsteps = {}
         ctx._children.add(self)
 
@@ -649,6 +657,26 @@ class Group:
         st = np.zeros(max(1, n), dtype=np.int32)
         self.ctx._check(self.ctx.lib.vp_group_step(self.h, recs, _ip(st)))
         return _records(recs, n), [int(x) for x in st[:n]]
+
+    def create_mps(self, items):
+        """Batched a1: items = [(layout, f host grid, chi, tol)] -> ([MPS or
+        None], [status]) as mps_create would make each."""
+        n = len(items)
+        lays = (CLayout * max(1, n))(*[clayout(l) for l, _, _, _ in items])
+        grids = [np.ascontiguousarray(f, dtype=np.float64) for _, f, _, _ in items]
+        fptr = (C.POINTER(C.c_double) * max(1, n))(*[_dp(gr) for gr in grids])
+        chis = np.array([c for _, _, c, _ in items], dtype=np.int32)
+        tols = np.array([t for _, _, _, t in items], dtype=np.float64)
+        outs = (C.c_void_p * max(1, n))()
+        st = np.zeros(max(1, n), dtype=np.int32)
+        self.ctx._check(self.ctx.lib.vp_group_mps_create(self.h, n, lays, fptr, _ip(chis), _dp(tols), outs, _ip(st)))
+        return [MPS(self.ctx, C.c_void_p(h)) if h else None for h in outs[:n]], [int(x) for x in st[:n]]
+
+    def stats(self):
+        """Last step: host wall ms, ms waiting for the device, waits, launches."""
+        a, b, c, d = C.c_double(), C.c_double(), C.c_int64(), C.c_int64()
+        self.ctx._check(self.ctx.lib.vp_group_stats(self.h, C.byref(a), C.byref(b), C.byref(c), C.byref(d)))
+        return {"step_ms": a.value, "wait_ms": b.value, "waits": c.value, "launches": d.value}
 
     def close(self):
         if self.h and self.ctx.h:

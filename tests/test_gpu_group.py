@@ -178,3 +178,49 @@ def test_ineligible_members_refused(ctx):
     with pytest.raises(VpError):
         grp.add(ctx.sim(lay, ctx.mps_from_grid(lay, f0, 8, 1e-10), 0.05, 8, streams=1))  # full
     grp.close()
+
+
+def test_batched_creation_equals_mps_create(ctx):
+    cases = member_cases()
+    items = [(lay, f0, chi, 1e-10) for lay, f0, dt, chi, prec in cases]
+    bad = cases[0][1].copy()
+    bad[1, 2] = np.nan
+    items.append((cases[0][0], bad, 8, 1e-10))             # NaN grid: fails alone
+    items.append((cases[1][0], cases[1][1], 8, 0.0))       # exact mode: not batched
+    grp = ctx.group(8)
+    ms, status = grp.create_mps(items)
+    assert status[:-2] == [0] * len(cases) and status[-2] == VP_ENUMERIC and status[-1] == VP_EINVAL
+    assert ms[-1] is None and ms[-2] is None
+    for (lay, f0, chi, tol), m in zip(items[:-2], ms[:-2]):
+        ref = ctx.mps_from_grid(lay, f0, chi, tol)
+        assert m.bonds() == ref.bonds()
+        assert all(np.array_equal(a, b) for a, b in zip(m.cores(), ref.cores()))
+    grp.close()
+
+
+def test_group_equals_alone_with_grid_factors(ctx):
+    # 9 + 9 interleaved members: the tolerance-only stage compressions carry
+    # bonds of r W (W ~ 12 + 3 D_F) whose factors exceed a cluster's shared
+    # memory and run on the cooperative grid kernel, several problems per launch
+    cases = []
+    for amp, chi, ic in ((0.3, 16, "landau"), (0.05, 32, "bump"), (0.2, 24, "landau")):
+        if ic == "landau":
+            lay = I.Layout(9, 9, 0.0, 4 * math.pi, -6.0, 6.0, I.INTERLEAVED)
+            f0 = I.landau(lay, amp, 0.5)
+        else:
+            lay = I.Layout(9, 9, 0.0, 2 * math.pi / 0.3, -8.0, 8.0, I.INTERLEAVED)
+            f0 = I.bump_on_tail(lay, amp, 0.3)
+        cases.append((lay, f0, 0.6 * (lay.xmax - lay.xmin) / lay.Nx / lay.vmax, chi))
+    grp = ctx.group(len(cases))
+    gs, al = [], []
+    for lay, f0, dt, chi in cases:
+        s = ctx.sim(lay, ctx.mps_from_grid(lay, f0, chi, 1e-10), dt, chi, streams=1)
+        grp.add(s)
+        gs.append(s)
+        al.append(ctx.sim(lay, ctx.mps_from_grid(lay, f0, chi, 1e-10), dt, chi))
+    recs, status = grp.step()
+    assert status == [0] * len(cases)
+    for i, (lay, *_r) in enumerate(cases):
+        assert recs[i] == al[i].step(1)[0], i
+        assert np.array_equal(gs[i].state().to_grid(lay), al[i].state().to_grid(lay)), i
+    grp.close()
