@@ -27,12 +27,35 @@ sys.path.insert(0, ROOT)
 
 WORKLOAD = "saturated_two_stream_1024x1024_seq"
 CHI, TOL, DT = 64, 1e-10, 0.002
-FP64_PEAK_GFLOPS = 2 * 2 * 152 * 2.070  # 2 DFMA/clk/SM x 2 flop x 152 SMs x 2070 MHz (nominal 1.25 TF/s)
+FP64_PEAK_GFLOPS = 2 * 2 * 152 * 2.070  # 2 DFMA/clk/SM x 2 flop x 152 SMs x 2070 MHz (nominal 1.26 TF/s)
+# The factorisations (QR, Q formation, Jacobi) run in double-word FP32: their
+# roof is the FP32 pipe (128 lanes/SM/clk x 152 SMs x 2070 MHz) over the FP32
+# instructions per pair of FP64-equivalent flops of their work mix -- half
+# compensated dot-product steps (12 instructions), half double-word axpy
+# updates (29): 20.5 instructions per 2 flops, 3.93 TF/s.
+DW_PEAK_GFLOPS = 128 * 152 * 2.070 * 2 / 20.5
 # What the path computes in: FP64 storage, contractions, Poisson and truncation
 # rule; the QR, Q formation and Jacobi SVD in double-word FP32 (~2^-48).
 DTYPE = "f64 storage/contractions, df32 (~2^-48) factorisations"
-NCU_TRAFFIC = {"qr_factor": 637.6e3, "jacobi": 70.3e3}  # DRAM bytes per launch from the ncu captures under profiles/
-NCU_TRAFFIC_SPECIES = {"qr_factor": 466.0e3}  # two-species workload, same source
+PROFILES = os.path.join(ROOT, "profiles")
+KERNEL_OF_CLASS = {"qr_factor": "k_qr_factor_cl", "jacobi": "k_jacobi_dw", "gemm": "k_gemm",
+                   "qr_formq": "k_qr_formq_reg", "apply": "k_site_sum", "select": "k_select"}
+
+
+def profile_traffic(kernel, workload):
+    """DRAM bytes (read + write) per launch of `kernel` on `workload`, from the
+    `bench-traffic:` lines of the ncu summaries under profiles/ (None when no
+    capture of that kernel and workload is committed)."""
+    if not os.path.isdir(PROFILES):
+        return None
+    for fn in sorted(os.listdir(PROFILES)):
+        if not fn.endswith(".md"):
+            continue
+        for line in open(os.path.join(PROFILES, fn)):
+            parts = line.split()
+            if len(parts) == 4 and parts[0] == "bench-traffic:" and parts[1] == kernel and parts[2] == workload:
+                return float(parts[3])
+    return None
 
 
 def parse():
@@ -43,7 +66,8 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline (profiling runs)")
-    p.add_argument("--mode", default="step", choices=["step", "batch", "serve", "precision", "species"],
+    p.add_argument("--mode", default="step", choices=["step", "batch", "serve", "precision", "species", "peaks",
+                                                          "compressibility"],
                    help="step: the headline single-run steps/s; batch / serve: many runs on one GPU; "
                         "species: electrons and ions on one field (Buneman, Dougherty collisions)")
     p.add_argument("--species-workload", default="saturated_buneman_512x512_s3",
@@ -182,6 +206,8 @@ def run_ours(args, rank, world):
     sim = ctx.sim(lay, m, DT, CHI, TOL, TOL)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > 129 MB L2
+    # measured rates of the units the kernels run on (outside the timed region)
+    probes = {k: ctx.peak_probe(k) for k in ("fp64_fma", "dw_dot", "dw_axpy", "fp32_fma", "dmma")}
     for _ in range(args.warmup):
         sim.step(1)
     torch.cuda.synchronize()
@@ -210,7 +236,7 @@ def run_ours(args, rank, world):
     ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev), world)
     steps_per_s = job_rate(world, args.steps, ms)
 
-    roof = roofline(prof, ms, world, NCU_TRAFFIC if WORKLOAD == "saturated_two_stream_1024x1024_seq" else {})
+    roof = roofline(prof, ms, world, WORKLOAD, probes)
 
     e2e = None
     if not args.no_e2e:
@@ -246,24 +272,43 @@ def run_ours(args, rank, world):
         print(json.dumps(out), flush=True)
 
 
-def roofline(prof, ms, world, traffic):
+def roofline(prof, ms, world, workload, probes=None):
     """Roofline entry of the dominant kernel class of the profiled window."""
     top = max(prof, key=lambda k: prof[k][0])
     tms, tl, work = prof[top]
     if top == "apply":
         achieved = work / (tms / 1e3) / 1e9
-        roof = {"bound": "hbm", "achieved": achieved, "peak": 6783.1, "unit": "GB/s"}
+        roof = {"bound": "hbm", "achieved": achieved, "peak": 6789.6, "unit": "GB/s",
+                "peak_basis": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
     else:
         achieved = work / (tms / 1e3) / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS / 1e3, "unit": "TFLOP/s"}
+        if top == "gemm":  # FP64 GEMMs on the FP64 pipe
+            roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS / 1e3, "unit": "TFLOP/s",
+                    "peak_basis": "FP64 FMA: 2 DFMA/clk/SM x 152 SMs x 2070 MHz (derived from unit counts)"}
+        else:  # double-word factorisations on the FP32 pipe
+            peak = DW_PEAK_GFLOPS / 1e3
+            basis = ("double-word FP32: 128 FP32 lanes/clk/SM x 152 SMs x 2070 MHz x 2 flops / 20.5 FP32 "
+                     "instructions (derived from unit counts)")
+            if probes and probes.get("dw_dot") and probes.get("dw_axpy"):
+                # the measured rate of the same dot/update mix, when higher
+                # (the compiler fuses a few of the counted instructions)
+                mix = 2.0 / (1.0 / probes["dw_dot"] + 1.0 / probes["dw_axpy"])
+                if mix > peak:
+                    peak = mix
+                    basis = "double-word FP32 dot/update mix, measured by vp_peak_probe on this GPU (of measured)"
+            roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "peak_basis": basis,
+                    "peak_fp64": FP64_PEAK_GFLOPS / 1e3, "frac_fp64": achieved / (FP64_PEAK_GFLOPS / 1e3)}
     roof["frac"] = roof["achieved"] / roof["peak"]
+    kernel = KERNEL_OF_CLASS.get(top, top)
     # DRAM bytes (read + write) per launch of the dominant kernel, from the ncu
-    # captures summarised under profiles/ (two launches each, that workload)
-    roof["traffic"] = traffic.get(top)
-    roof["kernel"] = {"qr_factor": "k_qr_factor_cl", "jacobi": "k_jacobi_dw", "gemm": "k_gemm",
-                      "qr_formq": "k_qr_formq_dw", "apply": "k_site_sum", "select": "k_select"}.get(top, top)
+    # captures summarised under profiles/
+    roof["traffic"] = profile_traffic(kernel, workload)
+    roof["kernel"] = kernel
+    roof["class"] = top
     roof["launches"] = tl
     roof["share_of_step"] = tms / ms * world if ms else None
+    if probes:
+        roof["measured_tflops"] = {k: round(v, 4) for k, v in probes.items()}
     return roof
 
 
@@ -330,7 +375,7 @@ def run_species(args, rank, world):
         "vs_baseline": None, "dtype": DTYPE, "data": "synthetic",
         "config": {"workload": name, "species": species, "chi": chi, "tol": TOL, "dt": dt,
                    "parallelism": f"replicas x{world}", "l2": "flushed between timed steps (256 MB write)"},
-        "roofline": roofline(prof, ms, world, NCU_TRAFFIC_SPECIES if name == "saturated_buneman_512x512_s3" else {}),
+        "roofline": roofline(prof, ms, world, name),
         "gpu_launches": launches, "clocks": clk, "e2e": e2e,
         "diag": {"max_bond": [max(r["max_bond"][s] for r in recs) for s in range(len(lays))],
                  "field_energy": recs[-1]["field_energy"], "kernel_ms": {k: round(v[0], 3) for k, v in prof.items()}},
@@ -567,8 +612,60 @@ def run_precision(args):
         "modes": modes}), flush=True)
 
 
+def run_compressibility(args):
+    """State compressibility (main text, "State Compressibility", the rms
+    compression error against D): nonlinear Landau (A = 0.5, k = 0.5, the
+    paper's set-up) run with no bond cap at tol = 1e-10 on several grids for
+    --steps steps, then the rms error over the grid of f - f_D for each D."""
+    import math
+    import __graft_entry__ as g
+    g.build()
+    from paper_2205_11990_gb300 import inputs as I
+    from paper_2205_11990_gb300 import vpmps
+    ctx = vpmps.Context()
+    chis = [2, 4, 8, 16, 32, 64]
+    out = {}
+    for bits in (6, 7, 8):
+        lay = I.Layout(bits, bits, 0.0, 4 * math.pi, -6.0, 6.0, I.SEQ)
+        f0 = I.landau(lay, 0.5, 0.5)
+        dt = 0.6 * (lay.xmax - lay.xmin) / lay.Nx / lay.vmax
+        full = 1 << bits
+        sim = ctx.sim(lay, ctx.mps_from_grid(lay, f0, full, TOL), dt, full, TOL, TOL)
+        t0 = time.perf_counter()
+        recs = sim.step(args.steps)
+        t = time.perf_counter() - t0
+        st = sim.state()
+        f = st.to_grid(lay)
+        rms_f = float((f * f).mean() ** 0.5)
+        err = ctx.compression_error(st, chis, 0.0)
+        out[f"{lay.Nx}x{lay.Nv}"] = {"t": recs[-1]["t"] + dt, "max_bond": max(st.bonds()), "rms_f": rms_f,
+                                    "rms_error": {str(c): float(e) for c, e in zip(chis, err)},
+                                    "steps_per_s": args.steps / t}
+        sim.close()
+    print(json.dumps({"metric": "rms compression error vs bond dimension (nonlinear Landau)", "unit": "rms of f - f_D",
+                      "dtype": DTYPE, "data": "synthetic", "config": {"ic": "Landau A=0.5 k=0.5, seq",
+                      "steps": args.steps, "tol": TOL, "D": chis}, "grids": out}), flush=True)
+
+
+def run_peaks(args):
+    """Measured rates of the arithmetic units the kernels run on."""
+    import __graft_entry__ as g
+    g.build()
+    from paper_2205_11990_gb300 import vpmps
+    ctx = vpmps.Context()
+    probes = {k: ctx.peak_probe(k) for k in vpmps.Context.PROBES}
+    print(json.dumps({"metric": "measured arithmetic rates", "unit": "TFLOP/s (FP64-equivalent flops)",
+                      "measured": probes,
+                      "derived": {"fp64_fma": FP64_PEAK_GFLOPS / 1e3, "dw_factorisation_mix": DW_PEAK_GFLOPS / 1e3,
+                                  "fp32_fma": 128 * 152 * 2.070 * 2 / 1e3}}), flush=True)
+
+
 def main():
     args = parse()
+    if args.mode == "peaks":
+        return run_peaks(args)
+    if args.mode == "compressibility":
+        return run_compressibility(args)
     if args.mode == "precision":
         return run_precision(args)
     if args.mode == "batch":

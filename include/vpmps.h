@@ -110,6 +110,18 @@ int vp_ctx_create(void* cuda_stream, vp_alloc_fn alloc, vp_free_fn free_fn, void
                   vp_ctx** out);
 int vp_ctx_destroy(vp_ctx* ctx);
 const char* vp_last_error(const vp_ctx* ctx);
+/* Arithmetic-rate probes (no counterpart in the paper; diagnostics for the
+ * roofline of the kernels): the measured throughput, TFLOP/s of FP64-
+ * equivalent flops, of one unit kind on this device -- VP_PROBE_FP64_FMA
+ * (FP64 FMA, 2 flops), VP_PROBE_FP32_FMA (FP32 FMA, 2 flops),
+ * VP_PROBE_DW_DOT (one double-word compensated dot-product step, 12 FP32
+ * instructions, 2 flops), VP_PROBE_DW_AXPY (one double-word c - w v element,
+ * 29 FP32 instructions, 2 flops), VP_PROBE_DMMA (FP64 mma.sync m8n8k4).  One
+ * warm-up and one timed launch of ~10 ms on the context's stream; no device
+ * setting is touched.  Errors: VP_EINVAL, VP_ENOMEM, VP_ECUDA. */
+enum { VP_PROBE_FP64_FMA = 0, VP_PROBE_FP32_FMA = 1, VP_PROBE_DW_DOT = 2, VP_PROBE_DW_AXPY = 3, VP_PROBE_DMMA = 4 };
+int vp_peak_probe(vp_ctx* ctx, int kind, double* tflops_out);
+
 /* Failure detection (no counterpart in the paper).  The device-side waits of
  * the cooperative kernels (the grid barrier, the published-reflector counter
  * of the grid QR) spin at most `clocks` SM clocks (default 2e9, ~1 s; 0
@@ -238,6 +250,14 @@ int mps_axpby(vp_ctx* ctx, double a, const mps_t* x, double b, const mps_t* y, m
  * trunc_err_out: n-1 doubles (host) or NULL.  Errors: VP_ETIMEOUT,
  * VP_ENUMERIC. */
 int mps_compress(vp_ctx* ctx, mps_t* inout, int chi, double tol, double* trunc_err_out);
+/* Compressibility diagnostic (main text, "State Compressibility", the rms
+ * compression error against the bond dimension D): for each chi[i] a copy of
+ * f compressed with bond cap chi[i] and tolerance tol (mps_compress), and
+ * rms_out[i] = sqrt(sum_j (f_j - f_D,j)^2 / 2^n), the rms difference of the
+ * two dense vectors over all 2^n grid points, summed on the GPU in a fixed
+ * order (never from MPS overlaps, which cancel catastrophically).  f is not
+ * changed.  n <= 24.  rms_out: nchi doubles (host).  Errors: VP_EINVAL. */
+int mps_compression_error(vp_ctx* ctx, const mps_t* f, int nchi, const int* chi, double tol, double* rms_out);
 /* Modified centre-bond-first compression (SI "Modified Compression Scheme")
  * about the bond after site split-1 (1 <= split < n; for a sequential
  * ordering, split = nx is the x / v cut): the bond is put at the centre of a

@@ -216,6 +216,19 @@ def compress_with_entropy(cores, chi, tol):
     return out, errs, ee
 
 
+def compression_error(cores, chis, tol=0.0):
+    """rms compression error against the bond dimension (main text, "State
+    Compressibility", the rms error figure): for each D in chis,
+    sqrt(mean((f - f_D)^2)) over all 2^n grid points, f_D the state
+    compressed with bond cap D and tolerance tol."""
+    f = to_dense(cores)
+    out = []
+    for chi in chis:
+        fd = to_dense(compress(cores, chi, tol)[0])
+        out.append(float(np.sqrt(np.mean((f - fd) ** 2))))
+    return np.array(out)
+
+
 def from_dense(vec, n, chi, tol):
     """Exact TT-SVD followed by :func:`compress` (used for f0 and for E)."""
     return compress(tt_svd(vec, n), chi, tol)[0]

@@ -1254,6 +1254,36 @@ int mps_compress(vp_ctx* ctx, mps_t* m, int chi, double tol, double* errs) {
   return VP_OK;
 }
 
+int mps_compression_error(vp_ctx* ctx, const mps_t* f, int nchi, const int* chi, double tol, double* rms_out) {
+  if (!ctx || !f || nchi < 1 || !chi || !rms_out || tol < 0 || f->n > 24)
+    return fail(ctx, VP_EINVAL, "mps_compression_error: bad argument");
+  for (int i = 0; i < nchi; ++i)
+    if (chi[i] < 1) return fail(ctx, VP_EINVAL, "mps_compression_error: chi < 1");
+  const size_t N = (size_t)1 << f->n;
+  DevBuf full, part, scratch;
+  VP_TRY(to_dense_dev(ctx, f, full));
+  VP_TRY(reserve(ctx, scratch, 1024 + 64));
+  int st = VP_OK;
+  for (int i = 0; i < nchi && st == VP_OK; ++i) {
+    mps_t c;
+    mps_init(ctx, &c, 0);
+    st = mps_copy(ctx, f, &c);
+    if (st == VP_OK) st = compress(ctx, &c, chi[i], tol, nullptr);
+    if (st == VP_OK) st = to_dense_dev(ctx, &c, part);
+    if (st == VP_OK) st = launch_sqdiff(ctx, full.p, part.p, N, scratch.p, scratch.p + 1024 + i % 64);
+    if (st == VP_OK && cudaMemcpyAsync(rms_out + i, scratch.p + 1024 + i % 64, sizeof(double), cudaMemcpyDeviceToHost,
+                                       ctx->stream) != cudaSuccess)
+      st = fail(ctx, VP_ECUDA, "mps_compression_error: copy failed");
+    if (st == VP_OK) st = sync_status(ctx);
+    mps_free(&c);
+    if (st == VP_OK) rms_out[i] = std::sqrt(rms_out[i] / (double)N);
+  }
+  release(ctx, full);
+  release(ctx, part);
+  release(ctx, scratch);
+  return st;
+}
+
 int vp_density(vp_ctx* ctx, const vp_layout* L, const mps_t* f, double* rho_dev) {
   if (!ctx || !f || !rho_dev || !layout_ok(L) || L->nx + L->nv != f->n)
     return fail(ctx, VP_EINVAL, "vp_density: bad argument");

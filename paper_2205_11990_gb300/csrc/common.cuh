@@ -245,6 +245,8 @@ int launch_site_sum(vp_ctx* ctx, const SiteSum& s, double* out, int ol, int orr)
 // T (rl x rr) = core[:,0,:] + core[:,1,:]
 int launch_phys_sum(vp_ctx* ctx, const double* core, int rl, int rr, double* T);
 int launch_copy(vp_ctx* ctx, const double* src, double* dst, size_t n);
+// *out (device) = sum_i (a_i - b_i)^2 in a fixed order; scratch: 1024 doubles.
+int launch_sqdiff(vp_ctx* ctx, const double* a, const double* b, size_t n, double* scratch, double* out);
 // Status error 2 (VP_ENUMERIC at the next status read) if x holds a NaN or Inf.
 int launch_check_finite(vp_ctx* ctx, const double* x, size_t n);
 int launch_scale(vp_ctx* ctx, double* x, size_t n, double s);

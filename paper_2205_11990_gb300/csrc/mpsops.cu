@@ -410,6 +410,43 @@ int launch_check_finite(vp_ctx* ctx, const double* x, size_t n) {
   return check_launch(ctx, "check_finite");
 }
 
+// Sum of squared differences of two vectors, in a fixed order: per-block
+// partial sums (grid-stride), then one block adds the partials in block
+// order (deterministic, unlike atomics).
+__global__ void k_sqdiff_partial(const double* __restrict__ a, const double* __restrict__ b, size_t n,
+                                 double* __restrict__ part) {
+  __shared__ double red[32];
+  double acc = 0.0;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    const double d = a[e] - b[e];
+    acc = fma(d, d, acc);
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    part[blockIdx.x] = t;
+  }
+}
+__global__ void k_sum_partials(const double* __restrict__ part, int nb, double* __restrict__ out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < nb; ++i) t += part[i];
+    *out = t;
+  }
+}
+
+int launch_sqdiff(vp_ctx* ctx, const double* a, const double* b, size_t n, double* scratch, double* out) {
+  const int blocks = std::min(1024, grid_for(ctx, n));
+  ctx->launches += 2;
+  k_sqdiff_partial<<<blocks, 256, 0, ctx->stream>>>(a, b, n, scratch);
+  VP_TRY(check_launch(ctx, "sqdiff"));
+  k_sum_partials<<<1, 32, 0, ctx->stream>>>(scratch, blocks, out);
+  return check_launch(ctx, "sum_partials");
+}
+
 // ====================================================== batched launches
 // (see common.cuh): the body of each single-problem kernel for the problem the
 // grid's y coordinate selects, with that problem's own x extent.

@@ -31,13 +31,14 @@ ERRORS = {1: "VP_EINVAL", 2: "VP_ENOMEM", 3: "VP_ECAPACITY", 4: "VP_ECUDA", 5: "
           6: "VP_ENUMERIC", 7: "VP_ECFL", 8: "VP_EBUSY", 9: "VP_EIO"}
 
 EXPORTS = [
-    "vp_ctx_create", "vp_ctx_destroy", "vp_last_error", "vp_ctx_set_wait_limit", "vp_kernel_launches", "vp_profile_enable",
+    "vp_ctx_create", "vp_ctx_destroy", "vp_last_error", "vp_ctx_set_wait_limit", "vp_kernel_launches",
+    "vp_peak_probe", "vp_profile_enable",
     "vp_profile_read", "vp_profile_trace",
     "mps_create", "mps_create_cores", "mps_destroy", "mps_num_sites", "mps_bonds", "mps_get_cores",
     "mps_to_dense", "mps_to_grid", "mps_save", "mps_load", "mps_file_info",
     "mpo_create_vp", "mpo_create_vlasov", "mpo_create_cores", "mpo_destroy", "mpo_num_sites", "mpo_bonds",
     "mpo_to_dense",
-    "mps_apply_mpo", "mps_axpby", "mps_compress", "mps_compress_modified", "vp_density", "vp_poisson", "vp_poisson_noalloc", "vp_gemm",
+    "mps_apply_mpo", "mps_axpby", "mps_compress", "mps_compress_modified", "mps_compression_error", "vp_density", "vp_poisson", "vp_poisson_noalloc", "vp_gemm",
     "vp_sim_create", "vp_sim_destroy", "vp_step", "vp_sim_state", "vp_sim_entropy", "vp_sim_flops", "vp_run",
     "vp_footprint_bytes", "vp_batch_create", "vp_batch_submit", "vp_batch_start", "vp_batch_wait", "vp_batch_poll",
     "vp_batch_records", "vp_batch_destroy", "vp_batch_set_lockstep",
@@ -114,6 +115,7 @@ def load():
         "vp_ctx_destroy": (I, [P]),
         "vp_last_error": (C.c_char_p, [P]),
         "vp_ctx_set_wait_limit": (I, [P, C.c_longlong]),
+        "vp_peak_probe": (I, [P, I, DP]),
         "vp_kernel_launches": (C.c_int64, [P]),
         "vp_profile_enable": (I, [P, I]),
         "vp_profile_read": (I, [P, I, DP, C.POINTER(C.c_int64), DP]),
@@ -140,6 +142,7 @@ def load():
         "mps_axpby": (I, [P, D, P, D, P, P]),
         "mps_compress": (I, [P, P, I, D, DP]),
         "mps_compress_modified": (I, [P, P, I, I, D, DP]),
+        "mps_compression_error": (I, [P, P, I, IP, D, DP]),
         "vp_density": (I, [P, C.POINTER(CLayout), P, P]),
         "vp_poisson": (I, [P, P, I, D, P, DP]),
         "vp_poisson_noalloc": (I, [P, P, I, D, P, DP, DP]),
@@ -257,6 +260,14 @@ class Context:
         Failure injection on the host: the allocator hook returns NULL."""
         self._budget[0] = n
 
+    PROBES = {"fp64_fma": 0, "fp32_fma": 1, "dw_dot": 2, "dw_axpy": 3, "dmma": 4}
+
+    def peak_probe(self, kind: str) -> float:
+        """Measured TFLOP/s (FP64-equivalent flops) of one unit kind."""
+        out = C.c_double()
+        self._check(self.lib.vp_peak_probe(self.h, self.PROBES[kind], C.byref(out)))
+        return out.value
+
     def set_wait_limit(self, clocks: int):
         """SM clocks a device-side wait spins before giving up (0: default)."""
         self._check(self.lib.vp_ctx_set_wait_limit(self.h, int(clocks)))
@@ -362,6 +373,13 @@ class Context:
         errs = np.zeros(max(1, x.n - 1))
         self._check(self.lib.mps_compress(self.h, x.h, chi, tol, _dp(errs)))
         return errs[: x.n - 1]
+
+    def compression_error(self, x: "MPS", chis, tol: float = 0.0) -> np.ndarray:
+        """rms over the grid of f - f_D for each bond cap D in chis."""
+        ch = np.ascontiguousarray(chis, dtype=np.int32)
+        out = np.zeros(len(ch))
+        self._check(self.lib.mps_compression_error(self.h, x.h, len(ch), _ip(ch), tol, _dp(out)))
+        return out
 
     def compress_modified(self, x: "MPS", split: int, chi: int, tol: float) -> np.ndarray:
         errs = np.zeros(max(1, x.n - 1))

@@ -104,3 +104,75 @@ def test_full_size_4096_step_against_stored_oracle(ctx):
     got = f1[np.array(g["ix"]), np.array(g["iv"])]
     assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-10
     sim.close()
+
+
+@pytest.mark.parametrize("chi", [32, 128])
+def test_full_size_step_other_chi(ctx, chi):
+    # the benchmark's state and grid at the other bond caps of the
+    # configuration (1024 x 1024 two-stream, chi in {32, 64, 128})
+    w = I.WORKLOADS["saturated_two_stream_1024x1024_seq"]
+    lay, dt = w["layout"], w["dt"]
+    f0 = I.initial_condition(w["ic"], lay)
+    m = ctx.mps_from_grid(lay, f0, chi, 1e-10)
+    ref = OV.mps_from_f(f0, lay, chi, 1e-10)
+    assert m.bonds() == [int(x) for x in [1] + [c.shape[2] for c in ref]]
+    sim = ctx.sim(lay, m, dt, chi)
+    rec = sim.step(1)[0]
+    ref, d = OV.rk4_step(ref, lay, dt, chi)
+    assert abs(rec["field_energy"] - d["field_energy"]) <= 1e-9 * d["field_energy"]
+    assert sim.state().bonds() == d["bonds"]
+    assert rel(sim.state().to_grid(lay), OV.mps_to_f(ref, lay)) < 1e-10
+
+
+@pytest.mark.parametrize("case", ["interleaved_1024_chi64", "seq_4096_chi256"])
+def test_full_size_step_against_stored_sketches(ctx, case):
+    # oracle steps that take minutes, stored by tests/golden/make_fullsize_sketch.py:
+    # the dense f(T) is compared through 64 seeded tensor-product sketches
+    # r_i^T F s_i (every grid value enters each; their relative error
+    # estimates the relative L2 error of f) and at 4096 seeded points
+    import json
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", f"fullsize_{case}.json")
+    if not os.path.exists(path):
+        pytest.skip(f"{path} not generated")
+    g = json.load(open(path))
+    nx, nv, xmin, xmax, vmin, vmax, mapping = g["layout"]
+    lay = I.Layout(nx, nv, xmin, xmax, vmin, vmax, mapping)
+    f0 = I.saturated_two_stream(lay, modes=g["modes"])
+    m = ctx.mps_from_grid(lay, f0, g["chi"], g["tol"])
+    assert m.bonds() == g["start_bonds"]
+    sim = ctx.sim(lay, m, g["dt"], g["chi"])
+    rec = sim.step(1)[0]
+    assert abs(rec["field_energy"] - g["field_energy"]) <= 1e-9 * g["field_energy"]
+    assert abs(rec["mass"] - g["mass"]) <= 1e-10 * abs(g["mass"])
+    assert sim.state().bonds() == g["bonds"]
+    f1 = sim.state().to_grid(lay)
+    sim.close()
+    ref = np.array(g["f"])
+    got = f1[np.array(g["ix"]), np.array(g["iv"])]
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-10
+    rng = np.random.Generator(np.random.PCG64(g["sketch_seed"]))
+    r = rng.standard_normal((len(g["sketches"]), lay.Nx))
+    s = rng.standard_normal((len(g["sketches"]), lay.Nv))
+    y = np.einsum("ix,xv,iv->i", r, f1, s)
+    y_ref = np.array(g["sketches"])
+    assert np.linalg.norm(y - y_ref) / np.linalg.norm(y_ref) < 1e-10
+
+
+def test_run_horizon_256(ctx):
+    # a 20-step run at 256 x 256 (8 + 8 sites, linear Landau, chi = 32):
+    # the GPU and the oracle step from the same state at every step, and the
+    # run stays within the FP64 contract over the whole horizon
+    lay = I.Layout(8, 8, 0.0, 4 * math.pi, -6.0, 6.0, I.SEQ)
+    f0 = I.landau(lay, 0.01, 0.5)
+    dt = OV.stable_dt(lay, 0.02)
+    chi = 32
+    sim = ctx.sim(lay, ctx.mps_from_grid(lay, f0, chi, 1e-10), dt, chi)
+    ref = OV.mps_from_f(f0, lay, chi, 1e-10)
+    recs = sim.step(20)
+    for n in range(20):
+        ref, d = OV.rk4_step(ref, lay, dt, chi)
+        assert abs(recs[n]["field_energy"] - d["field_energy"]) <= 1e-9 * d["field_energy"], n
+        assert abs(recs[n]["mass"] - d["mass"]) <= 1e-10 * abs(d["mass"]), n
+    assert sim.state().bonds() == d["bonds"]
+    assert rel(sim.state().to_grid(lay), OV.mps_to_f(ref, lay)) < 1e-10

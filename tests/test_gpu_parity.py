@@ -283,38 +283,40 @@ def test_compression_levels_and_field_cap(ctx, level, e_chi):
         assert rel(sim.state().to_grid(lay), OV.mps_to_f(ref, lay)) < F_TOL
 
 
-# --------------------------------------------------- precision configuration
-# contraction precision modes against the FP64 path (which matches the
-# oracle): field-energy error (absolute, normalised units), its relative
-# value, and the relative L2 error of f after four steps.
-# FP32 (CUDA cores) and split TF32x3 (tensor cores) meet |dW_E| <= 1e-6; W_E
-# comes from the O(1e-2) perturbation of f, so relative to W_E that is
-# ~1e-4.  TF32x3 carries 22-bit operands (tf32 hi + tf32 lo) and the tensor
-# core's FP32 accumulation, so its f error is ~10x that of FP32 FMA.  Plain
-# TF32 and BF16 round every operand to 10 / 7 mantissa bits; their bounds are
-# that rounding carried through four steps, so a broken kernel (errors of
-# order one) still fails.
-PREC_BOUNDS = {1: (1e-6, 5e-4, 1e-5), 4: (1e-6, 5e-4, 5e-4), 2: (1e-3, 0.5, 0.1), 3: (2e-2, 5.0, 0.5)}
+# Reduced-precision contraction modes against the FP64 oracle.  Each mode
+# rounds the operands of the sweeps' GEMMs (and of the density) to a unit
+# roundoff u: FP32 2^-24, TF32x3 ~2^-21 (11 + 11 significant bits, FP32
+# accumulation), TF32 2^-11, BF16 2^-8.  That rounding, carried through four
+# RK4-C1 steps (28 compressions), moves f and W_E by a modest multiple of u;
+# the bound is K u with one K for every mode (the condition of this workload's
+# steps, measured: the largest ratio seen is a few tens), and a floor of
+# 1e-3 u shows the mode is really active.
+PREC_U = {1: 2.0 ** -24, 4: 2.0 ** -21, 2: 2.0 ** -11, 3: 2.0 ** -8}
+PREC_K = 200.0
 
 
 @pytest.mark.parametrize("prec", [1, 4, 2, 3])
-def test_reduced_precision_contractions_vs_fp64(ctx, prec):
+def test_reduced_precision_contractions_vs_oracle(ctx, prec):
     lay = I.Layout(6, 6, 0.0, 10 * math.pi, -8.0, 8.0, I.SEQ)
     f0 = I.saturated_two_stream(lay, modes=8)
     chi, dt = 24, 0.02
-    runs = {}
-    for p in (0, prec):
-        m = ctx.mps_from_grid(lay, f0, chi, 1e-10)
-        sim = ctx.sim(lay, m, dt, chi, precision=p)
-        recs = sim.step(4)
-        runs[p] = (np.array([r["field_energy"] for r in recs]), sim.state().to_grid(lay))
-        sim.close()
-    we64, f64 = runs[0]
-    wep, fp = runs[prec]
-    we_abs, we_rel, f_rel = PREC_BOUNDS[prec]
-    assert np.max(np.abs(wep - we64)) < we_abs
-    assert np.max(np.abs(wep - we64) / we64) < we_rel
-    assert 0 < rel(fp, f64) < f_rel
+    m = ctx.mps_from_grid(lay, f0, chi, 1e-10)
+    sim = ctx.sim(lay, m, dt, chi, precision=prec)
+    recs = sim.step(4)
+    fp = sim.state().to_grid(lay)
+    sim.close()
+    ref = OV.mps_from_f(f0, lay, chi, 1e-10)
+    we_ref = []
+    for _ in range(4):
+        ref, d = OV.rk4_step(ref, lay, dt, chi)
+        we_ref.append(d["field_energy"])
+    we_ref = np.array(we_ref)
+    wep = np.array([r["field_energy"] for r in recs])
+    u = PREC_U[prec]
+    we_err = float(np.max(np.abs(wep - we_ref) / we_ref))
+    f_err = rel(fp, OV.mps_to_f(ref, lay))
+    assert we_err < PREC_K * u, (we_err / u)
+    assert 1e-3 * u < f_err < PREC_K * u, (f_err / u)
 
 
 def test_profile_trace_records(ctx):
@@ -377,3 +379,17 @@ def test_rk4_steps_modified_compression(ctx, mapping):
     lay_i = I.Layout(4, 4, 0.0, 4 * math.pi, -6.0, 6.0, I.INTERLEAVED)
     with pytest.raises(VpError):
         ctx.sim(lay_i, ctx.mps_from_grid(lay_i, I.landau(lay_i), 8, 1e-10), 0.05, 8, compression=1)
+
+
+def test_compression_error_vs_oracle(ctx):
+    # rms compression error against the bond dimension (State Compressibility)
+    lay = I.Layout(6, 6, 0.0, 10 * math.pi, -8.0, 8.0, I.SEQ)
+    f0 = I.saturated_two_stream(lay, modes=12)
+    m = ctx.mps_from_grid(lay, f0, 64, 0.0)
+    ref = OV.mps_from_f(f0, lay, 64, 0.0)
+    chis = [2, 4, 8, 16, 32, 64]
+    got = ctx.compression_error(m, chis, 0.0)
+    want = OS.compression_error(ref, chis, 0.0)
+    scale = float(np.sqrt(np.mean(f0 * f0)))
+    assert np.all(np.abs(got - want) <= 1e-10 * scale + 1e-6 * want)
+    assert got[-1] <= 1e-12 * scale and np.all(np.diff(got) <= 1e-12 * scale)

@@ -175,3 +175,25 @@ def test_modified_compression_error_bound():
         e = np.linalg.norm(S.to_dense(out) - d) / np.linalg.norm(d)
         assert e <= np.sqrt(np.sum(np.square(errs))) * (1 + 1e-9) + 1e-14
         assert max(c.shape[2] for c in out) <= chi
+
+
+def test_compression_error_pins():
+    # one bond (two sites of dimension 2^3 each): Eckart-Young, the rms error
+    # of the best rank-D approximation is sqrt(sum_{i>D} s_i^2 / N)
+    rng = np.random.default_rng(12)
+    M = rng.standard_normal((8, 8))
+    U, s, Vt = np.linalg.svd(M)
+    s = 2.0 ** -np.arange(8)
+    M = (U * s) @ Vt
+    cores = S.tt_svd(M.reshape(-1), 6, None, 0.0)  # bonds 1, 2, 4, 8, 4, 2, 1: the middle one is M
+    errs = S.compression_error(cores, [8, 4, 2], 0.0)
+    assert errs[0] < 1e-15
+    # at D = 4 and D = 2 only the middle bond (rank 8) is cut; bonds 1-2 and
+    # 4-5 have rank <= 4 and are exact
+    assert abs(errs[1] - np.sqrt(np.sum(s[4:] ** 2) / 64)) < 1e-14
+    exact2 = S.compression_error(S.tt_svd(M.reshape(-1), 6, None, 0.0), [2], 0.0)[0]
+    assert exact2 >= np.sqrt(np.sum(s[2:] ** 2) / 64) - 1e-14  # no rank-2 MPS beats Eckart-Young at that cut
+    # a state of bond 1 everywhere (a product) has no compression error at D = 1
+    prod = [np.array([1.0, 2.0]).reshape(1, 2, 1) for _ in range(5)]
+    f = S.to_dense(prod)
+    assert S.compression_error(prod, [1], 0.0)[0] < 1e-14 * np.sqrt(np.mean(f * f))
