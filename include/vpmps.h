@@ -318,8 +318,14 @@ typedef struct {
   int chi;          /* bond cap of f_{n+1} */
   double tol;       /* truncation tolerance of every compression (1e-10) */
   double e_tol;     /* tolerance of the E-field MPS (1e-10) */
-  int streams;      /* 1: one stream; 0 or 2: the two independent compressions of
-                       each RK stage run concurrently on a second stream */
+  int streams;      /* 1: one stream; 2: the two independent compressions of
+                       each RK stage run concurrently on a second stream;
+                       0: the step runs as a one-member lockstep group
+                       (vp_group_*: both compressions of a stage share every
+                       launch) where the configuration allows it (level C1,
+                       plain sweeps, FP64 or FP32 contractions, tol and e_tol
+                       >= 1e-13), else as 2.  The result is the same in
+                       every mode. */
   int level;        /* compression level (SI "Compressed time evolution
                        algorithm"), 0 or 1: C1; 2..5: C2..C5 -- C2 also caps the
                        intermediate states at chi, C3 also the running sum of

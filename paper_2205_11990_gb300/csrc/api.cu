@@ -1483,7 +1483,29 @@ static int sim_step_impl(vp_sim* s, vp_record* rec);
 // The contraction precision applies to this sim's steps only.
 // So does the compression scheme (the modified one cuts first at the x / v
 // bond, after the x sites).
+// cfg.streams == 0 on an eligible sim: the step runs as a one-member
+// lockstep group (the stage's two compressions share every launch), with the
+// same arithmetic as the paths below.
+static int sim_step_lockstep(vp_sim* s, vp_record* rec) {
+  vp_ctx* ctx = s->ctx;
+  if (!s->lockstep) {
+    VP_TRY(vp_group_create(ctx, 1, &s->lockstep));
+    const int st = vp_group_add(s->lockstep, s);
+    if (st != VP_OK) {
+      vp_group_destroy(s->lockstep);
+      s->lockstep = nullptr;
+      return st;
+    }
+  }
+  int mst = VP_OK;
+  VP_TRY(vp_group_step(s->lockstep, rec, &mst));
+  if (mst == VP_ETIMEOUT) return fail(ctx, mst, "a device-side wait gave up");
+  if (mst != VP_OK) return fail(ctx, mst, "NaN or Inf in the field or the singular values, or a Jacobi SVD that did not converge");
+  return VP_OK;
+}
+
 static int sim_step(vp_sim* s, vp_record* rec) {
+  if (s->cfg.streams == 0 && !s->ctxB && lockstep_eligible(s)) return sim_step_lockstep(s, rec);
   const int p0 = s->ctx->precision, m0 = s->ctx->modified_split, g0 = s->ctx->grouped;
   const int split = s->cfg.compression == VP_COMPRESS_MODIFIED ? s->lay.nx : 0;
   s->ctx->precision = s->cfg.precision;
@@ -1607,6 +1629,10 @@ static int upload_chain(vp_ctx* ctx, const Chain& c, std::vector<DevBuf>& out) {
 
 static void sim_free(vp_sim* s) {
   vp_ctx* ctx = s->ctx;
+  if (s->lockstep) {
+    vp_group_destroy(s->lockstep);
+    s->lockstep = nullptr;
+  }
   if (s->ctxB) {
     cudaStreamSynchronize(s->ctxB->stream);
     cudaStreamSynchronize(ctx->stream);
@@ -1673,7 +1699,9 @@ static int sim_create(vp_ctx* ctx, const vp_layout* L, const vp_config* cfg, con
   if (st == VP_OK && (cfg->compression < VP_COMPRESS_SWEEPS || cfg->compression > VP_COMPRESS_MODIFIED ||
                       (cfg->compression == VP_COMPRESS_MODIFIED && (interleaved(L) || L->nx < 1 || L->nv < 1))))
     st = fail(ctx, VP_EINVAL, "vp_sim_create: the modified compression needs a sequential ordering");
-  if (st == VP_OK && cfg->streams != 1 && cfg->level <= 1) {
+  // streams 2, or 0 where the lockstep path does not apply: the second stream
+  const bool lock = cfg->streams == 0 && !sp && lockstep_eligible(s);
+  if (st == VP_OK && cfg->streams != 1 && cfg->level <= 1 && !lock) {
     s->ctxB = ctx_child(ctx);
     if (s->ctxB) {
       s->fi.ctx = s->wb.ctx = s->ctxB;

@@ -172,6 +172,31 @@ std::vector<int> live_ids(const vp_group* g, const std::vector<int>& ids) {
 // The contraction mode of a member's GEMMs (its whole step, as in vp_step).
 int fp32_of(const Member* mb) { return mb->sim->cfg.precision == VP_PREC_FP32_CONTRACT ? 1 : 0; }
 
+// Algorithmic flops of an m x n Householder QR (the single path's count).
+double qr_flops(double m, double n) {
+  return m >= n ? 2 * m * n * n - 2.0 / 3.0 * n * n * n : 2 * n * m * m - 2.0 / 3.0 * m * m * m;
+}
+
+// Work of a problem's launches, added to its member's flop counters.
+void account(vp_group* g, const Task* t, double qr, double formq, double gemm, double jac) {
+  if (t->member < 0 || t->member >= (int)g->mem.size()) return;
+  Flops& f = g->mem[t->member]->sim->flops;
+  f.qr += qr;
+  f.formq += formq;
+  f.gemm += gemm;
+  f.jacobi += jac;
+}
+
+// A batched launch bracketed for the context's kernel-class timing (the
+// events go on the stream the launches go on).
+template <class F>
+int timed(vp_ctx* ctx, int cls, double work, F&& launch) {
+  prof_begin(ctx, cls);
+  const int st = launch();
+  prof_end(ctx, cls, work);
+  return st;
+}
+
 // Status words and rank records of every problem back to their initial
 // state (counters zero, the context's wait limit), in stream order.
 int reset_records(vp_group* g) {
@@ -229,17 +254,26 @@ int qr_sweep(vp_group* g, const Tasks& all) {
       gr.push_back({BG_RB, t->fp32, p, nn, n, 1.0, w.F[b].p, m, s->core[k + 1].p, nn, w.gemm.p, nn, &w.main});
       pv.push_back(p);
     }
+    double wq = 0, wf = 0, wg = 0;
+    for (size_t i = 0; i < ts.size(); ++i) {
+      const double m = qr[i].m, n = qr[i].n, p = pv[i], nn = gr[i].N;
+      const double a = qr_flops(m, n), f = 4.0 * m * p * p - 4.0 / 3.0 * p * p * p, gm = 2.0 * p * n * nn;
+      account(g, ts[i], a, f, gm, 0.0);
+      wq += a;
+      wf += f;
+      wg += gm;
+    }
     VP_TRY(blaunch_to_colmajor(ctx, ctx->stream, cm));
-    VP_TRY(blaunch_qr_factor(ctx, ctx->stream, qr));
+    VP_TRY(timed(ctx, VP_K_QR, wq, [&] { return blaunch_qr_factor(ctx, ctx->stream, qr); }));
     VP_CUDA(ctx, cudaEventRecord(g->ev_qf[b], ctx->stream));
     {
       OnSide side(ctx, &g->side);
       VP_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, g->ev_qf[b], 0));
-      VP_TRY(blaunch_qr_formq(ctx, ctx->stream, fq));
+      VP_TRY(timed(ctx, VP_K_FORMQ, wf, [&] { return blaunch_qr_formq(ctx, ctx->stream, fq); }));
       VP_CUDA(ctx, cudaEventRecord(g->ev_qd[b], ctx->stream));
     }
     join.busy[b] = true;
-    VP_TRY(blaunch_gemm(ctx, ctx->stream, gr));
+    VP_TRY(timed(ctx, VP_K_GEMM, wg, [&] { return blaunch_gemm(ctx, ctx->stream, gr); }));
     for (size_t i = 0; i < ts.size(); ++i) {
       std::swap(ts[i]->s->core[k + 1], ts[i]->w->gemm);
       ts[i]->s->r[k + 1] = pv[i];
@@ -327,19 +361,32 @@ int svd_sweep(vp_group* g, const Tasks& all) {
       double* sigma = w.vec.p + (q + 1) / 2 + 4;
       se.push_back({w.tmp.p, q, q, chi, tol, perm, sigma, &rec->rank, &rec->err, &rec->st});
     }
+    double wq = 0, wf = 0, wp = 0;
+    for (Task* t : ts) {
+      const double p = t->p, q = t->q;
+      const double a = qr_flops(p, q) + qr_flops(q, q), f = 4.0 * p * q * q - 4.0 / 3.0 * q * q * q + 8.0 / 3.0 * q * q * q;
+      const double gm = t->tall ? 2.0 * t->pl * q * t->m : 0.0;
+      account(g, t, a, f, gm, 0.0);
+      wq += a;
+      wf += f;
+      wp += gm;
+    }
     // A Pi = Q1 R1, R1^T = Q2 L^T
     VP_TRY(blaunch_norm_order(ctx, ctx->stream, no));
     VP_TRY(blaunch_gather_cm(ctx, ctx->stream, ga));
-    VP_TRY(blaunch_qr_factor(ctx, ctx->stream, qr1));
-    VP_TRY(blaunch_qr_getr(ctx, ctx->stream, gr));
-    VP_TRY(blaunch_qr_factor(ctx, ctx->stream, qr2));
+    VP_TRY(timed(ctx, VP_K_QR, wq, [&] {
+      int st = blaunch_qr_factor(ctx, ctx->stream, qr1);
+      if (st == VP_OK) st = blaunch_qr_getr(ctx, ctx->stream, gr);
+      if (st == VP_OK) st = blaunch_qr_factor(ctx, ctx->stream, qr2);
+      return st;
+    }));
     // Q1, Q2 (and, tall, P Q1) on the side stream while the Jacobi SVD runs
     VP_CUDA(ctx, cudaEventRecord(g->ev_fork, ctx->stream));
     VP_CUDA(ctx, cudaStreamWaitEvent(g->side, g->ev_fork, 0));
     {
       OnSide side(ctx, &g->side);
-      VP_TRY(blaunch_qr_formq(ctx, ctx->stream, fq));
-      VP_TRY(blaunch_gemm(ctx, ctx->stream, pq));
+      VP_TRY(timed(ctx, VP_K_FORMQ, wf, [&] { return blaunch_qr_formq(ctx, ctx->stream, fq); }));
+      VP_TRY(timed(ctx, VP_K_GEMM, wp, [&] { return blaunch_gemm(ctx, ctx->stream, pq); }));
       VP_CUDA(ctx, cudaEventRecord(g->ev_join, ctx->stream));
     }
     struct SideJoin {
@@ -348,11 +395,23 @@ int svd_sweep(vp_group* g, const Tasks& all) {
     } side_join{g};
     VP_TRY(blaunch_lower_from_upper(ctx, ctx->stream, lu));
     VP_TRY(blaunch_copy(ctx, ctx->stream, cp));
-    VP_TRY(blaunch_jacobi(ctx, ctx->stream, jc));
-    VP_TRY(blaunch_select(ctx, ctx->stream, se));
+    const size_t jac_mark = ctx->prof_on ? ctx->prof_marks.size() : (size_t)-1;
+    VP_TRY(timed(ctx, VP_K_JACOBI, 0.0, [&] { return blaunch_jacobi(ctx, ctx->stream, jc); }));
+    VP_TRY(timed(ctx, VP_K_SELECT, 0.0, [&] { return blaunch_select(ctx, ctx->stream, se); }));
     // one wait for the kept ranks of every problem at this step
     VP_TRY(sync_records(g, slots));
     mark_failures(g, ts);
+    {  // Jacobi work from the sweeps each problem took (the single path's count)
+      double wj = 0.0;
+      for (Task* t : ts) {
+        const double q = t->q, sweeps = g->h_task[t->slot].st.pad2;
+        const double j = q > 1 ? sweeps * 0.5 * q * (q - 1) * (6.0 * q + (t->tall ? 0.0 : 4.0 * q)) : 0.0;
+        account(g, t, 0, 0, 0, j);
+        wj += j;
+      }
+      if (ctx->prof_on) ctx->prof_work[VP_K_JACOBI] += wj;
+      if (jac_mark != (size_t)-1 && jac_mark < ctx->prof_marks.size()) ctx->prof_marks[jac_mark].m = (int)ts.size();
+    }
     ts = live(g, ts);
     std::vector<BSvdOut> so;
     std::vector<BSvdOutWide> sw;
@@ -394,13 +453,24 @@ int svd_sweep(vp_group* g, const Tasks& all) {
         g5.push_back({BG_AB, t->fp32, pl, r, m, 1.0, s->core[k - 1].p, m, w.tmp2.p, r, w.gemm.p, r, &w.main});
       }
     }
+    double wo = 0.0;
+    for (const auto* v : {&g2, &g3, &g5})
+      for (const BGemm& x : *v) wo += 2.0 * x.M * x.N * x.K;
+    for (Task* t : ts) {
+      const double q = t->q, r = t->r, m = t->m, c = t->c, pl = t->pl;
+      account(g, t, 0, 0, t->tall ? 2.0 * pl * r * q + 4.0 * r * q * q : 2.0 * r * c * m + 2.0 * m * r * m + 2.0 * pl * r * m,
+              0);
+    }
     VP_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, g->ev_join, 0));
-    VP_TRY(blaunch_svd_outputs(ctx, ctx->stream, so));
-    VP_TRY(blaunch_svd_outputs_wide(ctx, ctx->stream, sw));
-    VP_TRY(blaunch_gemm(ctx, ctx->stream, g2));
-    VP_TRY(blaunch_gemm(ctx, ctx->stream, g3));
-    VP_TRY(blaunch_scatter(ctx, ctx->stream, sc));
-    VP_TRY(blaunch_gemm(ctx, ctx->stream, g5));
+    VP_TRY(timed(ctx, VP_K_GEMM, wo, [&] {
+      int st = blaunch_svd_outputs(ctx, ctx->stream, so);
+      if (st == VP_OK) st = blaunch_svd_outputs_wide(ctx, ctx->stream, sw);
+      if (st == VP_OK) st = blaunch_gemm(ctx, ctx->stream, g2);
+      if (st == VP_OK) st = blaunch_gemm(ctx, ctx->stream, g3);
+      if (st == VP_OK) st = blaunch_scatter(ctx, ctx->stream, sc);
+      if (st == VP_OK) st = blaunch_gemm(ctx, ctx->stream, g5);
+      return st;
+    }));
     for (Task* t : ts) {
       std::swap(t->s->core[t->k - 1], t->w->gemm);
       t->s->r[t->k] = t->r;
@@ -772,7 +842,11 @@ int site_sums(vp_ctx* ctx, const std::vector<SumSpec>& v) {
     }
     sp.out->r = r;
   }
-  return blaunch_site_sum(ctx, ctx->stream, ss);
+  double bytes = 0.0;
+  for (const BSiteSum& b : ss)
+    bytes += 8.0 * ((double)b.ol * 2 * b.orr + (b.s.a ? (double)b.s.al * 2 * b.s.ar : 0.0) +
+                    (double)b.s.bl * 2 * b.s.br + (b.s.B ? (double)b.s.wl * 4 * b.s.wr : 0.0));
+  return timed(ctx, VP_K_APPLY, bytes, [&] { return blaunch_site_sum(ctx, ctx->stream, ss); });
 }
 
 // One RK4-C1 step of every live member (api.cu's sim_step_impl / c1_stage).
@@ -891,6 +965,13 @@ int group_step(vp_group* g, vp_record* recs) {
 
 using namespace vp;
 
+bool vp::lockstep_eligible(const vp_sim* s) {
+  const vp_config& c = s->cfg;
+  return c.level <= 1 && c.compression == VP_COMPRESS_SWEEPS && c.e_chi >= 0 &&
+         (c.precision == VP_PREC_FP64 || c.precision == VP_PREC_FP32_CONTRACT) && c.tol >= 1e-13 &&
+         c.e_tol >= 1e-13 && s->ecoef == 1.0;
+}
+
 extern "C" {
 
 int vp_group_create(vp_ctx* ctx, int max_members, vp_group** out) {
@@ -935,10 +1016,7 @@ int vp_group_add(vp_group* g, vp_sim* s) {
   for (Member* m : g->mem)
     if (m->sim == s) return fail(ctx, VP_EINVAL, "vp_group_add: already a member");
   if (s->ctx != ctx || s->ctxB) return fail(ctx, VP_EINVAL, "vp_group_add: the sim must be on the group's context, one stream");
-  const vp_config& c = s->cfg;
-  if (c.level > 1 || c.compression != VP_COMPRESS_SWEEPS || c.e_chi < 0 ||
-      (c.precision != VP_PREC_FP64 && c.precision != VP_PREC_FP32_CONTRACT) || c.tol < 1e-13 || c.e_tol < 1e-13 ||
-      s->ecoef != 1.0)
+  if (!lockstep_eligible(s))
     return fail(ctx, VP_EINVAL,
                 "vp_group_add: groups step level C1 with the plain sweeps, FP64 or FP32 contractions and tol >= 1e-13");
   Member* m = new (std::nothrow) Member();

@@ -49,4 +49,12 @@ struct vp_sim {
   cudaEvent_t evA = nullptr, evB = nullptr;
   double ecoef = 1.0;      // -q/m of the species: the field term is diag(ecoef E) (x) D_v
   int coop_div = 1;        // runs sharing the GPU at once: grid-cooperative QRs get num_sms / (2 coop_div)
+  vp_group* lockstep = nullptr;  // cfg.streams == 0: the one-member group that steps this sim
 };
+
+namespace vp {
+// A sim whose configuration the lockstep group steps: compression level C1,
+// the plain sweeps, FP64 or FP32 contractions, tolerances >= 1e-13, one
+// species against a fixed background.
+bool lockstep_eligible(const vp_sim* s);
+}  // namespace vp

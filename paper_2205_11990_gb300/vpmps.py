@@ -452,11 +452,11 @@ class Context:
         return Multi(self, h, list(lays))
 
     def run(self, lay: Layout, f0: np.ndarray, dt: float, nsteps: int, chi: int, tol: float = 1e-10,
-            e_tol: float = 1e-10, want_f: bool = True):
+            e_tol: float = 1e-10, want_f: bool = True, streams: int = 2):
         f0 = np.ascontiguousarray(f0, dtype=np.float64)
         fT = np.zeros((lay.Nx, lay.Nv)) if want_f else None
         recs = (CRecord * max(1, nsteps))()
-        cfg = CConfig(dt, chi, tol, e_tol, 2, 1, 0, 0)
+        cfg = CConfig(dt, chi, tol, e_tol, streams, 1, 0, 0)
         self._check(self.lib.vp_run(self.h, C.byref(clayout(lay)), C.byref(cfg), _dp(f0), nsteps,
                                     _dp(fT) if want_f else None, recs))
         return fT, _records(recs, nsteps)

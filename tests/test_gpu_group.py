@@ -224,3 +224,18 @@ def test_group_equals_alone_with_grid_factors(ctx):
         assert recs[i] == al[i].step(1)[0], i
         assert np.array_equal(gs[i].state().to_grid(lay), al[i].state().to_grid(lay)), i
     grp.close()
+
+
+def test_lockstep_stepping_mode_equals_two_streams(ctx):
+    # vp_step with streams = 0 runs a one-member lockstep group: the same
+    # records, state and entropies as the two-stream path, and the flop count
+    cases = member_cases()[:4]
+    for lay, f0, dt, chi, prec in cases:
+        a = ctx.sim(lay, ctx.mps_from_grid(lay, f0, chi, 1e-10), dt, chi, streams=0, precision=prec)
+        b = ctx.sim(lay, ctx.mps_from_grid(lay, f0, chi, 1e-10), dt, chi, streams=2, precision=prec)
+        assert a.step(2) == b.step(2)
+        assert np.array_equal(a.state().to_grid(lay), b.state().to_grid(lay))
+        assert np.array_equal(a.entropy(), b.entropy())
+        assert abs(a.flops - b.flops) <= 1e-9 * b.flops
+        a.close()
+        b.close()

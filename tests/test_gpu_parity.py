@@ -287,12 +287,15 @@ def test_compression_levels_and_field_cap(ctx, level, e_chi):
 # rounds the operands of the sweeps' GEMMs (and of the density) to a unit
 # roundoff u: FP32 2^-24, TF32x3 ~2^-21 (11 + 11 significant bits, FP32
 # accumulation), TF32 2^-11, BF16 2^-8.  That rounding, carried through four
-# RK4-C1 steps (28 compressions), moves f and W_E by a modest multiple of u;
-# the bound is K u with one K for every mode (the condition of this workload's
-# steps, measured: the largest ratio seen is a few tens), and a floor of
-# 1e-3 u shows the mode is really active.
+# RK4-C1 steps (28 compressions), moves f by a modest multiple of u: the bound
+# is K_f u with one K_f for every mode, and a floor of 1e-3 u shows the mode
+# is really active.  W_E is quadratic in the field of a perturbation of
+# relative size eps = 0.05 of the state (saturated_two_stream's amplitude), so
+# a relative change d of f moves W_E by ~2 d / eps: its bound is K_W = 2 K_f /
+# eps times u.
 PREC_U = {1: 2.0 ** -24, 4: 2.0 ** -21, 2: 2.0 ** -11, 3: 2.0 ** -8}
 PREC_K = 200.0
+PREC_KW = 2 * PREC_K / 0.05
 
 
 @pytest.mark.parametrize("prec", [1, 4, 2, 3])
@@ -315,8 +318,7 @@ def test_reduced_precision_contractions_vs_oracle(ctx, prec):
     u = PREC_U[prec]
     we_err = float(np.max(np.abs(wep - we_ref) / we_ref))
     f_err = rel(fp, OV.mps_to_f(ref, lay))
-    assert we_err < PREC_K * u, (we_err / u)
-    assert 1e-3 * u < f_err < PREC_K * u, (f_err / u)
+    assert we_err < PREC_KW * u and 1e-3 * u < f_err < PREC_K * u, (we_err / u, f_err / u)
 
 
 def test_profile_trace_records(ctx):
