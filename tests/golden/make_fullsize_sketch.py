@@ -5,7 +5,7 @@ Cases (saturated two-stream state, tol = 1e-10):
   interleaved_1024_chi64  1024 x 1024 (10 + 10 sites, IF ordering), chi = 64,
                           32 seeded modes
   seq_4096_chi256         4096 x 4096 (12 + 12 sites, sequential), chi = 256,
-                          160 seeded modes: the x / v cut needs ~2 x 160 + 1
+                          400 seeded modes: the x / v cut needs ~2 x 400 + 1
                           singular values, so the middle bonds sit at the cap
 
 Stored, besides the field energy and mass of the start state and the bonds
@@ -44,7 +44,7 @@ NSKETCH = 64
 CASES = {
     # name: (nx, nv, xmax / pi, vmax, mapping, chi, modes)
     "interleaved_1024_chi64": (10, 10, 10, 8.0, I.INTERLEAVED, 64, 32),
-    "seq_4096_chi256": (12, 12, 10, 8.0, I.SEQ, 256, 160),
+    "seq_4096_chi256": (12, 12, 10, 8.0, I.SEQ, 256, 400),
 }
 
 
