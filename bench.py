@@ -74,6 +74,7 @@ def parse():
                    help="named workload of paper_2205_11990_gb300.inputs.SPECIES_WORKLOADS (--mode species)")
     p.add_argument("--instances", type=int, default=32)
     p.add_argument("--concurrency", type=int, default=8)
+    p.add_argument("--time", type=float, default=4.0, help="compressibility: physical time of the runs")
     p.add_argument("--groups", type=int, default=4, help="batch / serve: lockstep groups (bucketed by site count)")
     p.add_argument("--bits", default="8,12", help="batch / serve: grid bits per dimension, min,max")
     p.add_argument("--chis", default="16,32,64,128", help="batch / serve: bond caps drawn uniformly")
@@ -617,8 +618,9 @@ def run_precision(args):
 def run_compressibility(args):
     """State compressibility (main text, "State Compressibility", the rms
     compression error against D): nonlinear Landau (A = 0.5, k = 0.5, the
-    paper's set-up) run with no bond cap at tol = 1e-10 on several grids for
-    --steps steps, then the rms error over the grid of f - f_D for each D."""
+    paper's set-up) run with no bond cap at tol = 1e-10 on several grids to
+    the same time T = --time, then the rms error over the grid of f - f_D for
+    each D."""
     import math
     import __graft_entry__ as g
     g.build()
@@ -630,11 +632,12 @@ def run_compressibility(args):
     for bits in (6, 7, 8):
         lay = I.Layout(bits, bits, 0.0, 4 * math.pi, -6.0, 6.0, I.SEQ)
         f0 = I.landau(lay, 0.5, 0.5)
-        dt = 0.6 * (lay.xmax - lay.xmin) / lay.Nx / lay.vmax
+        steps = max(1, int(math.ceil(args.time / (0.6 * (lay.xmax - lay.xmin) / lay.Nx / lay.vmax))))
+        dt = args.time / steps
         full = 1 << bits
-        sim = ctx.sim(lay, ctx.mps_from_grid(lay, f0, full, TOL), dt, full, TOL, TOL)
+        sim = ctx.sim(lay, ctx.mps_from_grid(lay, f0, full, TOL), dt, full, TOL, TOL, streams=0)
         t0 = time.perf_counter()
-        recs = sim.step(args.steps)
+        recs = sim.step(steps)
         t = time.perf_counter() - t0
         st = sim.state()
         f = st.to_grid(lay)
@@ -642,11 +645,11 @@ def run_compressibility(args):
         err = ctx.compression_error(st, chis, 0.0)
         out[f"{lay.Nx}x{lay.Nv}"] = {"t": recs[-1]["t"] + dt, "max_bond": max(st.bonds()), "rms_f": rms_f,
                                     "rms_error": {str(c): float(e) for c, e in zip(chis, err)},
-                                    "steps_per_s": args.steps / t}
+                                    "steps": steps, "steps_per_s": steps / t}
         sim.close()
     print(json.dumps({"metric": "rms compression error vs bond dimension (nonlinear Landau)", "unit": "rms of f - f_D",
                       "dtype": DTYPE, "data": "synthetic", "config": {"ic": "Landau A=0.5 k=0.5, seq",
-                      "steps": args.steps, "tol": TOL, "D": chis}, "grids": out}), flush=True)
+                      "time": args.time, "tol": TOL, "D": chis}, "grids": out}), flush=True)
 
 
 def run_peaks(args):
