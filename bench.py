@@ -38,8 +38,11 @@ DW_PEAK_GFLOPS = 128 * 152 * 2.070 * 2 / 20.5
 # rule; the QR, Q formation and Jacobi SVD in double-word FP32 (~2^-48).
 DTYPE = "f64 storage/contractions, df32 (~2^-48) factorisations"
 PROFILES = os.path.join(ROOT, "profiles")
-KERNEL_OF_CLASS = {"qr_factor": "k_qr_factor_cl", "jacobi": "k_jacobi_dw", "gemm": "k_gemm",
-                   "qr_formq": "k_qr_formq_reg", "apply": "k_site_sum", "select": "k_select"}
+# the dominant kernel of each class on the headline path (streams = 0: the
+# batched kernels of a one-member lockstep group) and on the two-stream path
+KERNEL_OF_CLASS = {"qr_factor": "kb_qr_factor_cl", "jacobi": "kb_jacobi_dw", "gemm": "kb_gemm",
+                   "qr_formq": "kb_qr_formq_reg", "apply": "kb_site_sum", "select": "kb_select"}
+KERNEL_OF_CLASS_STREAMS = {k: v[1:] for k, v in KERNEL_OF_CLASS.items()}
 
 
 def profile_traffic(kernel, workload):
@@ -275,7 +278,7 @@ def run_ours(args, rank, world):
         print(json.dumps(out), flush=True)
 
 
-def roofline(prof, ms, world, workload, probes=None):
+def roofline(prof, ms, world, workload, probes=None, lockstep=True):
     """Roofline entry of the dominant kernel class of the profiled window."""
     top = max(prof, key=lambda k: prof[k][0])
     tms, tl, work = prof[top]
@@ -302,7 +305,7 @@ def roofline(prof, ms, world, workload, probes=None):
             roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "peak_basis": basis,
                     "peak_fp64": FP64_PEAK_GFLOPS / 1e3, "frac_fp64": achieved / (FP64_PEAK_GFLOPS / 1e3)}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    kernel = KERNEL_OF_CLASS.get(top, top)
+    kernel = (KERNEL_OF_CLASS if lockstep else KERNEL_OF_CLASS_STREAMS).get(top, top)
     # DRAM bytes (read + write) per launch of the dominant kernel, from the ncu
     # captures summarised under profiles/
     roof["traffic"] = profile_traffic(kernel, workload)
@@ -378,7 +381,7 @@ def run_species(args, rank, world):
         "vs_baseline": None, "dtype": DTYPE, "data": "synthetic",
         "config": {"workload": name, "species": species, "chi": chi, "tol": TOL, "dt": dt,
                    "parallelism": f"replicas x{world}", "l2": "flushed between timed steps (256 MB write)"},
-        "roofline": roofline(prof, ms, world, name),
+        "roofline": roofline(prof, ms, world, name, lockstep=False),
         "gpu_launches": launches, "clocks": clk, "e2e": e2e,
         "diag": {"max_bond": [max(r["max_bond"][s] for r in recs) for s in range(len(lays))],
                  "field_energy": recs[-1]["field_energy"], "kernel_ms": {k: round(v[0], 3) for k, v in prof.items()}},
