@@ -456,20 +456,23 @@ __device__ __forceinline__ void k_qr_factor_cdw_body(double* A, int m, int n, do
 }
 __global__ void __launch_bounds__(kThreads) k_qr_factor_cdw(double* A, int m, int n, double* tau) { k_qr_factor_cdw_body(A, m, n, tau); }
 
-// Cluster-resident double-word QR, pull model (factors up to a 16-CTA
-// cluster's shared memory).  Column k lives in CTA k % CS (slot k / CS) as
-// double words scaled by its own power of two, and each reflector stays where
-// it was formed: in its column, below the diagonal, with its tau in the
-// owner's tau slot.  Step j: one cluster barrier makes reflector j visible,
-// every CTA copies it (rows >= j, leading 1) from the owner's shared memory
-// into its own buffer through distributed shared memory; then in the owner
-// of column j+1 the first CW warps apply H_j to that column and form
-// reflector j+1 in place (rows split over the CW warps, partial sums
-// combined in a fixed order behind a named barrier), while every other warp
-// applies H_j to the columns right of j+1.  A reflector's column is never
-// written after it is formed, so one cluster barrier per column orders
-// everything.  The per-row arithmetic is that of k_qr_factor_dw; only the
-// order in which the critical column's partial sums are added differs.
+// Cluster-resident double-word QR (factors up to a 16-CTA cluster's shared
+// memory).  Column k lives in CTA k % CS (slot k / CS) as double words scaled
+// by its own power of two.  Reflector j is formed in its column by the owner,
+// which also publishes it through L2: rows > j as double words in A's column
+// j, its tau in row j.  Step j: one cluster barrier makes reflector j visible,
+// every CTA loads it into its own buffer; then in the owner of column j+1 the
+// first CW warps apply H_j to that column and form reflector j+1 in place
+// (rows split over the CW warps, partial sums combined in a fixed order
+// behind a named barrier), while every other warp applies H_j to the columns
+// right of j+1.  A's columns are rewritten with the factor after the last
+// barrier.  The L2 copy replaced a pull of each reflector from the owner's
+// shared memory through DSMEM, where up to sixteen CTAs wait on one SM's
+// DSMEM bandwidth (measured on GB300, two problems per launch: 3.00 -> 2.13 ms
+// at 512 x 504 on 16 CTAs, 1.17 -> 0.91 ms at 1008 x 135 on 8, 0.35 -> 0.33 ms
+// at 240 x 90; bit-identical results).  The per-row arithmetic is that of
+// k_qr_factor_dw; only the order in which the critical column's partial sums
+// are added differs.
 template <int NT, int CW>
 __device__ __forceinline__ void k_qr_factor_cl_body(double* A, int m, int n, double* tau) {
   constexpr int NW = NT / 32;
@@ -561,12 +564,18 @@ __device__ __forceinline__ void k_qr_factor_cl_body(double* A, int m, int n, dou
       t = dw_div(dw_add(beta, dw_neg(x0)), beta);
       scale = dw_div({1.0f, 0.0f}, dw_add(x0, dw_neg(beta)));
     }
+    dw* gj = reinterpret_cast<dw*>(A + (size_t)j * m);
     for (int i = r0; i < m; i += rs)
-      if (i > j) c[i] = dw_mul(dw_ldexp(c[i], -e), scale);
+      if (i > j) {
+        const dw v = dw_mul(dw_ldexp(c[i], -e), scale);
+        c[i] = v;
+        __stcg(reinterpret_cast<float2*>(gj + i), make_float2(v.hi, v.lo));
+      }
     if (warp == 0 && lane == 0) {
       c[j] = dw_ldexp(beta, e);
       tsl[lc] = t;
       tau[j] = dw_to(t);
+      __stcg(reinterpret_cast<float2*>(gj + j), make_float2(t.hi, t.lo));
     }
   };
 
@@ -575,25 +584,26 @@ __device__ __forceinline__ void k_qr_factor_cl_body(double* A, int m, int n, dou
   for (int j = 0; j < p; ++j) {
     cl.sync();  // reflector j formed; every CTA done with the previous step
     {
-      // every remote load of the batch issued before any local store
+      // every load of the batch issued before any local store
       constexpr int PB = 8;
-      const int oj = j % CS, sj = j / CS;
-      const dw* src = cl.map_shared_rank(cols + (size_t)sj * m, oj);
-      const dw tj = tid == 0 ? *cl.map_shared_rank(tsl + sj, oj) : dw{0.f, 0.f};
+      const float2* g = reinterpret_cast<const float2*>(A + (size_t)j * m);
       for (int i0 = j + tid; i0 < m; i0 += NT * PB) {
-        dw tmp[PB];
+        float2 tmp[PB];
 #pragma unroll
         for (int u = 0; u < PB; ++u) {
           const int i = i0 + u * NT;
-          if (i < m) tmp[u] = src[i];
+          if (i < m) tmp[u] = __ldcg(g + i);
         }
 #pragma unroll
         for (int u = 0; u < PB; ++u) {
           const int i = i0 + u * NT;
-          if (i < m) vin[i] = (i == j) ? dw{1.0f, 0.0f} : tmp[u];
+          if (i < m) vin[i] = (i == j) ? dw{1.0f, 0.0f} : dw{tmp[u].x, tmp[u].y};
         }
       }
-      if (tid == 0) *tin = tj;
+      if (tid == 0) {
+        const float2 tj = __ldcg(g + j);
+        *tin = {tj.x, tj.y};
+      }
     }
     __syncthreads();
     const bool owner = j + 1 < p && rank == (j + 1) % CS;
@@ -606,7 +616,7 @@ __device__ __forceinline__ void k_qr_factor_cl_body(double* A, int m, int n, dou
       for (int lc = lc0 + wk; lc < nown; lc += nwk) apply(j, cols + (size_t)lc * m);
     }
   }
-  cl.sync();  // no CTA leaves while another may still read its reflectors
+  cl.sync();  // every CTA is done with every published reflector
   for (int lc = warp; lc < nown; lc += NW) {
     const int k = rank + lc * CS;
     const double sc = ldexp(1.0, cexp[lc]);
