@@ -184,6 +184,13 @@ QRPlan qr_plan(const vp_ctx* ctx, int m, int n);
 int launch_qr_formq(vp_ctx* ctx, const double* A, int m, int n, const double* tau, double* Q);
 // Upper-trapezoidal R (p x n) of the factored A, written row-major.
 int launch_qr_getr(vp_ctx* ctx, const double* A, int m, int n, double* R);
+// Output tile and split-K of a GEMM (shape and device only).
+struct GemmPlan {
+  int tile;    // 64 or 32
+  int slices;  // K slices (1: no split)
+  int kslice;  // columns of K per slice
+};
+GemmPlan gemm_plan(const vp_ctx* ctx, int M, int N, int K);
 // C (M x N) = alpha * A (M x K) * B (K x N), all row-major with given leading dims.
 int launch_gemm(vp_ctx* ctx, int M, int N, int K, double alpha, const double* A, int lda,
                 const double* B, int ldb, double* C, int ldc);

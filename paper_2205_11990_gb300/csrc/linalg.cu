@@ -907,9 +907,11 @@ int launch_qr_getr(vp_ctx* ctx, const double* A, int m, int n, double* R) {
 }
 
 // ------------------------------------------------------------------- GEMM
-// 64 x 64 output tile per block, K step 16, 256 threads with a 4 x 4
-// register tile each.  FP64 FMA, row-major B and C.  ALoad selects the A
-// operand: row-major, or the column-major upper triangle of a QR factor.
+// TILE x TILE output tile per block (64 or 32), K step 16, 256 threads with a
+// (TILE / 16)^2 register tile each.  FP64 FMA, row-major B and C.  ALoad
+// selects the A operand: row-major, or the column-major upper triangle of a
+// QR factor.  Each output is the sum over its K slice in ascending k, so the
+// tile size does not change the result; the K slicing does (gemm_plan).
 struct ARowMajor {
   const double* A;
   int lda;
@@ -935,58 +937,87 @@ struct BTransposed {
   __device__ double operator()(int k, int n) const { return B[(size_t)n * ldb + k]; }
 };
 
-template <class ALoad, class BLoad, class T>
+template <class ALoad, class BLoad, class T, int TILE>
 __device__ __forceinline__ void gemm_body(int M, int N, int K, double alpha, ALoad a, BLoad bl, double* __restrict__ C,
                                           int ldc, int kslice, size_t slice_stride, int bx, int by, int bz) {
-  __shared__ T As[16][64 + 1];
-  __shared__ T Bs[16][64];
+  constexpr int R = TILE / 16;  // outputs per thread along each dimension
+  __shared__ T As[16][TILE + 1];
+  __shared__ T Bs[16][TILE];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  const int row0 = bx * 64, col0 = by * 64;
+  const int row0 = bx * TILE, col0 = by * TILE;
   const int kbeg = bz * kslice, kend = min(K, kbeg + kslice);
   C += bz * slice_stride;
-  T acc[4][4] = {};
+  T acc[R][R] = {};
   for (int k0 = kbeg; k0 < kend; k0 += 16) {
-    for (int e = threadIdx.x; e < 64 * 16; e += 256) {
+    for (int e = threadIdx.x; e < TILE * 16; e += 256) {
       const int r = e / 16, kk = e % 16;
       const int gr = row0 + r, gk = k0 + kk;
       As[kk][r] = (T)((gr < M && gk < kend) ? a(gr, gk) : 0.0);
     }
-    for (int e = threadIdx.x; e < 16 * 64; e += 256) {
-      const int kk = e / 64, c = e % 64;
+    for (int e = threadIdx.x; e < 16 * TILE; e += 256) {
+      const int kk = e / TILE, c = e % TILE;
       const int gk = k0 + kk, gc = col0 + c;
       Bs[kk][c] = (T)((gk < kend && gc < N) ? bl(gk, gc) : 0.0);
     }
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < 16; ++kk) {
-      T av[4], bv[4];
+      T av[R], bv[R];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) av[i] = As[kk][ty + 16 * i];
+      for (int i = 0; i < R; ++i) av[i] = As[kk][ty + 16 * i];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) bv[i] = Bs[kk][tx + 16 * i];
+      for (int i = 0; i < R; ++i) bv[i] = Bs[kk][tx + 16 * i];
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < R; ++i)
 #pragma unroll
-        for (int jj = 0; jj < 4; ++jj) acc[i][jj] = fma(av[i], bv[jj], acc[i][jj]);
+        for (int jj = 0; jj < R; ++jj) acc[i][jj] = fma(av[i], bv[jj], acc[i][jj]);
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
+  for (int i = 0; i < R; ++i) {
     const int r = row0 + ty + 16 * i;
     if (r >= M) continue;
 #pragma unroll
-    for (int jj = 0; jj < 4; ++jj) {
+    for (int jj = 0; jj < R; ++jj) {
       const int c = col0 + tx + 16 * jj;
       if (c < N) C[(size_t)r * ldc + c] = alpha * (double)acc[i][jj];
     }
   }
 }
 
-template <class ALoad, class BLoad, class T = double>
+template <class ALoad, class BLoad, class T, int TILE>
 __global__ void __launch_bounds__(256) k_gemm(int M, int N, int K, double alpha, ALoad a, BLoad bl,
                                               double* __restrict__ C, int ldc, int kslice, size_t slice_stride) {
-  gemm_body<ALoad, BLoad, T>(M, N, K, alpha, a, bl, C, ldc, kslice, slice_stride, blockIdx.x, blockIdx.y, blockIdx.z);
+  gemm_body<ALoad, BLoad, T, TILE>(M, N, K, alpha, a, bl, C, ldc, kslice, slice_stride, blockIdx.x, blockIdx.y,
+                                   blockIdx.z);
+}
+
+// How a GEMM is spread over the SMs.  FP64 issues about two FMAs per SM per
+// clock on GB300, so a GEMM runs at the rate of the SMs it occupies: 64 x 64
+// tiles when they alone give every SM a block, else 32 x 32 tiles, and K
+// split into slices (multiples of 16, at most 32) until there are about two
+// blocks per SM; the slices' partial products are summed in a fixed order.
+// The plan depends on the shape and the device only, so a GEMM gives the same
+// bits alone, in a batch or in a group.
+GemmPlan gemm_plan(const vp_ctx* ctx, int M, int N, int K) {
+  GemmPlan g{64, 1, K};
+  const int t64 = ((M + 63) / 64) * ((N + 63) / 64);
+  if (t64 >= ctx->num_sms || K <= 16) return g;
+  int tiles = t64;
+  if (2 * t64 < ctx->num_sms) {
+    g.tile = 32;
+    tiles = ((M + 31) / 32) * ((N + 31) / 32);
+  }
+  const int target = 2 * ctx->num_sms;
+  if (tiles >= target) return g;
+  const int sl = std::min(std::min((target + tiles - 1) / tiles, K / 16), 32);
+  if (sl <= 1) return g;
+  const int ks = ((K + sl - 1) / sl + 15) / 16 * 16;
+  g.kslice = ks;
+  g.slices = (K + ks - 1) / ks;
+  if (g.slices <= 1) g.kslice = K;
+  return g;
 }
 
 // Sum of `slices` partial products (fixed order: deterministic).
@@ -1008,26 +1039,26 @@ static TcOperand tc_a(const AUpperColMajor& a) { return {a.A, a.lda, 2}; }
 static TcOperand tc_b(const BRowMajor& b) { return {b.B, b.ldb, 1}; }
 static TcOperand tc_b(const BTransposed& b) { return {b.B, b.ldb, 0}; }
 
-// Split K when the output has too few 64 x 64 tiles to occupy the SMs.
+// One GEMM launch (split K per gemm_plan, then the fixed-order slice sum).
 template <class ALoad, class BLoad>
 static int gemm_dispatch(vp_ctx* ctx, int M, int N, int K, double alpha, ALoad a, BLoad b, double* C, int ldc,
                          const char* what) {
   if (M <= 0 || N <= 0) return VP_OK;
   if (ctx->precision >= VP_PREC_TF32 && K > 0) return launch_tc_gemm(ctx, M, N, K, alpha, tc_a(a), tc_b(b), C, ldc);
-  dim3 grid((M + 63) / 64, (N + 63) / 64, 1);
+  const GemmPlan pl = gemm_plan(ctx, M, N, K);
+  dim3 grid((M + pl.tile - 1) / pl.tile, (N + pl.tile - 1) / pl.tile, 1);
   if (grid.y > 65535) return fail(ctx, VP_ECAPACITY, "gemm: N too large");
-  const int tiles = (int)(grid.x * grid.y);
-  int slices = 1;
-  if (tiles < ctx->num_sms && K >= 128) slices = std::min(std::min(2 * ctx->num_sms / tiles, K / 64), 32);
   // FP32 contraction mode: inputs rounded to FP32, FP32 FMA and accumulation
-  auto kern = ctx->precision == VP_PREC_FP32_CONTRACT ? k_gemm<ALoad, BLoad, float> : k_gemm<ALoad, BLoad, double>;
+  const bool f32 = ctx->precision == VP_PREC_FP32_CONTRACT;
+  auto kern = pl.tile == 64 ? (f32 ? k_gemm<ALoad, BLoad, float, 64> : k_gemm<ALoad, BLoad, double, 64>)
+                            : (f32 ? k_gemm<ALoad, BLoad, float, 32> : k_gemm<ALoad, BLoad, double, 32>);
+  int slices = pl.slices;
+  const int kslice = pl.kslice;
   if (slices <= 1) {
     ctx->launches++;
     kern<<<grid, 256, 0, ctx->stream>>>(M, N, K, alpha, a, b, C, ldc, K, 0);
     return check_launch(ctx, what);
   }
-  const int kslice = ((K + slices - 1) / slices + 15) / 16 * 16;
-  slices = (K + kslice - 1) / kslice;
   const size_t stride = (size_t)M * N;
   VP_TRY(reserve(ctx, ctx->w_split, stride * slices));
   grid.z = slices;
@@ -2438,13 +2469,13 @@ struct GemmJob {
   int ldc;
   size_t stride;
 };
-template <class ALoad, class BLoad, class T>
+template <class ALoad, class BLoad, class T, int TILE>
 __global__ void __launch_bounds__(256) kb_gemm(const __grid_constant__ Pack<GemmJob<ALoad, BLoad>> pk, int zs) {
   const GemmJob<ALoad, BLoad>& j = pk.a[blockIdx.z / zs];
   const int slice = blockIdx.z % zs;
-  if (slice >= j.slices || (int)blockIdx.x * 64 >= j.M || (int)blockIdx.y * 64 >= j.N) return;
-  gemm_body<ALoad, BLoad, T>(j.M, j.N, j.K, j.alpha, j.a, j.b, j.C, j.ldc, j.kslice, j.stride, blockIdx.x, blockIdx.y,
-                             slice);
+  if (slice >= j.slices || (int)blockIdx.x * TILE >= j.M || (int)blockIdx.y * TILE >= j.N) return;
+  gemm_body<ALoad, BLoad, T, TILE>(j.M, j.N, j.K, j.alpha, j.a, j.b, j.C, j.ldc, j.kslice, j.stride, blockIdx.x,
+                                   blockIdx.y, slice);
 }
 struct SumArgs {
   const double* P;
@@ -2459,22 +2490,7 @@ __global__ void kb_sum_slices(const __grid_constant__ Pack<SumArgs> pk) {
 }
 
 namespace {
-// Split-K choice of gemm_dispatch for one problem.
-void gemm_split(const vp_ctx* ctx, int M, int N, int K, int* slices, int* kslice) {
-  const int tiles = ((M + 63) / 64) * ((N + 63) / 64);
-  int sl = 1;
-  if (tiles < ctx->num_sms && K >= 128) sl = std::min(std::min(2 * ctx->num_sms / tiles, K / 64), 32);
-  if (sl <= 1) {
-    *slices = 1;
-    *kslice = K;
-    return;
-  }
-  const int ks = ((K + sl - 1) / sl + 15) / 16 * 16;
-  *kslice = ks;
-  *slices = (K + ks - 1) / ks;
-}
-
-template <class ALoad, class BLoad, class T>
+template <class ALoad, class BLoad, class T, int TILE>
 int gemm_group(vp_ctx* ctx, cudaStream_t st, const std::vector<GemmJob<ALoad, BLoad>>& jobs) {
   for (size_t i0 = 0; i0 < jobs.size(); i0 += kMaxBatch) {
     const int nb = (int)std::min<size_t>(kMaxBatch, jobs.size() - i0);
@@ -2483,13 +2499,13 @@ int gemm_group(vp_ctx* ctx, cudaStream_t st, const std::vector<GemmJob<ALoad, BL
     for (int i = 0; i < nb; ++i) {
       const auto& j = jobs[i0 + i];
       pk.a[i] = j;
-      gx = std::max(gx, (j.M + 63) / 64);
-      gy = std::max(gy, (j.N + 63) / 64);
+      gx = std::max(gx, (j.M + TILE - 1) / TILE);
+      gy = std::max(gy, (j.N + TILE - 1) / TILE);
       zs = std::max(zs, j.slices);
     }
     if (gy > 65535) return fail(ctx, VP_ECAPACITY, "gemm: N too large");
     ctx->launches++;
-    kb_gemm<ALoad, BLoad, T><<<dim3(gx, gy, nb * zs), 256, 0, st>>>(pk, zs);
+    kb_gemm<ALoad, BLoad, T, TILE><<<dim3(gx, gy, nb * zs), 256, 0, st>>>(pk, zs);
     VP_TRY(check_launch(ctx, "b_gemm"));
   }
   return VP_OK;
@@ -2497,15 +2513,16 @@ int gemm_group(vp_ctx* ctx, cudaStream_t st, const std::vector<GemmJob<ALoad, BL
 }  // namespace
 
 int blaunch_gemm(vp_ctx* ctx, cudaStream_t st, const std::vector<BGemm>& v) {
-  std::vector<GemmJob<ARowMajor, BRowMajor>> ab[2];
-  std::vector<GemmJob<ARowMajor, BTransposed>> abt[2];
-  std::vector<GemmJob<AUpperColMajor, BRowMajor>> rb[2];
+  // [FP32 contraction][tile 64 / 32]
+  std::vector<GemmJob<ARowMajor, BRowMajor>> ab[2][2];
+  std::vector<GemmJob<ARowMajor, BTransposed>> abt[2][2];
+  std::vector<GemmJob<AUpperColMajor, BRowMajor>> rb[2][2];
   std::vector<SumArgs> sums;
   SlotCounter slots;
   for (const BGemm& g : v) {
     if (g.M <= 0 || g.N <= 0) continue;
-    int slices = 1, kslice = g.K;
-    gemm_split(ctx, g.M, g.N, g.K, &slices, &kslice);
+    const GemmPlan pl = gemm_plan(ctx, g.M, g.N, g.K);
+    const int slices = pl.slices, kslice = pl.kslice, ti = pl.tile == 64 ? 0 : 1;
     double* C = g.C;
     int ldc = g.ldc;
     size_t stride = 0;
@@ -2520,21 +2537,27 @@ int blaunch_gemm(vp_ctx* ctx, cudaStream_t st, const std::vector<BGemm>& v) {
     }
     const int t = g.fp32 ? 1 : 0;
     if (g.kind == BG_AB)
-      ab[t].push_back({g.M, g.N, g.K, kslice, slices, g.alpha, ARowMajor{g.A, g.lda}, BRowMajor{g.B, g.ldb}, C, ldc,
+      ab[t][ti].push_back({g.M, g.N, g.K, kslice, slices, g.alpha, ARowMajor{g.A, g.lda}, BRowMajor{g.B, g.ldb}, C, ldc,
                        stride});
     else if (g.kind == BG_ABT)
-      abt[t].push_back({g.M, g.N, g.K, kslice, slices, g.alpha, ARowMajor{g.A, g.lda}, BTransposed{g.B, g.ldb}, C,
+      abt[t][ti].push_back({g.M, g.N, g.K, kslice, slices, g.alpha, ARowMajor{g.A, g.lda}, BTransposed{g.B, g.ldb}, C,
                         ldc, stride});
     else
-      rb[t].push_back({g.M, g.N, g.K, kslice, slices, g.alpha, AUpperColMajor{g.A, g.lda}, BRowMajor{g.B, g.ldb}, C,
+      rb[t][ti].push_back({g.M, g.N, g.K, kslice, slices, g.alpha, AUpperColMajor{g.A, g.lda}, BRowMajor{g.B, g.ldb}, C,
                        ldc, stride});
   }
-  VP_TRY((gemm_group<ARowMajor, BRowMajor, double>(ctx, st, ab[0])));
-  VP_TRY((gemm_group<ARowMajor, BRowMajor, float>(ctx, st, ab[1])));
-  VP_TRY((gemm_group<ARowMajor, BTransposed, double>(ctx, st, abt[0])));
-  VP_TRY((gemm_group<ARowMajor, BTransposed, float>(ctx, st, abt[1])));
-  VP_TRY((gemm_group<AUpperColMajor, BRowMajor, double>(ctx, st, rb[0])));
-  VP_TRY((gemm_group<AUpperColMajor, BRowMajor, float>(ctx, st, rb[1])));
+  VP_TRY((gemm_group<ARowMajor, BRowMajor, double, 64>(ctx, st, ab[0][0])));
+  VP_TRY((gemm_group<ARowMajor, BRowMajor, double, 32>(ctx, st, ab[0][1])));
+  VP_TRY((gemm_group<ARowMajor, BRowMajor, float, 64>(ctx, st, ab[1][0])));
+  VP_TRY((gemm_group<ARowMajor, BRowMajor, float, 32>(ctx, st, ab[1][1])));
+  VP_TRY((gemm_group<ARowMajor, BTransposed, double, 64>(ctx, st, abt[0][0])));
+  VP_TRY((gemm_group<ARowMajor, BTransposed, double, 32>(ctx, st, abt[0][1])));
+  VP_TRY((gemm_group<ARowMajor, BTransposed, float, 64>(ctx, st, abt[1][0])));
+  VP_TRY((gemm_group<ARowMajor, BTransposed, float, 32>(ctx, st, abt[1][1])));
+  VP_TRY((gemm_group<AUpperColMajor, BRowMajor, double, 64>(ctx, st, rb[0][0])));
+  VP_TRY((gemm_group<AUpperColMajor, BRowMajor, double, 32>(ctx, st, rb[0][1])));
+  VP_TRY((gemm_group<AUpperColMajor, BRowMajor, float, 64>(ctx, st, rb[1][0])));
+  VP_TRY((gemm_group<AUpperColMajor, BRowMajor, float, 32>(ctx, st, rb[1][1])));
   return run_packs(ctx, st, sums, kb_sum_slices, 256, 0,
                    [&](const SumArgs& a) { return grid_stride_blocks(ctx, a.stride, 8); }, "b_sum_slices");
 }
