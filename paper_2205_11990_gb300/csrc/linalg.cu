@@ -1601,9 +1601,63 @@ __device__ __forceinline__ void k_jacobi_dw_body(double* X, int b, int c, double
   unsigned* c0 = cl.map_shared_rank(cnt, 0);
   const float tiny = 1e-30f;
 
-  // one inner round over nb disjoint pairs: A dot products (a warp per pair),
-  // B rotation parameters (a lane per pair), C updates (a warp per pair)
+  // Rotation parameters of one pair from gamma = <x_i, x_j> and the squared
+  // norms alpha, beta held after each row (false: the pair is left alone).
+  auto pair_params = [&](dw al, dw be, dw g, dw& cs, dw& sn, dw& tg) -> bool {
+    if (!(al.hi > tiny && be.hi > tiny && fabsf(g.hi) * rsqrtf(al.hi) * rsqrtf(be.hi) > eps)) return false;
+    // tangent in FP32 after an exact power-of-two scaling of d and gamma
+    // (their squares would leave the FP32 range for small rows)
+    const float d0 = 0.5f * dw_add(be, dw_neg(al)).hi;
+    int e2;
+    frexpf(fmaxf(fabsf(d0), fabsf(g.hi)), &e2);
+    const float d = ldexpf(d0, -e2), gs = ldexpf(g.hi, -e2);
+    const float t = copysignf(1.0f, d) * gs / (fabsf(d) + sqrtf(fmaf(d, d, gs * gs)));
+    if (t == 0.f) return false;
+    const dw t2 = two_prod(t, t);
+    cs = dw_rsqrt(dw_add({1.0f, 0.0f}, t2));
+    sn = dw_mul_f(cs, t);
+    tg = dw_mul_f(g, t);
+    return true;
+  };
+  // One inner round over nb disjoint pairs.  With at most one pair per warp
+  // (nb <= kWarps, the usual case) pair i belongs to the wpp = kWarps / nb
+  // warps i wpp .. i wpp + wpp - 1: each of them forms gamma and the
+  // rotation itself (the same operations, so the same bits), and rotates its
+  // share of the columns; one named barrier of the pair's warps orders the
+  // reads of alpha and beta before their update, and one block barrier ends
+  // the round.  With more pairs than warps the round runs in three phases:
+  // A dot products (a warp per pair), B rotation parameters (a lane per
+  // pair), C updates (a warp per pair), each ended by a block barrier.
   auto inner_round = [&](auto pair_rows, unsigned& rotated) {
+    if (nb <= kWarps) {
+      const int wpp = kWarps / nb, pi = warp / wpp, part = warp % wpp;
+      if (pi < nb) {
+        dw *ri, *rj;
+        pair_rows(pi, ri, rj);
+        dw_acc acc;
+        dw_dot_rows(acc, ri, rj, 0, c, lane);
+        const dw g = dw_warp_sum(dw_acc_value(acc));
+        const dw al = ri[w], be = rj[w];
+        dw cs, sn, tg;
+        const bool rot = pair_params(al, be, g, cs, sn, tg);
+        // every warp of the pair has read alpha and beta before they change
+        if (wpp > 1)
+          asm volatile("bar.sync %0, %1;" ::"r"(1 + pi), "r"(32 * wpp) : "memory");
+        else
+          __syncwarp();
+        if (rot) {
+          if (part == 0 && lane == 0) {
+            ri[w] = dw_add(al, dw_neg(tg));
+            rj[w] = dw_add(be, tg);
+            ++rotated;
+          }
+          const int span = (w + wpp - 1) / wpp, q0 = part * span;
+          if (q0 < w) dw_rot_rows(ri + q0, rj + q0, cs, sn, min(span, w - q0), lane);
+        }
+      }
+      __syncthreads();
+      return;
+    }
     for (int pi = warp; pi < nb; pi += kWarps) {
       dw *ri, *rj;
       pair_rows(pi, ri, rj);
@@ -1617,43 +1671,26 @@ __device__ __forceinline__ void k_jacobi_dw_body(double* X, int b, int c, double
       for (int pi = lane; pi < nb; pi += 32) {
         dw *ri, *rj;
         pair_rows(pi, ri, rj);
-        const dw al = ri[w], be = rj[w], g = par[3 * pi];
+        const dw al = ri[w], be = rj[w];
+        dw cs, sn, tg;
         float flag = 0.f;
-        if (al.hi > tiny && be.hi > tiny && fabsf(g.hi) * rsqrtf(al.hi) * rsqrtf(be.hi) > eps) {
-          // tangent in FP32 after an exact power-of-two scaling of d and
-          // gamma (their squares would leave the FP32 range for small rows)
-          const float d0 = 0.5f * dw_add(be, dw_neg(al)).hi;
-          int e2;
-          frexpf(fmaxf(fabsf(d0), fabsf(g.hi)), &e2);
-          const float d = ldexpf(d0, -e2), gs = ldexpf(g.hi, -e2);
-          const float t = copysignf(1.0f, d) * gs / (fabsf(d) + sqrtf(fmaf(d, d, gs * gs)));
-          if (t != 0.f) {
-            const dw t2 = two_prod(t, t);
-            const dw cs = dw_rsqrt(dw_add({1.0f, 0.0f}, t2));
-            const dw sn = dw_mul_f(cs, t);
-            const dw tg = dw_mul_f(g, t);
-            ri[w] = dw_add(al, dw_neg(tg));
-            rj[w] = dw_add(be, tg);
-            par[3 * pi + 1] = cs;
-            par[3 * pi + 2] = sn;
-            flag = 1.f;
-            ++rotated;
-          }
+        if (pair_params(al, be, par[3 * pi], cs, sn, tg)) {
+          ri[w] = dw_add(al, dw_neg(tg));
+          rj[w] = dw_add(be, tg);
+          par[3 * pi + 1] = cs;
+          par[3 * pi + 2] = sn;
+          flag = 1.f;
+          ++rotated;
         }
         par[3 * pi].hi = flag;
       }
     }
     __syncthreads();
-    // the columns of a pair split over wpp warps when there are fewer pairs
-    // than warps (each column is rotated by the same steps either way)
-    const int wpp = nb >= kWarps ? 1 : (nb * 2 >= kWarps ? 2 : 4);
-    const int span = (w + wpp - 1) / wpp;
-    for (int pw = warp; pw < nb * wpp; pw += kWarps) {
-      const int pi = pw / wpp, q0 = (pw % wpp) * span;
-      if (par[3 * pi].hi == 0.f || q0 >= w) continue;
+    for (int pi = warp; pi < nb; pi += kWarps) {
+      if (par[3 * pi].hi == 0.f) continue;
       dw *ri, *rj;
       pair_rows(pi, ri, rj);
-      dw_rot_rows(ri + q0, rj + q0, par[3 * pi + 1], par[3 * pi + 2], min(span, w - q0), lane);
+      dw_rot_rows(ri, rj, par[3 * pi + 1], par[3 * pi + 2], w, lane);
     }
     __syncthreads();
   };
@@ -1692,7 +1729,7 @@ __device__ __forceinline__ void k_jacobi_dw_body(double* X, int b, int c, double
               rj = row(cur, 1, (pi + s) % nb);
             },
             rotated);
-      if (br == brounds - 1 && warp == 0) {
+      if (br == brounds - 1) {
         const unsigned tot = __reduce_add_sync(0xffffffffu, rotated);
         if (lane == 0 && tot) atomicAdd(&c0[sweep % 3], tot);
       }
