@@ -1695,10 +1695,31 @@ __device__ __forceinline__ void k_jacobi_dw_body(double* X, int b, int c, double
     __syncthreads();
   };
 
-  int cur = 0, sweep = 0;
-  bool converged = false;
+  // A pair that would rotate, counted without rotating (the test of
+  // inner_round on the same operands in the same order).
+  auto dry_pair = [&](const dw* ri, const dw* rj, unsigned& would) {
+    dw_acc acc;
+    dw_dot_rows(acc, ri, rj, 0, c, lane);
+    const dw g = dw_warp_sum(dw_acc_value(acc));
+    dw cs, sn, tg;
+    if (pair_params(ri[w], rj[w], g, cs, sn, tg) && lane == 0) ++would;
+  };
+
+  // Sweeps of the circle schedule until one rotates nothing.  After a sweep
+  // with few rotations (at most max(4, b/2)) the next pass is a dry sweep:
+  // every pair of the schedule is tested in the same order and orientation
+  // but nothing is rotated, so its pairs need no barriers between rounds.  If
+  // no pair would rotate, the plain sweep would have rotated nothing either
+  // (its operands never change) and the rows are final; otherwise nothing has
+  // changed and the plain sweep runs.  The result is the plain schedule's,
+  // bit for bit, without its last, rotation-free sweep.
+  int cur = 0, iter = 0, sweeps = 0;
+  bool converged = false, dry_failed = false;
+  unsigned last_rot = 0xffffffffu;
+  const unsigned dry_max = (unsigned)max(4, b / 2);
   const int brounds = 2 * CS - 1;
-  for (; sweep < max_sweeps; ++sweep) {
+  for (; sweeps < max_sweeps; ++iter) {
+    const bool dry = last_rot <= dry_max && !dry_failed;
     // exact squared norms of the local rows
     __syncthreads();
     for (int rr = warp; rr < 2 * nb; rr += kWarps) {
@@ -1708,30 +1729,43 @@ __device__ __forceinline__ void k_jacobi_dw_body(double* X, int b, int c, double
       const dw a = dw_warp_sum(dw_acc_value(acc));
       if (lane == 0) d[w] = a;
     }
-    if (rank == 0 && tid == 0) cnt[(sweep + 1) % 3] = 0u;
+    if (rank == 0 && tid == 0) cnt[(iter + 1) % 3] = 0u;
     cl.sync();
     unsigned rotated = 0;
     for (int br = 0; br < brounds; ++br) {
-      if (br == 0) {
-        for (int ir = 0; ir < nb - 1; ++ir)
+      if (dry) {
+        if (br == 0)
+          for (int e = warp; e < (nb - 1) * nb; e += kWarps) {
+            const int ir = e / nb, pi = e % nb;
+            const int slot = pi / (nb / 2), pos = pi % (nb / 2);
+            dry_pair(row(cur, slot, rr_index(pos, ir, nb)), row(cur, slot, rr_index(nb - 1 - pos, ir, nb)), rotated);
+          }
+        for (int e = warp; e < nb * nb; e += kWarps) {
+          const int sh = e / nb, pi = e % nb;
+          dry_pair(row(cur, 0, pi), row(cur, 1, (pi + sh) % nb), rotated);
+        }
+      } else {
+        if (br == 0) {
+          for (int ir = 0; ir < nb - 1; ++ir)
+            inner_round(
+                [&](int pi, dw*& ri, dw*& rj) {
+                  const int slot = pi / (nb / 2), pos = pi % (nb / 2);
+                  ri = row(cur, slot, rr_index(pos, ir, nb));
+                  rj = row(cur, slot, rr_index(nb - 1 - pos, ir, nb));
+                },
+                rotated);
+        }
+        for (int sh = 0; sh < nb; ++sh)
           inner_round(
               [&](int pi, dw*& ri, dw*& rj) {
-                const int slot = pi / (nb / 2), pos = pi % (nb / 2);
-                ri = row(cur, slot, rr_index(pos, ir, nb));
-                rj = row(cur, slot, rr_index(nb - 1 - pos, ir, nb));
+                ri = row(cur, 0, pi);
+                rj = row(cur, 1, (pi + sh) % nb);
               },
               rotated);
       }
-      for (int s = 0; s < nb; ++s)
-        inner_round(
-            [&](int pi, dw*& ri, dw*& rj) {
-              ri = row(cur, 0, pi);
-              rj = row(cur, 1, (pi + s) % nb);
-            },
-            rotated);
       if (br == brounds - 1) {
         const unsigned tot = __reduce_add_sync(0xffffffffu, rotated);
-        if (lane == 0 && tot) atomicAdd(&c0[sweep % 3], tot);
+        if (lane == 0 && tot) atomicAdd(&c0[iter % 3], tot);
       }
       if (CS > 1) {
         for (int slot = 0; slot < 2; ++slot) {
@@ -1745,9 +1779,16 @@ __device__ __forceinline__ void k_jacobi_dw_body(double* X, int b, int c, double
       }
       cl.sync();
     }
-    if (*(volatile unsigned*)&c0[sweep % 3] == 0u) {
+    const unsigned tot = *(volatile unsigned*)&c0[iter % 3];
+    if (tot == 0u) {
       converged = true;
+      ++sweeps;
       break;
+    }
+    dry_failed = dry;
+    if (!dry) {
+      ++sweeps;
+      last_rot = tot;
     }
   }
   __syncthreads();
@@ -1762,7 +1803,7 @@ __device__ __forceinline__ void k_jacobi_dw_body(double* X, int b, int c, double
     }
   }
   if (rank == 0 && tid == 0) {
-    st->pad2 = sweep + 1;
+    st->pad2 = converged ? sweeps : max_sweeps + 1;  // as the plain schedule counts them
     if (!converged) atomicCAS(&st->err, 0, 3);
   }
   cl.sync();  // keep every CTA's shared memory alive until all remote accesses are done
