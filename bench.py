@@ -500,6 +500,7 @@ def run_batch(args):
     arms = [("lockstep", dict(max_concurrent=args.instances, lockstep=args.groups)),
             ("sequential", dict(max_concurrent=1, lockstep=0))]
     results = {}
+    launches = 0
     for label, kw in arms:
         b = vpmps.Batch(ctx, kw["max_concurrent"], 200 << 30, lockstep=kw["lockstep"])
         ids = [b.submit(lay, f0, dt, steps, chi, keep_f=True) for lay, f0, dt, chi in reqs]
@@ -516,6 +517,8 @@ def run_batch(args):
                       "step_ms_p99": float(np.percentile(step_ms, 99)),
                       "run_ms_p50": float(np.median([r["queue_ms"] + r["run_ms"] for r in res.values()])),
                       "run_ms_p99": float(np.percentile([r["queue_ms"] + r["run_ms"] for r in res.values()], 99))}
+        out[label]["gpu_launches"] = b.kernel_launches
+        launches += b.kernel_launches
         b.close()
     # the two arms compute the same runs: every final state and record equal
     same = all(np.array_equal(a[2], c[2]) and a[0] == c[0] for a, c in zip(results["lockstep"], results["sequential"]))
@@ -527,7 +530,7 @@ def run_batch(args):
                    "lockstep_groups": args.groups, "seed": 0},
         "lockstep": out["lockstep"], "sequential_fp64_per_instance": out["sequential"],
         "speedup_vs_sequential": out["lockstep"]["sims_per_s"] / out["sequential"]["sims_per_s"],
-        "results_identical": bool(same), "gpu_launches": ctx.kernel_launches}), flush=True)
+        "results_identical": bool(same), "gpu_launches": ctx.kernel_launches + launches}), flush=True)
 
 
 def run_serve(args):
@@ -562,6 +565,7 @@ def run_serve(args):
         recs, ms, _ = b.records(r["id"])
         steps_ms += list(ms)
     run_lat = [r["queue_ms"] + r["run_ms"] for r in done]
+    launches = ctx.kernel_launches + b.kernel_launches
     b.close()
     print(json.dumps({
         "metric": "served sims/s with p50/p99 step and run latency (continuous batching)",
@@ -573,7 +577,7 @@ def run_serve(args):
                    "seed": 1},
         "step_ms_p50": float(np.percentile(steps_ms, 50)), "step_ms_p99": float(np.percentile(steps_ms, 99)),
         "run_ms_p50": float(np.percentile(run_lat, 50)), "run_ms_p99": float(np.percentile(run_lat, 99)),
-        "wall_s": wall, "gpu_launches": ctx.kernel_launches}), flush=True)
+        "wall_s": wall, "gpu_launches": launches}), flush=True)
 
 
 def run_precision(args):

@@ -553,6 +553,11 @@ int vp_batch_poll(vp_batch* b, vp_result* out, int max, int* n_out);
 /* Per-step records[nsteps], per-step wall times step_ms[nsteps] (host, may be
  * NULL) and f(T) on the grid (host, needs keep_f) of a finished run. */
 int vp_batch_records(vp_batch* b, uint64_t id, vp_record* records, double* step_ms, double* fT_host);
+/* Kernels launched so far by the batch's worker contexts (diagnostics; the
+ * caller's context counts its own launches in vp_kernel_launches).  Read it
+ * while the workers are idle: after vp_batch_wait, or once every submitted
+ * run has been polled.  0 for NULL or before vp_batch_start. */
+int64_t vp_batch_kernel_launches(const vp_batch* b);
 int vp_batch_destroy(vp_batch* b);
 
 #ifdef __cplusplus

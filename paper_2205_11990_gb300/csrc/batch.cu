@@ -431,6 +431,13 @@ int vp_batch_records(vp_batch* b, uint64_t id, vp_record* records, double* step_
   return VP_OK;
 }
 
+int64_t vp_batch_kernel_launches(const vp_batch* b) {
+  if (!b) return 0;
+  int64_t n = 0;
+  for (const vp_ctx* c : b->wctx) n += vp_kernel_launches(c);
+  return n;
+}
+
 int vp_batch_destroy(vp_batch* b) {
   if (!b) return VP_EINVAL;
   {

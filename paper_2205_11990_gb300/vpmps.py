@@ -41,7 +41,7 @@ EXPORTS = [
     "mps_apply_mpo", "mps_axpby", "mps_compress", "mps_compress_modified", "mps_compression_error", "vp_density", "vp_poisson", "vp_poisson_noalloc", "vp_gemm",
     "vp_sim_create", "vp_sim_destroy", "vp_step", "vp_sim_state", "vp_sim_entropy", "vp_sim_flops", "vp_run",
     "vp_footprint_bytes", "vp_batch_create", "vp_batch_submit", "vp_batch_start", "vp_batch_wait", "vp_batch_poll",
-    "vp_batch_records", "vp_batch_destroy", "vp_batch_set_lockstep",
+    "vp_batch_records", "vp_batch_destroy", "vp_batch_set_lockstep", "vp_batch_kernel_launches",
     "vp_multi_create", "vp_multi_destroy", "vp_multi_step", "vp_multi_state",
     "vp_group_create", "vp_group_add", "vp_group_remove", "vp_group_size", "vp_group_step", "vp_group_stats", "vp_group_mps_create", "vp_group_destroy",
 ]
@@ -163,6 +163,7 @@ def load():
         "vp_batch_records": (I, [P, C.c_uint64, C.POINTER(CRecord), DP, DP]),
         "vp_batch_destroy": (I, [P]),
         "vp_batch_set_lockstep": (I, [P, I]),
+        "vp_batch_kernel_launches": (C.c_int64, [P]),
         "vp_multi_create": (I, [P, I, C.POINTER(CLayout), C.POINTER(CSpecies), C.POINTER(CConfig), C.POINTER(P),
                                 C.POINTER(P)]),
         "vp_multi_destroy": (I, [P]),
@@ -507,6 +508,11 @@ class Batch:
         fT = np.zeros((lay.Nx, lay.Nv)) if want_f else None
         self.ctx._check(self.ctx.lib.vp_batch_records(self.h, rid, recs, _dp(ms), _dp(fT) if want_f else None))
         return _records(recs, nsteps), ms[:nsteps], fT
+
+    @property
+    def kernel_launches(self) -> int:
+        """Kernels launched by the batch's worker contexts (read while they are idle)."""
+        return int(self.ctx.lib.vp_batch_kernel_launches(self.h)) if self.h else 0
 
     def close(self):
         if self.h and self.ctx.h:
