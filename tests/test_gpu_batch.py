@@ -55,6 +55,8 @@ def test_mix_equals_alone_and_admission(ctx):
     mixed.wait()
     res = {r["id"]: r for r in mixed.poll()}
     assert sorted(res) == sorted(ids) and all(r["status"] == 0 for r in res.values())
+    # the runs stepped on the workers' contexts, whose launches the batch counts
+    assert mixed.kernel_launches > 0
     for rid, (lay, f0, dt, n, chi) in zip(ids, reqs):
         recs_mix, step_ms, f_mix = mixed.records(rid, want_f=True)
         alone = vpmps.Batch(ctx, 1, budget)
