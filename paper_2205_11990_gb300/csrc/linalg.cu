@@ -1944,25 +1944,46 @@ __device__ __forceinline__ bool sorts_before(double a, int ia, double b, int ib)
 
 // Single block: row norms, descending order (ties by index), kept rank by the
 // rule r = min(chi, r_tol), r_tol the smallest r with sqrt(sum_{i>=r} s_i^2)
-// <= tol ||s|| (tail summed smallest first, tol = 0: keep all), moved down
-// to the start of a cluster of values within a relative 1e-5.
+// <= tol ||s|| (tol = 0: keep all), moved down to the start of a cluster of
+// values within a relative 1e-5.  A dependent FP64 operation costs hundreds of
+// cycles on GB300, so nothing here runs as a serial chain over the values:
+// four rows per warp at a time for the norms (each row summed in the same
+// order as alone), the tail sums as a block-wide suffix scan (chunk sums,
+// then a scan of the chunk totals), r_tol as a minimum over the rows that
+// meet the tolerance, and the entanglement entropy as a fixed-order tree sum.
 __device__ __forceinline__ void k_select_body(const double* __restrict__ X, int b, int c, int chi, double tol, int* perm,
                          double* sigma, int* d_rank, double* d_err, DevStatus* st) {
   extern __shared__ double sm[];
   double* s = sm;          // b
   double* tail = sm + b;   // b + 1
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-  for (int i = warp; i < b; i += nwarps) {
-    double a = 0.0;
-    for (int q = lane; q < c; q += 32) {
-      const double u = X[(size_t)i * c + q];
-      a = fma(u, u, a);
-    }
-    a = warp_sum(a);
-    if (lane == 0) s[i] = sqrt(a);
+  __shared__ double ctot[1024];  // per-thread chunk totals, then their suffix sums
+  __shared__ double wpart[32];
+  __shared__ int rmin, rkeep;
+  const int T = blockDim.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = T >> 5;
+  constexpr int RB = 4;
+  for (int i0 = warp * RB; i0 < b; i0 += nwarps * RB) {
+    double a[RB];
+#pragma unroll
+    for (int u = 0; u < RB; ++u) a[u] = 0.0;
+    for (int q = lane; q < c; q += 32)
+#pragma unroll
+      for (int u = 0; u < RB; ++u)
+        if (i0 + u < b) {
+          const double x = X[(size_t)(i0 + u) * c + q];
+          a[u] = fma(x, x, a[u]);
+        }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+      for (int u = 0; u < RB; ++u) a[u] += __shfl_xor_sync(0xffffffffu, a[u], o);
+    if (lane == 0)
+#pragma unroll
+      for (int u = 0; u < RB; ++u)
+        if (i0 + u < b) s[i0 + u] = sqrt(a[u]);
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < b; i += blockDim.x) {
+  for (int i = threadIdx.x; i < b; i += T) {
     const double si = s[i];
     if (!isfinite(si)) atomicCAS(&st->err, 0, 2);
     int pos = 0;
@@ -1971,43 +1992,69 @@ __device__ __forceinline__ void k_select_body(const double* __restrict__ X, int 
     sigma[pos] = si;
   }
   __syncthreads();
+  // tail[i] = sum_{k >= i} sigma_k^2: each thread a chunk of k consecutive
+  // values (summed smallest first), then a suffix scan of the chunk totals
+  const int k = (b + T - 1) / T;
+  const int lo = threadIdx.x * k, hi = min(b, lo + k);
+  double acc = 0.0;
+  for (int i = hi - 1; i >= lo; --i) {
+    acc = fma(sigma[i], sigma[i], acc);
+    tail[i] = acc;
+  }
+  ctot[threadIdx.x] = acc;
   if (threadIdx.x == 0) {
-    double acc = 0.0;
     tail[b] = 0.0;
-    for (int i = b - 1; i >= 0; --i) {
-      acc = fma(sigma[i], sigma[i], acc);
-      tail[i] = acc;
-    }
-    const double nrm2 = tail[0];
+    rmin = b;
+  }
+  __syncthreads();
+  for (int off = 1; off < T; off <<= 1) {
+    const double v = ctot[threadIdx.x] + (threadIdx.x + off < T ? ctot[threadIdx.x + off] : 0.0);
+    __syncthreads();
+    ctot[threadIdx.x] = v;
+    __syncthreads();
+  }
+  const double after = threadIdx.x + 1 < T ? ctot[threadIdx.x + 1] : 0.0;
+  for (int i = lo; i < hi; ++i) tail[i] += after;
+  __syncthreads();
+  const double nrm2 = tail[0];
+  if (nrm2 > 0.0 && tol > 0.0) {
+    const double thr2 = tol * tol * nrm2;
+    for (int q = threadIdx.x + 1; q <= b; q += T)
+      if (tail[q] <= thr2) atomicMin(&rmin, q);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
     int r = 1;
     double err = 0.0;
     if (nrm2 > 0.0) {
-      int r_tol = b;
-      if (tol > 0.0) {
-        const double thr2 = tol * tol * nrm2;
-        for (int q = 1; q <= b; ++q)
-          if (tail[q] <= thr2) {
-            r_tol = q;
-            break;
-          }
-      }
-      r = min(min(chi, r_tol), b);
+      r = min(min(chi, rmin), b);
       while (r > 1 && r < b && (sigma[r - 1] - sigma[r]) <= 1e-5 * sigma[r - 1]) --r;
       if (r < 1) r = 1;
       err = sqrt(tail[r] / nrm2);
     }
-    // entanglement entropy of the kept values (main text, EE equation):
-    // -sum p log2 p with p_i = s_i^2 / sum_{kept} s^2
-    double ee = 0.0;
-    const double kept2 = tail[0] - tail[r];
-    if (kept2 > 0.0)
-      for (int q = 0; q < r; ++q) {
-        const double pq = sigma[q] * sigma[q] / kept2;
-        if (pq > 0.0) ee -= pq * log2(pq);
-      }
+    rkeep = r;
     *d_rank = r;
     d_err[0] = err;
-    d_err[1] = ee;
+  }
+  __syncthreads();
+  // entanglement entropy of the kept values (main text, EE equation):
+  // -sum p log2 p with p_i = s_i^2 / sum_{kept} s^2
+  const int r = rkeep;
+  const double kept2 = tail[0] - tail[r];
+  double ee = 0.0;
+  if (kept2 > 0.0)
+    for (int q = threadIdx.x; q < r; q += T) {
+      const double pq = sigma[q] * sigma[q] / kept2;
+      if (pq > 0.0) ee -= pq * log2(pq);
+    }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) ee += __shfl_xor_sync(0xffffffffu, ee, o);
+  if (lane == 0) wpart[warp] = ee;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tot = 0.0;
+    for (int w = 0; w < nwarps; ++w) tot += wpart[w];
+    d_err[1] = tot;
   }
 }
 __global__ void k_select(const double* __restrict__ X, int b, int c, int chi, double tol, int* perm,
