@@ -368,6 +368,13 @@ __device__ __forceinline__ void k_qr_factor_cdw_body(double* A, int m, int n, do
   dw* vbuf = cols + (size_t)nmax * m;         // 2 x m incoming reflectors
   dw* tbuf = vbuf + 2 * (size_t)m;            // 2 incoming taus
   int* cexp = reinterpret_cast<int*>(tbuf + 2);
+  // a one-CTA cluster needs only the block barrier
+  auto csync = [&] {
+    if (CS == 1)
+      __syncthreads();
+    else
+      cl.sync();
+  };
 
   for (int lc = warp; lc < nown; lc += kWarps) {
     const double* a = A + (size_t)(rank + lc * CS) * m;
@@ -429,9 +436,9 @@ __device__ __forceinline__ void k_qr_factor_cdw_body(double* A, int m, int n, do
     }
   };
 
-  cl.sync();  // every CTA resident before the first remote write
+  csync();  // every CTA resident before the first remote write
   if (rank == 0 && warp == 0 && p > 0) reflect_push(0, cols);
-  cl.sync();
+  csync();
   for (int j = 0; j < p; ++j) {
     const bool owner = j + 1 < p && rank == (j + 1) % CS;
     if (owner && warp == 0) {
@@ -444,7 +451,7 @@ __device__ __forceinline__ void k_qr_factor_cdw_body(double* A, int m, int n, do
       const int lc0 = (j + 2 - rank + CS - 1) / CS > 0 ? (j + 2 - rank + CS - 1) / CS : 0;
       for (int lc = lc0 + wk; lc < nown; lc += nwk) apply(j, cols + (size_t)lc * m);
     }
-    cl.sync();
+    csync();
   }
   for (int lc = warp; lc < nown; lc += kWarps) {
     const int k = rank + lc * CS;
@@ -683,8 +690,10 @@ QRPlan qr_plan(const vp_ctx* ctx, int m, int n) {
   if (std::min(m, n) <= 0) return {QR_NONE, 0};
   if (n > 2 * m && m >= 2) return {QR_WIDE, 0};
   if (ctx->cluster_size > 1 && (long long)m * n <= 4096) {
-    int cs = 2;
-    while (cs < std::min(ctx->cluster_size, 4) && cs * 8 < n) cs *= 2;
+    // one CTA up to 32 columns, else two (measured on GB300 for 2x2 .. 128x32
+    // and 50x50 .. 120x34: four CTAs were never faster; the result does not
+    // depend on the CTA count)
+    const int cs = n <= 32 ? 1 : 2;
     if (qr_cdw_smem(m, n, cs) <= 200 * 1024) return {QR_CDW, cs};
   }
   if (ctx->cluster_size >= 8 && 2 * m >= n) {
@@ -2463,7 +2472,7 @@ int blaunch_qr_factor(vp_ctx* ctx, cudaStream_t st, const std::vector<BQR>& v) {
           VP_TRY(qr_factor_grid(ctx, st, q.s->st, q.s->qrv, q.s->qrc, q.A, q.m, q.n, q.tau, q.vbuf));
     }
   }
-  for (int cs = 2; cs <= 16; ++cs) {
+  for (int cs = 1; cs <= 16; ++cs) {
     if (!cdw[cs].empty()) {
       static AttrOnce a;
       VP_TRY(a.ensure(ctx, (const void*)kb_qr_factor_cdw, 200 * 1024, true));
