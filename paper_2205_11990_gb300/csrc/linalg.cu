@@ -673,12 +673,11 @@ static size_t qr_cdw_smem(int m, int n, int CS) {
 }
 
 // Which kernel factors an m x n matrix.  Measured per column on GB300 (the
-// step's shapes): up to ~4e3 elements the push-model cluster kernel (2.5 us);
-// above, the pull-model kernel with four critical warps (128x128 2.9 us,
-// 368x128 4.2, 464x184 4.8, 512x341 5.9, 682x132 6.1, 1088x64 7.3, against
-// 3.7-17.7 for the grid kernel): 8 CTAs, 16 for many columns (the column
-// updates dominate), 4 for tall narrow ones (the reflector copies dominate);
-// the grid kernel takes what no cluster's shared memory holds.  Factors more
+// step's shapes): up to ~4e3 elements the small-factor kernel (one CTA up to
+// 32 columns, else two; ~2.3 us per column); above, the cluster kernel with
+// four critical warps on 16 CTAs (~3-5.5 us per column, against 3.7-17.7 for
+// the grid kernel); the grid kernel takes what no cluster's shared memory
+// holds.  Factors more
 // than twice as wide as tall: the m reflectors depend on the leading m
 // columns alone, so that square block (contiguous in the column-major layout)
 // is factored in place, Q is formed from its reflectors, and the rest of R is
@@ -697,9 +696,11 @@ QRPlan qr_plan(const vp_ctx* ctx, int m, int n) {
     if (qr_cdw_smem(m, n, cs) <= 200 * 1024) return {QR_CDW, cs};
   }
   if (ctx->cluster_size >= 8 && 2 * m >= n) {
-    int cs = n >= 300 ? 16 : (n <= 64 && m >= 512 ? 4 : 8);
-    while (cs < ctx->cluster_size && qr_cl_smem(m, n, cs) > 200 * 1024) cs *= 2;
-    if (cs <= ctx->cluster_size && qr_cl_smem(m, n, cs) <= 200 * 1024) return {QR_CL, cs};
+    // the largest cluster: with reflectors published through L2, 16 CTAs beat
+    // 8 by 10-21 % on every shape of the step (two problems per launch) and 4
+    // were never faster; the result does not depend on the CTA count
+    const int cs = ctx->cluster_size >= 16 ? 16 : 8;
+    if (qr_cl_smem(m, n, cs) <= 200 * 1024) return {QR_CL, cs};
   }
   return {QR_GRID, 0};
 }
@@ -2448,8 +2449,14 @@ int blaunch_qr_factor(vp_ctx* ctx, cudaStream_t st, const std::vector<BQR>& v) {
   std::vector<const BQR*> grid;
   std::vector<QRArgs> cdw[17], cl[17];
   size_t cdw_smem[17] = {}, cl_smem[17] = {};
+  // More than four cluster factors in one call: 8-CTA clusters where they fit,
+  // so that twice as many problems run side by side (the result does not
+  // depend on the CTA count).
+  int ncl = 0;
+  for (const BQR& q : v) ncl += qr_plan(ctx, q.m, q.n).kind == QR_CL;
   for (const BQR& q : v) {
-    const QRPlan pl = qr_plan(ctx, q.m, q.n);
+    QRPlan pl = qr_plan(ctx, q.m, q.n);
+    if (pl.kind == QR_CL && ncl > 4 && pl.cs > 8 && qr_cl_smem(q.m, q.n, 8) <= 200 * 1024) pl.cs = 8;
     switch (pl.kind) {
       case QR_NONE:
         break;
