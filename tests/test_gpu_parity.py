@@ -111,6 +111,9 @@ COMPRESS_CASES = [
     ([1, 2, 4, 8, 16, 32, 70, 150, 200, 75, 31, 8, 2, 1], 1 << 10, 1e-12),
     ([1, 2, 4, 8, 16, 32, 64, 130, 64, 17, 4, 2, 1], 24, 1e-10),
     ([1, 2, 3, 37, 90, 41, 7, 2, 1], 1 << 10, 1e-3),
+    # an SVD site of 700 rows: the truncation scan runs over chunks of several
+    # values per thread (more values than the block's 512 threads)
+    ([1, 2, 4, 8, 16, 32, 64, 128, 256, 512, 700, 512, 256, 128, 64, 32, 16, 8, 4, 2, 1], 1 << 10, 1e-10),
 ]
 
 

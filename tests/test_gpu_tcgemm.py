@@ -12,7 +12,11 @@ import pytest
 
 pytestmark = pytest.mark.gpu
 
-SHAPES = [(1, 1, 1), (128, 64, 32), (200, 77, 45), (300, 130, 300), (129, 129, 257), (64, 200, 96)]
+SHAPES = [(1, 1, 1), (128, 64, 32), (200, 77, 45), (300, 130, 300), (129, 129, 257), (64, 200, 96),
+          # the FP64 plan's other branches: 64 x 64 tiles without a split (>= one
+          # tile per SM), K <= 16 (no split), K just above a slice multiple, and a
+          # narrow output split into many K slices
+          (1024, 1000, 40), (7, 9, 16), (50, 60, 17), (33, 31, 500)]
 
 
 @pytest.fixture(scope="module")
