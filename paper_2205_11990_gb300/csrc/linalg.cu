@@ -2074,10 +2074,10 @@ int launch_select(vp_ctx* ctx, const double* X, int b, int c, int chi, double to
                   int* d_rank, double* d_err) {
   const size_t smem = (size_t)(2 * b + 1) * sizeof(double);
   if (smem > 200 * 1024) return fail(ctx, VP_ECAPACITY, "select: bond too large");
-  if (smem > 48 * 1024) {
-    static AttrOnce sattr;  // the largest size once, never lowered under another thread's launch
-    VP_TRY(sattr.ensure(ctx, (const void*)k_select, 200 * 1024, false));
-  }
+  // always: the kernel's own 8 KB of static shared memory counts against the
+  // 48 KB a block gets without the opt-in
+  static AttrOnce sattr;
+  VP_TRY(sattr.ensure(ctx, (const void*)k_select, 200 * 1024, false));
   ctx->launches++;
   k_select<<<1, 512, smem, ctx->stream>>>(X, b, c, chi, tol, perm, sigma, d_rank, d_err, ctx->status);
   return check_launch(ctx, "select");
