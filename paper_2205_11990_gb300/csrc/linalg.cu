@@ -922,15 +922,18 @@ int launch_qr_getr(vp_ctx* ctx, const double* A, int m, int n, double* R) {
 // selects the A operand: row-major, or the column-major upper triangle of a
 // QR factor.  Each output is the sum over its K slice in ascending k, so the
 // tile size does not change the result; the K slicing does (gemm_plan).
+// kfirst(row0): the first k that can be nonzero in rows >= row0.
 struct ARowMajor {
   const double* A;
   int lda;
   __device__ double operator()(int r, int k) const { return A[(size_t)r * lda + k]; }
+  __device__ int kfirst(int) const { return 0; }
 };
 struct AUpperColMajor {
   const double* A;
   int lda;
   __device__ double operator()(int r, int k) const { return r <= k ? A[(size_t)k * lda + r] : 0.0; }
+  __device__ int kfirst(int row0) const { return row0; }  // R[r][k] = 0 for k < r
 };
 
 // blockIdx.z selects a K slice of `kslice` columns (split-K); slice s writes
@@ -955,7 +958,9 @@ __device__ __forceinline__ void gemm_body(int M, int N, int K, double alpha, ALo
   __shared__ T Bs[16][TILE];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const int row0 = bx * TILE, col0 = by * TILE;
-  const int kbeg = bz * kslice, kend = min(K, kbeg + kslice);
+  // the terms below the triangle of an upper-triangular A are exact zeros:
+  // starting past them leaves every output's sum unchanged
+  const int kbeg = max(bz * kslice, a.kfirst(row0)), kend = min(K, bz * kslice + kslice);
   C += bz * slice_stride;
   T acc[R][R] = {};
   for (int k0 = kbeg; k0 < kend; k0 += 16) {
